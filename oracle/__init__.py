@@ -1,0 +1,186 @@
+"""CPU oracle for sampled sub-block Toeplitz hashing (arXiv 2308.02856).
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, ``__graft_entry__.smoke()``
+and the CPU-baseline leg of ``bench.py``.  The product path (the CUDA library
+and its binding) never imports this package.
+
+The arithmetic lives in ``oracle.c`` (plain C, one bit at a time); this module
+compiles it with gcc and marshals numpy arrays through ctypes.  Definitions
+(Sec. III.B steps 1, 3 and 4 of the paper, Sec. I for K = T . A'):
+
+* sampling label of position i: ``(x0 << 32) | x1`` of Philox4x32-10 with
+  counter ``(i_lo, i_hi, 0, 0)`` and key ``(K_lo, K_hi)``; the sampled order is
+  the stable argsort of the labels; sub-block j = sorted ranks [j*s, (j+1)*s);
+* ``K_j[i] = XOR_c seed_j[i - c + s - 1] AND A_j[c]`` for i < k;
+* output bit ``j*k + i = K_j[i]``, LSB-first in uint32 words, tail bits 0.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+SEED_PER_SUBBLOCK = 0x1
+IDENTITY_PERM = 0x2
+
+
+def KEY_BITS(b: int) -> int:
+    """Test hook: keep only the top ``b`` bits (1..63) of each sampling label."""
+    return (int(b) & 0x3F) << 8
+
+
+def build(force: bool = False) -> str:
+    """Compile ``oracle.c`` into ``liboracle.so`` (plain -O2, not tuned)."""
+    if (not force and os.path.exists(_LIB)
+            and os.path.getmtime(_LIB) >= max(os.path.getmtime(_SRC),
+                                              os.path.getmtime(os.path.join(_HERE, "oracle.h")))):
+        return _LIB
+    tmp = _LIB + ".tmp%d" % os.getpid()
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-pthread", "-o", tmp, _SRC]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB)
+        u64, u32, i32, vp = ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int, ctypes.c_void_p
+        L.oracle_philox4x32_10.argtypes = [vp, vp, vp]
+        L.oracle_philox4x32_10.restype = None
+        L.oracle_sampling_key.argtypes = [u64, u64, u32]
+        L.oracle_sampling_key.restype = u64
+        L.oracle_sampling_keys.argtypes = [u64, u64, u32, vp, i32]
+        L.oracle_sampling_keys.restype = None
+        L.oracle_perm.argtypes = [u64, vp, vp]
+        L.oracle_perm.restype = i32
+        L.oracle_perm_range.argtypes = [u64, vp, u64, u64, vp]
+        L.oracle_perm_range.restype = i32
+        L.oracle_subblock.argtypes = [vp, vp, u64, vp]
+        L.oracle_subblock.restype = None
+        L.oracle_toeplitz_bit.argtypes = [vp, u64, u64, vp, u64]
+        L.oracle_toeplitz_bit.restype = ctypes.c_uint8
+        L.oracle_toeplitz.argtypes = [vp, u64, u64, vp, u64, u64, vp]
+        L.oracle_toeplitz.restype = None
+        L.oracle_extract.argtypes = [u64, u64, u64, u64, vp, vp, u64, u32, vp, i32]
+        L.oracle_extract.restype = i32
+        L.oracle_extract_window.argtypes = [vp, vp, u64, u64, vp, u32, u64, u64, u64, u64, vp, i32]
+        L.oracle_extract_window.restype = None
+        _lib = L
+    return _lib
+
+
+def _ptr(a: np.ndarray) -> int:
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data
+
+
+def _threads(nthreads):
+    return int(nthreads) if nthreads else (os.cpu_count() or 1)
+
+
+def philox4x32_10(ctr, key) -> np.ndarray:
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    lib().oracle_philox4x32_10(_ptr(c), _ptr(k), _ptr(out))
+    return out
+
+
+def sampling_key(i: int, sampling_key_: int, flags: int = 0) -> int:
+    return int(lib().oracle_sampling_key(i, sampling_key_, flags))
+
+
+def sampling_keys(n: int, sampling_key_: int, flags: int = 0, nthreads=None) -> np.ndarray:
+    keys = np.empty(max(n, 1), dtype=np.uint64)
+    lib().oracle_sampling_keys(n, sampling_key_, flags, _ptr(keys), _threads(nthreads))
+    return keys[:n]
+
+
+def perm_from_keys(keys: np.ndarray) -> np.ndarray:
+    keys = np.ascontiguousarray(keys, dtype=np.uint64)
+    n = keys.shape[0]
+    perm = np.empty(max(n, 1), dtype=np.uint32)
+    rc = lib().oracle_perm(n, _ptr(keys) if n else 0, _ptr(perm))
+    if rc:
+        raise RuntimeError("oracle_perm failed: %d" % rc)
+    return perm[:n]
+
+
+def perm(n: int, sampling_key_: int, flags: int = 0, nthreads=None) -> np.ndarray:
+    if flags & IDENTITY_PERM:
+        return np.arange(n, dtype=np.uint32)
+    return perm_from_keys(sampling_keys(n, sampling_key_, flags, nthreads))
+
+
+def perm_range(keys: np.ndarray, lo: int, cnt: int) -> np.ndarray:
+    keys = np.ascontiguousarray(keys, dtype=np.uint64)
+    out = np.empty(max(cnt, 1), dtype=np.uint32)
+    rc = lib().oracle_perm_range(keys.shape[0], _ptr(keys), lo, cnt, _ptr(out))
+    if rc:
+        raise RuntimeError("oracle_perm_range failed: %d" % rc)
+    return out[:cnt]
+
+
+def subblock(in_bits: np.ndarray, pos: np.ndarray) -> np.ndarray:
+    in_bits = np.ascontiguousarray(in_bits, dtype=np.uint32)
+    pos = np.ascontiguousarray(pos, dtype=np.uint32)
+    A = np.empty(max(pos.shape[0], 1), dtype=np.uint8)
+    lib().oracle_subblock(_ptr(in_bits), _ptr(pos), pos.shape[0], _ptr(A))
+    return A[:pos.shape[0]]
+
+
+def toeplitz(seed_bits: np.ndarray, s: int, A: np.ndarray, i0: int, cnt: int, off: int = 0) -> np.ndarray:
+    seed_bits = np.ascontiguousarray(seed_bits, dtype=np.uint32)
+    A = np.ascontiguousarray(A, dtype=np.uint8)
+    assert A.shape[0] == s
+    K = np.empty(max(cnt, 1), dtype=np.uint8)
+    lib().oracle_toeplitz(_ptr(seed_bits), off, s, _ptr(A), i0, cnt, _ptr(K))
+    return K[:cnt]
+
+
+def toeplitz_bit(seed_bits: np.ndarray, s: int, A: np.ndarray, i: int, off: int = 0) -> int:
+    seed_bits = np.ascontiguousarray(seed_bits, dtype=np.uint32)
+    A = np.ascontiguousarray(A, dtype=np.uint8)
+    return int(lib().oracle_toeplitz_bit(_ptr(seed_bits), off, s, _ptr(A), i))
+
+
+def extract(n, m, s, k, in_bits, seed_bits, sampling_key_, flags=0, nthreads=None) -> np.ndarray:
+    in_bits = np.ascontiguousarray(in_bits, dtype=np.uint32)
+    seed_bits = np.ascontiguousarray(seed_bits, dtype=np.uint32)
+    out = np.zeros((m * k + 31) // 32, dtype=np.uint32)
+    rc = lib().oracle_extract(n, m, s, k, _ptr(in_bits), _ptr(seed_bits), sampling_key_, flags,
+                              _ptr(out), _threads(nthreads))
+    if rc:
+        raise ValueError("oracle_extract rejected the arguments (%d)" % rc)
+    return out
+
+
+def extract_window(in_bits, pos, s, k, seed_bits, flags, j0, nj, i0, ni, nthreads=None) -> np.ndarray:
+    """K_j[i] for j in [j0, j0+nj), i in [i0, i0+ni), one byte per bit, given
+    ``pos`` = the sampled positions of those sub-blocks (nj*s entries)."""
+    in_bits = np.ascontiguousarray(in_bits, dtype=np.uint32)
+    pos = np.ascontiguousarray(pos, dtype=np.uint32)
+    seed_bits = np.ascontiguousarray(seed_bits, dtype=np.uint32)
+    assert pos.shape[0] == nj * s
+    out = np.empty(max(nj * ni, 1), dtype=np.uint8)
+    lib().oracle_extract_window(_ptr(in_bits), _ptr(pos), s, k, _ptr(seed_bits), flags,
+                                j0, nj, i0, ni, _ptr(out), _threads(nthreads))
+    return out[:nj * ni].reshape(nj, ni)
+
+
+def bits_of(words: np.ndarray, nbits: int) -> np.ndarray:
+    """Unpack LSB-first uint32 words into one uint8 per bit (first nbits)."""
+    w = np.ascontiguousarray(words, dtype="<u4")
+    return np.unpackbits(w.view(np.uint8), bitorder="little")[:nbits]

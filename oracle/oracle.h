@@ -1,0 +1,91 @@
+/*
+ * Oracle for sampled sub-block Toeplitz hashing (arXiv 2308.02856).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This is a plain, slow, obviously correct CPU
+ * statement of what the hashing path computes.  Only the test suite, the
+ * package smoke check and the CPU-baseline leg of the benchmark may load it;
+ * the CUDA library never links, includes or calls it, and the two share no
+ * code.  Every bit of the path is computed one bit at a time, exactly as the
+ * definitions below state them.
+ *
+ * Bit convention (the paper fixes none; this is the reading used throughout):
+ *   bit(x, i) = (x[i >> 5] >> (i & 31)) & 1 for every packed string
+ *   (input block, Toeplitz seed, output).
+ *
+ * Definitions, in the order of the sub-block protocol of Sec. III.B:
+ *   1. Sampling (Sec. III.B step 1).  Position i gets the 64-bit label
+ *        key_i = (x0 << 32) | x1,  (x0..x3) = Philox4x32-10(ctr = (i_lo, i_hi, 0, 0),
+ *                                                        key = (K_lo, K_hi))
+ *      where K is the sampling key.  The sampled order is the stable argsort
+ *      of key_i (equal keys: lower index first); sub-block j is made of the
+ *      positions at sorted ranks [j*s, (j+1)*s), in rank order.
+ *   2. Extraction (Sec. I, Sec. III.B step 3): K_j = T * A_j mod 2 with the
+ *      k x s diagonal-constant matrix T[i][c] = seed_j[i - c + s - 1], i.e.
+ *        K_j[i] = XOR_{c < s} seed_j[i - c + s - 1] AND A_j[c].
+ *      seed_j is the shared seed (s + k - 1 bits), or, with
+ *      ORACLE_SEED_PER_SUBBLOCK, the j-th consecutive (s + k - 1)-bit span
+ *      of the seed string.
+ *   3. Concatenation (Sec. III.B step 4): output bit j*k + i = K_j[i]; the
+ *      tail bits of the last output word are 0.
+ */
+#ifndef ORACLE_H
+#define ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Flags, same meaning as the library's create flags. */
+#define ORACLE_SEED_PER_SUBBLOCK 0x1u
+#define ORACLE_IDENTITY_PERM     0x2u
+/* Test hook: keep only the top b (1..63) bits of every sampling key. */
+#define ORACLE_KEY_BITS(b)       (((uint32_t)(b) & 0x3fu) << 8)
+
+/* Philox4x32-10 block function (Salmon, Moraes, Dror, Shaw, SC'11). */
+void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+
+/* Sampling label of position i (definition 1 above). */
+uint64_t oracle_sampling_key(uint64_t i, uint64_t sampling_key, uint32_t flags);
+
+/* keys[i] = oracle_sampling_key(i) for i < n, split over nthreads threads. */
+void oracle_sampling_keys(uint64_t n, uint64_t sampling_key, uint32_t flags,
+                          uint64_t *keys, int nthreads);
+
+/* perm = stable argsort of keys[0..n) (qsort on (key, index) pairs). 0 = ok. */
+int oracle_perm(uint64_t n, const uint64_t *keys, uint32_t *perm);
+
+/* out[r] = perm[lo + r] for r < cnt, without sorting all n positions
+   (rank selection through a 16-bit key histogram, then a sort of the
+   candidates).  0 = ok. */
+int oracle_perm_range(uint64_t n, const uint64_t *keys, uint64_t lo, uint64_t cnt,
+                      uint32_t *out);
+
+/* Sub-block assembly: A[c] = bit(in, pos[c]) for c < s (one byte per bit). */
+void oracle_subblock(const uint32_t *in, const uint32_t *pos, uint64_t s, uint8_t *A);
+
+/* One Toeplitz output bit: XOR_{c<s} bit(seed, off + i - c + s - 1) AND A[c]. */
+uint8_t oracle_toeplitz_bit(const uint32_t *seed, uint64_t off, uint64_t s,
+                            const uint8_t *A, uint64_t i);
+
+/* K[i - i0] for i in [i0, i0 + cnt) (one byte per bit). */
+void oracle_toeplitz(const uint32_t *seed, uint64_t off, uint64_t s,
+                     const uint8_t *A, uint64_t i0, uint64_t cnt, uint8_t *K);
+
+/* The whole method (definitions 1-3): out gets ceil(m*k/32) words.
+   Sub-blocks are processed on nthreads threads.  0 = ok, <0 = bad args. */
+int oracle_extract(uint64_t n, uint64_t m, uint64_t s, uint64_t k,
+                   const uint32_t *in, const uint32_t *seed, uint64_t sampling_key,
+                   uint32_t flags, uint32_t *out, int nthreads);
+
+/* A window of the method: K_j[i] for j in [j0, j0+nj), i in [i0, i0+ni),
+   given the sampled positions of those sub-blocks (pos[(j-j0)*s + c]).
+   out[(j-j0)*ni + (i-i0)] is one byte per bit.  Threads split the j range. */
+void oracle_extract_window(const uint32_t *in, const uint32_t *pos, uint64_t s, uint64_t k,
+                           const uint32_t *seed, uint32_t flags, uint64_t j0, uint64_t nj,
+                           uint64_t i0, uint64_t ni, uint8_t *out, int nthreads);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
