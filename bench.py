@@ -1,0 +1,370 @@
+#!/usr/bin/env python3
+"""Benchmark of sampled sub-block Toeplitz hashing (arXiv 2308.02856) on GB300.
+
+One step = one pass of the hashing path over one synthetic input block with
+the sampled order resident on the device: gather of the m sub-blocks in
+sampled order, Toeplitz hash of each, concatenation of the outputs.  Building
+the sampled order (extract_create) happens once per sampling key and is
+timed separately (``create_ms``).
+
+Workload: the QRNG-shaped block, n = 2^30 Bernoulli(0.6) input bits, m = 1024
+sub-blocks of s = 2^20 bits, k = 2^19 output bits per sub-block (ratio 0.5),
+shared uniform seed of s + k - 1 bits (input seed 1, sampling key 2, Toeplitz
+seed 3).  The metric is extracted input Gbit/s (input bits hashed per second).
+
+Prints ONE JSON line (rank 0).  ``--impl reference`` times the CPU oracle on
+the host cores instead (the reference arm: a bounded sample per step).
+Multi-GPU (torchrun): every rank hashes its own block on its own GPU (replicas,
+weak scaling); no data crosses GPUs.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: n, m, s, k, Bernoulli p
+    "qrng_n2^30_m1024_s2^20_k2^19": (1 << 30, 1024, 1 << 20, 1 << 19, 0.6),
+    # smaller shape of the same kind, for quick checks only
+    "small_n2^24_m64_s2^18_k2^17": (1 << 24, 64, 1 << 18, 1 << 17, 0.6),
+}
+DEFAULT_WORKLOAD = "qrng_n2^30_m1024_s2^20_k2^19"
+IN_SEED, SAMPLING_KEY, TOEPLITZ_SEED = 1, 2, 3
+
+# Integer-pipe roofline of the hashing kernel (bound "alu"): LOP3 results per
+# SM per clock x SMs x maximum SM clock.  The lane count is the one measured
+# by a dependency-free LOP3 probe on GB300 (profiles/lop3_alu_peak.md).
+LOP3_LANES_PER_SM_CLK = 64
+# DRAM traffic of one hashing launch on this workload from ncu, bytes (None
+# until captured for the current kernel).
+HASH_TRAFFIC_BYTES = None
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0,
+                    help="target CPU time of the oracle sample")
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------------------
+# clocks during the timed region
+# --------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.gpu_id, "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def gpu_id_for(dev) -> str:
+    import torch
+    p = torch.cuda.get_device_properties(dev)
+    bus = getattr(p, "pci_bus_id", None)
+    dom = getattr(p, "pci_domain_id", 0)
+    did = getattr(p, "pci_device_id", 0)
+    if bus is not None:
+        return "%08X:%02X:%02X.0" % (dom, bus, did)
+    return str(dev)
+
+
+# --------------------------------------------------------------------------
+# CPU oracle sample (cpu_baseline and the reference arm)
+# --------------------------------------------------------------------------
+class OracleSample:
+    """The oracle on a bounded sample of the workload: nj whole sub-blocks'
+    assembly plus ni output rows of each, on nj host threads; scaled to the
+    whole block by the share of Toeplitz rows it computed."""
+
+    def __init__(self, n, m, s, k, in_w, seed_w, target_s):
+        import oracle
+        self.oracle = oracle
+        self.n, self.m, self.s, self.k = n, m, s, k
+        self.in_w, self.seed_w = in_w, seed_w
+        self.cores = os.cpu_count() or 1
+        self.nj = min(self.cores, m)
+        keys = oracle.sampling_keys(n, SAMPLING_KEY)
+        self.pos = oracle.perm_range(keys, 0, self.nj * s)
+        del keys
+        # calibrate the rows per sub-block to about target_s of wall time
+        ni = 8
+        t = self._time(ni)
+        self.ni = int(max(8, min(k, ni * target_s / max(t, 1e-3))))
+
+    def _time(self, ni):
+        t0 = time.perf_counter()
+        self.oracle.extract_window(self.in_w, self.pos, self.s, self.k, self.seed_w, 0, 0, self.nj, 0, ni,
+                                   nthreads=self.nj)
+        return time.perf_counter() - t0
+
+    def measure(self):
+        t = self._time(self.ni)
+        frac = (self.nj * self.ni) / float(self.m * self.k)
+        full_s = t / frac
+        return {"value": self.n / full_s / 1e9, "unit": "Gbit/s", "cores": self.nj, "kind": "oracle",
+                "seconds": t,
+                "sample": "oracle bit-loop on %d of %d sub-blocks x %d of %d output rows (%.2e of the "
+                          "Toeplitz work) on %d threads, %.1f s; scaled to the whole block"
+                          % (self.nj, self.m, self.ni, self.k, frac, self.nj, t)}
+
+
+def make_inputs(n, m, s, k, p):
+    from paper_2308_02856_gb300 import synth
+    in_w = synth.bernoulli_bits(n, p, IN_SEED)
+    seed_w = synth.uniform_bits(s + k - 1, TOEPLITZ_SEED)
+    return in_w, seed_w
+
+
+# --------------------------------------------------------------------------
+# arms
+# --------------------------------------------------------------------------
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    n, m, s, k, p = WORKLOADS[args.workload]
+    in_w, seed_w = make_inputs(n, m, s, k, p)
+    per_step = max(1.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+    smp = OracleSample(n, m, s, k, in_w, seed_w, per_step)
+    for _ in range(args.warmup):
+        smp.measure()
+    res = [smp.measure() for _ in range(args.steps)]
+    secs = [r["seconds"] / ((smp.nj * smp.ni) / float(m * k)) for r in res]
+    ms = statistics.mean(secs) * 1e3
+    value = n / (ms / 1e3) / 1e9
+    cb = dict(res[-1])
+    cb["value"] = value
+    cb.pop("seconds", None)
+    line = {
+        "impl": "reference",
+        "metric": "extracted input Gbit/s", "value": value, "unit": "Gbit/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32 (GF(2) bits)", "data": "synthetic",
+        "config": {"workload": args.workload, "n": n, "m": m, "s": s, "k": k, "bernoulli_p": p,
+                   "order": "resident (built once per sampling key)"},
+        "cpu_baseline": cb,
+        "e2e": {"value": value, "unit": "Gbit/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    from paper_2308_02856_gb300 import extract as X
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        dist = None
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    n, m, s, k, p = WORKLOADS[args.workload]
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+
+    X.load()  # fails loudly when the CUDA library is missing
+    in_w, seed_w = make_inputs(n, m, s, k, p)
+
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ex = X.Extractor(n, m, s, k, seed_w, SAMPLING_KEY)
+    create_ms = (time.perf_counter() - t0) * 1e3
+    plan = ex.describe()
+
+    d_in = torch.from_numpy(in_w.view(np.int32)).to(dev)
+    d_out = ex.new_output()
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.synchronize()
+
+    def step():
+        ex.gather(d_in, stream=stream)
+        ex.hash(d_out, stream=stream)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+
+    # timed region
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+            torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clk = ClockSampler(gpu_id_for(dev))
+    clk.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    start.record(stream)
+    for i in range(args.steps):
+        a, b, c = evs[i]
+        a.record(stream)
+        ex.gather(d_in, stream=stream)
+        b.record(stream)
+        ex.hash(d_out, stream=stream)
+        c.record(stream)
+    end.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = clk.stop()
+
+    ms_total = start.elapsed_time(end)
+    gather_ms = statistics.mean(a.elapsed_time(b) for a, b, _ in evs)
+    hash_ms = statistics.mean(b.elapsed_time(c) for _, b, c in evs)
+    if dist:
+        t = torch.tensor([ms_total], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    value = world * n / (ms_step / 1e3) / 1e9
+
+    # end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        h_in = torch.from_numpy(in_w.view(np.int32)).pin_memory()
+        h_out = torch.empty(ex.out_words, dtype=torch.int32).pin_memory()
+        ex.run_host(h_in, h_out, stream=stream)
+        if dist:
+            dist.barrier()
+        t1 = time.perf_counter()
+        for _ in range(args.steps):
+            ex.run_host(h_in, h_out, stream=stream)
+        e2e_s = (time.perf_counter() - t1) / args.steps
+        if dist:
+            t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e = {"value": world * n / e2e_s / 1e9, "unit": "Gbit/s", "ms_per_step": e2e_s * 1e3,
+               "h2d_bytes_per_step": int(in_w.nbytes), "d2h_bytes_per_step": int(ex.out_words * 4),
+               "api": "extract_run_host (pinned host buffers, copies and sync inside the timed region)"}
+
+    # roofline of the dominant kernel (toeplitz_lop3_kernel): integer ALU
+    lop3_per_launch = m * k * s / 32.0
+    achieved = lop3_per_launch / (hash_ms / 1e3) / 1e12
+    peak = sms * LOP3_LANES_PER_SM_CLK * 2070e6 / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TLOP3/s",
+                "frac": achieved / peak, "traffic": HASH_TRAFFIC_BYTES,
+                "kernel": "toeplitz_lop3_kernel",
+                "work_per_launch": "m*k*s/32 = %.4g LOP3 (32 bit-products each)" % lop3_per_launch,
+                "peak_basis": "%d SMs x %d LOP3/clk/SM x 2070 MHz max SM clock" % (sms, LOP3_LANES_PER_SM_CLK)}
+    if clocks.get("sm_mhz"):
+        roofline["frac_at_measured_clock"] = achieved / (sms * LOP3_LANES_PER_SM_CLK * clocks["sm_mhz"] * 1e6 / 1e12)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            smp = OracleSample(n, m, s, k, in_w, seed_w, args.cpu_seconds)
+            cpu = smp.measure()
+            cpu.pop("seconds", None)
+        except Exception as e:  # the baseline is context; report why it is missing
+            cpu = {"value": None, "unit": "Gbit/s", "kind": "oracle", "error": str(e)}
+
+    ex.close()
+    if rank == 0:
+        line = {
+            "metric": "extracted input Gbit/s", "value": value, "unit": "Gbit/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32 (GF(2) bits)", "data": "synthetic",
+            "config": {"workload": args.workload, "n": n, "m": m, "s": s, "k": k, "bernoulli_p": p,
+                       "seeds": {"input": IN_SEED, "sampling_key": SAMPLING_KEY, "toeplitz": TOEPLITZ_SEED},
+                       "order": "resident (built once per sampling key; see create_ms)",
+                       "l2": "inputs larger than L2: 4n-byte order + n/8-byte input read per step",
+                       "parallelism": "replicas" if world > 1 else "1 GPU",
+                       "plan": plan},
+            "create_ms": create_ms,
+            "gather_ms": gather_ms, "hash_ms": hash_ms,
+            "gpu_launches": 2 * args.steps,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "clocks": clocks,
+            "device": props.name, "sms": sms,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

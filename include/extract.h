@@ -1,0 +1,162 @@
+/*
+ * extract.h - C ABI of the GB300 (sm_103a) sampled sub-block Toeplitz hashing
+ * library, libextract.so.
+ *
+ * What it computes (arXiv 2308.02856, "Sampled sub-block hashing for large
+ * input randomness extraction"):
+ *
+ *   1. Sampling (Sec. III.B step 1).  Every input position i gets a 64-bit
+ *      label, (x0 << 32) | x1 of Philox4x32-10 with counter (i_lo, i_hi, 0, 0)
+ *      and key = the 64-bit sampling key (lo, hi).  The sampled order is the
+ *      stable argsort of the labels (equal labels: lower position first).
+ *      Sub-block j, for j < m, is the s positions at sorted ranks
+ *      [j*s, (j+1)*s), taken in rank order: A_j[c] = in[perm[j*s + c]].
+ *      Positions at ranks >= m*s are not hashed.  (The paper draws an i.i.d.
+ *      label per round and so gets sub-blocks of varying size; this library
+ *      cuts the sampled order into m equal sub-blocks instead.)
+ *   2. Extraction (Sec. I, K = T . A'; Sec. III.B step 3).  Each sub-block is
+ *      multiplied over GF(2) by the k x s diagonal-constant (Toeplitz) matrix
+ *      T[i][c] = seed_j[i - c + s - 1], built from an (s + k - 1)-bit seed:
+ *        K_j[i] = XOR_{c<s} seed_j[i - c + s - 1] AND A_j[c],   i < k.
+ *      T is never materialised.
+ *   3. Concatenation (Sec. III.B step 4).  Output bit j*k + i = K_j[i].
+ *
+ * Bit strings (input, seed, output) are packed LSB-first in uint32 words:
+ * bit t of a string is (w[t >> 5] >> (t & 31)) & 1.  Output bits past m*k in
+ * the last word are written as 0.
+ *
+ * Errors: every entry point returns EXTRACT_OK (0) or a negative code and
+ * never aborts the process; extract_last_error() gives the message of the
+ * last failure on the calling thread.  CUDA failures map to EXTRACT_ECUDA.
+ *
+ * Streams are passed as `void *` holding a cudaStream_t (NULL = the legacy
+ * default stream); all device work of a run is asynchronous on that stream.
+ */
+#ifndef EXTRACT_H
+#define EXTRACT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ---------------------------------------------------- */
+#define EXTRACT_OK         0
+#define EXTRACT_EINVAL    (-1)  /* bad argument (shape, null pointer, flag) */
+#define EXTRACT_ENOMEM    (-2)  /* device or host allocation failed          */
+#define EXTRACT_ECUDA     (-3)  /* a CUDA call failed; see extract_last_error */
+#define EXTRACT_ETIMEDOUT (-4)  /* a bounded wait ran out                     */
+#define EXTRACT_EBUDGET   (-5)  /* the job does not fit the memory budget     */
+#define EXTRACT_EBUSY     (-6)  /* no free slot / resource in use             */
+#define EXTRACT_EINTERNAL (-7)  /* an internal consistency check failed       */
+
+/* ---- create flags ---------------------------------------------------- */
+/* seed_bits holds m consecutive (s + k - 1)-bit seeds, one independent
+   Toeplitz matrix per sub-block (Sec. III.B step 3 draws f_RE,j
+   independently).  Without it, all sub-blocks share one seed. */
+#define EXTRACT_SEED_PER_SUBBLOCK 0x1u
+/* Skip sampling: perm = identity, so sub-block j is input bits
+   [j*s, (j+1)*s).  With m = 1 and s = n this is direct whole-block Toeplitz
+   hashing, the "traditional" method of Sec. IV.C. */
+#define EXTRACT_IDENTITY_PERM     0x2u
+/* Test hook: keep only the top b (1..63) bits of every sampling label, which
+   forces many equal labels so that the index tie-break is exercised. */
+#define EXTRACT_KEY_BITS(b)       ((((uint32_t)(b)) & 0x3fu) << 8)
+
+typedef struct extract_ctx extract_ctx;
+
+/*
+ * extract_create - validate the shape, copy the seed to the device and build
+ * the sampled order (step 1) on the GPU, resident until extract_destroy.
+ *
+ *   out            receives the new context (owned by the library).
+ *   n              input bits, m*s <= n <= 2^32.
+ *   m, s, k        sub-blocks, bits per sub-block, output bits per sub-block;
+ *                  1 <= m, 1 <= k <= s.
+ *   seed_bits_host host pointer to ceil(L/32) words with L = s + k - 1 (or
+ *                  m*(s + k - 1) with EXTRACT_SEED_PER_SUBBLOCK); copied, the
+ *                  caller keeps ownership.
+ *   sampling_key   64-bit Philox key of the sampling labels.
+ *   flags          EXTRACT_* create flags.
+ *
+ * Synchronous: it returns once the order is built.  Device memory held:
+ * 4n bytes of order (none with EXTRACT_IDENTITY_PERM) plus about n/8 bytes
+ * of sub-block buffer and the seed.  Errors: EINVAL, ENOMEM, ECUDA.
+ */
+int extract_create(extract_ctx **out, uint64_t n, uint32_t m, uint32_t s, uint32_t k,
+                   const uint32_t *seed_bits_host, uint64_t sampling_key, uint32_t flags);
+
+/*
+ * extract_run - steps 1-3 on one input block: gather the m sub-blocks in
+ * sampled order, hash each one and write the concatenated output.
+ *
+ *   stream        cudaStream_t (void *) the work is queued on.
+ *   in_bits_dev   device pointer, ceil(n/32) words, caller-owned, read only.
+ *   out_bits_dev  device pointer, ceil(m*k/32) words, caller-owned; fully
+ *                 overwritten.
+ *
+ * Asynchronous.  Both buffers must stay valid until the stream reaches the
+ * end of the run.  The context's sub-block buffer is reused by every run, so
+ * runs on one context must be ordered on one stream (or by events).
+ * Errors: EINVAL (null pointers), ECUDA (launch failure).
+ */
+int extract_run(extract_ctx *h, void *stream, const uint32_t *in_bits_dev,
+                uint32_t *out_bits_dev);
+
+/*
+ * extract_run_host - extract_run on host buffers, end to end: copies the
+ * ceil(n/32) input words from in_bits_host to the device, runs steps 1-3 and
+ * copies the ceil(m*k/32) output words back to out_bits_host, all on
+ * `stream`; returns once the output is in host memory.  The device staging
+ * buffers are allocated on the first call and kept until extract_destroy.
+ * Page-locked host buffers give full copy bandwidth; pageable ones work.
+ * Errors: EINVAL (null pointers), ENOMEM, ECUDA.
+ */
+int extract_run_host(extract_ctx *h, void *stream, const uint32_t *in_bits_host,
+                     uint32_t *out_bits_host);
+
+/* extract_gather - step 1's gather alone: fills the context's sub-block
+   buffer from in_bits_dev (same contract as extract_run). */
+int extract_gather(extract_ctx *h, void *stream, const uint32_t *in_bits_dev);
+
+/* extract_hash - steps 2-3 alone on the sub-block buffer filled by the last
+   extract_gather on the same stream; writes out_bits_dev as extract_run does. */
+int extract_hash(extract_ctx *h, void *stream, uint32_t *out_bits_dev);
+
+/*
+ * extract_run_plain - the same result as extract_run through the plain
+ * per-block path: after the gather, one kernel launch per sub-block, one
+ * thread per output bit, no register tiling and no seed reuse across
+ * sub-blocks.  It is the baseline the tuned path is measured against.
+ */
+int extract_run_plain(extract_ctx *h, void *stream, const uint32_t *in_bits_dev,
+                      uint32_t *out_bits_dev);
+
+/* extract_read_perm - copy ranks [start, start+count) of the sampled order
+   to host memory (synchronous).  With EXTRACT_IDENTITY_PERM it writes the
+   identity.  Errors: EINVAL if start + count > n. */
+int extract_read_perm(extract_ctx *h, uint64_t start, uint64_t count, uint32_t *dst_host);
+
+/* extract_read_subblock - copy sub-block j as gathered by the last run or
+   gather, ceil(s/32) words, to host memory (synchronous, waits for the
+   device).  Word layout: bit t of the copy is A_j[s - 1 - t], the sub-block
+   reversed, which is the order the hashing kernel consumes. */
+int extract_read_subblock(extract_ctx *h, uint32_t j, uint32_t *dst_host);
+
+/* extract_describe - write a one-line text description of the context's
+   kernel configuration (tile shape, split, grid) into buf. */
+int extract_describe(extract_ctx *h, char *buf, uint32_t buflen);
+
+/* extract_destroy - free the context and all device memory it holds
+   (synchronises the device first).  NULL is accepted. */
+int extract_destroy(extract_ctx *h);
+
+/* extract_last_error - message of the last failure on this thread ("" if
+   none); valid until the next failing call on the same thread. */
+const char *extract_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EXTRACT_H */

@@ -67,6 +67,8 @@ def lib():
         L.oracle_perm.restype = i32
         L.oracle_perm_range.argtypes = [u64, vp, u64, u64, vp]
         L.oracle_perm_range.restype = i32
+        L.oracle_check_order.argtypes = [u64, vp, vp, i32]
+        L.oracle_check_order.restype = ctypes.c_int64
         L.oracle_subblock.argtypes = [vp, vp, u64, vp]
         L.oracle_subblock.restype = None
         L.oracle_toeplitz_bit.argtypes = [vp, u64, u64, vp, u64]
@@ -131,6 +133,16 @@ def perm_range(keys: np.ndarray, lo: int, cnt: int) -> np.ndarray:
     if rc:
         raise RuntimeError("oracle_perm_range failed: %d" % rc)
     return out[:cnt]
+
+
+def check_order(keys: np.ndarray, perm_: np.ndarray, nthreads=None) -> int:
+    """-1 if ``perm_`` is the stable argsort of ``keys`` (checked as strict
+    increase in (label, position) order with every entry < n), else the first
+    offending rank."""
+    keys = np.ascontiguousarray(keys, dtype=np.uint64)
+    perm_ = np.ascontiguousarray(perm_, dtype=np.uint32)
+    assert keys.shape[0] == perm_.shape[0]
+    return int(lib().oracle_check_order(keys.shape[0], _ptr(keys), _ptr(perm_), _threads(nthreads)))
 
 
 def subblock(in_bits: np.ndarray, pos: np.ndarray) -> np.ndarray:

@@ -165,6 +165,49 @@ int oracle_perm_range(uint64_t n, const uint64_t *keys, uint64_t lo, uint64_t cn
     return 0;
 }
 
+typedef struct {
+    uint64_t n, lo, hi;
+    const uint64_t *keys;
+    const uint32_t *perm;
+    int64_t bad;
+} check_job;
+
+static void *check_worker(void *arg)
+{
+    check_job *c = (check_job *)arg;
+    c->bad = -1;
+    for (uint64_t t = c->lo; t < c->hi; ++t) {
+        if (c->perm[t] >= c->n) { c->bad = (int64_t)t; return NULL; }
+        if (t + 1 < c->n) {
+            uint32_t a = c->perm[t], b = c->perm[t + 1];
+            if (b >= c->n) { c->bad = (int64_t)(t + 1); return NULL; }
+            int ok = c->keys[a] < c->keys[b] || (c->keys[a] == c->keys[b] && a < b);
+            if (!ok) { c->bad = (int64_t)t; return NULL; }
+        }
+    }
+    return NULL;
+}
+
+int64_t oracle_check_order(uint64_t n, const uint64_t *keys, const uint32_t *perm, int nthreads)
+{
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > 256) nthreads = 256;
+    pthread_t th[256];
+    check_job jobs[256];
+    for (int t = 0; t < nthreads; ++t) {
+        jobs[t].n = n; jobs[t].keys = keys; jobs[t].perm = perm;
+        jobs[t].lo = n * (uint64_t)t / (uint64_t)nthreads;
+        jobs[t].hi = n * (uint64_t)(t + 1) / (uint64_t)nthreads;
+        pthread_create(&th[t], NULL, check_worker, &jobs[t]);
+    }
+    int64_t bad = -1;
+    for (int t = 0; t < nthreads; ++t) {
+        pthread_join(th[t], NULL);
+        if (jobs[t].bad >= 0 && (bad < 0 || jobs[t].bad < bad)) bad = jobs[t].bad;
+    }
+    return bad;
+}
+
 /* ---------------------------------------------------------------------- */
 /* Bits, sub-blocks and the Toeplitz product (Sec. I: K = T . A';           */
 /* Sec. III.B steps 3-4).                                                  */

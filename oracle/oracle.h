@@ -61,6 +61,13 @@ int oracle_perm(uint64_t n, const uint64_t *keys, uint32_t *perm);
 int oracle_perm_range(uint64_t n, const uint64_t *keys, uint64_t lo, uint64_t cnt,
                       uint32_t *out);
 
+/* Property check of a claimed sampled order (for sizes where sorting all n
+   positions on the CPU is too slow): returns -1 when every perm entry is
+   < n and the labels keys[perm[t]] increase strictly in (label, position)
+   order - which makes perm a bijection and the unique stable argsort -
+   else the first offending t. */
+int64_t oracle_check_order(uint64_t n, const uint64_t *keys, const uint32_t *perm, int nthreads);
+
 /* Sub-block assembly: A[c] = bit(in, pos[c]) for c < s (one byte per bit). */
 void oracle_subblock(const uint32_t *in, const uint32_t *pos, uint64_t s, uint8_t *A);
 

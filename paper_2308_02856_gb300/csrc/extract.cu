@@ -1,0 +1,261 @@
+// C ABI of libextract (declared in include/extract.h): context lifetime,
+// argument validation, device memory and the composition of the kernels.
+#include "common.cuh"
+#include "internal.h"
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstring>
+#include <new>
+#include <vector>
+
+namespace ex {
+
+static thread_local char g_err[512] = "";
+
+int set_error(int code, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int cuda_error(cudaError_t e, const char *what)
+{
+    return set_error(e == cudaErrorMemoryAllocation ? EXTRACT_ENOMEM : EXTRACT_ECUDA,
+                     "%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
+}
+
+}  // namespace ex
+
+using namespace ex;
+
+struct extract_ctx {
+    uint64_t n = 0;
+    uint32_t m = 0, s = 0, k = 0, flags = 0;
+    uint64_t sampling_key = 0;
+    int device = 0, num_sms = 0;
+    uint32_t w_pad = 0;        // words per stored sub-block (multiple of kWordChunk)
+    uint32_t seed_stride = 0;  // words per realigned seed
+    uint32_t nseeds = 0;
+    uint32_t *perm = nullptr;  // n entries (null with EXTRACT_IDENTITY_PERM)
+    uint32_t *arev = nullptr;  // m * w_pad words
+    uint32_t *seed = nullptr;  // nseeds * seed_stride words
+    uint32_t *stage_in = nullptr;   // extract_run_host staging, ceil(n/32) words
+    uint32_t *stage_out = nullptr;  // extract_run_host staging, ceil(m*k/32) words
+    HashPlan plan;
+};
+
+namespace {
+
+constexpr uint32_t kKnownFlags = EXTRACT_SEED_PER_SUBBLOCK | EXTRACT_IDENTITY_PERM | (0x3fu << 8);
+
+void free_ctx(extract_ctx *h)
+{
+    if (!h) return;
+    cudaFree(h->perm);
+    cudaFree(h->arev);
+    cudaFree(h->seed);
+    cudaFree(h->stage_in);
+    cudaFree(h->stage_out);
+    delete h;
+}
+
+// Bits [off, off + len) of a packed string, realigned to start at bit 0 of
+// dst (dst_words words, zero past len).
+void realign_bits(const uint32_t *src, uint64_t src_words, uint64_t off, uint64_t len,
+                  uint32_t *dst, uint64_t dst_words)
+{
+    std::memset(dst, 0, dst_words * 4);
+    const uint64_t w0 = off >> 5;
+    const uint32_t sh = (uint32_t)(off & 31u);
+    const uint64_t nw = (len + 31) / 32;
+    for (uint64_t t = 0; t < nw && t < dst_words; ++t) {
+        const uint64_t a = w0 + t;
+        uint32_t lo = a < src_words ? src[a] : 0u;
+        uint32_t hi = a + 1 < src_words ? src[a + 1] : 0u;
+        dst[t] = sh ? ((lo >> sh) | (hi << (32u - sh))) : lo;
+    }
+    if (len % 32 && nw - 1 < dst_words) dst[nw - 1] &= (1u << (len % 32)) - 1u;
+}
+
+int check_ctx(const extract_ctx *h)
+{
+    if (!h) return set_error(EXTRACT_EINVAL, "null context");
+    return EXTRACT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *extract_last_error(void) { return g_err; }
+
+int extract_create(extract_ctx **out, uint64_t n, uint32_t m, uint32_t s, uint32_t k,
+                   const uint32_t *seed_bits_host, uint64_t sampling_key, uint32_t flags)
+{
+    g_err[0] = 0;
+    if (!out) return set_error(EXTRACT_EINVAL, "out is null");
+    *out = nullptr;
+    if (!seed_bits_host) return set_error(EXTRACT_EINVAL, "seed_bits_host is null");
+    if (flags & ~kKnownFlags) return set_error(EXTRACT_EINVAL, "unknown flags 0x%x", flags);
+    if (m < 1 || s < 1 || k < 1 || k > s)
+        return set_error(EXTRACT_EINVAL, "need m >= 1 and 1 <= k <= s (m=%u s=%u k=%u)", m, s, k);
+    if (n > (1ull << 32)) return set_error(EXTRACT_EINVAL, "n = %llu exceeds 2^32", (unsigned long long)n);
+    if ((uint64_t)m * s > n)
+        return set_error(EXTRACT_EINVAL, "m*s = %llu exceeds n = %llu",
+                         (unsigned long long)((uint64_t)m * s), (unsigned long long)n);
+    const bool per_sub = (flags & EXTRACT_SEED_PER_SUBBLOCK) != 0;
+    const bool ident = (flags & EXTRACT_IDENTITY_PERM) != 0;
+
+    extract_ctx *h = new (std::nothrow) extract_ctx();
+    if (!h) return set_error(EXTRACT_ENOMEM, "host allocation failed");
+    h->n = n; h->m = m; h->s = s; h->k = k; h->flags = flags; h->sampling_key = sampling_key;
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+    if (e != cudaSuccess) { delete h; return cuda_error(e, "device query"); }
+
+    h->w_pad = (uint32_t)round_up(ceil_div(s, 32), kWordChunk);
+    h->plan = plan_hash(m, k, h->w_pad, per_sub, h->num_sms);
+    if ((uint64_t)h->plan.gx * h->plan.gy >= (1ull << 31)) {
+        delete h;
+        return set_error(EXTRACT_EINVAL, "too many tiles for one launch (m=%u k=%u)", m, k);
+    }
+    h->seed_stride = seed_stride_words(h->plan, k, h->w_pad);
+    h->nseeds = per_sub ? m : 1u;
+
+    // seeds, realigned to word boundaries and zero padded
+    const uint64_t L = (uint64_t)s + k - 1;
+    const uint64_t src_words = ceil_div(L * h->nseeds, 32);
+    std::vector<uint32_t> host;
+    try {
+        host.resize((size_t)h->nseeds * h->seed_stride);
+    } catch (...) {
+        delete h;
+        return set_error(EXTRACT_ENOMEM, "host allocation failed");
+    }
+    for (uint32_t j = 0; j < h->nseeds; ++j)
+        realign_bits(seed_bits_host, src_words, (uint64_t)j * L, L, host.data() + (size_t)j * h->seed_stride,
+                     h->seed_stride);
+
+    if ((e = cudaMalloc(&h->seed, host.size() * 4)) != cudaSuccess) { free_ctx(h); return cuda_error(e, "cudaMalloc(seed)"); }
+    if ((e = cudaMemcpy(h->seed, host.data(), host.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess) {
+        free_ctx(h); return cuda_error(e, "copy seed");
+    }
+    if ((e = cudaMalloc(&h->arev, (size_t)m * h->w_pad * 4)) != cudaSuccess) { free_ctx(h); return cuda_error(e, "cudaMalloc(sub-blocks)"); }
+    if ((e = cudaMemset(h->arev, 0, (size_t)m * h->w_pad * 4)) != cudaSuccess) { free_ctx(h); return cuda_error(e, "memset(sub-blocks)"); }
+    if (!ident) {
+        if ((e = cudaMalloc(&h->perm, (size_t)n * 4)) != cudaSuccess) { free_ctx(h); return cuda_error(e, "cudaMalloc(order)"); }
+        const uint32_t kb = (flags >> 8) & 0x3fu;
+        const uint64_t mask = kb ? ~((1ull << (64u - kb)) - 1ull) : ~0ull;
+        cudaStream_t st;
+        if ((e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) != cudaSuccess) { free_ctx(h); return cuda_error(e, "stream"); }
+        int rc = build_perm(n, sampling_key, mask, h->perm, st, h->num_sms);
+        cudaStreamDestroy(st);
+        if (rc != EXTRACT_OK) { free_ctx(h); return rc; }
+    }
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess) { free_ctx(h); return cuda_error(e, "create"); }
+    *out = h;
+    return EXTRACT_OK;
+}
+
+int extract_gather(extract_ctx *h, void *stream, const uint32_t *in_bits_dev)
+{
+    if (int rc = check_ctx(h)) return rc;
+    if (!in_bits_dev) return set_error(EXTRACT_EINVAL, "in_bits_dev is null");
+    return launch_gather(in_bits_dev, h->perm, h->m, h->s, h->w_pad, h->arev, (cudaStream_t)stream,
+                         h->num_sms);
+}
+
+int extract_hash(extract_ctx *h, void *stream, uint32_t *out_bits_dev)
+{
+    if (int rc = check_ctx(h)) return rc;
+    if (!out_bits_dev) return set_error(EXTRACT_EINVAL, "out_bits_dev is null");
+    return launch_hash(h->plan, h->seed, h->nseeds > 1 ? h->seed_stride : 0u, h->arev, h->w_pad, h->m,
+                       h->k, out_bits_dev, (cudaStream_t)stream);
+}
+
+int extract_run(extract_ctx *h, void *stream, const uint32_t *in_bits_dev, uint32_t *out_bits_dev)
+{
+    if (int rc = check_ctx(h)) return rc;
+    if (!out_bits_dev) return set_error(EXTRACT_EINVAL, "out_bits_dev is null");
+    if (int rc = extract_gather(h, stream, in_bits_dev)) return rc;
+    return extract_hash(h, stream, out_bits_dev);
+}
+
+int extract_run_host(extract_ctx *h, void *stream, const uint32_t *in_bits_host, uint32_t *out_bits_host)
+{
+    if (int rc = check_ctx(h)) return rc;
+    if (!in_bits_host || !out_bits_host) return set_error(EXTRACT_EINVAL, "null host buffer");
+    const size_t in_bytes = ceil_div(h->n, 32) * 4, out_bytes = ceil_div((uint64_t)h->m * h->k, 32) * 4;
+    if (!h->stage_in) EX_CUDA(cudaMalloc(&h->stage_in, in_bytes ? in_bytes : 4));
+    if (!h->stage_out) EX_CUDA(cudaMalloc(&h->stage_out, out_bytes));
+    cudaStream_t st = (cudaStream_t)stream;
+    EX_CUDA(cudaMemcpyAsync(h->stage_in, in_bits_host, in_bytes, cudaMemcpyHostToDevice, st));
+    if (int rc = extract_run(h, stream, h->stage_in, h->stage_out)) return rc;
+    EX_CUDA(cudaMemcpyAsync(out_bits_host, h->stage_out, out_bytes, cudaMemcpyDeviceToHost, st));
+    EX_CUDA(cudaStreamSynchronize(st));
+    return EXTRACT_OK;
+}
+
+int extract_run_plain(extract_ctx *h, void *stream, const uint32_t *in_bits_dev, uint32_t *out_bits_dev)
+{
+    if (int rc = check_ctx(h)) return rc;
+    if (!out_bits_dev) return set_error(EXTRACT_EINVAL, "out_bits_dev is null");
+    if (int rc = extract_gather(h, stream, in_bits_dev)) return rc;
+    return launch_hash_plain(h->seed, h->nseeds > 1 ? h->seed_stride : 0u, h->arev, h->w_pad, h->s, h->m,
+                             h->k, out_bits_dev, (cudaStream_t)stream);
+}
+
+int extract_read_perm(extract_ctx *h, uint64_t start, uint64_t count, uint32_t *dst_host)
+{
+    if (int rc = check_ctx(h)) return rc;
+    if (!dst_host && count) return set_error(EXTRACT_EINVAL, "dst_host is null");
+    if (start > h->n || count > h->n - start)
+        return set_error(EXTRACT_EINVAL, "range [%llu, +%llu) outside n = %llu", (unsigned long long)start,
+                         (unsigned long long)count, (unsigned long long)h->n);
+    if (!h->perm) {
+        for (uint64_t t = 0; t < count; ++t) dst_host[t] = (uint32_t)(start + t);
+        return EXTRACT_OK;
+    }
+    EX_CUDA(cudaDeviceSynchronize());
+    EX_CUDA(cudaMemcpy(dst_host, h->perm + start, count * 4, cudaMemcpyDeviceToHost));
+    return EXTRACT_OK;
+}
+
+int extract_read_subblock(extract_ctx *h, uint32_t j, uint32_t *dst_host)
+{
+    if (int rc = check_ctx(h)) return rc;
+    if (!dst_host) return set_error(EXTRACT_EINVAL, "dst_host is null");
+    if (j >= h->m) return set_error(EXTRACT_EINVAL, "sub-block %u >= m = %u", j, h->m);
+    EX_CUDA(cudaDeviceSynchronize());
+    EX_CUDA(cudaMemcpy(dst_host, h->arev + (size_t)j * h->w_pad, ceil_div(h->s, 32) * 4,
+                       cudaMemcpyDeviceToHost));
+    return EXTRACT_OK;
+}
+
+int extract_describe(extract_ctx *h, char *buf, uint32_t buflen)
+{
+    if (int rc = check_ctx(h)) return rc;
+    if (!buf || !buflen) return set_error(EXTRACT_EINVAL, "empty buffer");
+    const HashPlan &p = h->plan;
+    snprintf(buf, buflen,
+             "lop3 tile: rows=%u (q=%d x %d warps x 32) subblocks=%d words/chunk=%d grid=%ux%ux%u "
+             "(row tiles %u, sub-block tiles %u, split-K %u x %u chunks) w_pad=%u sms=%d",
+             p.rows(), p.q, p.warps, p.j, p.wc, p.gx * p.gy, 1u, p.splits, p.gx, p.gy, p.splits, p.cps,
+             h->w_pad, h->num_sms);
+    return EXTRACT_OK;
+}
+
+int extract_destroy(extract_ctx *h)
+{
+    if (!h) return EXTRACT_OK;
+    cudaError_t e = cudaDeviceSynchronize();
+    free_ctx(h);
+    if (e != cudaSuccess) return cuda_error(e, "destroy");
+    return EXTRACT_OK;
+}
+
+}  // extern "C"

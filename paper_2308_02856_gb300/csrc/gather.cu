@@ -1,0 +1,79 @@
+// Gather of the sampled sub-blocks (Sec. III.B step 1: bit A_i goes to
+// sub-block j when its label ranks it there; Sec. IV: the sampled bits are
+// stored before hashing).
+//
+// Output layout, read by the hashing kernels: sub-block j occupies words
+// [j * w_pad, (j+1) * w_pad) and is stored REVERSED, bit b of word w being
+// A_j[s - 1 - (32 w + b)] (0 past s).  With that order the Toeplitz row i is
+// the plain dot product of seed bits [i, i + s) with the stored string, so
+// the hashing kernel reads the seed forwards with funnel shifts only.
+//
+// One warp builds 32 consecutive output words: for each word every lane
+// fetches one order entry (32 consecutive entries: one coalesced 128-byte
+// load), then the input word that holds its bit (random 4-byte loads, 32 in
+// flight per lane), and a ballot packs the 32 bits.  The 32 words are stored
+// with one coalesced 128-byte store.
+#include "common.cuh"
+#include "internal.h"
+
+#include <algorithm>
+
+namespace ex {
+namespace {
+
+template <bool kIdentity>
+__global__ void __launch_bounds__(256)
+gather_kernel(const uint32_t *__restrict__ in, const uint32_t *__restrict__ perm, uint32_t m,
+              uint32_t s, uint32_t w_pad, uint64_t groups, uint32_t *__restrict__ arev)
+{
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint64_t gstride = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    const uint32_t gpr = w_pad >> 5;  // 32-word groups per sub-block
+    for (uint64_t g = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; g < groups;
+         g += gstride) {
+        const uint32_t j = (uint32_t)(g / gpr);
+        const uint32_t w0 = (uint32_t)(g % gpr) * 32u;
+        const uint64_t top = (uint64_t)j * s + (s - 1);  // rank of A_j[s-1]
+        uint32_t pos[32];
+#pragma unroll
+        for (int t = 0; t < 32; ++t) {
+            const uint64_t cr = (uint64_t)(w0 + t) * 32u + lane;  // reversed index s-1-c
+            if (cr < s) {
+                const uint64_t rank = top - cr;
+                pos[t] = kIdentity ? (uint32_t)rank : __ldg(perm + rank);
+            } else {
+                pos[t] = 0xffffffffu;
+            }
+        }
+        uint32_t mine = 0;
+#pragma unroll
+        for (int t = 0; t < 32; ++t) {
+            const uint64_t cr = (uint64_t)(w0 + t) * 32u + lane;
+            uint32_t bit = 0;
+            if (cr < s) bit = (__ldg(in + (pos[t] >> 5)) >> (pos[t] & 31u)) & 1u;
+            const uint32_t word = __ballot_sync(0xffffffffu, bit);
+            if (lane == (uint32_t)t) mine = word;
+        }
+        arev[(uint64_t)j * w_pad + w0 + lane] = mine;
+    }
+}
+
+}  // namespace
+
+int launch_gather(const uint32_t *in, const uint32_t *perm, uint32_t m, uint32_t s,
+                  uint32_t w_pad, uint32_t *arev, cudaStream_t st, int num_sms)
+{
+    if (w_pad % 32u) return set_error(EXTRACT_EINTERNAL, "gather: w_pad %u not a multiple of 32", w_pad);
+    const uint64_t groups = (uint64_t)m * (w_pad / 32u);
+    if (groups == 0) return EXTRACT_OK;
+    const uint64_t want = ceil_div(groups, 8);  // 8 warps per block
+    const uint32_t grid = (uint32_t)std::min<uint64_t>(want, (uint64_t)num_sms * 64);
+    if (perm)
+        gather_kernel<false><<<grid, 256, 0, st>>>(in, perm, m, s, w_pad, groups, arev);
+    else
+        gather_kernel<true><<<grid, 256, 0, st>>>(in, perm, m, s, w_pad, groups, arev);
+    EX_LAUNCH("gather_kernel");
+    return EXTRACT_OK;
+}
+
+}  // namespace ex

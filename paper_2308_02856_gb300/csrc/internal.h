@@ -1,0 +1,59 @@
+// Host-side launchers shared between the translation units of libextract.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ex {
+
+// ---- step 1: the sampled order ------------------------------------------
+// Builds perm[0..n) = stable argsort of the Philox sampling labels (index
+// tie-break) on `st`, then synchronises it.  `mask` keeps the top label bits
+// (all ones unless the test hook is set).  Allocates and frees its own
+// scratch.  Returns EXTRACT_OK or a negative code.
+int build_perm(uint64_t n, uint64_t sampling_key, uint64_t mask, uint32_t *perm,
+               cudaStream_t st, int num_sms);
+
+// ---- step 1 (gather) ----------------------------------------------------
+// arev[j * w_pad + w], for j < m and w < w_pad: bit b of the word is
+// in[perm[j*s + s-1-(32w+b)]] when 32w+b < s, else 0 (sub-block j reversed).
+// perm == nullptr means the identity order.
+int launch_gather(const uint32_t *in, const uint32_t *perm, uint32_t m, uint32_t s,
+                  uint32_t w_pad, uint32_t *arev, cudaStream_t st, int num_sms);
+
+// ---- steps 2-3: the Toeplitz product and concatenation ------------------
+struct HashPlan {
+    int q = 4;            // row groups of 32 per warp (rows per warp = 32 q)
+    int j = 32;           // sub-blocks per CTA sharing the seed windows
+    int warps = 8;        // warps per CTA, each on its own rows
+    int wc = 128;         // words of sub-block data staged per chunk
+    uint32_t gx = 0;      // row tiles
+    uint32_t gy = 0;      // sub-block tiles
+    uint32_t nchunks = 0; // w_pad / wc
+    uint32_t cps = 0;     // chunks per split
+    uint32_t splits = 0;  // split-K factor (gridDim.z)
+    uint32_t rows() const { return (uint32_t)(warps * 32 * q); }
+};
+
+// Word layout shared by the gather and the hash kernels.
+constexpr uint32_t kWordChunk = 128;
+
+// Pick the tile shape and split for (m, k, w_pad) on `num_sms` SMs.
+HashPlan plan_hash(uint32_t m, uint32_t k, uint32_t w_pad, bool per_subblock_seed, int num_sms);
+
+// Seed words each (realigned) seed needs for this plan: the kernels read
+// seed word (row >> 5) + w + 1 for every row tile and word chunk.
+uint32_t seed_stride_words(const HashPlan &p, uint32_t k, uint32_t w_pad);
+
+// out (ceil(m*k/32) words) is zeroed on `st` and then receives every K_j.
+// seed_stride = 0: one shared seed; else seed j starts at seed + j*seed_stride.
+int launch_hash(const HashPlan &p, const uint32_t *seed, uint32_t seed_stride,
+                const uint32_t *arev, uint32_t w_pad, uint32_t m, uint32_t k,
+                uint32_t *out, cudaStream_t st);
+
+// The plain per-block path: one launch per sub-block, one thread per row.
+int launch_hash_plain(const uint32_t *seed, uint32_t seed_stride, const uint32_t *arev,
+                      uint32_t w_pad, uint32_t s, uint32_t m, uint32_t k, uint32_t *out,
+                      cudaStream_t st);
+
+}  // namespace ex

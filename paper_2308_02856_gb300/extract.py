@@ -1,0 +1,241 @@
+"""Thin ctypes binding of libextract.so (include/extract.h), same names.
+
+Argument marshalling only: every step of the path runs in the CUDA library.
+Device buffers are passed as torch CUDA tensors of 32-bit words (int32 or
+uint32 dtype; the bits are what count) or as raw integer device addresses.
+There is no CPU fallback: if the library is not built, loading fails loudly.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libextract.so")
+
+EXTRACT_OK = 0
+EXTRACT_EINVAL = -1
+EXTRACT_ENOMEM = -2
+EXTRACT_ECUDA = -3
+EXTRACT_ETIMEDOUT = -4
+EXTRACT_EBUDGET = -5
+EXTRACT_EBUSY = -6
+EXTRACT_EINTERNAL = -7
+
+EXTRACT_SEED_PER_SUBBLOCK = 0x1
+EXTRACT_IDENTITY_PERM = 0x2
+
+
+def EXTRACT_KEY_BITS(b: int) -> int:
+    return (int(b) & 0x3F) << 8
+
+
+# Every symbol include/extract.h declares (checked by the CPU test suite).
+EXPORTED = [
+    "extract_create", "extract_run", "extract_run_host", "extract_gather", "extract_hash", "extract_run_plain",
+    "extract_read_perm", "extract_read_subblock", "extract_describe", "extract_destroy",
+    "extract_last_error",
+]
+
+
+class ExtractError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("libextract error %d: %s" % (code, msg))
+        self.code = code
+
+
+_lib = None
+
+
+def load() -> ctypes.CDLL:
+    """Load libextract.so; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libextract.so is not built (%s); run __graft_entry__.build(). "
+                           "There is no CPU fallback." % LIB_PATH)
+    L = ctypes.CDLL(LIB_PATH)
+    vp, u64, u32, i32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int
+    L.extract_create.argtypes = [ctypes.POINTER(vp), u64, u32, u32, u32, vp, u64, u32]
+    L.extract_run.argtypes = [vp, vp, vp, vp]
+    L.extract_run_host.argtypes = [vp, vp, vp, vp]
+    L.extract_gather.argtypes = [vp, vp, vp]
+    L.extract_hash.argtypes = [vp, vp, vp]
+    L.extract_run_plain.argtypes = [vp, vp, vp, vp]
+    L.extract_read_perm.argtypes = [vp, u64, u64, vp]
+    L.extract_read_subblock.argtypes = [vp, u32, vp]
+    L.extract_describe.argtypes = [vp, ctypes.c_char_p, u32]
+    L.extract_destroy.argtypes = [vp]
+    L.extract_last_error.argtypes = []
+    L.extract_last_error.restype = ctypes.c_char_p
+    for name in EXPORTED:
+        if name != "extract_last_error":
+            getattr(L, name).restype = i32
+    _lib = L
+    return L
+
+
+def _check(rc: int) -> int:
+    if rc != EXTRACT_OK:
+        raise ExtractError(rc, load().extract_last_error().decode(errors="replace"))
+    return rc
+
+
+def _dev_ptr(x) -> int:
+    if isinstance(x, int):
+        return x
+    if not x.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not x.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    if x.element_size() != 4:
+        raise ValueError("expected 32-bit words")
+    return x.data_ptr()
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def extract_create(n: int, m: int, s: int, k: int, seed_bits: np.ndarray, sampling_key: int,
+                   flags: int = 0) -> ctypes.c_void_p:
+    seed = np.ascontiguousarray(seed_bits, dtype=np.uint32)
+    h = ctypes.c_void_p()
+    _check(load().extract_create(ctypes.byref(h), n, m, s, k, seed.ctypes.data, sampling_key, flags))
+    return h
+
+
+def extract_run(h, stream, in_bits, out_bits) -> None:
+    _check(load().extract_run(h, _stream(stream), _dev_ptr(in_bits), _dev_ptr(out_bits)))
+
+
+def _host_ptr(x, writable=False) -> int:
+    if isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"] or x.dtype.itemsize != 4:
+            raise ValueError("expected a contiguous array of 32-bit words")
+        return x.ctypes.data
+    if x.is_cuda or not x.is_contiguous() or x.element_size() != 4:
+        raise ValueError("expected a contiguous host tensor of 32-bit words")
+    return x.data_ptr()
+
+
+def extract_run_host(h, stream, in_bits_host, out_bits_host) -> None:
+    _check(load().extract_run_host(h, _stream(stream), _host_ptr(in_bits_host), _host_ptr(out_bits_host)))
+
+
+def extract_gather(h, stream, in_bits) -> None:
+    _check(load().extract_gather(h, _stream(stream), _dev_ptr(in_bits)))
+
+
+def extract_hash(h, stream, out_bits) -> None:
+    _check(load().extract_hash(h, _stream(stream), _dev_ptr(out_bits)))
+
+
+def extract_run_plain(h, stream, in_bits, out_bits) -> None:
+    _check(load().extract_run_plain(h, _stream(stream), _dev_ptr(in_bits), _dev_ptr(out_bits)))
+
+
+def extract_read_perm(h, start: int, count: int) -> np.ndarray:
+    out = np.empty(max(count, 1), dtype=np.uint32)
+    _check(load().extract_read_perm(h, start, count, out.ctypes.data))
+    return out[:count]
+
+
+def extract_read_subblock(h, j: int, s: int) -> np.ndarray:
+    out = np.empty((s + 31) // 32, dtype=np.uint32)
+    _check(load().extract_read_subblock(h, j, out.ctypes.data))
+    return out
+
+
+def extract_describe(h) -> str:
+    buf = ctypes.create_string_buffer(512)
+    _check(load().extract_describe(h, buf, 512))
+    return buf.value.decode()
+
+
+def extract_destroy(h) -> None:
+    if h:
+        _check(load().extract_destroy(h))
+
+
+def extract_last_error() -> str:
+    return load().extract_last_error().decode(errors="replace")
+
+
+class Extractor:
+    """Owns one extract_ctx: ``with Extractor(n, m, s, k, seed, key) as ex: ex.run(in_t, out_t)``."""
+
+    def __init__(self, n, m, s, k, seed_bits, sampling_key, flags=0):
+        self.n, self.m, self.s, self.k, self.flags = n, m, s, k, flags
+        self.h = extract_create(n, m, s, k, seed_bits, sampling_key, flags)
+
+    @property
+    def out_words(self) -> int:
+        return (self.m * self.k + 31) // 32
+
+    def new_output(self):
+        import torch
+        return torch.empty(self.out_words, dtype=torch.int32, device="cuda")
+
+    def run(self, in_bits, out_bits=None, stream=None):
+        if out_bits is None:
+            out_bits = self.new_output()
+        extract_run(self.h, stream, in_bits, out_bits)
+        return out_bits
+
+    def run_host(self, in_bits_host, out_bits_host=None, stream=None):
+        if out_bits_host is None:
+            out_bits_host = np.empty(self.out_words, dtype=np.uint32)
+        extract_run_host(self.h, stream, in_bits_host, out_bits_host)
+        return out_bits_host
+
+    def run_plain(self, in_bits, out_bits=None, stream=None):
+        if out_bits is None:
+            out_bits = self.new_output()
+        extract_run_plain(self.h, stream, in_bits, out_bits)
+        return out_bits
+
+    def gather(self, in_bits, stream=None):
+        extract_gather(self.h, stream, in_bits)
+
+    def hash(self, out_bits=None, stream=None):
+        if out_bits is None:
+            out_bits = self.new_output()
+        extract_hash(self.h, stream, out_bits)
+        return out_bits
+
+    def read_perm(self, start=0, count=None):
+        return extract_read_perm(self.h, start, self.n - start if count is None else count)
+
+    def read_subblock(self, j):
+        return extract_read_subblock(self.h, j, self.s)
+
+    def describe(self) -> str:
+        return extract_describe(self.h)
+
+    def close(self):
+        if self.h:
+            extract_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -319,3 +319,19 @@ def test_extract_rejects_bad_shapes():
     for n, m, s, k in [(100, 2, 60, 10), (100, 1, 10, 11), (100, 0, 10, 1), (100, 1, 10, 0)]:
         with pytest.raises(ValueError):
             oracle.extract(n, m, s, k, w, w, 1)
+
+
+def test_check_order_accepts_only_the_stable_argsort():
+    n = 30000
+    keys = oracle.sampling_keys(n, 9, oracle.KEY_BITS(10))
+    p = oracle.perm_from_keys(keys)
+    assert oracle.check_order(keys, p, nthreads=4) == -1
+    q = p.copy()
+    q[[100, 101]] = q[[101, 100]]           # swap two neighbours
+    assert oracle.check_order(keys, q) in (99, 100, 101)
+    q = p.copy()
+    q[5000] = q[4000]                       # a duplicate, so not a bijection
+    assert oracle.check_order(keys, q) >= 0
+    q = p.copy()
+    q[7] = n                                # out of range
+    assert oracle.check_order(keys, q) >= 0
