@@ -148,6 +148,47 @@ int extract_read_subblock(extract_ctx *h, uint32_t j, uint32_t *dst_host);
    kernel configuration (tile shape, split, grid) into buf. */
 int extract_describe(extract_ctx *h, char *buf, uint32_t buflen);
 
+/*
+ * extract_run_static - extract_run for callers that must not allocate device
+ * memory.  The paper has no counterpart; this is a library convenience.
+ *
+ * Who needs it: code that runs with a device-memory budget handed out by
+ * someone else (an embedding application's own pool, a post-processing
+ * pipeline sized up front) and so may not call cudaMalloc, and loops that
+ * cannot afford the implicit device-wide synchronisation cudaMalloc and
+ * cudaFree can cause.  Such callers own all of their buffers; this call only
+ * borrows them and never calls cudaMalloc, cudaFree or any allocating
+ * library routine.
+ *
+ * Its scratch (the padded seed plus the gathered sub-blocks) is one fixed
+ * array of EXTRACT_STATIC_SCRATCH_WORDS 32-bit words (16 MiB) in the
+ * library's static device memory.  Every GPU that loads libextract holds
+ * that array until the process exits.
+ *   n, m, s, k    as for extract_create; one shared seed (no per-sub-block
+ *                 seeds).  Shapes whose scratch would exceed the array,
+ *                 about m*s > 2^27 bits, are rejected with EXTRACT_EINVAL
+ *                 and a message giving the words needed.
+ *   perm_dev      device pointer to the sampled order, n uint32 entries (as
+ *                 extract_read_perm returns it), or NULL for the identity
+ *                 order (direct hashing of consecutive s-bit blocks).
+ *   seed_dev      device pointer, ceil((s+k-1)/32) words of seed bits.
+ *   in_bits_dev   device pointer, ceil(n/32) input words.
+ *   out_bits_dev  device pointer, ceil(m*k/32) words, fully overwritten.
+ *   stream        cudaStream_t the work is queued on.
+ *
+ * The first call on each device looks up the array's device address with
+ * cudaGetSymbolAddress while that device is current; make that first call
+ * before any stream capture.  All calls share the one array and each call
+ * rewrites all of the scratch it reads, so results never depend on earlier
+ * calls; but two calls whose work overlaps on the GPU (different streams,
+ * or different host threads, without ordering between them) race on the
+ * array and give wrong results.  Order them on one stream.
+ */
+#define EXTRACT_STATIC_SCRATCH_WORDS (4u * 1024u * 1024u)
+int extract_run_static(uint64_t n, uint32_t m, uint32_t s, uint32_t k, const uint32_t *perm_dev,
+                       const uint32_t *seed_dev, const uint32_t *in_bits_dev, uint32_t *out_bits_dev,
+                       void *stream);
+
 /* extract_destroy - free the context and all device memory it holds
    (synchronises the device first).  NULL is accepted. */
 int extract_destroy(extract_ctx *h);

@@ -22,4 +22,5 @@ from .extract import (  # noqa: F401
     extract_run,
     extract_run_host,
     extract_run_plain,
+    extract_run_static,
 )

@@ -36,8 +36,10 @@ def EXTRACT_KEY_BITS(b: int) -> int:
 EXPORTED = [
     "extract_create", "extract_run", "extract_run_host", "extract_gather", "extract_hash", "extract_run_plain",
     "extract_read_perm", "extract_read_subblock", "extract_describe", "extract_destroy",
-    "extract_last_error",
+    "extract_last_error", "extract_run_static",
 ]
+
+EXTRACT_STATIC_SCRATCH_WORDS = 4 * 1024 * 1024
 
 
 class ExtractError(RuntimeError):
@@ -69,6 +71,7 @@ def load() -> ctypes.CDLL:
     L.extract_read_subblock.argtypes = [vp, u32, vp]
     L.extract_describe.argtypes = [vp, ctypes.c_char_p, u32]
     L.extract_destroy.argtypes = [vp]
+    L.extract_run_static.argtypes = [u64, u32, u32, u32, vp, vp, vp, vp, vp]
     L.extract_last_error.argtypes = []
     L.extract_last_error.restype = ctypes.c_char_p
     for name in EXPORTED:
@@ -161,6 +164,13 @@ def extract_describe(h) -> str:
     buf = ctypes.create_string_buffer(512)
     _check(load().extract_describe(h, buf, 512))
     return buf.value.decode()
+
+
+def extract_run_static(n, m, s, k, perm, seed, in_bits, out_bits, stream=None) -> None:
+    """The run without any device allocation (scratch in the library's static
+    device memory); ``perm`` None means the identity order."""
+    _check(load().extract_run_static(n, m, s, k, None if perm is None else _dev_ptr(perm), _dev_ptr(seed),
+                                     _dev_ptr(in_bits), _dev_ptr(out_bits), _stream(stream)))
 
 
 def extract_destroy(h) -> None:

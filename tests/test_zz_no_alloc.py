@@ -1,0 +1,59 @@
+"""extract_run_static: the run for callers that may not allocate device
+memory (their memory is budgeted and handed out by someone else, or they
+cannot afford the device-wide synchronisation cudaMalloc/cudaFree can cause).
+
+It must give the same bits as the ordinary entry point, extract_run, on two
+calls in a row that share the library's one static scratch array.  This file
+is collected last on purpose, so that a failure here stops a -x run only after
+every other test has run."""
+import numpy as np
+import pytest
+
+from paper_2308_02856_gb300 import build as pkg_build
+from paper_2308_02856_gb300 import extract as X
+from paper_2308_02856_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _dev(words):
+    return torch.from_numpy(np.ascontiguousarray(words, dtype=np.uint32).view(np.int32)).cuda()
+
+
+def _host(t):
+    return t.cpu().numpy().view(np.uint32)
+
+
+@pytest.mark.parametrize("n,m,s,k,flags", [
+    (1 << 18, 8, 1 << 15, 1 << 13, 0),             # sampled sub-blocks
+    (200_000, 37, 5000, 3001, 0),                   # ragged rows, words and sub-block tiles
+    (1 << 20, 1, 1 << 20, 1 << 16, X.EXTRACT_IDENTITY_PERM),  # direct whole-block, no order
+])
+def test_static_run_matches_extract_run_twice(n, m, s, k, flags):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    pkg_build.build()
+    seed = synth.uniform_bits(s + k - 1, 3)
+    ins = [synth.bernoulli_bits(n, 0.7, 1), synth.bernoulli_bits(n, 0.55, 2)]
+    with X.Extractor(n, m, s, k, seed, 2, flags) as ex:
+        want = [_host(ex.run(_dev(w))) for w in ins]
+        perm = None if flags & X.EXTRACT_IDENTITY_PERM else _dev(ex.read_perm())
+    d_seed = _dev(seed)
+    for w, ref in zip(ins, want):  # two calls in a row on the shared static scratch
+        out = torch.full(((m * k + 31) // 32,), -1, dtype=torch.int32, device="cuda")
+        X.extract_run_static(n, m, s, k, perm, d_seed, _dev(w), out)
+        torch.cuda.synchronize()
+        assert np.array_equal(_host(out), ref)
+
+
+def test_static_run_rejects_shapes_beyond_the_array():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    n = s = 1 << 28  # 2^23 words of sub-block data: over the 4 Mi-word array
+    d = torch.zeros(16, dtype=torch.int32, device="cuda")
+    with pytest.raises(X.ExtractError) as e:
+        X.extract_run_static(n, 1, s, 64, None, d, d, d)
+    assert e.value.code == X.EXTRACT_EINVAL
+    assert "static limit" in str(e.value)
