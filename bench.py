@@ -37,7 +37,8 @@ if ROOT not in sys.path:
 WORKLOADS = {
     # name: n, m, s, k, Bernoulli p
     "qrng_n2^30_m1024_s2^20_k2^19": (1 << 30, 1024, 1 << 20, 1 << 19, 0.6),
-    # smaller shape of the same kind, for quick checks only
+    # smaller shapes of the same kind, for profiling and quick checks only
+    "mid_n2^27_m128_s2^20_k2^16": (1 << 27, 128, 1 << 20, 1 << 16, 0.6),
     "small_n2^24_m64_s2^18_k2^17": (1 << 24, 64, 1 << 18, 1 << 17, 0.6),
 }
 DEFAULT_WORKLOAD = "qrng_n2^30_m1024_s2^20_k2^19"
@@ -47,9 +48,13 @@ IN_SEED, SAMPLING_KEY, TOEPLITZ_SEED = 1, 2, 3
 # SM per clock x SMs x maximum SM clock.  The lane count is the one measured
 # by a dependency-free LOP3 probe on GB300 (profiles/lop3_alu_peak.md).
 LOP3_LANES_PER_SM_CLK = 64
-# DRAM traffic of one hashing launch on this workload from ncu, bytes (None
-# until captured for the current kernel).
-HASH_TRAFFIC_BYTES = None
+# DRAM bytes (read + write) of one hashing launch on the QRNG-shaped block:
+# the ncu capture of the mid-size block (m = 128: 18.04 MB,
+# profiles/toeplitz_lop3_kernel_mid_n2^27_m128_s2^20_k2^16.md) scaled by the
+# sub-block count to m = 1024; traffic grows with the sub-block data.  Set to
+# None whenever the kernel changes until it is captured again.
+HASH_TRAFFIC_BYTES = {"qrng_n2^30_m1024_s2^20_k2^19": 18.04e6 * 1024 / 128,
+                      "mid_n2^27_m128_s2^20_k2^16": 18.04e6}
 
 
 def parse_args():
@@ -316,7 +321,7 @@ def run_ours(args):
     achieved = lop3_per_launch / (hash_ms / 1e3) / 1e12
     peak = sms * LOP3_LANES_PER_SM_CLK * 2070e6 / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TLOP3/s",
-                "frac": achieved / peak, "traffic": HASH_TRAFFIC_BYTES,
+                "frac": achieved / peak, "traffic": HASH_TRAFFIC_BYTES.get(args.workload),
                 "kernel": "toeplitz_lop3_kernel",
                 "work_per_launch": "m*k*s/32 = %.4g LOP3 (32 bit-products each)" % lop3_per_launch,
                 "peak_basis": "%d SMs x %d LOP3/clk/SM x 2070 MHz max SM clock" % (sms, LOP3_LANES_PER_SM_CLK)}
