@@ -189,6 +189,62 @@ int extract_run_static(uint64_t n, uint32_t m, uint32_t s, uint32_t k, const uin
                        const uint32_t *seed_dev, const uint32_t *in_bits_dev, uint32_t *out_bits_dev,
                        void *stream);
 
+/* ---- batching: many blocks of uneven n, s, k in one persistent launch -- */
+
+/* One block of a batch or a served job: the arguments of extract_create. */
+typedef struct extract_job_desc {
+    uint64_t n;
+    uint32_t m, s, k;
+    uint32_t flags;                  /* EXTRACT_* create flags */
+    uint64_t sampling_key;
+    const uint32_t *seed_bits_host;  /* as in extract_create; copied */
+} extract_job_desc;
+
+typedef struct extract_batch extract_batch;
+
+/* batch flags */
+#define EXTRACT_BATCH_NO_GRAPH 0x1u  /* launch the kernels directly instead of replaying a CUDA graph */
+#define EXTRACT_BATCH_NO_TUNE  0x2u  /* use the single-block heuristic tile instead of the autotuned one */
+
+/*
+ * extract_batch_create - set up njobs independent blocks (the method of
+ * Sec. III.B applied to each) for hashing in one persistent launch.
+ *
+ * Builds every job's sampled order (synchronous), chooses every job's tile
+ * shape with the autotuner (measured cost per tile variant, cached per
+ * device, then the least predicted time including padding), splits word
+ * ranges so the tiles balance across SMs, orders the tiles longest first,
+ * and captures the per-run kernels (zero outputs, gather all jobs, persistent
+ * hash) into a CUDA graph.  Device memory held: per job as extract_create.
+ * Errors: EINVAL (empty list, a bad job shape or flags), ENOMEM, ECUDA.
+ */
+int extract_batch_create(extract_batch **out, const extract_job_desc *jobs, uint32_t njobs,
+                         uint32_t flags);
+
+/*
+ * extract_batch_run - hash every job's input into its output on `stream`
+ * (asynchronous).  in_bits_dev[i] / out_bits_dev[i] are job i's device
+ * buffers with the sizes of extract_run; the two host arrays of pointers are
+ * read before the call returns.  Output i is fully overwritten with exactly
+ * what extract_run would give for job i.  Runs of one batch must be ordered
+ * on one stream.  Errors: EINVAL, ECUDA.
+ */
+int extract_batch_run(extract_batch *b, void *stream, const uint32_t *const *in_bits_dev,
+                      uint32_t *const *out_bits_dev);
+
+/* extract_batch_run_sequential - the same result with one gather and one
+   hash launch per block, each with the single-block heuristic tile: the
+   baseline the persistent launch is measured against. */
+int extract_batch_run_sequential(extract_batch *b, void *stream, const uint32_t *const *in_bits_dev,
+                                 uint32_t *const *out_bits_dev);
+
+/* extract_batch_describe - one line: jobs, tiles, graph, chosen variants and
+   their measured cost. */
+int extract_batch_describe(extract_batch *b, char *buf, uint32_t buflen);
+
+/* extract_batch_destroy - synchronise the device and free the batch. */
+int extract_batch_destroy(extract_batch *b);
+
 /* extract_destroy - free the context and all device memory it holds
    (synchronises the device first).  NULL is accepted. */
 int extract_destroy(extract_ctx *h);

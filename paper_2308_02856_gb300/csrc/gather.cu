@@ -14,6 +14,7 @@
 // flight per lane), and a ballot packs the 32 bits.  The 32 words are stored
 // with one coalesced 128-byte store.
 #include "common.cuh"
+#include "gather_body.cuh"
 #include "internal.h"
 
 #include <algorithm>
@@ -30,32 +31,8 @@ gather_kernel(const uint32_t *__restrict__ in, const uint32_t *__restrict__ perm
     const uint64_t gstride = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     const uint32_t gpr = w_pad >> 5;  // 32-word groups per sub-block
     for (uint64_t g = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; g < groups;
-         g += gstride) {
-        const uint32_t j = (uint32_t)(g / gpr);
-        const uint32_t w0 = (uint32_t)(g % gpr) * 32u;
-        const uint64_t top = (uint64_t)j * s + (s - 1);  // rank of A_j[s-1]
-        uint32_t pos[32];
-#pragma unroll
-        for (int t = 0; t < 32; ++t) {
-            const uint64_t cr = (uint64_t)(w0 + t) * 32u + lane;  // reversed index s-1-c
-            if (cr < s) {
-                const uint64_t rank = top - cr;
-                pos[t] = kIdentity ? (uint32_t)rank : __ldg(perm + rank);
-            } else {
-                pos[t] = 0xffffffffu;
-            }
-        }
-        uint32_t mine = 0;
-#pragma unroll
-        for (int t = 0; t < 32; ++t) {
-            const uint64_t cr = (uint64_t)(w0 + t) * 32u + lane;
-            uint32_t bit = 0;
-            if (cr < s) bit = (__ldg(in + (pos[t] >> 5)) >> (pos[t] & 31u)) & 1u;
-            const uint32_t word = __ballot_sync(0xffffffffu, bit);
-            if (lane == (uint32_t)t) mine = word;
-        }
-        arev[(uint64_t)j * w_pad + w0 + lane] = mine;
-    }
+         g += gstride)
+        gather_group<kIdentity>(in, perm, s, w_pad, (uint32_t)(g / gpr), (uint32_t)(g % gpr) * 32u, lane, arev);
 }
 
 }  // namespace

@@ -1,27 +1,11 @@
 // Toeplitz hashing of the gathered sub-blocks and concatenation of the
 // outputs (Sec. I: K = T . A'; Sec. III.B steps 3 and 4).
 //
-// With the sub-block stored reversed (see gather.cu), output bit i of
-// sub-block j is
-//     K_j[i] = parity( XOR_w  win(seed_j, i + 32 w) AND Arev_j[w] )
-// where win(x, p) is the 32 seed bits starting at bit p.  One "AND then XOR
-// into the accumulator" on 32-bit words is one LOP3 instruction and does 32
-// bit-products of T . A; that instruction is the whole hot loop.
-//
-// Tiling (integer-ALU bound, no tensor cores: GF(2) AND/XOR on packed bits):
-//  * lane l of a warp owns rows r + l + 32 q (q < Q), so its funnel-shift
-//    amount is the constant l and one shift serves all J sub-blocks of the
-//    CTA, which share the seed (Q x 4 shifts per 4 words, Q x J x 4 LOP3);
-//  * the J sub-blocks' words are staged in shared memory and read as one
-//    16-byte broadcast per sub-block per 4 words;
-//  * accumulators stay in registers (Q x J words per lane) until the end;
-//    a popcount gives each row's parity and a ballot packs 32 rows into a
-//    word;
-//  * the word range can be split across CTAs (split-K); partial parities
-//    are combined with atomicXor straight into the caller's output at bit
-//    offset j*k + i, which also performs the concatenation (k need not be a
-//    multiple of 32).
+// The tile body and its design notes are in hash_tile.cuh; this file holds
+// the single-block launch, the plan heuristic and the plain per-block
+// baseline kernel.
 #include "common.cuh"
+#include "hash_tile.cuh"
 #include "internal.h"
 
 #include <algorithm>
@@ -29,87 +13,25 @@
 namespace ex {
 namespace {
 
-constexpr int kWarps = 8;
-constexpr int kWC = (int)kWordChunk;
+constexpr int kWarps = kHashWarps;
+constexpr int kWC = kHashWC;
 
 template <int Q, int J>
-__global__ void __launch_bounds__(kWarps * 32, 1)
+__global__ void __launch_bounds__(kHashThreads, 1)
 toeplitz_lop3_kernel(const uint32_t *__restrict__ seed, uint32_t seed_stride,
                      const uint32_t *__restrict__ arev, uint32_t w_pad, uint32_t m, uint32_t k,
                      uint32_t gx, uint32_t nchunks, uint32_t cps, uint32_t *__restrict__ out)
 {
     constexpr int kRows = kWarps * 32 * Q;
-    constexpr int kSeedW = kWarps * Q + kWC + 1;
-    __shared__ __align__(16) uint32_t a_s[J][kWC];
-    __shared__ __align__(16) uint32_t s_s[(kSeedW + 3) & ~3];
-
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __shared__ __align__(16) uint32_t a_s[J * kWC];
+    __shared__ __align__(16) uint32_t s_s[kSeedSmemWords];
     const uint32_t bx = blockIdx.x % gx, by = blockIdx.x / gx;
     const uint32_t r0 = bx * kRows;
     const uint32_t j0 = by * J;
     const uint32_t c_begin = blockIdx.z * cps;
     const uint32_t c_end = min(nchunks, c_begin + cps);
     const uint32_t *sd = seed + (size_t)(seed_stride ? j0 : 0u) * seed_stride + (r0 >> 5);
-
-    uint32_t acc[Q][J];
-#pragma unroll
-    for (int q = 0; q < Q; ++q)
-#pragma unroll
-        for (int j = 0; j < J; ++j) acc[q][j] = 0u;
-
-    for (uint32_t c = c_begin; c < c_end; ++c) {
-        const uint32_t wc = c * kWC;
-        for (int t = threadIdx.x; t < kSeedW; t += blockDim.x) s_s[t] = __ldg(sd + wc + t);
-        for (int t = threadIdx.x; t < J * kWC / 4; t += blockDim.x) {
-            const int jj = t / (kWC / 4), ww = t % (kWC / 4);
-            uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if (j0 + jj < m)
-                v = __ldg(reinterpret_cast<const uint4 *>(arev + (size_t)(j0 + jj) * w_pad + wc) + ww);
-            *reinterpret_cast<uint4 *>(&a_s[jj][ww * 4]) = v;
-        }
-        __syncthreads();
-#pragma unroll 1
-        for (int w = 0; w < kWC; w += 4) {
-            uint32_t sw[Q + 4];
-#pragma unroll
-            for (int t = 0; t < Q + 4; ++t) sw[t] = s_s[warp * Q + w + t];
-            uint32_t win[Q][4];
-#pragma unroll
-            for (int q = 0; q < Q; ++q)
-#pragma unroll
-                for (int u = 0; u < 4; ++u) win[q][u] = __funnelshift_r(sw[q + u], sw[q + u + 1], lane);
-#pragma unroll
-            for (int j = 0; j < J; ++j) {
-                const uint4 a = *reinterpret_cast<const uint4 *>(&a_s[j][w]);
-#pragma unroll
-                for (int q = 0; q < Q; ++q) {
-                    acc[q][j] ^= win[q][0] & a.x;
-                    acc[q][j] ^= win[q][1] & a.y;
-                    acc[q][j] ^= win[q][2] & a.z;
-                    acc[q][j] ^= win[q][3] & a.w;
-                }
-            }
-        }
-        __syncthreads();
-    }
-
-    // parity, pack 32 rows per ballot, XOR into the output at bit j*k + i
-#pragma unroll
-    for (int q = 0; q < Q; ++q) {
-        const uint32_t ib = r0 + (uint32_t)(warp * Q + q) * 32u;
-#pragma unroll
-        for (int j = 0; j < J; ++j) {
-            uint32_t word = __ballot_sync(0xffffffffu, __popc(acc[q][j]) & 1u);
-            const uint32_t jj = j0 + j;
-            if (lane == (j & 31) && jj < m && ib < k && word) {
-                if (k - ib < 32u) word &= (1u << (k - ib)) - 1u;
-                const uint64_t P = (uint64_t)jj * k + ib;
-                const uint32_t sh = (uint32_t)(P & 31u);
-                atomicXor(out + (P >> 5), word << sh);
-                if (sh && (word >> (32u - sh))) atomicXor(out + (P >> 5) + 1, word >> (32u - sh));
-            }
-        }
-    }
+    hash_tile<Q, J>(sd, arev, w_pad, m, k, r0, j0, c_begin, c_end, out, a_s, s_s);
 }
 
 // Plain per-block baseline: one thread per output row of one sub-block.

@@ -37,7 +37,18 @@ EXPORTED = [
     "extract_create", "extract_run", "extract_run_host", "extract_gather", "extract_hash", "extract_run_plain",
     "extract_read_perm", "extract_read_subblock", "extract_describe", "extract_destroy",
     "extract_last_error", "extract_run_static",
+    "extract_batch_create", "extract_batch_run", "extract_batch_run_sequential", "extract_batch_describe",
+    "extract_batch_destroy",
 ]
+
+EXTRACT_BATCH_NO_GRAPH = 0x1
+EXTRACT_BATCH_NO_TUNE = 0x2
+
+
+class extract_job_desc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_uint64), ("m", ctypes.c_uint32), ("s", ctypes.c_uint32), ("k", ctypes.c_uint32),
+                ("flags", ctypes.c_uint32), ("sampling_key", ctypes.c_uint64),
+                ("seed_bits_host", ctypes.c_void_p)]
 
 EXTRACT_STATIC_SCRATCH_WORDS = 4 * 1024 * 1024
 
@@ -72,6 +83,11 @@ def load() -> ctypes.CDLL:
     L.extract_describe.argtypes = [vp, ctypes.c_char_p, u32]
     L.extract_destroy.argtypes = [vp]
     L.extract_run_static.argtypes = [u64, u32, u32, u32, vp, vp, vp, vp, vp]
+    L.extract_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(extract_job_desc), u32, u32]
+    L.extract_batch_run.argtypes = [vp, vp, vp, vp]
+    L.extract_batch_run_sequential.argtypes = [vp, vp, vp, vp]
+    L.extract_batch_describe.argtypes = [vp, ctypes.c_char_p, u32]
+    L.extract_batch_destroy.argtypes = [vp]
     L.extract_last_error.argtypes = []
     L.extract_last_error.restype = ctypes.c_char_p
     for name in EXPORTED:
@@ -180,6 +196,59 @@ def extract_destroy(h) -> None:
 
 def extract_last_error() -> str:
     return load().extract_last_error().decode(errors="replace")
+
+
+class Batch:
+    """Owns one extract_batch.  ``jobs``: list of dicts with n, m, s, k, seed
+    (np.uint32 words), key and optional flags."""
+
+    def __init__(self, jobs, flags=0):
+        self._seeds = [np.ascontiguousarray(j["seed"], dtype=np.uint32) for j in jobs]
+        arr = (extract_job_desc * len(jobs))()
+        for i, j in enumerate(jobs):
+            arr[i] = extract_job_desc(j["n"], j["m"], j["s"], j["k"], j.get("flags", 0), j["key"],
+                                      self._seeds[i].ctypes.data)
+        self.jobs = jobs
+        self.h = ctypes.c_void_p()
+        _check(load().extract_batch_create(ctypes.byref(self.h), arr, len(jobs), flags))
+
+    def _ptrs(self, ins, outs):
+        n = len(self.jobs)
+        if len(ins) != n or len(outs) != n:
+            raise ValueError("need one input and one output per job")
+        pi = (ctypes.c_void_p * n)(*[_dev_ptr(x) for x in ins])
+        po = (ctypes.c_void_p * n)(*[_dev_ptr(x) for x in outs])
+        return pi, po
+
+    def run(self, ins, outs, stream=None):
+        pi, po = self._ptrs(ins, outs)
+        _check(load().extract_batch_run(self.h, _stream(stream), pi, po))
+
+    def run_sequential(self, ins, outs, stream=None):
+        pi, po = self._ptrs(ins, outs)
+        _check(load().extract_batch_run_sequential(self.h, _stream(stream), pi, po))
+
+    def describe(self) -> str:
+        buf = ctypes.create_string_buffer(1024)
+        _check(load().extract_batch_describe(self.h, buf, 1024))
+        return buf.value.decode()
+
+    def close(self):
+        if self.h:
+            _check(load().extract_batch_destroy(self.h))
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Extractor:

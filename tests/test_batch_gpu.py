@@ -1,0 +1,157 @@
+"""Batching: many blocks of uneven n, s, k in one persistent launch, through
+the C ABI, bit-exact against the CPU oracle and against one-launch-per-block
+runs."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2308_02856_gb300 import build as pkg_build
+from paper_2308_02856_gb300 import extract as X
+from paper_2308_02856_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    pkg_build.build()
+    X.load()
+
+
+def _dev(words):
+    return torch.from_numpy(np.ascontiguousarray(words, dtype=np.uint32).view(np.int32)).cuda()
+
+
+def _host(t):
+    return t.cpu().numpy().view(np.uint32)
+
+
+def _seed_len(j):
+    L = j["s"] + j["k"] - 1
+    return L * j["m"] if j.get("flags", 0) & X.EXTRACT_SEED_PER_SUBBLOCK else L
+
+
+def _materialise(shapes):
+    jobs, ins = [], []
+    for j in shapes:
+        j = dict(j)
+        j["seed"] = synth.uniform_bits(_seed_len(j), j["seed_seed"])
+        jobs.append(j)
+        ins.append(synth.bernoulli_bits(j["n"], j["p"], j["in_seed"]))
+    return jobs, ins
+
+
+SMALL = [
+    # n, m, s, k, flags
+    (4096, 4, 1000, 77, 0),
+    (70000, 3, 20000, 4000, 0),
+    (1 << 17, 8, 1 << 14, 1 << 12, 0),
+    (5000, 1, 5000, 2500, X.EXTRACT_IDENTITY_PERM),
+    (100, 3, 33, 31, 0),
+    (65536, 64, 1024, 300, 0),
+    (200_000, 37, 5000, 3001, 0),
+    (2048, 8, 256, 100, X.EXTRACT_SEED_PER_SUBBLOCK),
+    (4096, 16, 256, 64, X.EXTRACT_KEY_BITS(4)),
+    (33, 1, 33, 1, 0),
+    (300_000, 5, 60000, 600, 0),
+    (1 << 16, 2, 1 << 15, 1 << 15, 0),
+]
+
+
+def _small_jobs():
+    shapes = []
+    for i, (n, m, s, k, fl) in enumerate(SMALL):
+        shapes.append({"n": n, "m": m, "s": s, "k": k, "flags": fl, "p": 0.55 + 0.03 * i,
+                       "in_seed": 100 + i, "seed_seed": 200 + i, "key": 300 + i})
+    return _materialise(shapes)
+
+
+def _outs(jobs, fill=-1):
+    return [torch.full(((j["m"] * j["k"] + 31) // 32,), fill, dtype=torch.int32, device="cuda") for j in jobs]
+
+
+@pytest.mark.parametrize("flags", [0, X.EXTRACT_BATCH_NO_GRAPH, X.EXTRACT_BATCH_NO_TUNE,
+                                   X.EXTRACT_BATCH_NO_GRAPH | X.EXTRACT_BATCH_NO_TUNE])
+def test_batch_matches_oracle(flags):
+    jobs, ins = _small_jobs()
+    want = [oracle.extract(j["n"], j["m"], j["s"], j["k"], w, j["seed"], j["key"], j["flags"])
+            for j, w in zip(jobs, ins)]
+    d_in = [_dev(w) for w in ins]
+    with X.Batch(jobs, flags) as b:
+        assert "jobs" in b.describe()
+        outs = _outs(jobs)
+        b.run(d_in, outs)
+        torch.cuda.synchronize()
+        for i, (o, w) in enumerate(zip(outs, want)):
+            assert np.array_equal(_host(o), w), "job %d %s" % (i, SMALL[i])
+        seq = _outs(jobs)
+        b.run_sequential(d_in, seq)
+        torch.cuda.synchronize()
+        for i, (o, w) in enumerate(zip(seq, want)):
+            assert np.array_equal(_host(o), w), "sequential job %d" % i
+
+
+def test_batch_reruns_with_new_buffers():
+    jobs, ins = _small_jobs()
+    with X.Batch(jobs) as b:
+        for rnd in range(3):
+            ins2 = [synth.bernoulli_bits(j["n"], 0.6, 1000 * rnd + i) for i, j in enumerate(jobs)]
+            outs = _outs(jobs, fill=rnd)
+            b.run([_dev(w) for w in ins2], outs)
+            torch.cuda.synchronize()
+            for j, w, o in zip(jobs, ins2, outs):
+                want = oracle.extract(j["n"], j["m"], j["s"], j["k"], w, j["seed"], j["key"], j["flags"])
+                assert np.array_equal(_host(o), want)
+
+
+def test_batch_equals_single_block_runs_on_uneven_shapes():
+    shapes = synth.job_shapes(24, 41, 2 ** 14, 2 ** 22, s_set=(1 << 12, 1 << 14, 1 << 16))
+    jobs, ins = _materialise(shapes)
+    d_in = [_dev(w) for w in ins]
+    with X.Batch(jobs) as b:
+        outs = _outs(jobs)
+        b.run(d_in, outs)
+        torch.cuda.synchronize()
+        for j, d, o in zip(jobs, d_in, outs):
+            with X.Extractor(j["n"], j["m"], j["s"], j["k"], j["seed"], j["key"]) as ex:
+                assert np.array_equal(_host(o), _host(ex.run(d)))
+
+
+def _check_rows_against_oracle(j, in_w, got_words, js, nrows, rng):
+    """Sampled sub-blocks x rows of one job against the oracle."""
+    n, m, s, k = j["n"], j["m"], j["s"], j["k"]
+    got = oracle.bits_of(got_words, m * k)
+    keys = oracle.sampling_keys(n, j["key"])
+    for jj in js:
+        pos = oracle.perm_range(keys, jj * s, s)
+        A = oracle.subblock(in_w, pos)
+        rows = np.unique(np.concatenate([np.arange(min(8, k)), np.arange(max(0, k - 8), k),
+                                         rng.choice(k, min(k, nrows), replace=False)]))
+        for i in rows:
+            assert got[jj * k + i] == oracle.toeplitz_bit(j["seed"], s, A, int(i)), (jj, i)
+
+
+def test_batch_of_256_uneven_blocks_full_size():
+    """The batching workload: 256 blocks, n log-uniform in [2^20, 2^28],
+    s in {2^16, 2^18, 2^20}, k/s uniform in [0.05, 0.5], p uniform in
+    [0.55, 0.95]: persistent launch == one launch per block, and sampled
+    outputs of the smallest and largest blocks == oracle."""
+    shapes = synth.job_shapes(256, 4, 2 ** 20, 2 ** 28)
+    jobs, ins = _materialise(shapes)
+    d_in = [_dev(w) for w in ins]
+    with X.Batch(jobs) as b:
+        outs, seq = _outs(jobs), _outs(jobs, fill=7)
+        b.run(d_in, outs)
+        b.run_sequential(d_in, seq)
+        torch.cuda.synchronize()
+        for i in range(len(jobs)):
+            assert torch.equal(outs[i], seq[i]), "job %d" % i
+    rng = np.random.default_rng(0)
+    order = sorted(range(len(jobs)), key=lambda i: jobs[i]["n"] * jobs[i]["k"])
+    for i in (order[0], order[1], order[-1]):
+        j = jobs[i]
+        _check_rows_against_oracle(j, ins[i], _host(outs[i]), sorted({0, j["m"] - 1, j["m"] // 2}), 24, rng)
