@@ -245,6 +245,68 @@ int extract_batch_describe(extract_batch *b, char *buf, uint32_t buflen);
 /* extract_batch_destroy - synchronise the device and free the batch. */
 int extract_batch_destroy(extract_batch *b);
 
+/* ---- serving: continuous batching under a device-memory budget -------- */
+
+typedef struct extract_server extract_server;
+
+typedef struct extract_stats {
+    uint64_t submitted, admitted, completed, failed, rejected;
+    uint64_t queued, active, waves;
+    uint64_t bytes_in_use, bytes_peak;  /* budget charge now / at most */
+    double p50_ms, p99_ms, mean_ms, max_ms;  /* latency: submit -> done */
+    double input_bits_done;                  /* sum of n over completed jobs */
+    double span_s;                           /* first submit -> last completion */
+    double gbit_per_s;                       /* input_bits_done / span_s / 1e9 */
+} extract_stats;
+
+/*
+ * extract_server_create - start a serving loop on the current device.
+ *
+ *   hbm_budget_bytes  device memory the admitted jobs may hold at once: each
+ *                     job is charged its order (4n bytes, returned once its
+ *                     sub-blocks are gathered), sub-block buffer, seed, and
+ *                     its input and output buffers.
+ *   max_slots         most jobs admitted at once.
+ *   wave_us           GPU time of one hashing wave in microseconds (0: 2000).
+ *   flags             must be 0.
+ *
+ * Jobs are admitted first come first served while budget and slots allow;
+ * admitted jobs are set up (order, gather) on their own stream while others
+ * hash, and every hashing launch ("wave") mixes tiles of all ready jobs,
+ * shortest remaining work first, so jobs join and leave the running work
+ * continuously.  Two host threads run the loop.  Errors: EINVAL, ENOMEM,
+ * ECUDA.
+ */
+int extract_server_create(extract_server **out, uint64_t hbm_budget_bytes, uint32_t max_slots,
+                          uint32_t wave_us, uint32_t flags);
+
+/*
+ * extract_server_submit - queue one job (thread-safe).  The seed is copied;
+ * in_bits_dev (ceil(n/32) words) and out_bits_dev (ceil(m*k/32) words) are
+ * the caller's device buffers and must stay valid until the job completes;
+ * the output is fully overwritten with exactly what extract_run gives.
+ * *ticket identifies the job.  Errors: EINVAL (shape, flags, null),
+ * EBUDGET (the job alone exceeds the budget), EBUSY (server stopping).
+ */
+int extract_server_submit(extract_server *srv, const extract_job_desc *job, const uint32_t *in_bits_dev,
+                          uint32_t *out_bits_dev, uint64_t *ticket);
+
+/*
+ * extract_server_wait - block until the job completes or timeout_ms passes.
+ * EXTRACT_OK: done (latency_ms, if not NULL, gets submit -> completion);
+ * EXTRACT_ETIMEDOUT: not yet (the ticket stays valid); otherwise the job's
+ * own error.  A completed ticket is forgotten after a successful wait.
+ */
+int extract_server_wait(extract_server *srv, uint64_t ticket, uint32_t timeout_ms, double *latency_ms);
+
+/* extract_server_stats - counters, budget use and latency percentiles of
+   all jobs completed so far. */
+int extract_server_stats(extract_server *srv, extract_stats *st);
+
+/* extract_server_destroy - finish every submitted job, stop the loop and
+   free everything. */
+int extract_server_destroy(extract_server *srv);
+
 /* extract_destroy - free the context and all device memory it holds
    (synchronises the device first).  NULL is accepted. */
 int extract_destroy(extract_ctx *h);

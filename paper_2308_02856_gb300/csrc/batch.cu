@@ -30,22 +30,6 @@
 
 namespace ex {
 
-struct BatchJobDev {
-    const uint32_t *perm;  // null: identity order
-    const uint32_t *in;    // refreshed per run
-    uint32_t *out;         // refreshed per run
-    const uint32_t *seed;  // realigned seeds
-    uint32_t *arev;
-    uint64_t groups_before;  // prefix of gather groups (m * w_pad / 32)
-    uint64_t outw_before;    // prefix of output words
-    uint32_t seed_stride;    // 0: one shared seed
-    uint32_t m, s, k, w_pad;
-};
-
-struct BatchTileDev {
-    uint32_t job, variant, r0, j0, c_begin, c_end;
-};
-
 namespace {
 
 __device__ __forceinline__ uint32_t find_job(const BatchJobDev *jobs, uint32_t njobs, uint64_t x, bool by_groups)
@@ -187,7 +171,7 @@ int measure_variants(int dev, int sms, TuneTable &tt)
     return rc;
 }
 
-int tune_table(int dev, int sms, const TuneTable **out)
+int tune_table_locked(int dev, int sms, const TuneTable **out)
 {
     if (dev < 0 || dev >= 64) return set_error(EXTRACT_EINVAL, "device %d out of range", dev);
     std::lock_guard<std::mutex> lock(g_tune_mu);
@@ -196,6 +180,41 @@ int tune_table(int dev, int sms, const TuneTable **out)
     *out = &g_tune[dev];
     return EXTRACT_OK;
 }
+
+}  // namespace
+
+int tile_costs(int dev, int sms, const double **ns_per_chunk)
+{
+    const TuneTable *tt = nullptr;
+    if (int rc = tune_table_locked(dev, sms, &tt)) return rc;
+    *ns_per_chunk = tt->ns_per_chunk;
+    return EXTRACT_OK;
+}
+
+int choose_variant(uint32_t m, uint32_t k, uint32_t w_pad, bool per_sub, const double *ns_per_chunk)
+{
+    const uint32_t nchunks = w_pad / kWordChunk;
+    double best = 1e300;
+    int pick = variant_id(4, 1);
+    for (int v = 0; v < kNumVariants; ++v) {
+        if (per_sub && variant_j(v) != 1) continue;
+        const double tiles = (double)ceil_div(k, (uint64_t)kHashWarps * 32 * variant_q(v)) *
+                             (double)ceil_div(m, (uint64_t)variant_j(v));
+        const double t = tiles * nchunks * ns_per_chunk[v];
+        if (t < best) { best = t; pick = v; }
+    }
+    return pick;
+}
+
+int launch_batch_hash(const BatchJobDev *jobs, const BatchTileDev *tiles, uint32_t ntiles, uint32_t *counter,
+                      int sms, cudaStream_t st)
+{
+    batch_hash_kernel<<<sms, kHashThreads, 0, st>>>(jobs, tiles, ntiles, counter);
+    EX_LAUNCH("batch_hash_kernel");
+    return EXTRACT_OK;
+}
+
+namespace {
 
 struct BatchJobHost {
     uint64_t n;
@@ -302,7 +321,7 @@ int extract_batch_create(extract_batch **out, const extract_job_desc *jobs, uint
     const TuneTable *tt = nullptr;
     TuneTable untuned;
     if (!(flags & EXTRACT_BATCH_NO_TUNE)) {
-        if (int rc = tune_table(b->device, b->num_sms, &tt)) { delete b; return rc; }
+        if (int rc = tune_table_locked(b->device, b->num_sms, &tt)) { delete b; return rc; }
     } else {
         for (int v = 0; v < kNumVariants; ++v) untuned.ns_per_chunk[v] = 1.0;
         tt = &untuned;
@@ -319,18 +338,10 @@ int extract_batch_create(extract_batch **out, const extract_job_desc *jobs, uint
         const bool per_sub = (d.flags & EXTRACT_SEED_PER_SUBBLOCK) != 0;
         J.plain_plan = plan_hash(d.m, d.k, J.w_pad, per_sub, b->num_sms);
         const uint32_t nchunks = J.w_pad / kWordChunk;
-        if (flags & EXTRACT_BATCH_NO_TUNE) {
+        if (flags & EXTRACT_BATCH_NO_TUNE)
             J.variant = (uint32_t)variant_id(J.plain_plan.q, J.plain_plan.j);
-        } else {
-            double best = 1e300;
-            for (int v = 0; v < kNumVariants; ++v) {
-                if (per_sub && variant_j(v) != 1) continue;
-                const double tiles = (double)ceil_div(d.k, (uint64_t)kHashWarps * 32 * variant_q(v)) *
-                                     (double)ceil_div(d.m, (uint64_t)variant_j(v));
-                const double t = tiles * nchunks * tt->ns_per_chunk[v];
-                if (t < best) { best = t; J.variant = (uint32_t)v; }
-            }
-        }
+        else
+            J.variant = (uint32_t)choose_variant(d.m, d.k, J.w_pad, per_sub, tt->ns_per_chunk);
         const uint64_t tiles = ceil_div(d.k, (uint64_t)kHashWarps * 32 * variant_q(J.variant)) *
                                ceil_div(d.m, (uint64_t)variant_j(J.variant));
         total_ns += (double)tiles * nchunks * tt->ns_per_chunk[J.variant];
@@ -340,7 +351,7 @@ int extract_batch_create(extract_batch **out, const extract_job_desc *jobs, uint
         J.seed_stride = std::max(seed_stride_words(vp, d.k, J.w_pad), seed_stride_words(J.plain_plan, d.k, J.w_pad));
         J.nseeds = per_sub ? d.m : 1u;
     }
-    b->predicted_ms = total_ns / 1e6 / b->num_sms;
+    b->predicted_ms = total_ns / 1e6;  // costs are whole-GPU time per CTA-chunk
     // split word ranges so no tile exceeds ~1/8 of an SM's share of the batch
     const double tile_cap_ns = std::max(1.0, total_ns / ((double)b->num_sms * 8.0));
     std::vector<std::pair<double, BatchTileDev>> tl;

@@ -56,4 +56,34 @@ int launch_hash_plain(const uint32_t *seed, uint32_t seed_stride, const uint32_t
                       uint32_t w_pad, uint32_t s, uint32_t m, uint32_t k, uint32_t *out,
                       cudaStream_t st);
 
+// ---- batching and serving: the persistent multi-job hash kernel ----------
+struct BatchJobDev {
+    const uint32_t *perm;  // null: identity order
+    const uint32_t *in;    // refreshed per run
+    uint32_t *out;         // refreshed per run
+    const uint32_t *seed;  // realigned seeds
+    uint32_t *arev;
+    uint64_t groups_before;  // prefix of gather groups (m * w_pad / 32)
+    uint64_t outw_before;    // prefix of output words
+    uint32_t seed_stride;    // 0: one shared seed
+    uint32_t m, s, k, w_pad;
+};
+
+// One CTA work item: rows [r0, r0 + rows(variant)) x sub-blocks
+// [j0, j0 + J(variant)) x word chunks [c_begin, c_end) of job `job`.
+struct BatchTileDev {
+    uint32_t job, variant, r0, j0, c_begin, c_end;
+};
+
+// GPU nanoseconds per (CTA, 128-word chunk) of each tile variant, measured
+// once per device inside the persistent kernel and cached.
+int tile_costs(int dev, int sms, const double **ns_per_chunk);
+
+// The variant with the least predicted time (tiles x chunks x cost).
+int choose_variant(uint32_t m, uint32_t k, uint32_t w_pad, bool per_sub, const double *ns_per_chunk);
+
+// One CTA per SM pulls tiles[0..ntiles) through *counter (which must be 0).
+int launch_batch_hash(const BatchJobDev *jobs, const BatchTileDev *tiles, uint32_t ntiles, uint32_t *counter,
+                      int sms, cudaStream_t st);
+
 }  // namespace ex

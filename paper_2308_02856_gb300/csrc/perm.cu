@@ -295,11 +295,11 @@ int build_perm(uint64_t n, uint64_t sampling_key, uint64_t mask, uint32_t *perm,
     auto fail = [&](int code) { rc = code; };
     do {
         cudaError_t e;
-        if ((e = cudaMalloc(&cnt, sizeof(uint32_t) * nb)) != cudaSuccess) { fail(cuda_error(e, "cudaMalloc(perm hist)")); break; }
-        if ((e = cudaMalloc(&start, sizeof(uint64_t) * (nb + 1))) != cudaSuccess) { fail(cuda_error(e, "cudaMalloc(perm start)")); break; }
-        if ((e = cudaMalloc(&bsum, sizeof(uint64_t) * nblk)) != cudaSuccess) { fail(cuda_error(e, "cudaMalloc(perm bsum)")); break; }
-        if ((e = cudaMalloc(&big_list, sizeof(uint32_t) * nb)) != cudaSuccess) { fail(cuda_error(e, "cudaMalloc(perm big)")); break; }
-        if ((e = cudaMalloc(&big_count, sizeof(uint32_t))) != cudaSuccess) { fail(cuda_error(e, "cudaMalloc(perm bigc)")); break; }
+        if ((e = cudaMallocAsync(&cnt, sizeof(uint32_t) * nb, st)) != cudaSuccess) { fail(cuda_error(e, "cudaMalloc(perm hist)")); break; }
+        if ((e = cudaMallocAsync(&start, sizeof(uint64_t) * (nb + 1), st)) != cudaSuccess) { fail(cuda_error(e, "cudaMalloc(perm start)")); break; }
+        if ((e = cudaMallocAsync(&bsum, sizeof(uint64_t) * nblk, st)) != cudaSuccess) { fail(cuda_error(e, "cudaMalloc(perm bsum)")); break; }
+        if ((e = cudaMallocAsync(&big_list, sizeof(uint32_t) * nb, st)) != cudaSuccess) { fail(cuda_error(e, "cudaMalloc(perm big)")); break; }
+        if ((e = cudaMallocAsync(&big_count, sizeof(uint32_t), st)) != cudaSuccess) { fail(cuda_error(e, "cudaMalloc(perm bigc)")); break; }
         if ((e = cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * nb, st)) != cudaSuccess) { fail(cuda_error(e, "memset")); break; }
         if ((e = cudaMemsetAsync(big_count, 0, sizeof(uint32_t), st)) != cudaSuccess) { fail(cuda_error(e, "memset")); break; }
 
@@ -329,18 +329,22 @@ int build_perm(uint64_t n, uint64_t sampling_key, uint64_t mask, uint32_t *perm,
 
         // rare path: all-pairs ranking of the oversized buckets
         uint32_t *blist = new uint32_t[nbig];
-        if ((e = cudaMemcpy(blist, big_list, sizeof(uint32_t) * nbig, cudaMemcpyDeviceToHost)) != cudaSuccess) {
+        if ((e = cudaMemcpyAsync(blist, big_list, sizeof(uint32_t) * nbig, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(st)) != cudaSuccess) {
             delete[] blist; fail(cuda_error(e, "read big list")); break;
         }
         for (uint32_t t = 0; t < nbig && rc == EXTRACT_OK; ++t) {
             uint64_t se[2];
-            if ((e = cudaMemcpy(se, start + blist[t], sizeof(se), cudaMemcpyDeviceToHost)) != cudaSuccess) { fail(cuda_error(e, "read bucket")); break; }
+            if ((e = cudaMemcpyAsync(se, start + blist[t], sizeof(se), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+                (e = cudaStreamSynchronize(st)) != cudaSuccess) { fail(cuda_error(e, "read bucket")); break; }
             const uint64_t L = se[1] - se[0];
             uint64_t *lab = nullptr;
             uint32_t *idx = nullptr, *dst = nullptr;
-            if (cudaMalloc(&lab, L * 8) != cudaSuccess || cudaMalloc(&idx, L * 4) != cudaSuccess ||
-                cudaMalloc(&dst, L * 4) != cudaSuccess) {
-                cudaFree(lab); cudaFree(idx); cudaFree(dst);
+            if (cudaMallocAsync(&lab, L * 8, st) != cudaSuccess || cudaMallocAsync(&idx, L * 4, st) != cudaSuccess ||
+                cudaMallocAsync(&dst, L * 4, st) != cudaSuccess) {
+                if (lab) cudaFreeAsync(lab, st);
+                if (idx) cudaFreeAsync(idx, st);
+                if (dst) cudaFreeAsync(dst, st);
                 fail(set_error(EXTRACT_ENOMEM, "perm: no memory for an oversized bucket of %llu",
                                (unsigned long long)L));
                 break;
@@ -349,17 +353,23 @@ int build_perm(uint64_t n, uint64_t sampling_key, uint64_t mask, uint32_t *perm,
                 perm + se[0], L, key, mask, lab, idx);
             big_rank_kernel<<<(uint32_t)ceil_div(L, 256), 256, 0, st>>>(lab, idx, L, dst);
             cudaMemcpyAsync(perm + se[0], dst, L * 4, cudaMemcpyDeviceToDevice, st);
+            cudaFreeAsync(lab, st);
+            cudaFreeAsync(idx, st);
+            cudaFreeAsync(dst, st);
             e = cudaStreamSynchronize(st);
-            cudaFree(lab); cudaFree(idx); cudaFree(dst);
             if (e != cudaSuccess) fail(cuda_error(e, "oversized bucket rank"));
         }
         delete[] blist;
     } while (0);
-    cudaFree(cnt);
-    cudaFree(start);
-    cudaFree(bsum);
-    cudaFree(big_list);
-    cudaFree(big_count);
+    // stream-ordered frees: no device-wide synchronisation, so an order can
+    // be built while other streams keep hashing
+    if (cnt) cudaFreeAsync(cnt, st);
+    if (start) cudaFreeAsync(start, st);
+    if (bsum) cudaFreeAsync(bsum, st);
+    if (big_list) cudaFreeAsync(big_list, st);
+    if (big_count) cudaFreeAsync(big_count, st);
+    cudaError_t fe = cudaStreamSynchronize(st);
+    if (rc == EXTRACT_OK && fe != cudaSuccess) rc = cuda_error(fe, "perm build");
     return rc;
 }
 

@@ -39,6 +39,8 @@ EXPORTED = [
     "extract_last_error", "extract_run_static",
     "extract_batch_create", "extract_batch_run", "extract_batch_run_sequential", "extract_batch_describe",
     "extract_batch_destroy",
+    "extract_server_create", "extract_server_submit", "extract_server_wait", "extract_server_stats",
+    "extract_server_destroy",
 ]
 
 EXTRACT_BATCH_NO_GRAPH = 0x1
@@ -49,6 +51,14 @@ class extract_job_desc(ctypes.Structure):
     _fields_ = [("n", ctypes.c_uint64), ("m", ctypes.c_uint32), ("s", ctypes.c_uint32), ("k", ctypes.c_uint32),
                 ("flags", ctypes.c_uint32), ("sampling_key", ctypes.c_uint64),
                 ("seed_bits_host", ctypes.c_void_p)]
+
+
+class extract_stats(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_uint64) for name in
+                ("submitted", "admitted", "completed", "failed", "rejected", "queued", "active", "waves",
+                 "bytes_in_use", "bytes_peak")] + \
+               [(name, ctypes.c_double) for name in
+                ("p50_ms", "p99_ms", "mean_ms", "max_ms", "input_bits_done", "span_s", "gbit_per_s")]
 
 EXTRACT_STATIC_SCRATCH_WORDS = 4 * 1024 * 1024
 
@@ -88,6 +98,11 @@ def load() -> ctypes.CDLL:
     L.extract_batch_run_sequential.argtypes = [vp, vp, vp, vp]
     L.extract_batch_describe.argtypes = [vp, ctypes.c_char_p, u32]
     L.extract_batch_destroy.argtypes = [vp]
+    L.extract_server_create.argtypes = [ctypes.POINTER(vp), u64, u32, u32, u32]
+    L.extract_server_submit.argtypes = [vp, ctypes.POINTER(extract_job_desc), vp, vp, ctypes.POINTER(u64)]
+    L.extract_server_wait.argtypes = [vp, u64, u32, ctypes.POINTER(ctypes.c_double)]
+    L.extract_server_stats.argtypes = [vp, ctypes.POINTER(extract_stats)]
+    L.extract_server_destroy.argtypes = [vp]
     L.extract_last_error.argtypes = []
     L.extract_last_error.restype = ctypes.c_char_p
     for name in EXPORTED:
@@ -237,6 +252,57 @@ class Batch:
         if self.h:
             _check(load().extract_batch_destroy(self.h))
             self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Owns one extract_server (continuous batching under a memory budget)."""
+
+    def __init__(self, hbm_budget_bytes, max_slots=64, wave_us=0):
+        self.h = ctypes.c_void_p()
+        self._keep = {}
+        _check(load().extract_server_create(ctypes.byref(self.h), int(hbm_budget_bytes), max_slots, wave_us, 0))
+
+    def submit(self, job, in_bits, out_bits) -> int:
+        """``job``: dict with n, m, s, k, seed, key (and optional flags)."""
+        seed = np.ascontiguousarray(job["seed"], dtype=np.uint32)
+        d = extract_job_desc(job["n"], job["m"], job["s"], job["k"], job.get("flags", 0), job["key"],
+                             seed.ctypes.data)
+        t = ctypes.c_uint64()
+        _check(load().extract_server_submit(self.h, ctypes.byref(d), _dev_ptr(in_bits), _dev_ptr(out_bits),
+                                            ctypes.byref(t)))
+        self._keep[t.value] = (in_bits, out_bits)
+        return t.value
+
+    def wait(self, ticket: int, timeout_ms: int = 600000) -> float:
+        lat = ctypes.c_double()
+        rc = load().extract_server_wait(self.h, ticket, timeout_ms, ctypes.byref(lat))
+        if rc == EXTRACT_OK:
+            self._keep.pop(ticket, None)
+        _check(rc)
+        return lat.value
+
+    def stats(self) -> dict:
+        st = extract_stats()
+        _check(load().extract_server_stats(self.h, ctypes.byref(st)))
+        return {name: getattr(st, name) for name, _ in st._fields_}
+
+    def close(self):
+        if self.h:
+            _check(load().extract_server_destroy(self.h))
+            self.h = None
+            self._keep.clear()
 
     def __enter__(self):
         return self

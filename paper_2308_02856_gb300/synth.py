@@ -114,3 +114,27 @@ def poisson_arrivals(count: int, rate: float, seed: int) -> np.ndarray:
     rng = np.random.Generator(np.random.Philox(seed))
     u = rng.random(count)
     return np.cumsum(-np.log1p(-u) / rate)
+
+
+def bernoulli_bits_device(nbits: int, p: float, seed: int, device="cuda"):
+    """i.i.d. Bernoulli(p) bits drawn on the GPU with torch's seeded
+    generator, packed LSB-first into an int32 tensor of ceil(nbits/32) words
+    (bits past nbits zero).  For large benchmark inputs that no CPU check
+    reads; CPU-checked inputs come from bernoulli_bits."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    words = (nbits + 31) // 32
+    out = torch.empty(words, dtype=torch.int32, device=device)
+    shifts = torch.arange(32, device=device, dtype=torch.int64)
+    chunk = 1 << 21  # words per chunk
+    for w0 in range(0, words, chunk):
+        cw = min(chunk, words - w0)
+        b = (torch.rand((cw, 32), generator=g, device=device) < p).to(torch.int64)
+        lo = w0 * 32
+        if lo + cw * 32 > nbits:  # clear bits past nbits
+            idx = torch.arange(cw * 32, device=device).view(cw, 32) + lo
+            b = b * (idx < nbits).to(torch.int64)
+        v = (b << shifts).sum(1)
+        out[w0:w0 + cw] = torch.where(v >= 2 ** 31, v - 2 ** 32, v).to(torch.int32)  # same 32 bits
+    return out
