@@ -71,14 +71,6 @@ batch_gather_kernel(const BatchJobDev *__restrict__ jobs, uint32_t njobs, uint64
     }
 }
 
-template <int V>
-__device__ __forceinline__ void run_variant(const BatchJobDev &J, const BatchTileDev &t, uint32_t *a_s, uint32_t *s_s)
-{
-    constexpr int Q = variant_q(V), JJ = variant_j(V);
-    const uint32_t *sd = J.seed + (size_t)(J.seed_stride ? t.j0 : 0u) * J.seed_stride + (t.r0 >> 5);
-    hash_tile<Q, JJ>(sd, J.arev, J.w_pad, J.m, J.k, t.r0, t.j0, t.c_begin, t.c_end, J.out, a_s, s_s);
-}
-
 __global__ void __launch_bounds__(kHashThreads, 1)
 batch_hash_kernel(const BatchJobDev *__restrict__ jobs, const BatchTileDev *__restrict__ tiles, uint32_t ntiles,
                   uint32_t *counter)
@@ -94,18 +86,11 @@ batch_hash_kernel(const BatchJobDev *__restrict__ jobs, const BatchTileDev *__re
         if (ti >= ntiles) break;
         const BatchTileDev t = tiles[ti];
         const BatchJobDev &J = jobs[t.job];
-        switch (t.variant) {
-        case 0: run_variant<0>(J, t, a_s, s_s); break;
-        case 1: run_variant<1>(J, t, a_s, s_s); break;
-        case 2: run_variant<2>(J, t, a_s, s_s); break;
-        case 3: run_variant<3>(J, t, a_s, s_s); break;
-        case 4: run_variant<4>(J, t, a_s, s_s); break;
-        case 5: run_variant<5>(J, t, a_s, s_s); break;
-        case 6: run_variant<6>(J, t, a_s, s_s); break;
-        case 7: run_variant<7>(J, t, a_s, s_s); break;
-        case 8: run_variant<8>(J, t, a_s, s_s); break;
-        default: run_variant<9>(J, t, a_s, s_s); break;
-        }
+        const uint32_t *sd = J.seed + (size_t)(J.seed_stride ? t.j0 : 0u) * J.seed_stride + (t.r0 >> 5);
+#define EX_RUN_TILE(Q_, J_) \
+    hash_tile<Q_, J_>(sd, J.arev, J.w_pad, J.m, J.k, t.r0, t.j0, t.c_begin, t.c_end, J.out, a_s, s_s)
+        EX_FOR_VARIANT(t.variant, EX_RUN_TILE)
+#undef EX_RUN_TILE
     }
 }
 
@@ -119,7 +104,9 @@ TuneTable g_tune[64];
 
 int measure_variants(int dev, int sms, TuneTable &tt)
 {
-    constexpr uint32_t kM = 32, kChunks = 8, kW = kChunks * kHashWC, kK = 1024;
+    // one synthetic job big enough for every variant's tile (k = the tallest
+    // tile, m = the widest) so all reads stay inside its buffers
+    constexpr uint32_t kM = 32, kChunks = 8, kW = kChunks * kHashWC, kK = kHashWarps * 32 * kMaxQ;
     const uint32_t stride = kK / 32 + kW + 8;
     const uint32_t ntiles = (uint32_t)sms * 3;
     uint32_t *arev = nullptr, *seed = nullptr, *out = nullptr, *counter = nullptr;
@@ -339,7 +326,7 @@ int extract_batch_create(extract_batch **out, const extract_job_desc *jobs, uint
         J.plain_plan = plan_hash(d.m, d.k, J.w_pad, per_sub, b->num_sms);
         const uint32_t nchunks = J.w_pad / kWordChunk;
         if (flags & EXTRACT_BATCH_NO_TUNE)
-            J.variant = (uint32_t)variant_id(J.plain_plan.q, J.plain_plan.j);
+            J.variant = (uint32_t)J.plain_plan.variant;
         else
             J.variant = (uint32_t)choose_variant(d.m, d.k, J.w_pad, per_sub, tt->ns_per_chunk);
         const uint64_t tiles = ceil_div(d.k, (uint64_t)kHashWarps * 32 * variant_q(J.variant)) *

@@ -23,6 +23,7 @@ int launch_gather(const uint32_t *in, const uint32_t *perm, uint32_t m, uint32_t
 
 // ---- steps 2-3: the Toeplitz product and concatenation ------------------
 struct HashPlan {
+    int variant = 7;      // tile variant (see hash_tile.cuh)
     int q = 4;            // row groups of 32 per warp (rows per warp = 32 q)
     int j = 32;           // sub-blocks per CTA sharing the seed windows
     int warps = 8;        // warps per CTA, each on its own rows

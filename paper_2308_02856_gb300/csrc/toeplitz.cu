@@ -63,30 +63,31 @@ void launch_tile(const HashPlan &p, const uint32_t *seed, uint32_t seed_stride, 
                                                               p.gx, p.nchunks, p.cps, out);
 }
 
-template <int Q>
-bool dispatch_j(const HashPlan &p, const uint32_t *seed, uint32_t seed_stride, const uint32_t *arev,
-                uint32_t w_pad, uint32_t m, uint32_t k, uint32_t *out, cudaStream_t st)
-{
-    switch (p.j) {
-    case 1: launch_tile<Q, 1>(p, seed, seed_stride, arev, w_pad, m, k, out, st); return true;
-    case 4: launch_tile<Q, 4>(p, seed, seed_stride, arev, w_pad, m, k, out, st); return true;
-    case 8: launch_tile<Q, 8>(p, seed, seed_stride, arev, w_pad, m, k, out, st); return true;
-    case 16: launch_tile<Q, 16>(p, seed, seed_stride, arev, w_pad, m, k, out, st); return true;
-    case 32: launch_tile<Q, 32>(p, seed, seed_stride, arev, w_pad, m, k, out, st); return true;
-    default: return false;
-    }
-}
-
 }  // namespace
 
 HashPlan plan_hash(uint32_t m, uint32_t k, uint32_t w_pad, bool per_subblock_seed, int num_sms)
 {
+    // Model: padded work of the tile grid divided by the share of ALU issue
+    // slots that are LOP3 (one SHF per distinct window: Q + kWinBlock - 1
+    // SHF per Q x J x kWinBlock LOP3).
     HashPlan p;
+    double best = 1e300;
+    for (int v = 0; v < kNumVariants; ++v) {
+        const int q = variant_q(v), j = variant_j(v);
+        if (per_subblock_seed && j != 1) continue;
+        const double tiles = (double)ceil_div(k, variant_rows(v)) * (double)ceil_div(m, (uint32_t)j);
+        const double lop3 = (double)q * j * kWinBlock;
+        const double eff = lop3 / (lop3 + q + kWinBlock - 1);
+        const double t = tiles * variant_rows(v) * j / eff;
+        if (t < best * 0.999) {
+            best = t;
+            p.variant = v;
+        }
+    }
+    p.q = variant_q(p.variant);
+    p.j = variant_j(p.variant);
     p.warps = kWarps;
     p.wc = kWC;
-    if (per_subblock_seed) p.j = 1;
-    else p.j = m >= 32 ? 32 : m >= 16 ? 16 : m >= 8 ? 8 : m >= 4 ? 4 : 1;
-    p.q = k > 512 ? 4 : 1;
     p.gx = (uint32_t)ceil_div(k, p.rows());
     p.gy = (uint32_t)ceil_div(m, (uint32_t)p.j);
     p.nchunks = w_pad / (uint32_t)p.wc;
@@ -110,10 +111,11 @@ int launch_hash(const HashPlan &p, const uint32_t *seed, uint32_t seed_stride, c
 {
     const uint64_t out_words = ceil_div((uint64_t)m * k, 32);
     EX_CUDA(cudaMemsetAsync(out, 0, out_words * sizeof(uint32_t), st));
-    bool ok = false;
-    if (p.q == 4) ok = dispatch_j<4>(p, seed, seed_stride, arev, w_pad, m, k, out, st);
-    else if (p.q == 1) ok = dispatch_j<1>(p, seed, seed_stride, arev, w_pad, m, k, out, st);
-    if (!ok) return set_error(EXTRACT_EINTERNAL, "no kernel for tile q=%d j=%d", p.q, p.j);
+    if (p.variant < 0 || p.variant >= kNumVariants || variant_q(p.variant) != p.q || variant_j(p.variant) != p.j)
+        return set_error(EXTRACT_EINTERNAL, "no kernel for tile q=%d j=%d", p.q, p.j);
+#define EX_LAUNCH_TILE(Q_, J_) launch_tile<Q_, J_>(p, seed, seed_stride, arev, w_pad, m, k, out, st)
+    EX_FOR_VARIANT(p.variant, EX_LAUNCH_TILE)
+#undef EX_LAUNCH_TILE
     EX_LAUNCH("toeplitz_lop3_kernel");
     return EXTRACT_OK;
 }
