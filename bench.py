@@ -68,6 +68,8 @@ def parse_args():
                     help="block: one large block (default); batch: 256 uneven blocks in one persistent "
                          "launch vs one launch per block; serve: Poisson job arrivals under an HBM budget")
     ap.add_argument("--jobs", type=int, default=0, help="jobs per serving trace (default 120)")
+    ap.add_argument("--method", choices=["auto", "direct", "ntt"], default="auto",
+                    help="hashing method of the block mode (auto: the library's choice)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
@@ -182,6 +184,29 @@ class OracleSample:
                           % (self.nj, self.m, self.ni, self.k, frac, self.nj, t)}
 
 
+def launches_per_step(is_ntt, m, plan):
+    """Kernels of ours per step: the gather plus the hash (one launch direct;
+    three per group of sub-blocks for the NTT method)."""
+    if not is_ntt:
+        return 2
+    g = int(plan.split("sub-blocks per launch group")[0].split(",")[-1])
+    return 1 + 3 * ((m + g - 1) // g)
+
+
+def ntt_roofline(n, m, s, k, hash_ms, plan):
+    """NTT path: the transform work (forward + inverse, N/2 log2 N butterflies
+    each, per sub-block) against the integer pipe; a butterfly is one Shoup
+    product (3 IMAD) plus 4 adds/mins, ~7 integer instructions."""
+    N = int(plan.split("N=")[1].split(" ")[0])
+    import math
+    bfly = m * 2 * (N // 2) * math.log2(N)
+    achieved = bfly / (hash_ms / 1e3) / 1e12
+    return {"bound": "alu", "achieved": achieved, "unit": "Tbutterfly/s", "peak": None, "frac": None,
+            "traffic": None, "kernel": "ntt passes (A, B, A')",
+            "work_per_launch": "m x 2 x N/2 log2 N = %.4g radix-2 butterflies mod p (N=%d)" % (bfly, N),
+            "note": "does less work than the direct m*k*s product; reported in absolute Gbit/s"}
+
+
 def make_inputs(n, m, s, k, p):
     from paper_2308_02856_gb300 import synth
     in_w = synth.bernoulli_bits(n, p, IN_SEED)
@@ -247,11 +272,13 @@ def run_ours(args):
     X.load()  # fails loudly when the CUDA library is missing
     in_w, seed_w = make_inputs(n, m, s, k, p)
 
+    method_flags = {"auto": 0, "direct": X.EXTRACT_METHOD_DIRECT, "ntt": X.EXTRACT_METHOD_NTT}[args.method]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    ex = X.Extractor(n, m, s, k, seed_w, SAMPLING_KEY)
+    ex = X.Extractor(n, m, s, k, seed_w, SAMPLING_KEY, method_flags)
     create_ms = (time.perf_counter() - t0) * 1e3
     plan = ex.describe()
+    is_ntt = plan.startswith("ntt")
 
     d_in = torch.from_numpy(in_w.view(np.int32)).to(dev)
     d_out = ex.new_output()
@@ -320,17 +347,40 @@ def run_ours(args):
                "h2d_bytes_per_step": int(in_w.nbytes), "d2h_bytes_per_step": int(ex.out_words * 4),
                "api": "extract_run_host (pinned host buffers, copies and sync inside the timed region)"}
 
-    # roofline of the dominant kernel (toeplitz_lop3_kernel): integer ALU
-    lop3_per_launch = m * k * s / 32.0
-    achieved = lop3_per_launch / (hash_ms / 1e3) / 1e12
+    # the direct GF(2) kernel (toeplitz_lop3_kernel): integer-ALU roofline
     peak = sms * LOP3_LANES_PER_SM_CLK * 2070e6 / 1e12
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TLOP3/s",
-                "frac": achieved / peak, "traffic": HASH_TRAFFIC_BYTES.get(args.workload),
-                "kernel": "toeplitz_lop3_kernel",
-                "work_per_launch": "m*k*s/32 = %.4g LOP3 (32 bit-products each)" % lop3_per_launch,
-                "peak_basis": "%d SMs x %d LOP3/clk/SM x 2070 MHz max SM clock" % (sms, LOP3_LANES_PER_SM_CLK)}
-    if clocks.get("sm_mhz"):
-        roofline["frac_at_measured_clock"] = achieved / (sms * LOP3_LANES_PER_SM_CLK * clocks["sm_mhz"] * 1e6 / 1e12)
+    lop3_per_launch = m * k * s / 32.0
+
+    def lop3_roofline(hms):
+        achieved = lop3_per_launch / (hms / 1e3) / 1e12
+        r = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TLOP3/s",
+             "frac": achieved / peak, "traffic": HASH_TRAFFIC_BYTES.get(args.workload),
+             "kernel": "toeplitz_lop3_kernel",
+             "work_per_launch": "m*k*s/32 = %.4g LOP3 (32 bit-products each)" % lop3_per_launch,
+             "peak_basis": "%d SMs x %d LOP3/clk/SM x 2070 MHz max SM clock" % (sms, LOP3_LANES_PER_SM_CLK)}
+        if clocks.get("sm_mhz"):
+            r["frac_at_measured_clock"] = achieved / (sms * LOP3_LANES_PER_SM_CLK * clocks["sm_mhz"] * 1e6 / 1e12)
+        return r
+
+    direct = None
+    if is_ntt:
+        roofline = ntt_roofline(n, m, s, k, hash_ms, plan)
+        # the direct kernel on the same block, for the record (2 timed steps)
+        exd = X.Extractor(n, m, s, k, seed_w, SAMPLING_KEY, X.EXTRACT_METHOD_DIRECT)
+        exd.gather(d_in, stream=stream)
+        exd.hash(d_out, stream=stream)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(2):
+            exd.hash(d_out, stream=stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        dms = a.elapsed_time(b) / 2
+        direct = {"hash_ms": dms, "value": world * n / ((dms + gather_ms) / 1e3) / 1e9, "unit": "Gbit/s",
+                  "roofline": lop3_roofline(dms), "plan": exd.describe()}
+        exd.close()
+    else:
+        roofline = lop3_roofline(hash_ms)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -353,9 +403,11 @@ def run_ours(args):
                        "l2": "inputs larger than L2: 4n-byte order + n/8-byte input read per step",
                        "parallelism": "replicas" if world > 1 else "1 GPU",
                        "plan": plan},
+            "method": "ntt" if is_ntt else "direct",
             "create_ms": create_ms,
             "gather_ms": gather_ms, "hash_ms": hash_ms,
-            "gpu_launches": 2 * args.steps,
+            "gpu_launches": launches_per_step(is_ntt, m, plan) * args.steps,
+            "direct_lop3": direct,
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,

@@ -60,6 +60,15 @@ extern "C" {
    [j*s, (j+1)*s).  With m = 1 and s = n this is direct whole-block Toeplitz
    hashing, the "traditional" method of Sec. IV.C. */
 #define EXTRACT_IDENTITY_PERM     0x2u
+/* Hashing method.  Default (neither flag): the library picks the faster of
+   the two exact methods for the shape.  EXTRACT_METHOD_DIRECT forces the
+   direct GF(2) product (bit-sliced AND/XOR, work m*k*s); EXTRACT_METHOD_NTT
+   forces the number-theoretic-transform middle product (work about
+   m * N log N with N the power of two >= s+k-1), which needs a shared seed
+   and 2^11 < s+k-1 <= 2^22 (EXTRACT_EINVAL otherwise).  Both give the same
+   bits. */
+#define EXTRACT_METHOD_DIRECT     0x4u
+#define EXTRACT_METHOD_NTT        0x8u
 /* Test hook: keep only the top b (1..63) bits of every sampling label, which
    forces many equal labels so that the index tie-break is exercised. */
 #define EXTRACT_KEY_BITS(b)       ((((uint32_t)(b)) & 0x3fu) << 8)

@@ -8,6 +8,8 @@ from . import synth  # noqa: F401
 from .extract import (  # noqa: F401
     EXTRACT_IDENTITY_PERM,
     EXTRACT_KEY_BITS,
+    EXTRACT_METHOD_DIRECT,
+    EXTRACT_METHOD_NTT,
     EXTRACT_SEED_PER_SUBBLOCK,
     ExtractError,
     Extractor,

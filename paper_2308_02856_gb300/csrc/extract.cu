@@ -4,6 +4,7 @@
 #include "internal.h"
 
 #include <algorithm>
+#include <cmath>
 #include <cstdarg>
 #include <cstring>
 #include <new>
@@ -46,11 +47,25 @@ struct extract_ctx {
     uint32_t *stage_in = nullptr;   // extract_run_host staging, ceil(n/32) words
     uint32_t *stage_out = nullptr;  // extract_run_host staging, ceil(m*k/32) words
     HashPlan plan;
+    NttPlan *ntt = nullptr;  // set when the NTT method hashes this shape
 };
 
 namespace {
 
-constexpr uint32_t kKnownFlags = EXTRACT_SEED_PER_SUBBLOCK | EXTRACT_IDENTITY_PERM | (0x3fu << 8);
+constexpr uint32_t kKnownFlags = EXTRACT_SEED_PER_SUBBLOCK | EXTRACT_IDENTITY_PERM | EXTRACT_METHOD_DIRECT |
+                                  EXTRACT_METHOD_NTT | (0x3fu << 8);
+
+// Predicted seconds of the two methods (direct: the LOP3 rate the kernel
+// reaches; NTT: measured cost per transformed element and stage).
+double predict_direct_s(uint32_t m, uint32_t k, uint32_t s)
+{
+    return (double)m * k * ((s + 31) / 32) / 19e12;
+}
+double predict_ntt_s(uint32_t m, uint32_t s, uint32_t k)
+{
+    const double N = (double)ntt_length(s, k);
+    return (double)m * N * (std::log2(N) + 4.0) * 2.0e-12;
+}
 
 void free_ctx(extract_ctx *h)
 {
@@ -60,6 +75,7 @@ void free_ctx(extract_ctx *h)
     cudaFree(h->seed);
     cudaFree(h->stage_in);
     cudaFree(h->stage_out);
+    ntt_destroy(h->ntt);
     delete h;
 }
 
@@ -109,6 +125,13 @@ int extract_create(extract_ctx **out, uint64_t n, uint32_t m, uint32_t s, uint32
                          (unsigned long long)((uint64_t)m * s), (unsigned long long)n);
     const bool per_sub = (flags & EXTRACT_SEED_PER_SUBBLOCK) != 0;
     const bool ident = (flags & EXTRACT_IDENTITY_PERM) != 0;
+    if ((flags & EXTRACT_METHOD_DIRECT) && (flags & EXTRACT_METHOD_NTT))
+        return set_error(EXTRACT_EINVAL, "EXTRACT_METHOD_DIRECT and EXTRACT_METHOD_NTT are exclusive");
+    const bool ntt_ok = !per_sub && ntt_eligible(s, k);
+    if ((flags & EXTRACT_METHOD_NTT) && !ntt_ok)
+        return set_error(EXTRACT_EINVAL, "the NTT method needs a shared seed and 2^11 < s+k-1 <= 2^22 (s=%u k=%u)", s, k);
+    const bool use_ntt = ntt_ok && !(flags & EXTRACT_METHOD_DIRECT) &&
+                         ((flags & EXTRACT_METHOD_NTT) || predict_ntt_s(m, s, k) < predict_direct_s(m, k, s));
 
     extract_ctx *h = new (std::nothrow) extract_ctx();
     if (!h) return set_error(EXTRACT_ENOMEM, "host allocation failed");
@@ -144,6 +167,13 @@ int extract_create(extract_ctx **out, uint64_t n, uint32_t m, uint32_t s, uint32
     if ((e = cudaMemcpy(h->seed, host.data(), host.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess) {
         free_ctx(h); return cuda_error(e, "copy seed");
     }
+    if (use_ntt) {
+        cudaStream_t st;
+        if ((e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) != cudaSuccess) { free_ctx(h); return cuda_error(e, "stream"); }
+        int rc = ntt_create(&h->ntt, m, s, k, h->seed, st);
+        cudaStreamDestroy(st);
+        if (rc != EXTRACT_OK) { free_ctx(h); return rc; }
+    }
     if ((e = cudaMalloc(&h->arev, (size_t)m * h->w_pad * 4)) != cudaSuccess) { free_ctx(h); return cuda_error(e, "cudaMalloc(sub-blocks)"); }
     if ((e = cudaMemset(h->arev, 0, (size_t)m * h->w_pad * 4)) != cudaSuccess) { free_ctx(h); return cuda_error(e, "memset(sub-blocks)"); }
     if (!ident) {
@@ -173,6 +203,7 @@ int extract_hash(extract_ctx *h, void *stream, uint32_t *out_bits_dev)
 {
     if (int rc = check_ctx(h)) return rc;
     if (!out_bits_dev) return set_error(EXTRACT_EINVAL, "out_bits_dev is null");
+    if (h->ntt) return ntt_hash(h->ntt, h->arev, h->w_pad, h->m, h->s, h->k, out_bits_dev, (cudaStream_t)stream);
     return launch_hash(h->plan, h->seed, h->nseeds > 1 ? h->seed_stride : 0u, h->arev, h->w_pad, h->m,
                        h->k, out_bits_dev, (cudaStream_t)stream);
 }
@@ -241,6 +272,11 @@ int extract_describe(extract_ctx *h, char *buf, uint32_t buflen)
     if (int rc = check_ctx(h)) return rc;
     if (!buf || !buflen) return set_error(EXTRACT_EINVAL, "empty buffer");
     const HashPlan &p = h->plan;
+    if (h->ntt) {
+        snprintf(buf, buflen, "ntt: N=%u (%u x 2048), %u sub-blocks per launch group, prime 15*2^27+1; sms=%d",
+                 ntt_size(h->ntt), ntt_size(h->ntt) / 2048, ntt_group(h->ntt), h->num_sms);
+        return EXTRACT_OK;
+    }
     snprintf(buf, buflen,
              "lop3 tile: rows=%u (q=%d x %d warps x 32) subblocks=%d words/chunk=%d grid=%ux%ux%u "
              "(row tiles %u, sub-block tiles %u, split-K %u x %u chunks) w_pad=%u sms=%d",

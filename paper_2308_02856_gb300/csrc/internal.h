@@ -87,4 +87,17 @@ int choose_variant(uint32_t m, uint32_t k, uint32_t w_pad, bool per_sub, const d
 int launch_batch_hash(const BatchJobDev *jobs, const BatchTileDev *tiles, uint32_t ntiles, uint32_t *counter,
                       int sms, cudaStream_t st);
 
+// ---- exact NTT middle product (ntt.cu) -----------------------------------
+struct NttPlan;
+bool ntt_eligible(uint32_t s, uint32_t k);  // 2^11 < s + k - 1 <= 2^22
+uint32_t ntt_length(uint32_t s, uint32_t k);
+// Builds the twiddle tables and the seed spectrum (synchronous on st).
+int ntt_create(NttPlan **out, uint32_t m, uint32_t s, uint32_t k, const uint32_t *seed_dev, cudaStream_t st);
+// Hashes all m gathered sub-blocks; zeroes and fills out.
+int ntt_hash(const NttPlan *p, const uint32_t *arev, uint32_t w_pad, uint32_t m, uint32_t s, uint32_t k,
+             uint32_t *out, cudaStream_t st);
+void ntt_destroy(NttPlan *p);
+uint32_t ntt_group(const NttPlan *p);
+uint32_t ntt_size(const NttPlan *p);
+
 }  // namespace ex

@@ -1,0 +1,442 @@
+// Exact fast Toeplitz hashing by number-theoretic transform: the FFT-based
+// direction the paper names for CPUs and GPUs (Sec. I, Sec. V), done exactly
+// in integer arithmetic.
+//
+// K_j[i] = XOR_c seed[i - c + s - 1] A_j[c] is the parity of coefficient
+// i + s - 1 of the integer product sigma(x) a_j(x), sigma = sum seed[t] x^t
+// (L = s + k - 1 terms), a_j = sum A_j[c] x^c (s terms).  That coefficient
+// is at most s < p = 15 * 2^27 + 1, so one NTT modulo p gives it exactly.  A
+// cyclic convolution of length N = 2^e >= s + k - 1 leaves coefficients
+// s-1 .. s+k-2 free of wrap-around (no index pair reaches N + s - 1).
+//
+// Four-step layout, N = R1 x R2 with R2 = 2048 (element t = t1 R2 + t2):
+//   pass A  (one CTA per 16 columns t2 of one sub-block): load the bits,
+//           R1-point DIF NTT along t1, multiply by w_N^(k1 t2);
+//   pass B  (one CTA per rows): 2048-point DIF NTT of each row, multiply by
+//           the seed spectrum (laid out the same way, with 1/N folded in),
+//           2048-point inverse DIT NTT;
+//   pass A' (per 16 columns): multiply by w_N^(-k1 t2), R1-point inverse DIT
+//           NTT along t1, then the parity of every coefficient t in
+//           [s-1, s+k-1) goes straight to output bit j k + t - (s-1).
+// DIF leaves bit-reversed order and DIT consumes it, so nothing is permuted.
+// Arithmetic: values in [0, p); a + b and a - b + p stay below 2^32 because
+// p < 2^31; fixed multipliers (stage twiddles, the seed spectrum) use Shoup's
+// precomputed quotient, computed twist factors use Montgomery form.
+#include "common.cuh"
+#include "internal.h"
+
+#include <algorithm>
+#include <vector>
+
+namespace ex {
+namespace {
+
+constexpr uint32_t kP = 2013265921u;  // 15 * 2^27 + 1
+constexpr uint32_t kGen = 31u;        // a primitive root modulo p
+constexpr int kR2Log = 11;
+constexpr uint32_t kR2 = 1u << kR2Log;
+constexpr int kCW = 16;               // columns per pass-A CTA
+constexpr int kCS = kCW + 1;          // padded smem row (no bank conflicts)
+constexpr int kRowsB = 2;             // rows per pass-B CTA
+constexpr int kThreads = 256;
+
+// -p^{-1} mod 2^32 by Newton iteration
+constexpr uint32_t neg_inv32(uint32_t p)
+{
+    uint32_t x = p;  // p * p == 1 mod 8
+    for (int i = 0; i < 5; ++i) x *= 2u - p * x;
+    return 0u - x;
+}
+constexpr uint32_t kPNegInv = neg_inv32(kP);
+
+__device__ __forceinline__ uint32_t add_p(uint32_t a, uint32_t b)
+{
+    const uint32_t r = a + b;
+    return min(r, r - kP);
+}
+__device__ __forceinline__ uint32_t sub_p(uint32_t a, uint32_t b)
+{
+    const uint32_t r = a - b + kP;
+    return min(r, r - kP);
+}
+// a * w mod p with wq = floor(w 2^32 / p) (Shoup)
+__device__ __forceinline__ uint32_t mul_shoup(uint32_t a, uint32_t w, uint32_t wq)
+{
+    const uint32_t q = __umulhi(a, wq);
+    const uint32_t r = a * w - q * kP;
+    return min(r, r - kP);
+}
+// a * b * 2^-32 mod p (Montgomery)
+__device__ __forceinline__ uint32_t mul_mont(uint32_t a, uint32_t b)
+{
+    const uint64_t t = (uint64_t)a * b;
+    const uint32_t m = (uint32_t)t * kPNegInv;
+    const uint32_t u = (uint32_t)((t + (uint64_t)m * kP) >> 32);
+    return min(u, u - kP);
+}
+
+__device__ __forceinline__ uint32_t bitrev(uint32_t x, int bits)
+{
+    return bits ? __brev(x) >> (32 - bits) : 0u;
+}
+
+// Twiddle tables in device memory (one plan per context).
+struct Tables {
+    // stage twiddles w_R^i, i < R/2, and their Shoup quotients, for the
+    // column (R1) and row (R2) transforms, forward and inverse
+    const uint32_t *col_f, *col_fq, *col_i, *col_iq;
+    const uint32_t *row_f, *row_fq, *row_i, *row_iq;
+    // twist factors in Montgomery form: w_N^x = lo[x & 2047] * hi[x >> 11]
+    const uint32_t *tw_lo_f, *tw_hi_f, *tw_lo_i, *tw_hi_i;
+};
+
+__device__ __forceinline__ uint32_t twist_mont(const uint32_t *lo, const uint32_t *hi, uint32_t x)
+{
+    return mul_mont(__ldg(lo + (x & (kR2 - 1))), __ldg(hi + (x >> kR2Log)));
+}
+
+// DIF NTT of length R over the first index of x[r * kCS + c], c < kCW.
+__device__ __forceinline__ void dif_cols(uint32_t *x, uint32_t R, const uint32_t *tw, const uint32_t *twq)
+{
+    for (uint32_t h = R >> 1; h >= 1; h >>= 1) {
+        const uint32_t stride = R / (2 * h);
+        for (uint32_t it = threadIdx.x; it < (R >> 1) * kCW; it += blockDim.x) {
+            const uint32_t c = it % kCW, b = it / kCW;
+            const uint32_t off = b & (h - 1), i = ((b - off) << 1) + off;
+            uint32_t *pu = x + i * kCS + c, *pv = x + (i + h) * kCS + c;
+            const uint32_t u = *pu, v = *pv;
+            const uint32_t ti = off * stride;
+            *pu = add_p(u, v);
+            *pv = mul_shoup(sub_p(u, v), __ldg(tw + ti), __ldg(twq + ti));
+        }
+        __syncthreads();
+    }
+}
+
+// DIT inverse NTT of length R (bit-reversed in, natural out) over columns.
+__device__ __forceinline__ void dit_cols(uint32_t *x, uint32_t R, const uint32_t *tw, const uint32_t *twq)
+{
+    for (uint32_t h = 1; h < R; h <<= 1) {
+        const uint32_t stride = R / (2 * h);
+        for (uint32_t it = threadIdx.x; it < (R >> 1) * kCW; it += blockDim.x) {
+            const uint32_t c = it % kCW, b = it / kCW;
+            const uint32_t off = b & (h - 1), i = ((b - off) << 1) + off;
+            uint32_t *pu = x + i * kCS + c, *pv = x + (i + h) * kCS + c;
+            const uint32_t ti = off * stride;
+            const uint32_t u = *pu, v = mul_shoup(*pv, __ldg(tw + ti), __ldg(twq + ti));
+            *pu = add_p(u, v);
+            *pv = sub_p(u, v);
+        }
+        __syncthreads();
+    }
+}
+
+// Pass A: bits -> column DIF -> twist -> buf (row-major R1 x R2).
+// kReversed: bits are a gathered sub-block stored reversed (bit s-1-t of
+// row j holds A_j[t]); else bit t holds coefficient t (the seed).
+template <bool kReversed>
+__global__ void __launch_bounds__(kThreads)
+ntt_pass_a_kernel(const uint32_t *__restrict__ bits, uint64_t bits_stride, uint32_t len, uint32_t R1, int r1_log,
+                  uint32_t N, Tables T, uint32_t *__restrict__ buf)
+{
+    extern __shared__ uint32_t x[];  // R1 * kCS
+    const uint32_t g = blockIdx.y;
+    const uint32_t c0 = blockIdx.x * kCW;
+    const uint32_t *b = bits + (size_t)g * bits_stride;
+    for (uint32_t t1 = threadIdx.x; t1 < R1; t1 += blockDim.x) {
+        const uint32_t base = t1 * kR2 + c0;
+#pragma unroll
+        for (int c = 0; c < kCW; ++c) {
+            const uint32_t t = base + c;
+            uint32_t v = 0;
+            if (t < len) {
+                const uint32_t pos = kReversed ? (len - 1 - t) : t;
+                v = (__ldg(b + (pos >> 5)) >> (pos & 31u)) & 1u;
+            }
+            x[t1 * kCS + c] = v;
+        }
+    }
+    __syncthreads();
+    dif_cols(x, R1, T.col_f, T.col_fq);
+    // row r now holds frequency k1 = bitrev(r); multiply by w_N^(k1 t2)
+    for (uint32_t it = threadIdx.x; it < R1 * kCW; it += blockDim.x) {
+        const uint32_t c = it % kCW, r = it / kCW;
+        const uint32_t e = bitrev(r, r1_log) * (c0 + c);  // < N
+        x[r * kCS + c] = mul_mont(x[r * kCS + c], twist_mont(T.tw_lo_f, T.tw_hi_f, e));
+    }
+    __syncthreads();
+    uint32_t *o = buf + (size_t)g * N;
+    for (uint32_t it = threadIdx.x; it < R1 * kCW; it += blockDim.x) {
+        const uint32_t c = it % kCW, r = it / kCW;
+        o[(size_t)r * kR2 + c0 + c] = x[r * kCS + c];
+    }
+}
+
+// Pass B: per row, 2048-point DIF, times spectrum (if given), and the
+// 2048-point inverse DIT (if kInverse).
+template <bool kInverse>
+__global__ void __launch_bounds__(kThreads)
+ntt_pass_b_kernel(uint32_t *__restrict__ buf, uint32_t N, uint32_t R1, const uint32_t *__restrict__ S,
+                  const uint32_t *__restrict__ Sq, Tables T)
+{
+    __shared__ __align__(16) uint32_t x[kRowsB][kR2];
+    const uint32_t g = blockIdx.y;
+    const uint32_t r0 = blockIdx.x * kRowsB;
+    uint32_t *base = buf + (size_t)g * N;
+    for (uint32_t it = threadIdx.x; it < kRowsB * kR2 / 4; it += blockDim.x) {
+        const uint32_t rr = it / (kR2 / 4), c4 = it % (kR2 / 4);
+        uint4 v = make_uint4(0, 0, 0, 0);
+        if (r0 + rr < R1) v = reinterpret_cast<const uint4 *>(base + (size_t)(r0 + rr) * kR2)[c4];
+        reinterpret_cast<uint4 *>(x[rr])[c4] = v;
+    }
+    __syncthreads();
+    for (uint32_t h = kR2 >> 1; h >= 1; h >>= 1) {  // DIF
+        const uint32_t stride = kR2 / (2 * h);
+        for (uint32_t it = threadIdx.x; it < kRowsB * (kR2 >> 1); it += blockDim.x) {
+            const uint32_t rr = it / (kR2 >> 1), b = it % (kR2 >> 1);
+            const uint32_t off = b & (h - 1), i = ((b - off) << 1) + off;
+            const uint32_t u = x[rr][i], v = x[rr][i + h];
+            const uint32_t ti = off * stride;
+            x[rr][i] = add_p(u, v);
+            x[rr][i + h] = mul_shoup(sub_p(u, v), __ldg(T.row_f + ti), __ldg(T.row_fq + ti));
+        }
+        __syncthreads();
+    }
+    if (kInverse) {
+        for (uint32_t it = threadIdx.x; it < kRowsB * kR2; it += blockDim.x) {
+            const uint32_t rr = it / kR2, c = it % kR2;
+            const size_t gi = (size_t)(r0 + rr) * kR2 + c;
+            if (r0 + rr < R1) x[rr][c] = mul_shoup(x[rr][c], __ldg(S + gi), __ldg(Sq + gi));
+        }
+        __syncthreads();
+        for (uint32_t h = 1; h < kR2; h <<= 1) {  // inverse DIT
+            const uint32_t stride = kR2 / (2 * h);
+            for (uint32_t it = threadIdx.x; it < kRowsB * (kR2 >> 1); it += blockDim.x) {
+                const uint32_t rr = it / (kR2 >> 1), b = it % (kR2 >> 1);
+                const uint32_t off = b & (h - 1), i = ((b - off) << 1) + off;
+                const uint32_t ti = off * stride;
+                const uint32_t u = x[rr][i], v = mul_shoup(x[rr][i + h], __ldg(T.row_i + ti), __ldg(T.row_iq + ti));
+                x[rr][i] = add_p(u, v);
+                x[rr][i + h] = sub_p(u, v);
+            }
+            __syncthreads();
+        }
+    }
+    for (uint32_t it = threadIdx.x; it < kRowsB * kR2 / 4; it += blockDim.x) {
+        const uint32_t rr = it / (kR2 / 4), c4 = it % (kR2 / 4);
+        if (r0 + rr < R1) reinterpret_cast<uint4 *>(base + (size_t)(r0 + rr) * kR2)[c4] = reinterpret_cast<const uint4 *>(x[rr])[c4];
+    }
+}
+
+// Pass A': untwist, column inverse DIT, parity of coefficients
+// [s-1, s+k-1) into output bits j k + t - (s-1).
+__global__ void __launch_bounds__(kThreads)
+ntt_pass_a_inv_kernel(const uint32_t *__restrict__ buf, uint32_t N, uint32_t R1, int r1_log, Tables T, uint32_t j0,
+                      uint32_t s, uint32_t k, uint32_t *__restrict__ out)
+{
+    extern __shared__ uint32_t x[];  // R1 * kCS
+    const uint32_t g = blockIdx.y;
+    const uint32_t c0 = blockIdx.x * kCW;
+    const uint32_t *in = buf + (size_t)g * N;
+    for (uint32_t it = threadIdx.x; it < R1 * kCW; it += blockDim.x) {
+        const uint32_t c = it % kCW, r = it / kCW;
+        const uint32_t e = bitrev(r, r1_log) * (c0 + c);
+        x[r * kCS + c] = mul_mont(in[(size_t)r * kR2 + c0 + c], twist_mont(T.tw_lo_i, T.tw_hi_i, e));
+    }
+    __syncthreads();
+    dit_cols(x, R1, T.col_i, T.col_iq);
+    const uint64_t jk = (uint64_t)(j0 + g) * k;
+    const uint32_t lo_t = s - 1, hi_t = s - 1 + k;  // wanted coefficients
+    for (uint32_t t1 = threadIdx.x; t1 < R1; t1 += blockDim.x) {
+        const uint32_t base = t1 * kR2 + c0;
+        if (base + kCW <= lo_t || base >= hi_t) continue;
+        uint32_t bits16 = 0;
+#pragma unroll
+        for (int c = 0; c < kCW; ++c) {
+            const uint32_t t = base + c;
+            if (t >= lo_t && t < hi_t) bits16 |= (x[t1 * kCS + c] & 1u) << c;
+        }
+        uint64_t P;  // output bit of the lowest kept coefficient
+        if (base < lo_t) {
+            bits16 >>= (lo_t - base);
+            P = jk;
+        } else {
+            P = jk + (base - lo_t);
+        }
+        if (!bits16) continue;
+        const uint32_t sh = (uint32_t)(P & 31u);
+        atomicXor(out + (P >> 5), bits16 << sh);
+        if (sh > 16 && (bits16 >> (32u - sh))) atomicXor(out + (P >> 5) + 1, bits16 >> (32u - sh));
+    }
+}
+
+// S = spectrum * N^-1 and its Shoup quotients.
+__global__ void ntt_finish_spectrum_kernel(uint32_t *S, uint32_t *Sq, uint32_t N, uint32_t ninv, uint32_t ninv_q)
+{
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+        const uint32_t v = mul_shoup(S[i], ninv, ninv_q);
+        S[i] = v;
+        Sq[i] = (uint32_t)(((uint64_t)v << 32) / kP);
+    }
+}
+
+// ---- host side -----------------------------------------------------------
+uint32_t powmod(uint64_t b, uint64_t e)
+{
+    uint64_t r = 1;
+    b %= kP;
+    while (e) {
+        if (e & 1) r = r * b % kP;
+        b = b * b % kP;
+        e >>= 1;
+    }
+    return (uint32_t)r;
+}
+uint32_t shoup_q(uint32_t w) { return (uint32_t)(((uint64_t)w << 32) / kP); }
+uint32_t to_mont(uint32_t w) { return (uint32_t)(((uint64_t)w << 32) % kP); }
+
+}  // namespace
+
+struct NttPlan {
+    int e = 0, r1_log = 0;
+    uint32_t N = 0, R1 = 0, G = 0;
+    uint32_t *buf = nullptr, *S = nullptr, *Sq = nullptr, *tables = nullptr;
+    Tables T{};
+};
+
+bool ntt_eligible(uint32_t s, uint32_t k)
+{
+    const uint64_t need = (uint64_t)s + k - 1;
+    return need > kR2 && need <= (1ull << (kR2Log + 11));  // 2^12 <= N <= 2^22
+}
+
+uint32_t ntt_length(uint32_t s, uint32_t k)
+{
+    uint32_t N = kR2;
+    while ((uint64_t)N < (uint64_t)s + k - 1) N <<= 1;
+    return N;
+}
+
+void ntt_destroy(NttPlan *p)
+{
+    if (!p) return;
+    cudaFree(p->buf);
+    cudaFree(p->S);
+    cudaFree(p->Sq);
+    cudaFree(p->tables);
+    delete p;
+}
+
+size_t ntt_pass_a_smem(uint32_t R1) { return (size_t)R1 * kCS * 4; }
+
+// seed: realigned seed bits (bit t = seed[t]), L = s + k - 1 bits.
+int ntt_create(NttPlan **out, uint32_t m, uint32_t s, uint32_t k, const uint32_t *seed_dev, cudaStream_t st)
+{
+    *out = nullptr;
+    if (!ntt_eligible(s, k)) return set_error(EXTRACT_EINVAL, "NTT path needs 2^11 < s+k-1 <= 2^22");
+    NttPlan *p = new NttPlan();
+    p->N = ntt_length(s, k);
+    p->e = 0;
+    while ((1u << p->e) < p->N) ++p->e;
+    p->R1 = p->N / kR2;
+    p->r1_log = p->e - kR2Log;
+    // sub-blocks per launch: keep the working buffer near 64 MB (L2-sized)
+    p->G = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(m, (16ull << 20) / p->N));
+    const uint32_t R1 = p->R1;
+    // table layout (words): col_f, col_fq, col_i, col_iq (R1/2 each, >= 1),
+    // row_f, row_fq, row_i, row_iq (1024 each), tw_lo_f, tw_lo_i (2048),
+    // tw_hi_f, tw_hi_i (R1 each, >= 1)
+    const uint32_t ch = std::max<uint32_t>(1, R1 / 2);
+    std::vector<uint32_t> h;
+    auto push_stage = [&](uint32_t R, uint32_t count, bool inverse) {
+        const uint32_t w = powmod(kGen, (kP - 1) / R);
+        const uint32_t wi = powmod(w, kP - 2);
+        std::vector<uint32_t> f(count), q(count);
+        uint64_t cur = 1;
+        for (uint32_t i = 0; i < count; ++i) {
+            f[i] = (uint32_t)cur;
+            q[i] = shoup_q(f[i]);
+            cur = cur * (inverse ? wi : w) % kP;
+        }
+        h.insert(h.end(), f.begin(), f.end());
+        h.insert(h.end(), q.begin(), q.end());
+    };
+    const size_t o_col_f = 0;
+    push_stage(std::max<uint32_t>(2, R1), ch, false);
+    const size_t o_col_i = h.size();
+    push_stage(std::max<uint32_t>(2, R1), ch, true);
+    const size_t o_row_f = h.size();
+    push_stage(kR2, kR2 / 2, false);
+    const size_t o_row_i = h.size();
+    push_stage(kR2, kR2 / 2, true);
+    const uint32_t wN = powmod(kGen, (kP - 1) / p->N), wNi = powmod(wN, kP - 2);
+    const size_t o_tw = h.size();
+    for (int inv = 0; inv < 2; ++inv) {
+        const uint32_t w = inv ? wNi : wN;
+        for (uint32_t x = 0; x < kR2; ++x) h.push_back(to_mont(powmod(w, x)));
+        const uint32_t w2 = powmod(w, kR2);
+        for (uint32_t x = 0; x < std::max<uint32_t>(1, R1); ++x) h.push_back(to_mont(powmod(w2, x)));
+    }
+    int rc = EXTRACT_OK;
+    do {
+        cudaError_t e;
+        if ((e = cudaMalloc(&p->tables, h.size() * 4)) != cudaSuccess) { rc = cuda_error(e, "ntt tables"); break; }
+        if ((e = cudaMemcpy(p->tables, h.data(), h.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess) { rc = cuda_error(e, "ntt tables copy"); break; }
+        const uint32_t *t = p->tables;
+        p->T.col_f = t + o_col_f; p->T.col_fq = t + o_col_f + ch;
+        p->T.col_i = t + o_col_i; p->T.col_iq = t + o_col_i + ch;
+        p->T.row_f = t + o_row_f; p->T.row_fq = t + o_row_f + kR2 / 2;
+        p->T.row_i = t + o_row_i; p->T.row_iq = t + o_row_i + kR2 / 2;
+        const uint32_t hiN = std::max<uint32_t>(1, R1);
+        p->T.tw_lo_f = t + o_tw; p->T.tw_hi_f = t + o_tw + kR2;
+        p->T.tw_lo_i = t + o_tw + kR2 + hiN; p->T.tw_hi_i = t + o_tw + 2 * kR2 + hiN;
+        if ((e = cudaMalloc(&p->buf, (size_t)p->G * p->N * 4)) != cudaSuccess) { rc = cuda_error(e, "ntt buffer"); break; }
+        if ((e = cudaMalloc(&p->S, (size_t)p->N * 4)) != cudaSuccess) { rc = cuda_error(e, "ntt spectrum"); break; }
+        if ((e = cudaMalloc(&p->Sq, (size_t)p->N * 4)) != cudaSuccess) { rc = cuda_error(e, "ntt spectrum"); break; }
+        const size_t smem = ntt_pass_a_smem(R1);
+        if ((e = cudaFuncSetAttribute(ntt_pass_a_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess ||
+            (e = cudaFuncSetAttribute(ntt_pass_a_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess ||
+            (e = cudaFuncSetAttribute(ntt_pass_a_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) {
+            rc = cuda_error(e, "ntt smem attribute");
+            break;
+        }
+        // seed spectrum: pass A (forward bits) + row DIF into S, then scale by 1/N
+        const uint32_t L = s + k - 1;
+        ntt_pass_a_kernel<false><<<dim3(kR2 / kCW, 1), kThreads, smem, st>>>(seed_dev, 0, L, R1, p->r1_log, p->N,
+                                                                           p->T, p->S);
+        ntt_pass_b_kernel<false><<<dim3((uint32_t)ceil_div(R1, kRowsB), 1), kThreads, 0, st>>>(p->S, p->N, R1,
+                                                                                             nullptr, nullptr, p->T);
+        const uint32_t ninv = powmod(p->N, kP - 2);
+        ntt_finish_spectrum_kernel<<<(uint32_t)std::min<uint64_t>(ceil_div(p->N, 256), 4096), 256, 0, st>>>(
+            p->S, p->Sq, p->N, ninv, shoup_q(ninv));
+        if ((e = cudaGetLastError()) != cudaSuccess) { rc = cuda_error(e, "ntt spectrum kernels"); break; }
+        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) { rc = cuda_error(e, "ntt spectrum"); break; }
+    } while (0);
+    if (rc != EXTRACT_OK) { ntt_destroy(p); return rc; }
+    *out = p;
+    return EXTRACT_OK;
+}
+
+// Hash every sub-block: out (zeroed here) gets K_j at bit j*k.
+int ntt_hash(const NttPlan *p, const uint32_t *arev, uint32_t w_pad, uint32_t m, uint32_t s, uint32_t k,
+             uint32_t *out, cudaStream_t st)
+{
+    EX_CUDA(cudaMemsetAsync(out, 0, ceil_div((uint64_t)m * k, 32) * 4, st));
+    const size_t smem = ntt_pass_a_smem(p->R1);
+    for (uint32_t j0 = 0; j0 < m; j0 += p->G) {
+        const uint32_t g = std::min(p->G, m - j0);
+        ntt_pass_a_kernel<true><<<dim3(kR2 / kCW, g), kThreads, smem, st>>>(arev + (size_t)j0 * w_pad, w_pad, s, p->R1,
+                                                                          p->r1_log, p->N, p->T, p->buf);
+        ntt_pass_b_kernel<true><<<dim3((uint32_t)ceil_div(p->R1, kRowsB), g), kThreads, 0, st>>>(p->buf, p->N, p->R1,
+                                                                                               p->S, p->Sq, p->T);
+        ntt_pass_a_inv_kernel<<<dim3(kR2 / kCW, g), kThreads, smem, st>>>(p->buf, p->N, p->R1, p->r1_log, p->T, j0, s,
+                                                                         k, out);
+    }
+    EX_LAUNCH("ntt kernels");
+    return EXTRACT_OK;
+}
+
+uint32_t ntt_group(const NttPlan *p) { return p->G; }
+uint32_t ntt_size(const NttPlan *p) { return p->N; }
+
+}  // namespace ex

@@ -26,6 +26,8 @@ EXTRACT_EINTERNAL = -7
 
 EXTRACT_SEED_PER_SUBBLOCK = 0x1
 EXTRACT_IDENTITY_PERM = 0x2
+EXTRACT_METHOD_DIRECT = 0x4
+EXTRACT_METHOD_NTT = 0x8
 
 
 def EXTRACT_KEY_BITS(b: int) -> int:
