@@ -184,6 +184,22 @@ class OracleSample:
                           % (self.nj, self.m, self.ni, self.k, frac, self.nj, t)}
 
 
+def max_over_ranks(x: float, dist, device) -> float:
+    """The slowest rank's time (every rank must call it); x itself on 1 rank."""
+    if not dist:
+        return x
+    import torch
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(n_per_rank: int, world: int, ms_per_step: float) -> float:
+    """Whole-job input Gbit/s: every rank hashes its own n-bit block (weak
+    scaling), the step takes the slowest rank's time."""
+    return world * n_per_rank / (ms_per_step / 1e3) / 1e9
+
+
 def launches_per_step(is_ntt, m, plan):
     """Kernels of ours per step: the gather plus the hash (one launch direct;
     three per group of sub-blocks for the NTT method)."""
@@ -320,12 +336,9 @@ def run_ours(args):
     ms_total = start.elapsed_time(end)
     gather_ms = statistics.mean(a.elapsed_time(b) for a, b, _ in evs)
     hash_ms = statistics.mean(b.elapsed_time(c) for _, b, c in evs)
-    if dist:
-        t = torch.tensor([ms_total], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = max_over_ranks(ms_total, dist, dev)
     ms_step = ms_total / args.steps
-    value = world * n / (ms_step / 1e3) / 1e9
+    value = aggregate_rate(n, world, ms_step)
 
     # end to end through the C ABI with host buffers
     e2e = None
@@ -339,11 +352,8 @@ def run_ours(args):
         for _ in range(args.steps):
             ex.run_host(h_in, h_out, stream=stream)
         e2e_s = (time.perf_counter() - t1) / args.steps
-        if dist:
-            t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
-        e2e = {"value": world * n / e2e_s / 1e9, "unit": "Gbit/s", "ms_per_step": e2e_s * 1e3,
+        e2e_s = max_over_ranks(e2e_s, dist, dev)
+        e2e = {"value": aggregate_rate(n, world, e2e_s * 1e3), "unit": "Gbit/s", "ms_per_step": e2e_s * 1e3,
                "h2d_bytes_per_step": int(in_w.nbytes), "d2h_bytes_per_step": int(ex.out_words * 4),
                "api": "extract_run_host (pinned host buffers, copies and sync inside the timed region)"}
 

@@ -88,6 +88,10 @@ struct Tables {
     const uint32_t *row_f, *row_fq, *row_i, *row_iq;
     // twist factors in Montgomery form: w_N^x = lo[x & 2047] * hi[x >> 11]
     const uint32_t *tw_lo_f, *tw_hi_f, *tw_lo_i, *tw_hi_i;
+    // per-stage tables for the warp transforms: entry (h - 1) + r holds
+    // (w_2h^r, Shoup quotient) for r < h, every h = 1, 2, 4, ... < R
+    const uint2 *row_stage_f, *row_stage_i;  // R = 2048
+    const uint2 *col_stage_f, *col_stage_i;  // R = R1
 };
 
 __device__ __forceinline__ uint32_t twist_mont(const uint32_t *lo, const uint32_t *hi, uint32_t x)
@@ -280,6 +284,189 @@ __global__ void ntt_finish_spectrum_kernel(uint32_t *S, uint32_t *Sq, uint32_t N
     }
 }
 
+
+// ---- warp-resident transforms --------------------------------------------
+// A warp holds R = 32 EPL values; lane l, register j holds position l + 32 j.
+// Stages whose pair distance h is >= 32 pair two registers of one lane;
+// stages with h <= 16 pair lanes l and l ^ h through a shuffle.
+constexpr uint32_t kOneQ = (uint32_t)(((uint64_t)1 << 32) / kP);  // Shoup quotient of 1
+
+// DIF (natural positions in, bit-reversed out), twiddles w_2h^(i mod 2h).
+template <int EPL>
+__device__ __forceinline__ void warp_dif(uint32_t (&e)[EPL], const uint2 *__restrict__ tw, int lane)
+{
+#pragma unroll
+    for (int hp = EPL / 2; hp >= 1; hp >>= 1) {
+        const int h = hp * 32;
+#pragma unroll
+        for (int j = 0; j < EPL; ++j) {
+            if (j & hp) continue;
+            const uint2 w = __ldg(tw + (h - 1) + lane + 32 * (j & (hp - 1)));
+            const uint32_t u = e[j], v = e[j + hp];
+            e[j] = add_p(u, v);
+            e[j + hp] = mul_shoup(sub_p(u, v), w.x, w.y);
+        }
+    }
+#pragma unroll
+    for (int h = 16; h >= 1; h >>= 1) {
+        const bool upper = (lane & h) != 0;
+        const uint2 w = upper ? __ldg(tw + (h - 1) + (lane & (h - 1))) : make_uint2(1u, kOneQ);
+#pragma unroll
+        for (int j = 0; j < EPL; ++j) {
+            const uint32_t p = __shfl_xor_sync(0xffffffffu, e[j], h);
+            const uint32_t d = upper ? sub_p(p, e[j]) : add_p(e[j], p);
+            e[j] = mul_shoup(d, w.x, w.y);
+        }
+    }
+}
+
+// DIT (bit-reversed positions in, natural out), twiddles w_2h^-(i mod 2h).
+template <int EPL>
+__device__ __forceinline__ void warp_dit(uint32_t (&e)[EPL], const uint2 *__restrict__ tw, int lane)
+{
+#pragma unroll
+    for (int h = 1; h <= 16; h <<= 1) {
+        const bool upper = (lane & h) != 0;
+        const uint2 w = __ldg(tw + (h - 1) + (lane & (h - 1)));
+#pragma unroll
+        for (int j = 0; j < EPL; ++j) {
+            const uint32_t p = __shfl_xor_sync(0xffffffffu, e[j], h);
+            const uint32_t m = mul_shoup(upper ? e[j] : p, w.x, w.y);  // w * (upper element)
+            e[j] = upper ? sub_p(p, m) : add_p(e[j], m);
+        }
+    }
+#pragma unroll
+    for (int hp = 1; hp <= EPL / 2; hp <<= 1) {
+        const int h = hp * 32;
+#pragma unroll
+        for (int j = 0; j < EPL; ++j) {
+            if (j & hp) continue;
+            const uint2 w = __ldg(tw + (h - 1) + lane + 32 * (j & (hp - 1)));
+            const uint32_t u = e[j], v = mul_shoup(e[j + hp], w.x, w.y);
+            e[j] = add_p(u, v);
+            e[j + hp] = sub_p(u, v);
+        }
+    }
+}
+
+// Pass B, one warp per 2048-word row: DIF, times the spectrum, inverse DIT
+// (kInverse false: DIF only, for the seed spectrum).
+template <bool kInverse>
+__global__ void __launch_bounds__(256)
+ntt_rows_kernel(uint32_t *__restrict__ buf, uint32_t N, uint32_t R1, uint32_t rows, const uint32_t *__restrict__ S,
+                const uint32_t *__restrict__ Sq, Tables T)
+{
+    const int lane = threadIdx.x & 31;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < rows; row += nwarps) {
+        const uint32_t g = row / R1, r = row % R1;
+        uint32_t *x = buf + (size_t)g * N + (size_t)r * kR2;
+        uint32_t e[64];
+#pragma unroll
+        for (int j = 0; j < 64; ++j) e[j] = x[lane + 32 * j];
+        warp_dif<64>(e, T.row_stage_f, lane);
+        if (kInverse) {
+            const uint32_t *sv = S + (size_t)r * kR2, *sq = Sq + (size_t)r * kR2;
+#pragma unroll
+            for (int j = 0; j < 64; ++j) e[j] = mul_shoup(e[j], __ldg(sv + lane + 32 * j), __ldg(sq + lane + 32 * j));
+            warp_dit<64>(e, T.row_stage_i, lane);
+        }
+#pragma unroll
+        for (int j = 0; j < 64; ++j) x[lane + 32 * j] = e[j];
+    }
+}
+
+// Pass A, one warp per column (16 per CTA): bits -> DIF along t1 -> twist,
+// staged through shared memory so the row-major stores are coalesced.
+template <int EPL, bool kReversed>
+__global__ void __launch_bounds__(kCW * 32)
+ntt_cols_fwd_kernel(const uint32_t *__restrict__ bits, uint64_t bits_stride, uint32_t len, int r1_log, uint32_t N,
+                    Tables T, uint32_t *__restrict__ buf)
+{
+    constexpr uint32_t R1 = 32u * EPL;
+    extern __shared__ uint32_t x[];  // R1 * kCS
+    const int lane = threadIdx.x & 31, c = threadIdx.x >> 5;
+    const uint32_t g = blockIdx.y, c0 = blockIdx.x * kCW, t2 = c0 + c;
+    const uint32_t *b = bits + (size_t)g * bits_stride;
+    uint32_t e[EPL];
+#pragma unroll
+    for (int j = 0; j < EPL; ++j) {
+        const uint32_t t = (lane + 32u * j) * kR2 + t2;
+        uint32_t v = 0;
+        if (t < len) {
+            const uint32_t pos = kReversed ? (len - 1 - t) : t;
+            v = (__ldg(b + (pos >> 5)) >> (pos & 31u)) & 1u;
+        }
+        e[j] = v;
+    }
+    warp_dif<EPL>(e, T.col_stage_f, lane);
+#pragma unroll
+    for (int j = 0; j < EPL; ++j) {
+        const uint32_t r = lane + 32u * j;
+        e[j] = mul_mont(e[j], twist_mont(T.tw_lo_f, T.tw_hi_f, bitrev(r, r1_log) * t2));
+        x[r * kCS + c] = e[j];
+    }
+    __syncthreads();
+    uint32_t *o = buf + (size_t)g * N;
+    for (uint32_t it = threadIdx.x; it < R1 * kCW; it += blockDim.x) {
+        const uint32_t cc = it % kCW, r = it / kCW;
+        o[(size_t)r * kR2 + c0 + cc] = x[r * kCS + cc];
+    }
+}
+
+// Pass A', one warp per column: coalesced load through shared memory,
+// untwist, inverse DIT along t1, parity of the wanted coefficients.
+template <int EPL>
+__global__ void __launch_bounds__(kCW * 32)
+ntt_cols_inv_kernel(const uint32_t *__restrict__ buf, uint32_t N, int r1_log, Tables T, uint32_t j0, uint32_t s,
+                    uint32_t k, uint32_t *__restrict__ out)
+{
+    constexpr uint32_t R1 = 32u * EPL;
+    extern __shared__ uint32_t x[];  // R1 * kCS
+    const int lane = threadIdx.x & 31, c = threadIdx.x >> 5;
+    const uint32_t g = blockIdx.y, c0 = blockIdx.x * kCW, t2 = c0 + c;
+    const uint32_t *in = buf + (size_t)g * N;
+    for (uint32_t it = threadIdx.x; it < R1 * kCW; it += blockDim.x) {
+        const uint32_t cc = it % kCW, r = it / kCW;
+        x[r * kCS + cc] = in[(size_t)r * kR2 + c0 + cc];
+    }
+    __syncthreads();
+    uint32_t e[EPL];
+#pragma unroll
+    for (int j = 0; j < EPL; ++j) {
+        const uint32_t r = lane + 32u * j;
+        e[j] = mul_mont(x[r * kCS + c], twist_mont(T.tw_lo_i, T.tw_hi_i, bitrev(r, r1_log) * t2));
+    }
+    warp_dit<EPL>(e, T.col_stage_i, lane);
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < EPL; ++j) x[(lane + 32u * j) * kCS + c] = e[j] & 1u;
+    __syncthreads();
+    const uint64_t jk = (uint64_t)(j0 + g) * k;
+    const uint32_t lo_t = s - 1, hi_t = s - 1 + k;
+    for (uint32_t t1 = threadIdx.x; t1 < R1; t1 += blockDim.x) {
+        const uint32_t base = t1 * kR2 + c0;
+        if (base + kCW <= lo_t || base >= hi_t) continue;
+        uint32_t bits16 = 0;
+#pragma unroll
+        for (int cc = 0; cc < kCW; ++cc) {
+            const uint32_t t = base + cc;
+            if (t >= lo_t && t < hi_t) bits16 |= x[t1 * kCS + cc] << cc;
+        }
+        uint64_t P;
+        if (base < lo_t) {
+            bits16 >>= (lo_t - base);
+            P = jk;
+        } else {
+            P = jk + (base - lo_t);
+        }
+        if (!bits16) continue;
+        const uint32_t sh = (uint32_t)(P & 31u);
+        atomicXor(out + (P >> 5), bits16 << sh);
+        if (sh > 16 && (bits16 >> (32u - sh))) atomicXor(out + (P >> 5) + 1, bits16 >> (32u - sh));
+    }
+}
+
 // ---- host side -----------------------------------------------------------
 uint32_t powmod(uint64_t b, uint64_t e)
 {
@@ -303,6 +490,67 @@ struct NttPlan {
     uint32_t *buf = nullptr, *S = nullptr, *Sq = nullptr, *tables = nullptr;
     Tables T{};
 };
+
+namespace {
+
+// pass A for g sub-blocks (bits stride bits_stride words) into dst
+int ntt_launch_a(const NttPlan *p, const uint32_t *bits, uint64_t bits_stride, uint32_t len, bool reversed, uint32_t g,
+                 uint32_t *dst, cudaStream_t st)
+{
+    const size_t smem = (size_t)p->R1 * kCS * 4;
+    const dim3 grid(kR2 / kCW, g);
+    if (p->R1 < 32) {
+        if (reversed)
+            ntt_pass_a_kernel<true><<<grid, kThreads, smem, st>>>(bits, bits_stride, len, p->R1, p->r1_log, p->N, p->T, dst);
+        else
+            ntt_pass_a_kernel<false><<<grid, kThreads, smem, st>>>(bits, bits_stride, len, p->R1, p->r1_log, p->N, p->T, dst);
+        return EXTRACT_OK;
+    }
+    const int epl = (int)(p->R1 / 32);
+#define EX_COLS_FWD(E)                                                                                         \
+    if (epl == E) {                                                                                            \
+        if (reversed)                                                                                          \
+            ntt_cols_fwd_kernel<E, true><<<grid, kCW * 32, smem, st>>>(bits, bits_stride, len, p->r1_log, p->N, p->T, dst); \
+        else                                                                                                   \
+            ntt_cols_fwd_kernel<E, false><<<grid, kCW * 32, smem, st>>>(bits, bits_stride, len, p->r1_log, p->N, p->T, dst); \
+        return EXTRACT_OK;                                                                                     \
+    }
+    EX_COLS_FWD(1) EX_COLS_FWD(2) EX_COLS_FWD(4) EX_COLS_FWD(8) EX_COLS_FWD(16) EX_COLS_FWD(32) EX_COLS_FWD(64)
+#undef EX_COLS_FWD
+    return set_error(EXTRACT_EINTERNAL, "ntt: no column kernel for R1=%u", p->R1);
+}
+
+// pass B over the g * R1 rows of dst (inverse: times S and back)
+void ntt_launch_rows(const NttPlan *p, uint32_t *dst, uint32_t g, const uint32_t *S, const uint32_t *Sq, bool inverse,
+                     cudaStream_t st)
+{
+    const uint32_t rows = p->R1 * g;
+    const uint32_t grid = (uint32_t)std::max<uint64_t>(1, ceil_div(rows, 8));  // 8 warps per CTA, a warp per row
+    if (inverse) ntt_rows_kernel<true><<<grid, 256, 0, st>>>(dst, p->N, p->R1, rows, S, Sq, p->T);
+    else ntt_rows_kernel<false><<<grid, 256, 0, st>>>(dst, p->N, p->R1, rows, S, Sq, p->T);
+}
+
+// pass A' for g sub-blocks, output bits of sub-blocks j0 .. j0+g-1
+int ntt_launch_a_inv(const NttPlan *p, uint32_t g, uint32_t j0, uint32_t s, uint32_t k, uint32_t *out, cudaStream_t st)
+{
+    const size_t smem = (size_t)p->R1 * kCS * 4;
+    const dim3 grid(kR2 / kCW, g);
+    if (p->R1 < 32) {
+        ntt_pass_a_inv_kernel<<<grid, kThreads, smem, st>>>(p->buf, p->N, p->R1, p->r1_log, p->T, j0, s, k, out);
+        return EXTRACT_OK;
+    }
+    const int epl = (int)(p->R1 / 32);
+#define EX_COLS_INV(E)                                                                                     \
+    if (epl == E) {                                                                                        \
+        ntt_cols_inv_kernel<E><<<grid, kCW * 32, smem, st>>>(p->buf, p->N, p->r1_log, p->T, j0, s, k, out); \
+        return EXTRACT_OK;                                                                                 \
+    }
+    EX_COLS_INV(1) EX_COLS_INV(2) EX_COLS_INV(4) EX_COLS_INV(8) EX_COLS_INV(16) EX_COLS_INV(32) EX_COLS_INV(64)
+#undef EX_COLS_INV
+    return set_error(EXTRACT_EINTERNAL, "ntt: no column kernel for R1=%u", p->R1);
+}
+
+}  // namespace
 
 bool ntt_eligible(uint32_t s, uint32_t k)
 {
@@ -369,6 +617,25 @@ int ntt_create(NttPlan **out, uint32_t m, uint32_t s, uint32_t k, const uint32_t
     push_stage(kR2, kR2 / 2, false);
     const size_t o_row_i = h.size();
     push_stage(kR2, kR2 / 2, true);
+    // per-stage (w_2h^r, quotient) tables for the warp transforms, 8-byte aligned
+    auto push_per_stage = [&](uint32_t R, bool inverse) {
+        if (h.size() & 1) h.push_back(0);
+        const size_t at = h.size();
+        for (uint32_t hh = 1; hh < R; hh <<= 1) {
+            const uint32_t w = powmod(kGen, (kP - 1) / (2 * hh));
+            const uint32_t step = inverse ? powmod(w, kP - 2) : w;
+            uint64_t cur = 1;
+            for (uint32_t r = 0; r < hh; ++r) {
+                h.push_back((uint32_t)cur);
+                h.push_back(shoup_q((uint32_t)cur));
+                cur = cur * step % kP;
+            }
+        }
+        return at;
+    };
+    const size_t o_rs_f = push_per_stage(kR2, false), o_rs_i = push_per_stage(kR2, true);
+    const size_t o_cs_f = push_per_stage(std::max<uint32_t>(2, R1), false);
+    const size_t o_cs_i = push_per_stage(std::max<uint32_t>(2, R1), true);
     const uint32_t wN = powmod(kGen, (kP - 1) / p->N), wNi = powmod(wN, kP - 2);
     const size_t o_tw = h.size();
     for (int inv = 0; inv < 2; ++inv) {
@@ -390,6 +657,10 @@ int ntt_create(NttPlan **out, uint32_t m, uint32_t s, uint32_t k, const uint32_t
         const uint32_t hiN = std::max<uint32_t>(1, R1);
         p->T.tw_lo_f = t + o_tw; p->T.tw_hi_f = t + o_tw + kR2;
         p->T.tw_lo_i = t + o_tw + kR2 + hiN; p->T.tw_hi_i = t + o_tw + 2 * kR2 + hiN;
+        p->T.row_stage_f = reinterpret_cast<const uint2 *>(t + o_rs_f);
+        p->T.row_stage_i = reinterpret_cast<const uint2 *>(t + o_rs_i);
+        p->T.col_stage_f = reinterpret_cast<const uint2 *>(t + o_cs_f);
+        p->T.col_stage_i = reinterpret_cast<const uint2 *>(t + o_cs_i);
         if ((e = cudaMalloc(&p->buf, (size_t)p->G * p->N * 4)) != cudaSuccess) { rc = cuda_error(e, "ntt buffer"); break; }
         if ((e = cudaMalloc(&p->S, (size_t)p->N * 4)) != cudaSuccess) { rc = cuda_error(e, "ntt spectrum"); break; }
         if ((e = cudaMalloc(&p->Sq, (size_t)p->N * 4)) != cudaSuccess) { rc = cuda_error(e, "ntt spectrum"); break; }
@@ -400,12 +671,22 @@ int ntt_create(NttPlan **out, uint32_t m, uint32_t s, uint32_t k, const uint32_t
             rc = cuda_error(e, "ntt smem attribute");
             break;
         }
+        if (R1 >= 32) {
+            const int epl = (int)(R1 / 32);
+#define EX_SET_SMEM(E)                                                                                      \
+    if (epl == E) {                                                                                         \
+        e = cudaFuncSetAttribute(ntt_cols_fwd_kernel<E, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(ntt_cols_fwd_kernel<E, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(ntt_cols_inv_kernel<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+    }
+            EX_SET_SMEM(1) EX_SET_SMEM(2) EX_SET_SMEM(4) EX_SET_SMEM(8) EX_SET_SMEM(16) EX_SET_SMEM(32) EX_SET_SMEM(64)
+#undef EX_SET_SMEM
+            if (e != cudaSuccess) { rc = cuda_error(e, "ntt smem attribute"); break; }
+        }
         // seed spectrum: pass A (forward bits) + row DIF into S, then scale by 1/N
         const uint32_t L = s + k - 1;
-        ntt_pass_a_kernel<false><<<dim3(kR2 / kCW, 1), kThreads, smem, st>>>(seed_dev, 0, L, R1, p->r1_log, p->N,
-                                                                           p->T, p->S);
-        ntt_pass_b_kernel<false><<<dim3((uint32_t)ceil_div(R1, kRowsB), 1), kThreads, 0, st>>>(p->S, p->N, R1,
-                                                                                             nullptr, nullptr, p->T);
+        if (int lrc = ntt_launch_a(p, seed_dev, 0, L, false, 1, p->S, st)) { rc = lrc; break; }
+        ntt_launch_rows(p, p->S, 1, nullptr, nullptr, false, st);
         const uint32_t ninv = powmod(p->N, kP - 2);
         ntt_finish_spectrum_kernel<<<(uint32_t)std::min<uint64_t>(ceil_div(p->N, 256), 4096), 256, 0, st>>>(
             p->S, p->Sq, p->N, ninv, shoup_q(ninv));
@@ -422,15 +703,11 @@ int ntt_hash(const NttPlan *p, const uint32_t *arev, uint32_t w_pad, uint32_t m,
              uint32_t *out, cudaStream_t st)
 {
     EX_CUDA(cudaMemsetAsync(out, 0, ceil_div((uint64_t)m * k, 32) * 4, st));
-    const size_t smem = ntt_pass_a_smem(p->R1);
     for (uint32_t j0 = 0; j0 < m; j0 += p->G) {
         const uint32_t g = std::min(p->G, m - j0);
-        ntt_pass_a_kernel<true><<<dim3(kR2 / kCW, g), kThreads, smem, st>>>(arev + (size_t)j0 * w_pad, w_pad, s, p->R1,
-                                                                          p->r1_log, p->N, p->T, p->buf);
-        ntt_pass_b_kernel<true><<<dim3((uint32_t)ceil_div(p->R1, kRowsB), g), kThreads, 0, st>>>(p->buf, p->N, p->R1,
-                                                                                               p->S, p->Sq, p->T);
-        ntt_pass_a_inv_kernel<<<dim3(kR2 / kCW, g), kThreads, smem, st>>>(p->buf, p->N, p->R1, p->r1_log, p->T, j0, s,
-                                                                         k, out);
+        if (int rc = ntt_launch_a(p, arev + (size_t)j0 * w_pad, w_pad, s, true, g, p->buf, st)) return rc;
+        ntt_launch_rows(p, p->buf, g, p->S, p->Sq, true, st);
+        if (int rc = ntt_launch_a_inv(p, g, j0, s, k, out, st)) return rc;
     }
     EX_LAUNCH("ntt kernels");
     return EXTRACT_OK;
