@@ -51,35 +51,40 @@ def build(force: bool = False) -> str:
 _lib = None
 
 
+def load_library(path: str) -> ctypes.CDLL:
+    """Open a compiled oracle library and declare its C signatures."""
+    L = ctypes.CDLL(path)
+    u64, u32, i32, vp = ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int, ctypes.c_void_p
+    L.oracle_philox4x32_10.argtypes = [vp, vp, vp]
+    L.oracle_philox4x32_10.restype = None
+    L.oracle_sampling_key.argtypes = [u64, u64, u32]
+    L.oracle_sampling_key.restype = u64
+    L.oracle_sampling_keys.argtypes = [u64, u64, u32, vp, i32]
+    L.oracle_sampling_keys.restype = None
+    L.oracle_perm.argtypes = [u64, vp, vp]
+    L.oracle_perm.restype = i32
+    L.oracle_perm_range.argtypes = [u64, vp, u64, u64, vp]
+    L.oracle_perm_range.restype = i32
+    L.oracle_check_order.argtypes = [u64, vp, vp, i32]
+    L.oracle_check_order.restype = ctypes.c_int64
+    L.oracle_subblock.argtypes = [vp, vp, u64, vp]
+    L.oracle_subblock.restype = None
+    L.oracle_toeplitz_bit.argtypes = [vp, u64, u64, vp, u64]
+    L.oracle_toeplitz_bit.restype = ctypes.c_uint8
+    L.oracle_toeplitz.argtypes = [vp, u64, u64, vp, u64, u64, vp]
+    L.oracle_toeplitz.restype = None
+    L.oracle_extract.argtypes = [u64, u64, u64, u64, vp, vp, u64, u32, vp, i32]
+    L.oracle_extract.restype = i32
+    L.oracle_extract_window.argtypes = [vp, vp, u64, u64, vp, u32, u64, u64, u64, u64, vp, i32]
+    L.oracle_extract_window.restype = None
+    return L
+
+
 def lib():
     global _lib
     if _lib is None:
         build()
-        L = ctypes.CDLL(_LIB)
-        u64, u32, i32, vp = ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int, ctypes.c_void_p
-        L.oracle_philox4x32_10.argtypes = [vp, vp, vp]
-        L.oracle_philox4x32_10.restype = None
-        L.oracle_sampling_key.argtypes = [u64, u64, u32]
-        L.oracle_sampling_key.restype = u64
-        L.oracle_sampling_keys.argtypes = [u64, u64, u32, vp, i32]
-        L.oracle_sampling_keys.restype = None
-        L.oracle_perm.argtypes = [u64, vp, vp]
-        L.oracle_perm.restype = i32
-        L.oracle_perm_range.argtypes = [u64, vp, u64, u64, vp]
-        L.oracle_perm_range.restype = i32
-        L.oracle_check_order.argtypes = [u64, vp, vp, i32]
-        L.oracle_check_order.restype = ctypes.c_int64
-        L.oracle_subblock.argtypes = [vp, vp, u64, vp]
-        L.oracle_subblock.restype = None
-        L.oracle_toeplitz_bit.argtypes = [vp, u64, u64, vp, u64]
-        L.oracle_toeplitz_bit.restype = ctypes.c_uint8
-        L.oracle_toeplitz.argtypes = [vp, u64, u64, vp, u64, u64, vp]
-        L.oracle_toeplitz.restype = None
-        L.oracle_extract.argtypes = [u64, u64, u64, u64, vp, vp, u64, u32, vp, i32]
-        L.oracle_extract.restype = i32
-        L.oracle_extract_window.argtypes = [vp, vp, u64, u64, vp, u32, u64, u64, u64, u64, vp, i32]
-        L.oracle_extract_window.restype = None
-        _lib = L
+        _lib = load_library(_LIB)
     return _lib
 
 

@@ -5,23 +5,32 @@
 // K_j[i] = XOR_c seed[i - c + s - 1] A_j[c] is the parity of coefficient
 // i + s - 1 of the integer product sigma(x) a_j(x), sigma = sum seed[t] x^t
 // (L = s + k - 1 terms), a_j = sum A_j[c] x^c (s terms).  That coefficient
-// is at most s < p = 15 * 2^27 + 1, so one NTT modulo p gives it exactly.  A
+// is at most s < p = 7 * 2^26 + 1, so one NTT modulo p gives it exactly.  A
 // cyclic convolution of length N = 2^e >= s + k - 1 leaves coefficients
 // s-1 .. s+k-2 free of wrap-around (no index pair reaches N + s - 1).
 //
 // Four-step layout, N = R1 x R2 with R2 = 2048 (element t = t1 R2 + t2):
-//   pass A  (one CTA per 16 columns t2 of one sub-block): load the bits,
-//           R1-point DIF NTT along t1, multiply by w_N^(k1 t2);
-//   pass B  (one CTA per rows): 2048-point DIF NTT of each row, multiply by
-//           the seed spectrum (laid out the same way, with 1/N folded in),
+//   pass A  (16 columns t2 of one sub-block per CTA): load the bits, R1-point
+//           DIF NTT along t1, multiply by w_N^(k1 t2);
+//   pass B  (two warps per row): 2048-point DIF NTT of the row, multiply by
+//           the seed spectrum (laid out the same way, 1/N folded in),
 //           2048-point inverse DIT NTT;
-//   pass A' (per 16 columns): multiply by w_N^(-k1 t2), R1-point inverse DIT
-//           NTT along t1, then the parity of every coefficient t in
+//   pass A' (16 columns per CTA): multiply by w_N^(-k1 t2), R1-point inverse
+//           DIT NTT along t1, then the parity of every coefficient t in
 //           [s-1, s+k-1) goes straight to output bit j k + t - (s-1).
 // DIF leaves bit-reversed order and DIT consumes it, so nothing is permuted.
-// Arithmetic: values in [0, p); a + b and a - b + p stay below 2^32 because
-// p < 2^31; fixed multipliers (stage twiddles, the seed spectrum) use Shoup's
-// precomputed quotient, computed twist factors use Montgomery form.
+//
+// Warp transforms: a warp holds 32 EPL values, lane l / register j at
+// position 32 j + l; stages with pair distance >= 32 run inside registers,
+// then a swizzled shared-memory transpose (word 32 j + (l ^ j)) gives each
+// lane whole rows of 32 and the distance < 32 stages run in registers too,
+// with their twiddles as constant-bank operands.
+//
+// Arithmetic (Harvey's lazy butterflies): 4p < 2^31, so DIF values stay in
+// [0, 2p) and DIT values in [0, 4p) with one conditional subtraction per
+// sum; fixed multipliers use Shoup's precomputed quotient (result in
+// [0, 2p)), computed twist factors use Montgomery form.  Values are reduced
+// to [0, p) only where a parity is taken.
 #include "common.cuh"
 #include "internal.h"
 
@@ -31,8 +40,9 @@
 namespace ex {
 namespace {
 
-constexpr uint32_t kP = 2013265921u;  // 15 * 2^27 + 1
-constexpr uint32_t kGen = 31u;        // a primitive root modulo p
+constexpr uint32_t kP = 469762049u;   // 7 * 2^26 + 1
+constexpr uint32_t k2P = 2u * kP;
+constexpr uint32_t kGen = 3u;         // a primitive root modulo p
 constexpr int kR2Log = 11;
 constexpr uint32_t kR2 = 1u << kR2Log;
 constexpr int kCW = 16;               // columns per pass-A CTA
@@ -73,6 +83,34 @@ __device__ __forceinline__ uint32_t mul_mont(uint32_t a, uint32_t b)
     const uint32_t m = (uint32_t)t * kPNegInv;
     const uint32_t u = (uint32_t)((t + (uint64_t)m * kP) >> 32);
     return min(u, u - kP);
+}
+
+// lazy forms
+__device__ __forceinline__ uint32_t red2p(uint32_t x) { return min(x, x - k2P); }  // [0,4p) -> [0,2p)
+__device__ __forceinline__ uint32_t redp(uint32_t x) { return min(x, x - kP); }    // [0,2p) -> [0,p)
+__device__ __forceinline__ uint32_t shoup_lazy(uint32_t a, uint32_t w, uint32_t wq)  // any a: [0,2p)
+{
+    return a * w - __umulhi(a, wq) * kP;
+}
+__device__ __forceinline__ uint32_t mont_lazy(uint32_t a, uint32_t b)  // a < 4p, b < 2p: [0,2p)
+{
+    const uint64_t t = (uint64_t)a * b;
+    const uint32_t m = (uint32_t)t * kPNegInv;
+    return (uint32_t)((t + (uint64_t)m * kP) >> 32);
+}
+// DIF butterfly, inputs and outputs in [0, 2p)
+__device__ __forceinline__ void bf_dif(uint32_t &x, uint32_t &y, uint32_t w, uint32_t wq)
+{
+    const uint32_t d = x - y + k2P;
+    x = red2p(x + y);
+    y = shoup_lazy(d, w, wq);
+}
+// DIT butterfly, inputs and outputs in [0, 4p)
+__device__ __forceinline__ void bf_dit(uint32_t &x, uint32_t &y, uint32_t w, uint32_t wq)
+{
+    const uint32_t a = red2p(x), t = shoup_lazy(y, w, wq);
+    x = a + t;
+    y = a - t + k2P;
 }
 
 __device__ __forceinline__ uint32_t bitrev(uint32_t x, int bits)
@@ -173,62 +211,6 @@ ntt_pass_a_kernel(const uint32_t *__restrict__ bits, uint64_t bits_stride, uint3
     for (uint32_t it = threadIdx.x; it < R1 * kCW; it += blockDim.x) {
         const uint32_t c = it % kCW, r = it / kCW;
         o[(size_t)r * kR2 + c0 + c] = x[r * kCS + c];
-    }
-}
-
-// Pass B: per row, 2048-point DIF, times spectrum (if given), and the
-// 2048-point inverse DIT (if kInverse).
-template <bool kInverse>
-__global__ void __launch_bounds__(kThreads)
-ntt_pass_b_kernel(uint32_t *__restrict__ buf, uint32_t N, uint32_t R1, const uint32_t *__restrict__ S,
-                  const uint32_t *__restrict__ Sq, Tables T)
-{
-    __shared__ __align__(16) uint32_t x[kRowsB][kR2];
-    const uint32_t g = blockIdx.y;
-    const uint32_t r0 = blockIdx.x * kRowsB;
-    uint32_t *base = buf + (size_t)g * N;
-    for (uint32_t it = threadIdx.x; it < kRowsB * kR2 / 4; it += blockDim.x) {
-        const uint32_t rr = it / (kR2 / 4), c4 = it % (kR2 / 4);
-        uint4 v = make_uint4(0, 0, 0, 0);
-        if (r0 + rr < R1) v = reinterpret_cast<const uint4 *>(base + (size_t)(r0 + rr) * kR2)[c4];
-        reinterpret_cast<uint4 *>(x[rr])[c4] = v;
-    }
-    __syncthreads();
-    for (uint32_t h = kR2 >> 1; h >= 1; h >>= 1) {  // DIF
-        const uint32_t stride = kR2 / (2 * h);
-        for (uint32_t it = threadIdx.x; it < kRowsB * (kR2 >> 1); it += blockDim.x) {
-            const uint32_t rr = it / (kR2 >> 1), b = it % (kR2 >> 1);
-            const uint32_t off = b & (h - 1), i = ((b - off) << 1) + off;
-            const uint32_t u = x[rr][i], v = x[rr][i + h];
-            const uint32_t ti = off * stride;
-            x[rr][i] = add_p(u, v);
-            x[rr][i + h] = mul_shoup(sub_p(u, v), __ldg(T.row_f + ti), __ldg(T.row_fq + ti));
-        }
-        __syncthreads();
-    }
-    if (kInverse) {
-        for (uint32_t it = threadIdx.x; it < kRowsB * kR2; it += blockDim.x) {
-            const uint32_t rr = it / kR2, c = it % kR2;
-            const size_t gi = (size_t)(r0 + rr) * kR2 + c;
-            if (r0 + rr < R1) x[rr][c] = mul_shoup(x[rr][c], __ldg(S + gi), __ldg(Sq + gi));
-        }
-        __syncthreads();
-        for (uint32_t h = 1; h < kR2; h <<= 1) {  // inverse DIT
-            const uint32_t stride = kR2 / (2 * h);
-            for (uint32_t it = threadIdx.x; it < kRowsB * (kR2 >> 1); it += blockDim.x) {
-                const uint32_t rr = it / (kR2 >> 1), b = it % (kR2 >> 1);
-                const uint32_t off = b & (h - 1), i = ((b - off) << 1) + off;
-                const uint32_t ti = off * stride;
-                const uint32_t u = x[rr][i], v = mul_shoup(x[rr][i + h], __ldg(T.row_i + ti), __ldg(T.row_iq + ti));
-                x[rr][i] = add_p(u, v);
-                x[rr][i + h] = sub_p(u, v);
-            }
-            __syncthreads();
-        }
-    }
-    for (uint32_t it = threadIdx.x; it < kRowsB * kR2 / 4; it += blockDim.x) {
-        const uint32_t rr = it / (kR2 / 4), c4 = it % (kR2 / 4);
-        if (r0 + rr < R1) reinterpret_cast<uint4 *>(base + (size_t)(r0 + rr) * kR2)[c4] = reinterpret_cast<const uint4 *>(x[rr])[c4];
     }
 }
 
@@ -349,30 +331,239 @@ __device__ __forceinline__ void warp_dit(uint32_t (&e)[EPL], const uint2 *__rest
     }
 }
 
-// Pass B, one warp per 2048-word row: DIF, times the spectrum, inverse DIT
-// (kInverse false: DIF only, for the seed spectrum).
+// ---- transposed warp transforms (32 EPL values, EPL in {32, 64}) ---------
+// distance < 32 stages: twiddle w_2h^r for r < h at (h - 1) + r, h = 1..16
+__constant__ uint2 c_low_f[31];
+__constant__ uint2 c_low_i[31];
+
+__device__ __forceinline__ uint32_t swz(uint32_t t) { return (t & ~31u) | ((t ^ (t >> 5)) & 31u); }
+
+// DIF: layout A in (e[j] = position 32 j + l), layout B out (e[32 q + i] =
+// position 32 (l + 32 q) + i).  sw: this warp's 32 EPL-word scratch.
+template <int EPL>
+__device__ __forceinline__ void dif_warp_t(uint32_t (&e)[EPL], uint32_t *sw, const uint2 *__restrict__ tw, int lane)
+{
+#pragma unroll
+    for (int hp = EPL / 2; hp >= 1; hp >>= 1) {
+#pragma unroll
+        for (int j = 0; j < EPL; ++j) {
+            if (j & hp) continue;
+            const uint2 w = __ldg(tw + (32 * hp - 1) + lane + 32 * (j & (hp - 1)));
+            bf_dif(e[j], e[j + hp], w.x, w.y);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < EPL; ++j) sw[swz(32u * j + lane)] = e[j];
+    __syncwarp();
+#pragma unroll
+    for (int q = 0; q < EPL / 32; ++q)
+#pragma unroll
+        for (int i = 0; i < 32; ++i) e[32 * q + i] = sw[swz(32u * (lane + 32 * q) + i)];
+    __syncwarp();
+#pragma unroll
+    for (int h = 16; h >= 1; h >>= 1)
+#pragma unroll
+        for (int q = 0; q < EPL / 32; ++q)
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+                if (i & h) continue;
+                const uint2 w = c_low_f[(h - 1) + (i & (h - 1))];
+                bf_dif(e[32 * q + i], e[32 * q + i + h], w.x, w.y);
+            }
+}
+
+// DIT: layout B in, layout A out (the exact reverse of dif_warp_t).
+template <int EPL>
+__device__ __forceinline__ void dit_warp_t(uint32_t (&e)[EPL], uint32_t *sw, const uint2 *__restrict__ tw, int lane)
+{
+#pragma unroll
+    for (int h = 1; h <= 16; h <<= 1)
+#pragma unroll
+        for (int q = 0; q < EPL / 32; ++q)
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+                if (i & h) continue;
+                const uint2 w = c_low_i[(h - 1) + (i & (h - 1))];
+                bf_dit(e[32 * q + i], e[32 * q + i + h], w.x, w.y);
+            }
+#pragma unroll
+    for (int q = 0; q < EPL / 32; ++q)
+#pragma unroll
+        for (int i = 0; i < 32; ++i) sw[swz(32u * (lane + 32 * q) + i)] = e[32 * q + i];
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < EPL; ++j) e[j] = sw[swz(32u * j + lane)];
+    __syncwarp();
+#pragma unroll
+    for (int hp = 1; hp <= EPL / 2; hp <<= 1) {
+#pragma unroll
+        for (int j = 0; j < EPL; ++j) {
+            if (j & hp) continue;
+            const uint2 w = __ldg(tw + (32 * hp - 1) + lane + 32 * (j & (hp - 1)));
+            bf_dit(e[j], e[j + hp], w.x, w.y);
+        }
+    }
+}
+
+// Pass B: one CTA of two warps per 2048-word row; warp w owns half
+// [1024 w, 1024 w + 1024).  The distance-1024 DIF stage is done while
+// loading (each warp reads both halves), the distance-1024 DIT stage by an
+// exchange through shared memory.  kInverse false: forward DIF only (the
+// seed spectrum), stored in layout B order.
 template <bool kInverse>
-__global__ void __launch_bounds__(256)
-ntt_rows_kernel(uint32_t *__restrict__ buf, uint32_t N, uint32_t R1, uint32_t rows, const uint32_t *__restrict__ S,
+__global__ void __launch_bounds__(64)
+ntt_rows_kernel(uint32_t *__restrict__ buf, uint32_t N, uint32_t R1, const uint32_t *__restrict__ S,
                 const uint32_t *__restrict__ Sq, Tables T)
 {
-    const int lane = threadIdx.x & 31;
-    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
-    for (uint32_t row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < rows; row += nwarps) {
-        const uint32_t g = row / R1, r = row % R1;
-        uint32_t *x = buf + (size_t)g * N + (size_t)r * kR2;
-        uint32_t e[64];
+    __shared__ __align__(16) uint32_t sw[2][1024];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const uint32_t row = blockIdx.x, g = row / R1, r = row % R1;
+    uint32_t *x = buf + (size_t)g * N + (size_t)r * kR2;
+    uint32_t e[32];
 #pragma unroll
-        for (int j = 0; j < 64; ++j) e[j] = x[lane + 32 * j];
-        warp_dif<64>(e, T.row_stage_f, lane);
-        if (kInverse) {
-            const uint32_t *sv = S + (size_t)r * kR2, *sq = Sq + (size_t)r * kR2;
-#pragma unroll
-            for (int j = 0; j < 64; ++j) e[j] = mul_shoup(e[j], __ldg(sv + lane + 32 * j), __ldg(sq + lane + 32 * j));
-            warp_dit<64>(e, T.row_stage_i, lane);
+    for (int j = 0; j < 32; ++j) {
+        const uint32_t pos = 32u * j + lane;
+        const uint32_t a = x[pos], b = x[pos + 1024];
+        if (w == 0) {
+            e[j] = red2p(a + b);
+        } else {
+            const uint2 tw = __ldg(T.row_stage_f + 1023 + pos);
+            e[j] = shoup_lazy(a - b + k2P, tw.x, tw.y);
         }
+    }
+    dif_warp_t<32>(e, sw[w], T.row_stage_f, lane);
+    const uint32_t base = 1024u * w + 32u * lane;  // layout B: e[i] at base + i
+    if (!kInverse) {
 #pragma unroll
-        for (int j = 0; j < 64; ++j) x[lane + 32 * j] = e[j];
+        for (int i = 0; i < 32; i += 4)
+            *reinterpret_cast<uint4 *>(x + base + i) = make_uint4(e[i], e[i + 1], e[i + 2], e[i + 3]);
+        return;
+    }
+    const uint32_t *sv = S + (size_t)r * kR2 + base, *sq = Sq + (size_t)r * kR2 + base;
+#pragma unroll
+    for (int i = 0; i < 32; i += 4) {
+        const uint4 a = __ldg(reinterpret_cast<const uint4 *>(sv + i)), b = __ldg(reinterpret_cast<const uint4 *>(sq + i));
+        e[i] = shoup_lazy(e[i], a.x, b.x);
+        e[i + 1] = shoup_lazy(e[i + 1], a.y, b.y);
+        e[i + 2] = shoup_lazy(e[i + 2], a.z, b.z);
+        e[i + 3] = shoup_lazy(e[i + 3], a.w, b.w);
+    }
+    dit_warp_t<32>(e, sw[w], T.row_stage_i, lane);
+    // distance-1024 DIT stage: x' = x + w y, y' = x - w y (w = w_2048^-pos)
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+        const uint32_t pos = 32u * j + lane;
+        if (w == 0) {
+            sw[0][pos] = red2p(e[j]);
+        } else {
+            const uint2 tw = __ldg(T.row_stage_i + 1023 + pos);
+            sw[1][pos] = shoup_lazy(e[j], tw.x, tw.y);
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+        const uint32_t pos = 32u * j + lane;
+        const uint32_t a = sw[0][pos], t = sw[1][pos];
+        x[pos + 1024u * w] = w == 0 ? a + t : a - t + k2P;
+    }
+}
+
+// Pass A with transposed warps (R1 = 32 EPL, EPL in {32, 64}): one warp per
+// column; the CTA's 16 columns are staged (column-major, swizzled) in shared
+// memory for coalesced row-major stores.
+template <int EPL, bool kReversed>
+__global__ void __launch_bounds__(kCW * 32)
+ntt_cols_fwd_t_kernel(const uint32_t *__restrict__ bits, uint64_t bits_stride, uint32_t len, int r1_log, uint32_t N,
+                      Tables T, uint32_t *__restrict__ buf)
+{
+    constexpr uint32_t R1 = 32u * EPL, kStr = R1 + 1;
+    extern __shared__ uint32_t xs[];  // kCW * kStr
+    const int lane = threadIdx.x & 31, c = threadIdx.x >> 5;
+    const uint32_t g = blockIdx.y, c0 = blockIdx.x * kCW, t2 = c0 + c;
+    uint32_t *col = xs + c * kStr;
+    const uint32_t *b = bits + (size_t)g * bits_stride;
+    uint32_t e[EPL];
+#pragma unroll
+    for (int j = 0; j < EPL; ++j) {
+        const uint32_t t = (32u * j + lane) * kR2 + t2;
+        uint32_t v = 0;
+        if (t < len) {
+            const uint32_t pos = kReversed ? (len - 1 - t) : t;
+            v = (__ldg(b + (pos >> 5)) >> (pos & 31u)) & 1u;
+        }
+        e[j] = v;
+    }
+    dif_warp_t<EPL>(e, col, T.col_stage_f, lane);
+    // layout B: e[32 q + i] is row r = 32 (lane + 32 q) + i, frequency bitrev(r)
+#pragma unroll
+    for (int q = 0; q < EPL / 32; ++q)
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+            const uint32_t rr = 32u * (lane + 32 * q) + i;
+            col[swz(rr)] = mont_lazy(e[32 * q + i], twist_mont(T.tw_lo_f, T.tw_hi_f, bitrev(rr, r1_log) * t2));
+        }
+    __syncthreads();
+    uint32_t *o = buf + (size_t)g * N;
+    for (uint32_t it = threadIdx.x; it < R1 * kCW; it += blockDim.x) {
+        const uint32_t cc = it % kCW, rr = it / kCW;
+        o[(size_t)rr * kR2 + c0 + cc] = xs[cc * kStr + swz(rr)];
+    }
+}
+
+// Pass A' with transposed warps: coalesced tile load, untwist, inverse DIT
+// along t1, parity of the wanted coefficients into the output.
+template <int EPL>
+__global__ void __launch_bounds__(kCW * 32)
+ntt_cols_inv_t_kernel(const uint32_t *__restrict__ buf, uint32_t N, int r1_log, Tables T, uint32_t j0, uint32_t s,
+                      uint32_t k, uint32_t *__restrict__ out)
+{
+    constexpr uint32_t R1 = 32u * EPL, kStr = R1 + 1;
+    extern __shared__ uint32_t xs[];  // kCW * kStr
+    const int lane = threadIdx.x & 31, c = threadIdx.x >> 5;
+    const uint32_t g = blockIdx.y, c0 = blockIdx.x * kCW, t2 = c0 + c;
+    uint32_t *col = xs + c * kStr;
+    const uint32_t *in = buf + (size_t)g * N;
+    for (uint32_t it = threadIdx.x; it < R1 * kCW; it += blockDim.x) {
+        const uint32_t cc = it % kCW, rr = it / kCW;
+        xs[cc * kStr + swz(rr)] = in[(size_t)rr * kR2 + c0 + cc];
+    }
+    __syncthreads();
+    uint32_t e[EPL];
+#pragma unroll
+    for (int q = 0; q < EPL / 32; ++q)
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+            const uint32_t rr = 32u * (lane + 32 * q) + i;
+            e[32 * q + i] = mont_lazy(col[swz(rr)], twist_mont(T.tw_lo_i, T.tw_hi_i, bitrev(rr, r1_log) * t2));
+        }
+    dit_warp_t<EPL>(e, col, T.col_stage_i, lane);
+    // layout A: e[j] is coefficient row t1 = 32 j + lane; store its parity
+#pragma unroll
+    for (int j = 0; j < EPL; ++j) col[swz(32u * j + lane)] = redp(red2p(e[j])) & 1u;
+    __syncthreads();
+    const uint64_t jk = (uint64_t)(j0 + g) * k;
+    const uint32_t lo_t = s - 1, hi_t = s - 1 + k;
+    for (uint32_t t1 = threadIdx.x; t1 < R1; t1 += blockDim.x) {
+        const uint32_t base = t1 * kR2 + c0;
+        if (base + kCW <= lo_t || base >= hi_t) continue;
+        uint32_t bits16 = 0;
+#pragma unroll
+        for (int cc = 0; cc < kCW; ++cc) {
+            const uint32_t t = base + cc;
+            if (t >= lo_t && t < hi_t) bits16 |= xs[cc * kStr + swz(t1)] << cc;
+        }
+        uint64_t P;
+        if (base < lo_t) {
+            bits16 >>= (lo_t - base);
+            P = jk;
+        } else {
+            P = jk + (base - lo_t);
+        }
+        if (!bits16) continue;
+        const uint32_t sh = (uint32_t)(P & 31u);
+        atomicXor(out + (P >> 5), bits16 << sh);
+        if (sh > 16 && (bits16 >> (32u - sh))) atomicXor(out + (P >> 5) + 1, bits16 >> (32u - sh));
     }
 }
 
@@ -493,61 +684,75 @@ struct NttPlan {
 
 namespace {
 
+size_t smem_generic(uint32_t R1) { return (size_t)R1 * kCS * 4; }      // R1 < 1024 kernels
+size_t smem_transposed(uint32_t R1) { return (size_t)kCW * (R1 + 1) * 4; }  // R1 >= 1024 kernels
+
 // pass A for g sub-blocks (bits stride bits_stride words) into dst
 int ntt_launch_a(const NttPlan *p, const uint32_t *bits, uint64_t bits_stride, uint32_t len, bool reversed, uint32_t g,
                  uint32_t *dst, cudaStream_t st)
 {
-    const size_t smem = (size_t)p->R1 * kCS * 4;
     const dim3 grid(kR2 / kCW, g);
-    if (p->R1 < 32) {
+    const uint32_t R1 = p->R1;
+    if (R1 < 32) {
+        const size_t smem = smem_generic(R1);
         if (reversed)
-            ntt_pass_a_kernel<true><<<grid, kThreads, smem, st>>>(bits, bits_stride, len, p->R1, p->r1_log, p->N, p->T, dst);
+            ntt_pass_a_kernel<true><<<grid, kThreads, smem, st>>>(bits, bits_stride, len, R1, p->r1_log, p->N, p->T, dst);
         else
-            ntt_pass_a_kernel<false><<<grid, kThreads, smem, st>>>(bits, bits_stride, len, p->R1, p->r1_log, p->N, p->T, dst);
+            ntt_pass_a_kernel<false><<<grid, kThreads, smem, st>>>(bits, bits_stride, len, R1, p->r1_log, p->N, p->T, dst);
         return EXTRACT_OK;
     }
-    const int epl = (int)(p->R1 / 32);
-#define EX_COLS_FWD(E)                                                                                         \
-    if (epl == E) {                                                                                            \
-        if (reversed)                                                                                          \
-            ntt_cols_fwd_kernel<E, true><<<grid, kCW * 32, smem, st>>>(bits, bits_stride, len, p->r1_log, p->N, p->T, dst); \
-        else                                                                                                   \
-            ntt_cols_fwd_kernel<E, false><<<grid, kCW * 32, smem, st>>>(bits, bits_stride, len, p->r1_log, p->N, p->T, dst); \
-        return EXTRACT_OK;                                                                                     \
+    const int epl = (int)(R1 / 32);
+#define EX_COLS_FWD(E, K, SMEM)                                                                               \
+    if (epl == E) {                                                                                           \
+        if (reversed) K<E, true><<<grid, kCW * 32, SMEM, st>>>(bits, bits_stride, len, p->r1_log, p->N, p->T, dst); \
+        else K<E, false><<<grid, kCW * 32, SMEM, st>>>(bits, bits_stride, len, p->r1_log, p->N, p->T, dst);       \
+        return EXTRACT_OK;                                                                                    \
     }
-    EX_COLS_FWD(1) EX_COLS_FWD(2) EX_COLS_FWD(4) EX_COLS_FWD(8) EX_COLS_FWD(16) EX_COLS_FWD(32) EX_COLS_FWD(64)
+    EX_COLS_FWD(1, ntt_cols_fwd_kernel, smem_generic(R1))
+    EX_COLS_FWD(2, ntt_cols_fwd_kernel, smem_generic(R1))
+    EX_COLS_FWD(4, ntt_cols_fwd_kernel, smem_generic(R1))
+    EX_COLS_FWD(8, ntt_cols_fwd_kernel, smem_generic(R1))
+    EX_COLS_FWD(16, ntt_cols_fwd_kernel, smem_generic(R1))
+    EX_COLS_FWD(32, ntt_cols_fwd_t_kernel, smem_transposed(R1))
+    EX_COLS_FWD(64, ntt_cols_fwd_t_kernel, smem_transposed(R1))
 #undef EX_COLS_FWD
-    return set_error(EXTRACT_EINTERNAL, "ntt: no column kernel for R1=%u", p->R1);
+    return set_error(EXTRACT_EINTERNAL, "ntt: no column kernel for R1=%u", R1);
 }
 
-// pass B over the g * R1 rows of dst (inverse: times S and back)
+// pass B over the g * R1 rows of dst (inverse: times S and back); one CTA of
+// two warps per row
 void ntt_launch_rows(const NttPlan *p, uint32_t *dst, uint32_t g, const uint32_t *S, const uint32_t *Sq, bool inverse,
                      cudaStream_t st)
 {
     const uint32_t rows = p->R1 * g;
-    const uint32_t grid = (uint32_t)std::max<uint64_t>(1, ceil_div(rows, 8));  // 8 warps per CTA, a warp per row
-    if (inverse) ntt_rows_kernel<true><<<grid, 256, 0, st>>>(dst, p->N, p->R1, rows, S, Sq, p->T);
-    else ntt_rows_kernel<false><<<grid, 256, 0, st>>>(dst, p->N, p->R1, rows, S, Sq, p->T);
+    if (inverse) ntt_rows_kernel<true><<<rows, 64, 0, st>>>(dst, p->N, p->R1, S, Sq, p->T);
+    else ntt_rows_kernel<false><<<rows, 64, 0, st>>>(dst, p->N, p->R1, S, Sq, p->T);
 }
 
 // pass A' for g sub-blocks, output bits of sub-blocks j0 .. j0+g-1
 int ntt_launch_a_inv(const NttPlan *p, uint32_t g, uint32_t j0, uint32_t s, uint32_t k, uint32_t *out, cudaStream_t st)
 {
-    const size_t smem = (size_t)p->R1 * kCS * 4;
     const dim3 grid(kR2 / kCW, g);
-    if (p->R1 < 32) {
-        ntt_pass_a_inv_kernel<<<grid, kThreads, smem, st>>>(p->buf, p->N, p->R1, p->r1_log, p->T, j0, s, k, out);
+    const uint32_t R1 = p->R1;
+    if (R1 < 32) {
+        ntt_pass_a_inv_kernel<<<grid, kThreads, smem_generic(R1), st>>>(p->buf, p->N, R1, p->r1_log, p->T, j0, s, k, out);
         return EXTRACT_OK;
     }
-    const int epl = (int)(p->R1 / 32);
-#define EX_COLS_INV(E)                                                                                     \
-    if (epl == E) {                                                                                        \
-        ntt_cols_inv_kernel<E><<<grid, kCW * 32, smem, st>>>(p->buf, p->N, p->r1_log, p->T, j0, s, k, out); \
-        return EXTRACT_OK;                                                                                 \
+    const int epl = (int)(R1 / 32);
+#define EX_COLS_INV(E, K, SMEM)                                                                        \
+    if (epl == E) {                                                                                    \
+        K<E><<<grid, kCW * 32, SMEM, st>>>(p->buf, p->N, p->r1_log, p->T, j0, s, k, out);            \
+        return EXTRACT_OK;                                                                             \
     }
-    EX_COLS_INV(1) EX_COLS_INV(2) EX_COLS_INV(4) EX_COLS_INV(8) EX_COLS_INV(16) EX_COLS_INV(32) EX_COLS_INV(64)
+    EX_COLS_INV(1, ntt_cols_inv_kernel, smem_generic(R1))
+    EX_COLS_INV(2, ntt_cols_inv_kernel, smem_generic(R1))
+    EX_COLS_INV(4, ntt_cols_inv_kernel, smem_generic(R1))
+    EX_COLS_INV(8, ntt_cols_inv_kernel, smem_generic(R1))
+    EX_COLS_INV(16, ntt_cols_inv_kernel, smem_generic(R1))
+    EX_COLS_INV(32, ntt_cols_inv_t_kernel, smem_transposed(R1))
+    EX_COLS_INV(64, ntt_cols_inv_t_kernel, smem_transposed(R1))
 #undef EX_COLS_INV
-    return set_error(EXTRACT_EINTERNAL, "ntt: no column kernel for R1=%u", p->R1);
+    return set_error(EXTRACT_EINTERNAL, "ntt: no column kernel for R1=%u", R1);
 }
 
 }  // namespace
@@ -575,7 +780,6 @@ void ntt_destroy(NttPlan *p)
     delete p;
 }
 
-size_t ntt_pass_a_smem(uint32_t R1) { return (size_t)R1 * kCS * 4; }
 
 // seed: realigned seed bits (bit t = seed[t]), L = s + k - 1 bits.
 int ntt_create(NttPlan **out, uint32_t m, uint32_t s, uint32_t k, const uint32_t *seed_dev, cudaStream_t st)
@@ -664,7 +868,7 @@ int ntt_create(NttPlan **out, uint32_t m, uint32_t s, uint32_t k, const uint32_t
         if ((e = cudaMalloc(&p->buf, (size_t)p->G * p->N * 4)) != cudaSuccess) { rc = cuda_error(e, "ntt buffer"); break; }
         if ((e = cudaMalloc(&p->S, (size_t)p->N * 4)) != cudaSuccess) { rc = cuda_error(e, "ntt spectrum"); break; }
         if ((e = cudaMalloc(&p->Sq, (size_t)p->N * 4)) != cudaSuccess) { rc = cuda_error(e, "ntt spectrum"); break; }
-        const size_t smem = ntt_pass_a_smem(R1);
+        const size_t smem = smem_generic(R1);
         if ((e = cudaFuncSetAttribute(ntt_pass_a_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess ||
             (e = cudaFuncSetAttribute(ntt_pass_a_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess ||
             (e = cudaFuncSetAttribute(ntt_pass_a_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) {
@@ -673,15 +877,38 @@ int ntt_create(NttPlan **out, uint32_t m, uint32_t s, uint32_t k, const uint32_t
         }
         if (R1 >= 32) {
             const int epl = (int)(R1 / 32);
-#define EX_SET_SMEM(E)                                                                                      \
-    if (epl == E) {                                                                                         \
-        e = cudaFuncSetAttribute(ntt_cols_fwd_kernel<E, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(ntt_cols_fwd_kernel<E, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(ntt_cols_inv_kernel<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+#define EX_SET_SMEM(E, KF, KI, SMEM)                                                                            \
+    if (epl == E) {                                                                                            \
+        e = cudaFuncSetAttribute(KF<E, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(SMEM));         \
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(KF<E, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(SMEM)); \
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(KI<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(SMEM)); \
     }
-            EX_SET_SMEM(1) EX_SET_SMEM(2) EX_SET_SMEM(4) EX_SET_SMEM(8) EX_SET_SMEM(16) EX_SET_SMEM(32) EX_SET_SMEM(64)
+            EX_SET_SMEM(1, ntt_cols_fwd_kernel, ntt_cols_inv_kernel, smem_generic(R1))
+            EX_SET_SMEM(2, ntt_cols_fwd_kernel, ntt_cols_inv_kernel, smem_generic(R1))
+            EX_SET_SMEM(4, ntt_cols_fwd_kernel, ntt_cols_inv_kernel, smem_generic(R1))
+            EX_SET_SMEM(8, ntt_cols_fwd_kernel, ntt_cols_inv_kernel, smem_generic(R1))
+            EX_SET_SMEM(16, ntt_cols_fwd_kernel, ntt_cols_inv_kernel, smem_generic(R1))
+            EX_SET_SMEM(32, ntt_cols_fwd_t_kernel, ntt_cols_inv_t_kernel, smem_transposed(R1))
+            EX_SET_SMEM(64, ntt_cols_fwd_t_kernel, ntt_cols_inv_t_kernel, smem_transposed(R1))
 #undef EX_SET_SMEM
             if (e != cudaSuccess) { rc = cuda_error(e, "ntt smem attribute"); break; }
+        }
+        // twiddles of the distance < 32 stages, as constant-bank operands
+        {
+            uint2 lf[31], li[31];
+            for (uint32_t hh = 1; hh <= 16; hh <<= 1) {
+                const uint32_t wf = powmod(kGen, (kP - 1) / (2 * hh)), wi = powmod(wf, kP - 2);
+                for (uint32_t r = 0; r < hh; ++r) {
+                    const uint32_t a = powmod(wf, r), b = powmod(wi, r);
+                    lf[hh - 1 + r] = make_uint2(a, shoup_q(a));
+                    li[hh - 1 + r] = make_uint2(b, shoup_q(b));
+                }
+            }
+            if ((e = cudaMemcpyToSymbol(c_low_f, lf, sizeof(lf))) != cudaSuccess ||
+                (e = cudaMemcpyToSymbol(c_low_i, li, sizeof(li))) != cudaSuccess) {
+                rc = cuda_error(e, "ntt constant twiddles");
+                break;
+            }
         }
         // seed spectrum: pass A (forward bits) + row DIF into S, then scale by 1/N
         const uint32_t L = s + k - 1;
