@@ -64,7 +64,7 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
-    ap.add_argument("--mode", choices=["block", "batch", "serve"], default="block",
+    ap.add_argument("--mode", choices=["block", "batch", "serve", "compare"], default="block",
                     help="block: one large block (default); batch: 256 uneven blocks in one persistent "
                          "launch vs one launch per block; serve: Poisson job arrivals under an HBM budget")
     ap.add_argument("--jobs", type=int, default=0, help="jobs per serving trace (default 120)")
@@ -201,26 +201,30 @@ def aggregate_rate(n_per_rank: int, world: int, ms_per_step: float) -> float:
 
 
 def launches_per_step(is_ntt, m, plan):
-    """Kernels of ours per step: the gather plus the hash (one launch direct;
-    three per group of sub-blocks for the NTT method)."""
+    """Kernels of ours per step: gather + hash (direct), or per group of
+    sub-blocks a gather and three transform passes (NTT)."""
     if not is_ntt:
         return 2
     g = int(plan.split("sub-blocks per launch group")[0].split(",")[-1])
-    return 1 + 3 * ((m + g - 1) // g)
+    return 4 * ((m + g - 1) // g)
 
 
-def ntt_roofline(n, m, s, k, hash_ms, plan):
-    """NTT path: the transform work (forward + inverse, N/2 log2 N butterflies
-    each, per sub-block) against the integer pipe; a butterfly is one Shoup
-    product (3 IMAD) plus 4 adds/mins, ~7 integer instructions."""
-    N = int(plan.split("N=")[1].split(" ")[0])
+def ntt_roofline(n, m, s, k, hash_ms, plan, sms=152):
+    """NTT path: the transform work (forward + inverse, N/2 log2 N radix-2
+    butterflies each, per sub-block) against the integer ALU pipe.  A lazy
+    butterfly is 7 integer instructions, 4 of them (adds, subtracts, min) on
+    the 64-lane ALU pipe and 3 IMAD on the FMA pipe, so the ALU pipe bounds
+    it at SMs x 64 / 4 butterflies per clock."""
     import math
+    N = int(plan.split("N=")[1].split(" ")[0])
     bfly = m * 2 * (N // 2) * math.log2(N)
     achieved = bfly / (hash_ms / 1e3) / 1e12
-    return {"bound": "alu", "achieved": achieved, "unit": "Tbutterfly/s", "peak": None, "frac": None,
-            "traffic": None, "kernel": "ntt passes (A, B, A')",
+    peak = sms * 64 / 4.0 * 2070e6 / 1e12
+    return {"bound": "alu", "achieved": achieved, "unit": "Tbutterfly/s", "peak": peak, "frac": achieved / peak,
+            "traffic": None, "kernel": "ntt_cols_fwd_t / ntt_rows / ntt_cols_inv_t (one hash)",
             "work_per_launch": "m x 2 x N/2 log2 N = %.4g radix-2 butterflies mod p (N=%d)" % (bfly, N),
-            "note": "does less work than the direct m*k*s product; reported in absolute Gbit/s"}
+            "peak_basis": "%d SMs x 64 ALU lanes / 4 ALU ops per lazy butterfly x 2070 MHz" % sms,
+            "note": "does %.0fx less work than the direct m*k*s product" % ((m * k * s / 32.0) / bfly)}
 
 
 def make_inputs(n, m, s, k, p):
@@ -302,16 +306,13 @@ def run_ours(args):
     torch.cuda.synchronize()
 
     def step():
-        ex.gather(d_in, stream=stream)
-        ex.hash(d_out, stream=stream)
+        ex.run(d_in, d_out, stream=stream)
 
     for _ in range(max(3, args.warmup)):
         step()
     torch.cuda.synchronize()
 
-    # timed region
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
-            torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    # timed region: whole runs (gather + hash, overlapped where the method allows)
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clk = ClockSampler(gpu_id_for(dev))
     clk.start()
@@ -321,19 +322,24 @@ def run_ours(args):
     torch.cuda.synchronize()
     start.record(stream)
     for i in range(args.steps):
-        a, b, c = evs[i]
-        a.record(stream)
-        ex.gather(d_in, stream=stream)
-        b.record(stream)
-        ex.hash(d_out, stream=stream)
-        c.record(stream)
+        step()
     end.record(stream)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     clocks = clk.stop()
-
     ms_total = start.elapsed_time(end)
+
+    # breakdown, outside the timed region: gather alone, then hash alone
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+            torch.cuda.Event(enable_timing=True)) for _ in range(2)]
+    for a, b, c in evs:
+        a.record(stream)
+        ex.gather(d_in, stream=stream)
+        b.record(stream)
+        ex.hash(d_out, stream=stream)
+        c.record(stream)
+    torch.cuda.synchronize()
     gather_ms = statistics.mean(a.elapsed_time(b) for a, b, _ in evs)
     hash_ms = statistics.mean(b.elapsed_time(c) for _, b, c in evs)
     ms_total = max_over_ranks(ms_total, dist, dev)
@@ -374,7 +380,7 @@ def run_ours(args):
 
     direct = None
     if is_ntt:
-        roofline = ntt_roofline(n, m, s, k, hash_ms, plan)
+        roofline = ntt_roofline(n, m, s, k, hash_ms, plan, sms)
         # the direct kernel on the same block, for the record (2 timed steps)
         exd = X.Extractor(n, m, s, k, seed_w, SAMPLING_KEY, X.EXTRACT_METHOD_DIRECT)
         exd.gather(d_in, stream=stream)
@@ -433,8 +439,10 @@ def run_ours(args):
 def run_batch(args):
     """256 independent blocks: n log-uniform in [2^20, 2^28], s in {2^16,
     2^18, 2^20}, k/s uniform in [0.05, 0.5], p uniform in [0.55, 0.95]
-    (job-shape seed 4): one persistent launch (autotuned tiles, CUDA graph)
-    against one gather + hash launch per block."""
+    (job-shape seed 4): one batch run (the NTT-method jobs on a concurrent
+    stream, the rest in one persistent launch with autotuned tiles replayed
+    from a CUDA graph) against one launch sequence per block, plus the
+    direct-only batch whose persistent kernel gives the LOP3 roofline."""
     import torch
     from paper_2308_02856_gb300 import extract as X
     from paper_2308_02856_gb300 import synth
@@ -450,38 +458,46 @@ def run_batch(args):
         outs.append(torch.empty((j["m"] * j["k"] + 31) // 32, dtype=torch.int32, device="cuda"))
     total_n = sum(j["n"] for j in jobs)
     lop3 = sum(j["m"] * j["k"] * j["s"] / 32.0 for j in jobs)
-    t0 = time.perf_counter()
-    b = X.Batch(jobs)
-    create_ms = (time.perf_counter() - t0) * 1e3
     st = torch.cuda.Stream()
-    res = {}
-    for name, fn in (("batched", b.run), ("sequential", b.run_sequential)):
-        for _ in range(max(1, args.warmup)):
+
+    def timed(fn, reps, warm):
+        for _ in range(warm):
             fn(ins, outs, stream=st)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(st)
-        for _ in range(args.steps):
+        for _ in range(reps):
             fn(ins, outs, stream=st)
         e1.record(st)
         torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / args.steps
-        res[name] = {"ms_per_step": ms, "value": total_n / (ms / 1e3) / 1e9,
-                     "tlop3_per_s": lop3 / (ms / 1e3) / 1e12}
+        ms = e0.elapsed_time(e1) / reps
+        return {"ms_per_step": ms, "value": total_n / (ms / 1e3) / 1e9,
+                "direct_equivalent_tlop3_per_s": lop3 / (ms / 1e3) / 1e12}
+
+    t0 = time.perf_counter()
+    b = X.Batch(jobs)
+    create_ms = (time.perf_counter() - t0) * 1e3
+    res = {"batched": timed(b.run, args.steps, max(1, args.warmup)),
+           "sequential": timed(b.run_sequential, args.steps, max(1, args.warmup))}
     desc = b.describe()
     b.close()
+    bd = X.Batch(jobs, X.EXTRACT_BATCH_DIRECT_ONLY)
+    res["batched_direct_only"] = timed(bd.run, 1, 1)
+    desc_d = bd.describe()
+    bd.close()
     props = torch.cuda.get_device_properties(0)
     peak = props.multi_processor_count * LOP3_LANES_PER_SM_CLK * 2070e6 / 1e12
+    ach = res["batched_direct_only"]["direct_equivalent_tlop3_per_s"]
     line = {"metric": "extracted input Gbit/s (batched)", "value": res["batched"]["value"], "unit": "Gbit/s",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": res["batched"]["ms_per_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32 (GF(2) bits)", "data": "synthetic",
             "config": {"workload": "batch256_n2^20-2^28_s{2^16,2^18,2^20}", "jobs": len(jobs),
-                       "input_bits": total_n, "lop3": lop3, "plan": desc},
-            "create_ms": create_ms, "sequential": res["sequential"],
+                       "input_bits": total_n, "direct_lop3_work": lop3, "plan": desc, "plan_direct_only": desc_d},
+            "create_ms": create_ms, "sequential": res["sequential"], "direct_only": res["batched_direct_only"],
             "speedup_vs_sequential": res["sequential"]["ms_per_step"] / res["batched"]["ms_per_step"],
-            "roofline": {"bound": "alu", "achieved": res["batched"]["tlop3_per_s"], "peak": peak,
-                         "unit": "TLOP3/s", "frac": res["batched"]["tlop3_per_s"] / peak}}
+            "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TLOP3/s", "frac": ach / peak,
+                         "kernel": "batch_hash_kernel (direct-only batch)"}}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -526,7 +542,8 @@ def run_serve(args):
             "offered_jobs_per_s": rate, "jobs": njobs, "completed": st["completed"],
             "sustained_jobs_per_s": st["completed"] / st["span_s"] if st["span_s"] else None,
             "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"], "max_ms": st["max_ms"],
-            "gbit_per_s": st["gbit_per_s"], "tlop3_per_s": work / st["span_s"] / 1e12 if st["span_s"] else None,
+            "gbit_per_s": st["gbit_per_s"],
+            "direct_equivalent_tlop3_per_s": work / st["span_s"] / 1e12 if st["span_s"] else None,
             "waves": st["waves"], "bytes_peak": st["bytes_peak"]}
         del ins, outs
         torch.cuda.empty_cache()
@@ -541,6 +558,66 @@ def run_serve(args):
     return 0
 
 
+def run_compare(args):
+    """The comparison points: on the QKD-shaped block (n = 2^32, m = 4096,
+    s = 2^20, k = 104858, p = 0.9) the library's method, the direct tiled
+    kernel and the plain per-block path (one launch per sub-block, one thread
+    per output row); and direct whole-block Toeplitz hashing (m = 1, identity
+    order) at n = 2^24, k = 2^23 and at n = 2^18, k = 2^16, tiled and plain.
+    Inputs are drawn on the GPU (the parity tests check these shapes)."""
+    import torch
+    from paper_2308_02856_gb300 import extract as X
+    from paper_2308_02856_gb300 import synth
+    torch.cuda.set_device(0)
+    X.load()
+    st = torch.cuda.Stream()
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        for _ in range(reps):
+            fn()
+        b.record(st)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    res = {}
+    n, m, s, k = 1 << 32, 4096, 1 << 20, 104858
+    d_in = synth.bernoulli_bits_device(n, 0.9, IN_SEED)
+    seed = synth.uniform_bits(s + k - 1, TOEPLITZ_SEED)
+    for name, flags, reps in (("library_choice", 0, 3), ("direct_tiled", X.EXTRACT_METHOD_DIRECT, 1)):
+        with X.Extractor(n, m, s, k, seed, SAMPLING_KEY, flags) as ex:
+            out = ex.new_output()
+            ms = timed(lambda: ex.run(d_in, out, stream=st), reps)
+            res["qkd_n2^32_" + name] = {"ms": ms, "gbit_per_s": n / (ms / 1e3) / 1e9, "plan": ex.describe()}
+            if name == "direct_tiled":
+                pms = timed(lambda: ex.run_plain(d_in, out, stream=st), 1)
+                res["qkd_n2^32_plain_per_block"] = {"ms": pms, "gbit_per_s": n / (pms / 1e3) / 1e9,
+                                                    "launches": m + 1}
+    del d_in
+    torch.cuda.empty_cache()
+    for n2, k2 in ((1 << 24, 1 << 23), (1 << 18, 1 << 16)):
+        d_in = synth.bernoulli_bits_device(n2, 0.6, IN_SEED)
+        seed = synth.uniform_bits(n2 + k2 - 1, TOEPLITZ_SEED)
+        with X.Extractor(n2, 1, n2, k2, seed, 0, X.EXTRACT_IDENTITY_PERM) as ex:
+            out = ex.new_output()
+            ms = timed(lambda: ex.run(d_in, out, stream=st), 2)
+            pms = timed(lambda: ex.run_plain(d_in, out, stream=st), 1)
+            res["direct_whole_block_n%d_k%d" % (n2, k2)] = {
+                "tiled_ms": ms, "tiled_gbit_per_s": n2 / (ms / 1e3) / 1e9, "plain_ms": pms,
+                "plain_gbit_per_s": n2 / (pms / 1e3) / 1e9, "plan": ex.describe()}
+    q = res
+    line = {"metric": "extracted input Gbit/s (comparison points)", "unit": "Gbit/s", "n_gpus": 1,
+            "value": q["qkd_n2^32_library_choice"]["gbit_per_s"], "higher_is_better": True,
+            "speedup_vs_plain_per_block": q["qkd_n2^32_plain_per_block"]["ms"] / q["qkd_n2^32_library_choice"]["ms"],
+            "speedup_direct_tiled_vs_plain": q["qkd_n2^32_plain_per_block"]["ms"] / q["qkd_n2^32_direct_tiled"]["ms"],
+            "data": "synthetic", "results": res}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
@@ -549,6 +626,8 @@ def main():
         return run_batch(args)
     if args.mode == "serve":
         return run_serve(args)
+    if args.mode == "compare":
+        return run_compare(args)
     return run_ours(args)
 
 

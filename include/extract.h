@@ -214,17 +214,23 @@ typedef struct extract_batch extract_batch;
 /* batch flags */
 #define EXTRACT_BATCH_NO_GRAPH 0x1u  /* launch the kernels directly instead of replaying a CUDA graph */
 #define EXTRACT_BATCH_NO_TUNE  0x2u  /* use the single-block heuristic tile instead of the autotuned one */
+#define EXTRACT_BATCH_DIRECT_ONLY 0x4u  /* hash every job with the direct method (no NTT jobs) */
 
 /*
  * extract_batch_create - set up njobs independent blocks (the method of
  * Sec. III.B applied to each) for hashing in one persistent launch.
  *
- * Builds every job's sampled order (synchronous), chooses every job's tile
- * shape with the autotuner (measured cost per tile variant, cached per
- * device, then the least predicted time including padding), splits word
- * ranges so the tiles balance across SMs, orders the tiles longest first,
- * and captures the per-run kernels (zero outputs, gather all jobs, persistent
- * hash) into a CUDA graph.  Device memory held: per job as extract_create.
+ * Builds every job's sampled order (synchronous) and picks each job's
+ * method: the NTT method where it is eligible and predicted faster (those
+ * jobs run one after another on a stream of the batch, concurrent with the
+ * rest), else the direct method, whose tile shape the autotuner chooses
+ * (measured cost per tile variant, cached per device, then the least
+ * predicted time including padding).  Direct jobs' word ranges are split so
+ * the tiles balance across SMs, the tiles are ordered longest first, and
+ * their per-run kernels (zero outputs, gather, persistent hash) are
+ * captured into a CUDA graph.  Device memory held: per job as
+ * extract_create (plus the NTT tables of NTT jobs and one shared NTT work
+ * buffer).
  * Errors: EINVAL (empty list, a bad job shape or flags), ENOMEM, ECUDA.
  */
 int extract_batch_create(extract_batch **out, const extract_job_desc *jobs, uint32_t njobs,

@@ -209,6 +209,8 @@ struct BatchJobHost {
     uint32_t w_pad, variant, seed_stride, nseeds, cps;
     HashPlan plain_plan;  // the single-block heuristic plan (one launch per block)
     uint32_t *perm = nullptr, *arev = nullptr, *seed = nullptr;
+    NttPlan *ntt = nullptr;  // set when this job is hashed by the NTT method
+    int table_index = -1;    // row of the device job table (direct-method jobs)
 };
 
 }  // namespace
@@ -227,6 +229,10 @@ struct extract_batch {
     uint32_t *d_counter = nullptr;
     uint64_t total_groups = 0, total_out_words = 0;
     double predicted_ms = 0;
+    uint32_t ndirect = 0, nntt = 0;
+    uint32_t *ntt_work = nullptr;  // shared by the NTT jobs, which run one after another
+    cudaStream_t aux = nullptr;    // the NTT jobs' stream, concurrent with the persistent launch
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     std::string desc;
@@ -243,7 +249,12 @@ void free_batch(extract_batch *b)
         cudaFree(j.perm);
         cudaFree(j.arev);
         cudaFree(j.seed);
+        ntt_destroy(j.ntt);
     }
+    cudaFree(b->ntt_work);
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+    if (b->ev_join) cudaEventDestroy(b->ev_join);
+    if (b->aux) cudaStreamDestroy(b->aux);
     cudaFree(b->d_jobs);
     cudaFree(b->d_tiles);
     cudaFree(b->d_counter);
@@ -266,7 +277,8 @@ void realign(const uint32_t *src, uint64_t src_words, uint64_t off, uint64_t len
 
 int launch_batch(extract_batch *b, cudaStream_t st)
 {
-    const uint32_t nj = (uint32_t)b->jobs.size();
+    const uint32_t nj = b->ndirect;
+    if (nj == 0) return EXTRACT_OK;
     const uint32_t zgrid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(ceil_div(b->total_out_words, 256),
                                                                              (uint64_t)b->num_sms * 8));
     batch_zero_kernel<<<zgrid, 256, 0, st>>>(b->d_jobs, nj, b->total_out_words, b->d_counter);
@@ -287,7 +299,7 @@ int extract_batch_create(extract_batch **out, const extract_job_desc *jobs, uint
     if (!out) return set_error(EXTRACT_EINVAL, "out is null");
     *out = nullptr;
     if (!jobs || njobs == 0) return set_error(EXTRACT_EINVAL, "empty job list");
-    if (flags & ~(EXTRACT_BATCH_NO_GRAPH | EXTRACT_BATCH_NO_TUNE))
+    if (flags & ~(EXTRACT_BATCH_NO_GRAPH | EXTRACT_BATCH_NO_TUNE | EXTRACT_BATCH_DIRECT_ONLY))
         return set_error(EXTRACT_EINVAL, "unknown batch flags 0x%x", flags);
     const uint32_t known = EXTRACT_SEED_PER_SUBBLOCK | EXTRACT_IDENTITY_PERM | (0x3fu << 8);
     for (uint32_t i = 0; i < njobs; ++i) {
@@ -331,7 +343,11 @@ int extract_batch_create(extract_batch **out, const extract_job_desc *jobs, uint
             J.variant = (uint32_t)choose_variant(d.m, d.k, J.w_pad, per_sub, tt->ns_per_chunk);
         const uint64_t tiles = ceil_div(d.k, (uint64_t)kHashWarps * 32 * variant_q(J.variant)) *
                                ceil_div(d.m, (uint64_t)variant_j(J.variant));
-        total_ns += (double)tiles * nchunks * tt->ns_per_chunk[J.variant];
+        const double direct_ns = (double)tiles * nchunks * tt->ns_per_chunk[J.variant];
+        const bool want_ntt = !(flags & EXTRACT_BATCH_DIRECT_ONLY) && !per_sub && ntt_eligible(d.s, d.k) &&
+                              predict_ntt_s(d.m, d.s, d.k) * 1e9 < direct_ns;
+        if (want_ntt) J.table_index = -2;  // marks an NTT job until its plan exists
+        else total_ns += direct_ns;
         HashPlan vp;
         vp.q = variant_q(J.variant); vp.j = variant_j(J.variant);
         vp.gx = (uint32_t)ceil_div(d.k, vp.rows());
@@ -344,6 +360,11 @@ int extract_batch_create(extract_batch **out, const extract_job_desc *jobs, uint
     std::vector<std::pair<double, BatchTileDev>> tl;
     for (uint32_t i = 0; i < njobs; ++i) {
         BatchJobHost &J = b->jobs[i];
+        if (J.table_index == -2) {
+            ++b->nntt;
+            continue;
+        }
+        J.table_index = (int)b->ndirect++;
         const uint32_t nchunks = J.w_pad / kWordChunk;
         const double cost = tt->ns_per_chunk[J.variant];
         J.cps = (uint32_t)std::max<double>(1.0, std::min<double>((double)nchunks, tile_cap_ns / cost));
@@ -353,7 +374,7 @@ int extract_batch_create(extract_batch **out, const extract_job_desc *jobs, uint
             for (uint32_t bx = 0; bx < gx; ++bx)
                 for (uint32_t c = 0; c < nchunks; c += J.cps) {
                     const uint32_t ce = std::min(nchunks, c + J.cps);
-                    tl.push_back({(ce - c) * cost, BatchTileDev{i, J.variant, bx * rows,
+                    tl.push_back({(ce - c) * cost, BatchTileDev{(uint32_t)J.table_index, J.variant, bx * rows,
                                                                 by * (uint32_t)variant_j(J.variant), c, ce}});
                 }
     }
@@ -365,8 +386,19 @@ int extract_batch_create(extract_batch **out, const extract_job_desc *jobs, uint
     cudaStream_t st = nullptr;
     do {
         if ((e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) != cudaSuccess) { rc = cuda_error(e, "stream"); break; }
-        b->table.resize(njobs);
-        uint64_t groups = 0, outw = 0;
+        b->table.resize(b->ndirect);
+        uint64_t groups = 0, outw = 0, work = 0;
+        for (uint32_t i = 0; i < njobs; ++i)
+            if (b->jobs[i].table_index == -2) work = std::max(work, ntt_work_words(jobs[i].m, jobs[i].s, jobs[i].k));
+        if (work) {
+            if ((e = cudaMalloc(&b->ntt_work, work * 4)) != cudaSuccess) { rc = cuda_error(e, "cudaMalloc(ntt work)"); break; }
+            if ((e = cudaStreamCreateWithFlags(&b->aux, cudaStreamNonBlocking)) != cudaSuccess ||
+                (e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming)) != cudaSuccess ||
+                (e = cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming)) != cudaSuccess) {
+                rc = cuda_error(e, "ntt stream");
+                break;
+            }
+        }
         for (uint32_t i = 0; i < njobs && rc == EXTRACT_OK; ++i) {
             const extract_job_desc &d = jobs[i];
             BatchJobHost &J = b->jobs[i];
@@ -385,7 +417,11 @@ int extract_batch_create(extract_batch **out, const extract_job_desc *jobs, uint
                 const uint64_t mask = kb ? ~((1ull << (64u - kb)) - 1ull) : ~0ull;
                 if ((rc = build_perm(d.n, d.sampling_key, mask, J.perm, st, b->num_sms)) != EXTRACT_OK) break;
             }
-            BatchJobDev &T = b->table[i];
+            if (J.table_index == -2) {
+                if ((rc = ntt_create(&J.ntt, d.m, d.s, d.k, J.seed, st, b->ntt_work)) != EXTRACT_OK) break;
+                continue;
+            }
+            BatchJobDev &T = b->table[J.table_index];
             T.perm = J.perm; T.in = nullptr; T.out = nullptr; T.seed = J.seed; T.arev = J.arev;
             T.groups_before = groups; T.outw_before = outw;
             T.seed_stride = J.nseeds > 1 ? J.seed_stride : 0u;
@@ -396,14 +432,15 @@ int extract_batch_create(extract_batch **out, const extract_job_desc *jobs, uint
         if (rc != EXTRACT_OK) break;
         b->total_groups = groups;
         b->total_out_words = outw;
-        if ((e = cudaMalloc(&b->d_jobs, sizeof(BatchJobDev) * njobs)) != cudaSuccess) { rc = cuda_error(e, "cudaMalloc(jobs)"); break; }
+        if ((e = cudaMalloc(&b->d_jobs, sizeof(BatchJobDev) * std::max<uint32_t>(1, b->ndirect))) != cudaSuccess) { rc = cuda_error(e, "cudaMalloc(jobs)"); break; }
         if ((e = cudaMalloc(&b->d_tiles, sizeof(BatchTileDev) * std::max<size_t>(1, tl.size()))) != cudaSuccess) { rc = cuda_error(e, "cudaMalloc(tiles)"); break; }
         if ((e = cudaMalloc(&b->d_counter, 4)) != cudaSuccess) { rc = cuda_error(e, "cudaMalloc(counter)"); break; }
         std::vector<BatchTileDev> ht(tl.size());
         for (size_t t = 0; t < tl.size(); ++t) ht[t] = tl[t].second;
         if ((e = cudaMemcpy(b->d_tiles, ht.data(), sizeof(BatchTileDev) * ht.size(), cudaMemcpyHostToDevice)) != cudaSuccess) { rc = cuda_error(e, "tiles copy"); break; }
-        if ((e = cudaMemcpy(b->d_jobs, b->table.data(), sizeof(BatchJobDev) * njobs, cudaMemcpyHostToDevice)) != cudaSuccess) { rc = cuda_error(e, "jobs copy"); break; }
-        if (!(flags & EXTRACT_BATCH_NO_GRAPH)) {
+        if (b->ndirect &&
+            (e = cudaMemcpy(b->d_jobs, b->table.data(), sizeof(BatchJobDev) * b->ndirect, cudaMemcpyHostToDevice)) != cudaSuccess) { rc = cuda_error(e, "jobs copy"); break; }
+        if (b->ndirect && !(flags & EXTRACT_BATCH_NO_GRAPH)) {
             if ((e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) { rc = cuda_error(e, "capture"); break; }
             int lrc = launch_batch(b, st);
             e = cudaStreamEndCapture(st, &b->graph);
@@ -417,11 +454,14 @@ int extract_batch_create(extract_batch **out, const extract_job_desc *jobs, uint
     if (rc != EXTRACT_OK) { free_batch(b); return rc; }
 
     int counts[kNumVariants] = {};
-    for (auto &J : b->jobs) counts[J.variant]++;
+    for (auto &J : b->jobs)
+        if (!J.ntt) counts[J.variant]++;
     char buf[1024];
-    int len = snprintf(buf, sizeof(buf), "batch: %u jobs, %u tiles, graph=%s, tuned=%s, predicted %.3f ms; variants",
-                       njobs, b->ntiles, b->exec ? "yes" : "no", (flags & EXTRACT_BATCH_NO_TUNE) ? "no" : "yes",
-                       b->predicted_ms);
+    int len = snprintf(buf, sizeof(buf),
+                       "batch: %u jobs (%u NTT on a concurrent stream, %u direct), %u tiles, graph=%s, tuned=%s, "
+                       "direct part predicted %.3f ms; variants",
+                       njobs, b->nntt, b->ndirect, b->ntiles, b->exec ? "yes" : "no",
+                       (flags & EXTRACT_BATCH_NO_TUNE) ? "no" : "yes", b->predicted_ms);
     for (int v = 0; v < kNumVariants && len < (int)sizeof(buf) - 64; ++v)
         if (counts[v])
             len += snprintf(buf + len, sizeof(buf) - len, " q%d/j%d:%d(%.1fns/chunk)", variant_q(v), variant_j(v),
@@ -439,18 +479,39 @@ int extract_batch_run(extract_batch *b, void *stream, const uint32_t *const *in_
     const size_t nj = b->jobs.size();
     for (size_t i = 0; i < nj; ++i) {
         if (!in_bits_dev[i] || !out_bits_dev[i]) return set_error(EXTRACT_EINVAL, "job %zu: null buffer", i);
-        b->table[i].in = in_bits_dev[i];
-        b->table[i].out = out_bits_dev[i];
+        const int t = b->jobs[i].table_index;
+        if (t >= 0) {
+            b->table[t].in = in_bits_dev[i];
+            b->table[t].out = out_bits_dev[i];
+        }
     }
     cudaStream_t st = (cudaStream_t)stream;
-    // pageable source: the copy is staged before the call returns, so the
-    // host table can be rewritten by the next run at once
-    EX_CUDA(cudaMemcpyAsync(b->d_jobs, b->table.data(), sizeof(BatchJobDev) * nj, cudaMemcpyHostToDevice, st));
-    if (b->exec) {
-        EX_CUDA(cudaGraphLaunch(b->exec, st));
-        return EXTRACT_OK;
+    // NTT jobs: forked onto the batch's own stream, one after another (they
+    // share one work buffer), concurrent with the persistent launch below
+    if (b->nntt) {
+        EX_CUDA(cudaEventRecord(b->ev_fork, st));
+        EX_CUDA(cudaStreamWaitEvent(b->aux, b->ev_fork, 0));
+        for (size_t i = 0; i < nj; ++i) {
+            const BatchJobHost &J = b->jobs[i];
+            if (!J.ntt) continue;
+            if (int rc = launch_gather(in_bits_dev[i], J.perm, J.m, J.s, J.w_pad, J.arev, b->aux, b->num_sms)) return rc;
+            if (int rc = ntt_hash(J.ntt, J.arev, J.w_pad, J.m, J.s, J.k, out_bits_dev[i], b->aux)) return rc;
+        }
+        EX_CUDA(cudaEventRecord(b->ev_join, b->aux));
     }
-    return launch_batch(b, st);
+    if (b->ndirect) {
+        // pageable source: the copy is staged before the call returns, so the
+        // host table can be rewritten by the next run at once
+        EX_CUDA(cudaMemcpyAsync(b->d_jobs, b->table.data(), sizeof(BatchJobDev) * b->ndirect, cudaMemcpyHostToDevice,
+                                st));
+        if (b->exec) {
+            EX_CUDA(cudaGraphLaunch(b->exec, st));
+        } else if (int rc = launch_batch(b, st)) {
+            return rc;
+        }
+    }
+    if (b->nntt) EX_CUDA(cudaStreamWaitEvent(st, b->ev_join, 0));
+    return EXTRACT_OK;
 }
 
 int extract_batch_run_sequential(extract_batch *b, void *stream, const uint32_t *const *in_bits_dev,
@@ -463,9 +524,12 @@ int extract_batch_run_sequential(extract_batch *b, void *stream, const uint32_t 
         const BatchJobHost &J = b->jobs[i];
         if (!in_bits_dev[i] || !out_bits_dev[i]) return set_error(EXTRACT_EINVAL, "job %zu: null buffer", i);
         if (int rc = launch_gather(in_bits_dev[i], J.perm, J.m, J.s, J.w_pad, J.arev, st, b->num_sms)) return rc;
-        if (int rc = launch_hash(J.plain_plan, J.seed, J.nseeds > 1 ? J.seed_stride : 0u, J.arev, J.w_pad, J.m,
-                                 J.k, out_bits_dev[i], st))
+        if (J.ntt) {
+            if (int rc = ntt_hash(J.ntt, J.arev, J.w_pad, J.m, J.s, J.k, out_bits_dev[i], st)) return rc;
+        } else if (int rc = launch_hash(J.plain_plan, J.seed, J.nseeds > 1 ? J.seed_stride : 0u, J.arev, J.w_pad,
+                                        J.m, J.k, out_bits_dev[i], st)) {
             return rc;
+        }
     }
     return EXTRACT_OK;
 }

@@ -29,6 +29,17 @@ int cuda_error(cudaError_t e, const char *what)
                      "%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
 }
 
+double predict_direct_s(uint32_t m, uint32_t k, uint32_t s)
+{
+    return (double)m * k * ((s + 31) / 32) / 19e12;
+}
+
+double predict_ntt_s(uint32_t m, uint32_t s, uint32_t k)
+{
+    const double N = (double)ntt_length(s, k);
+    return (double)m * N * (std::log2(N) + 4.0) * 0.65e-12;
+}
+
 }  // namespace ex
 
 using namespace ex;
@@ -48,24 +59,14 @@ struct extract_ctx {
     uint32_t *stage_out = nullptr;  // extract_run_host staging, ceil(m*k/32) words
     HashPlan plan;
     NttPlan *ntt = nullptr;  // set when the NTT method hashes this shape
+    cudaStream_t aux = nullptr;                       // gather stream of the overlapped NTT run
+    cudaEvent_t ev_fork = nullptr, ev_group = nullptr;
 };
 
 namespace {
 
 constexpr uint32_t kKnownFlags = EXTRACT_SEED_PER_SUBBLOCK | EXTRACT_IDENTITY_PERM | EXTRACT_METHOD_DIRECT |
                                   EXTRACT_METHOD_NTT | (0x3fu << 8);
-
-// Predicted seconds of the two methods (direct: the LOP3 rate the kernel
-// reaches; NTT: measured cost per transformed element and stage).
-double predict_direct_s(uint32_t m, uint32_t k, uint32_t s)
-{
-    return (double)m * k * ((s + 31) / 32) / 19e12;
-}
-double predict_ntt_s(uint32_t m, uint32_t s, uint32_t k)
-{
-    const double N = (double)ntt_length(s, k);
-    return (double)m * N * (std::log2(N) + 4.0) * 2.0e-12;
-}
 
 void free_ctx(extract_ctx *h)
 {
@@ -76,6 +77,9 @@ void free_ctx(extract_ctx *h)
     cudaFree(h->stage_in);
     cudaFree(h->stage_out);
     ntt_destroy(h->ntt);
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_group) cudaEventDestroy(h->ev_group);
+    if (h->aux) cudaStreamDestroy(h->aux);
     delete h;
 }
 
@@ -173,6 +177,12 @@ int extract_create(extract_ctx **out, uint64_t n, uint32_t m, uint32_t s, uint32
         int rc = ntt_create(&h->ntt, m, s, k, h->seed, st);
         cudaStreamDestroy(st);
         if (rc != EXTRACT_OK) { free_ctx(h); return rc; }
+        if ((e = cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&h->ev_group, cudaEventDisableTiming)) != cudaSuccess) {
+            free_ctx(h);
+            return cuda_error(e, "overlap stream");
+        }
     }
     if ((e = cudaMalloc(&h->arev, (size_t)m * h->w_pad * 4)) != cudaSuccess) { free_ctx(h); return cuda_error(e, "cudaMalloc(sub-blocks)"); }
     if ((e = cudaMemset(h->arev, 0, (size_t)m * h->w_pad * 4)) != cudaSuccess) { free_ctx(h); return cuda_error(e, "memset(sub-blocks)"); }
@@ -212,6 +222,11 @@ int extract_run(extract_ctx *h, void *stream, const uint32_t *in_bits_dev, uint3
 {
     if (int rc = check_ctx(h)) return rc;
     if (!out_bits_dev) return set_error(EXTRACT_EINVAL, "out_bits_dev is null");
+    if (h->ntt) {
+        if (!in_bits_dev) return set_error(EXTRACT_EINVAL, "in_bits_dev is null");
+        return ntt_run_overlapped(h->ntt, in_bits_dev, h->perm, h->arev, h->w_pad, h->m, h->s, h->k, out_bits_dev,
+                                  (cudaStream_t)stream, h->aux, h->ev_fork, h->ev_group, h->num_sms);
+    }
     if (int rc = extract_gather(h, stream, in_bits_dev)) return rc;
     return extract_hash(h, stream, out_bits_dev);
 }
@@ -273,7 +288,7 @@ int extract_describe(extract_ctx *h, char *buf, uint32_t buflen)
     if (!buf || !buflen) return set_error(EXTRACT_EINVAL, "empty buffer");
     const HashPlan &p = h->plan;
     if (h->ntt) {
-        snprintf(buf, buflen, "ntt: N=%u (%u x 2048), %u sub-blocks per launch group, prime 15*2^27+1; sms=%d",
+        snprintf(buf, buflen, "ntt: N=%u (%u x 2048), %u sub-blocks per launch group, prime 7*2^26+1; sms=%d",
                  ntt_size(h->ntt), ntt_size(h->ntt) / 2048, ntt_group(h->ntt), h->num_sms);
         return EXTRACT_OK;
     }

@@ -25,20 +25,20 @@ namespace {
 template <bool kIdentity>
 __global__ void __launch_bounds__(256)
 gather_kernel(const uint32_t *__restrict__ in, const uint32_t *__restrict__ perm, uint32_t m,
-              uint32_t s, uint32_t w_pad, uint64_t groups, uint32_t *__restrict__ arev)
+              uint32_t s, uint32_t w_pad, uint64_t groups, uint32_t *__restrict__ arev, uint64_t rank0)
 {
     const uint32_t lane = threadIdx.x & 31u;
     const uint64_t gstride = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     const uint32_t gpr = w_pad >> 5;  // 32-word groups per sub-block
     for (uint64_t g = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; g < groups;
          g += gstride)
-        gather_group<kIdentity>(in, perm, s, w_pad, (uint32_t)(g / gpr), (uint32_t)(g % gpr) * 32u, lane, arev);
+        gather_group<kIdentity>(in, perm, s, w_pad, (uint32_t)(g / gpr), (uint32_t)(g % gpr) * 32u, lane, arev, rank0);
 }
 
 }  // namespace
 
 int launch_gather(const uint32_t *in, const uint32_t *perm, uint32_t m, uint32_t s,
-                  uint32_t w_pad, uint32_t *arev, cudaStream_t st, int num_sms)
+                  uint32_t w_pad, uint32_t *arev, cudaStream_t st, int num_sms, uint64_t rank0)
 {
     if (w_pad % 32u) return set_error(EXTRACT_EINTERNAL, "gather: w_pad %u not a multiple of 32", w_pad);
     const uint64_t groups = (uint64_t)m * (w_pad / 32u);
@@ -46,9 +46,9 @@ int launch_gather(const uint32_t *in, const uint32_t *perm, uint32_t m, uint32_t
     const uint64_t want = ceil_div(groups, 8);  // 8 warps per block
     const uint32_t grid = (uint32_t)std::min<uint64_t>(want, (uint64_t)num_sms * 64);
     if (perm)
-        gather_kernel<false><<<grid, 256, 0, st>>>(in, perm, m, s, w_pad, groups, arev);
+        gather_kernel<false><<<grid, 256, 0, st>>>(in, perm, m, s, w_pad, groups, arev, rank0);
     else
-        gather_kernel<true><<<grid, 256, 0, st>>>(in, perm, m, s, w_pad, groups, arev);
+        gather_kernel<true><<<grid, 256, 0, st>>>(in, perm, m, s, w_pad, groups, arev, rank0);
     EX_LAUNCH("gather_kernel");
     return EXTRACT_OK;
 }

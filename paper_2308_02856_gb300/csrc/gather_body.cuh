@@ -8,23 +8,26 @@
 namespace ex {
 
 // Words [w0, w0 + 32) of sub-block j, stored reversed: bit b of word w is
-// in[perm[j*s + s-1-(32w+b)]] when 32w+b < s, else 0.  The warp issues 32
+// in[perm[rank0 + j*s + s-1-(32w+b)]] when 32w+b < s, else 0 (rank0: the
+// first rank of sub-block 0 of this launch).  The warp issues 32
 // coalesced 128-byte loads of the order, then 32 independent input loads
 // per lane, packs each word with a ballot and stores the 32 words with one
 // coalesced store.  kIdentity: perm is the identity (perm unused).
 template <bool kIdentity>
 __device__ __forceinline__ void gather_group(const uint32_t *__restrict__ in, const uint32_t *__restrict__ perm,
                                              uint32_t s, uint32_t w_pad, uint32_t j, uint32_t w0, uint32_t lane,
-                                             uint32_t *__restrict__ arev)
+                                             uint32_t *__restrict__ arev, uint64_t rank0 = 0)
 {
-    const uint64_t top = (uint64_t)j * s + (s - 1);  // rank of A_j[s-1]
+    const uint64_t top = rank0 + (uint64_t)j * s + (s - 1);  // rank of A_j[s-1]
     uint32_t pos[32];
 #pragma unroll
     for (int t = 0; t < 32; ++t) {
         const uint64_t cr = (uint64_t)(w0 + t) * 32u + lane;  // reversed index s-1-c
         if (cr < s) {
             const uint64_t rank = top - cr;
-            pos[t] = kIdentity ? (uint32_t)rank : __ldg(perm + rank);
+            // the order is streamed once: evict it first so that the input
+            // words, read at random, stay in L2
+            pos[t] = kIdentity ? (uint32_t)rank : __ldcs(perm + rank);
         } else {
             pos[t] = 0xffffffffu;
         }
@@ -38,7 +41,7 @@ __device__ __forceinline__ void gather_group(const uint32_t *__restrict__ in, co
         const uint32_t word = __ballot_sync(0xffffffffu, bit);
         if (lane == (uint32_t)t) mine = word;
     }
-    arev[(uint64_t)j * w_pad + w0 + lane] = mine;
+    __stcs(arev + (uint64_t)j * w_pad + w0 + lane, mine);
 }
 
 }  // namespace ex

@@ -18,8 +18,10 @@ int build_perm(uint64_t n, uint64_t sampling_key, uint64_t mask, uint32_t *perm,
 // arev[j * w_pad + w], for j < m and w < w_pad: bit b of the word is
 // in[perm[j*s + s-1-(32w+b)]] when 32w+b < s, else 0 (sub-block j reversed).
 // perm == nullptr means the identity order.
+// rank0: rank of the first position of sub-block 0 of this launch (arev
+// then holds sub-blocks starting at that rank).
 int launch_gather(const uint32_t *in, const uint32_t *perm, uint32_t m, uint32_t s,
-                  uint32_t w_pad, uint32_t *arev, cudaStream_t st, int num_sms);
+                  uint32_t w_pad, uint32_t *arev, cudaStream_t st, int num_sms, uint64_t rank0 = 0);
 
 // ---- steps 2-3: the Toeplitz product and concatenation ------------------
 struct HashPlan {
@@ -91,12 +93,33 @@ int launch_batch_hash(const BatchJobDev *jobs, const BatchTileDev *tiles, uint32
 struct NttPlan;
 bool ntt_eligible(uint32_t s, uint32_t k);  // 2^11 < s + k - 1 <= 2^22
 uint32_t ntt_length(uint32_t s, uint32_t k);
-// Builds the twiddle tables and the seed spectrum (synchronous on st).
-int ntt_create(NttPlan **out, uint32_t m, uint32_t s, uint32_t k, const uint32_t *seed_dev, cudaStream_t st);
+// Words of the work buffer a plan for (m, s, k) uses.
+uint64_t ntt_work_words(uint32_t m, uint32_t s, uint32_t k);
+// Builds the twiddle tables and the seed spectrum (synchronous on st).  work:
+// a caller-owned buffer of ntt_work_words() words shared by plans that never
+// run concurrently, or null to allocate one.
+int ntt_create(NttPlan **out, uint32_t m, uint32_t s, uint32_t k, const uint32_t *seed_dev, cudaStream_t st,
+               uint32_t *work = nullptr);
 // Hashes all m gathered sub-blocks; zeroes and fills out.
 int ntt_hash(const NttPlan *p, const uint32_t *arev, uint32_t w_pad, uint32_t m, uint32_t s, uint32_t k,
              uint32_t *out, cudaStream_t st);
+// Gather and hash with the gather of each launch group on `aux` overlapping
+// the transforms of the previous group on `st`; ordered after prior work on
+// st and fully ordered before later work on st.  ev_fork, ev_group: events
+// owned by the caller.
+int ntt_run_overlapped(const NttPlan *p, const uint32_t *in, const uint32_t *perm, uint32_t *arev, uint32_t w_pad,
+                       uint32_t m, uint32_t s, uint32_t k, uint32_t *out, cudaStream_t st, cudaStream_t aux,
+                       cudaEvent_t ev_fork, cudaEvent_t ev_group, int num_sms);
 void ntt_destroy(NttPlan *p);
+// Stream-ordered release (no device-wide synchronisation).
+void ntt_destroy_async(NttPlan *p, cudaStream_t st);
+// Device bytes a plan holds besides the shared work buffer.
+uint64_t ntt_plan_bytes(uint32_t s, uint32_t k);
+// Predicted seconds of the two hashing methods for m sub-blocks (direct: the
+// LOP3 rate the tiled kernel reaches; NTT: the measured cost per transformed
+// element and stage).
+double predict_direct_s(uint32_t m, uint32_t k, uint32_t s);
+double predict_ntt_s(uint32_t m, uint32_t s, uint32_t k);
 uint32_t ntt_group(const NttPlan *p);
 uint32_t ntt_size(const NttPlan *p);
 

@@ -130,6 +130,9 @@ struct Tables {
     // (w_2h^r, Shoup quotient) for r < h, every h = 1, 2, 4, ... < R
     const uint2 *row_stage_f, *row_stage_i;  // R = 2048
     const uint2 *col_stage_f, *col_stage_i;  // R = R1
+    // full twist tables for R1 >= 1024 (Montgomery form): entry t2 * R1 + r
+    // is w_N^(+-bitrev(r) t2)
+    const uint32_t *twist_f, *twist_i;
 };
 
 __device__ __forceinline__ uint32_t twist_mont(const uint32_t *lo, const uint32_t *hi, uint32_t x)
@@ -253,6 +256,18 @@ ntt_pass_a_inv_kernel(const uint32_t *__restrict__ buf, uint32_t N, uint32_t R1,
         const uint32_t sh = (uint32_t)(P & 31u);
         atomicXor(out + (P >> 5), bits16 << sh);
         if (sh > 16 && (bits16 >> (32u - sh))) atomicXor(out + (P >> 5) + 1, bits16 >> (32u - sh));
+    }
+}
+
+// Full twist tables: tw[t2 * R1 + r] = w_N^(+-bitrev(r) t2), Montgomery form.
+__global__ void ntt_twist_table_kernel(uint32_t *twf, uint32_t *twi, uint32_t R1, int r1_log, Tables T)
+{
+    const uint32_t total = R1 * kR2;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+        const uint32_t t2 = i / R1, r = i % R1;
+        const uint32_t e = bitrev(r, r1_log) * t2;
+        twf[i] = twist_mont(T.tw_lo_f, T.tw_hi_f, e);
+        twi[i] = twist_mont(T.tw_lo_i, T.tw_hi_i, e);
     }
 }
 
@@ -496,12 +511,17 @@ ntt_cols_fwd_t_kernel(const uint32_t *__restrict__ bits, uint64_t bits_stride, u
     }
     dif_warp_t<EPL>(e, col, T.col_stage_f, lane);
     // layout B: e[32 q + i] is row r = 32 (lane + 32 q) + i, frequency bitrev(r)
+    const uint32_t *twr = T.twist_f + (size_t)t2 * R1;
 #pragma unroll
     for (int q = 0; q < EPL / 32; ++q)
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {
+        for (int i = 0; i < 32; i += 4) {
             const uint32_t rr = 32u * (lane + 32 * q) + i;
-            col[swz(rr)] = mont_lazy(e[32 * q + i], twist_mont(T.tw_lo_f, T.tw_hi_f, bitrev(rr, r1_log) * t2));
+            const uint4 tw = __ldg(reinterpret_cast<const uint4 *>(twr + rr));
+            col[swz(rr)] = mont_lazy(e[32 * q + i], tw.x);
+            col[swz(rr + 1)] = mont_lazy(e[32 * q + i + 1], tw.y);
+            col[swz(rr + 2)] = mont_lazy(e[32 * q + i + 2], tw.z);
+            col[swz(rr + 3)] = mont_lazy(e[32 * q + i + 3], tw.w);
         }
     __syncthreads();
     uint32_t *o = buf + (size_t)g * N;
@@ -530,12 +550,17 @@ ntt_cols_inv_t_kernel(const uint32_t *__restrict__ buf, uint32_t N, int r1_log, 
     }
     __syncthreads();
     uint32_t e[EPL];
+    const uint32_t *twr = T.twist_i + (size_t)t2 * R1;
 #pragma unroll
     for (int q = 0; q < EPL / 32; ++q)
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {
+        for (int i = 0; i < 32; i += 4) {
             const uint32_t rr = 32u * (lane + 32 * q) + i;
-            e[32 * q + i] = mont_lazy(col[swz(rr)], twist_mont(T.tw_lo_i, T.tw_hi_i, bitrev(rr, r1_log) * t2));
+            const uint4 tw = __ldg(reinterpret_cast<const uint4 *>(twr + rr));
+            e[32 * q + i] = mont_lazy(col[swz(rr)], tw.x);
+            e[32 * q + i + 1] = mont_lazy(col[swz(rr + 1)], tw.y);
+            e[32 * q + i + 2] = mont_lazy(col[swz(rr + 2)], tw.z);
+            e[32 * q + i + 3] = mont_lazy(col[swz(rr + 3)], tw.w);
         }
     dit_warp_t<EPL>(e, col, T.col_stage_i, lane);
     // layout A: e[j] is coefficient row t1 = 32 j + lane; store its parity
@@ -678,7 +703,8 @@ uint32_t to_mont(uint32_t w) { return (uint32_t)(((uint64_t)w << 32) % kP); }
 struct NttPlan {
     int e = 0, r1_log = 0;
     uint32_t N = 0, R1 = 0, G = 0;
-    uint32_t *buf = nullptr, *S = nullptr, *Sq = nullptr, *tables = nullptr;
+    uint32_t *buf = nullptr, *S = nullptr, *Sq = nullptr, *tables = nullptr, *twist = nullptr;
+    bool own_buf = true;
     Tables T{};
 };
 
@@ -770,19 +796,45 @@ uint32_t ntt_length(uint32_t s, uint32_t k)
     return N;
 }
 
+void ntt_destroy_async(NttPlan *p, cudaStream_t st)
+{
+    if (!p) return;
+    if (p->own_buf && p->buf) cudaFreeAsync(p->buf, st);
+    if (p->S) cudaFreeAsync(p->S, st);
+    if (p->Sq) cudaFreeAsync(p->Sq, st);
+    if (p->tables) cudaFreeAsync(p->tables, st);
+    if (p->twist) cudaFreeAsync(p->twist, st);
+    delete p;
+}
+
 void ntt_destroy(NttPlan *p)
 {
     if (!p) return;
-    cudaFree(p->buf);
+    if (p->own_buf) cudaFree(p->buf);
     cudaFree(p->S);
     cudaFree(p->Sq);
     cudaFree(p->tables);
+    cudaFree(p->twist);
     delete p;
 }
 
 
 // seed: realigned seed bits (bit t = seed[t]), L = s + k - 1 bits.
-int ntt_create(NttPlan **out, uint32_t m, uint32_t s, uint32_t k, const uint32_t *seed_dev, cudaStream_t st)
+uint64_t ntt_plan_bytes(uint32_t s, uint32_t k)
+{
+    const uint64_t N = ntt_length(s, k);
+    return 4 * N * 4 + 64 * 1024;  // spectrum + quotients, twist tables, stage tables
+}
+
+uint64_t ntt_work_words(uint32_t m, uint32_t s, uint32_t k)
+{
+    const uint64_t N = ntt_length(s, k);
+    const uint64_t G = std::max<uint64_t>(1, std::min<uint64_t>(m, (16ull << 20) / N));
+    return G * N;
+}
+
+int ntt_create(NttPlan **out, uint32_t m, uint32_t s, uint32_t k, const uint32_t *seed_dev, cudaStream_t st,
+               uint32_t *work)
 {
     *out = nullptr;
     if (!ntt_eligible(s, k)) return set_error(EXTRACT_EINVAL, "NTT path needs 2^11 < s+k-1 <= 2^22");
@@ -851,8 +903,9 @@ int ntt_create(NttPlan **out, uint32_t m, uint32_t s, uint32_t k, const uint32_t
     int rc = EXTRACT_OK;
     do {
         cudaError_t e;
-        if ((e = cudaMalloc(&p->tables, h.size() * 4)) != cudaSuccess) { rc = cuda_error(e, "ntt tables"); break; }
-        if ((e = cudaMemcpy(p->tables, h.data(), h.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess) { rc = cuda_error(e, "ntt tables copy"); break; }
+        if ((e = cudaMallocAsync(&p->tables, h.size() * 4, st)) != cudaSuccess) { rc = cuda_error(e, "ntt tables"); break; }
+        if ((e = cudaMemcpyAsync(p->tables, h.data(), h.size() * 4, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(st)) != cudaSuccess) { rc = cuda_error(e, "ntt tables copy"); break; }
         const uint32_t *t = p->tables;
         p->T.col_f = t + o_col_f; p->T.col_fq = t + o_col_f + ch;
         p->T.col_i = t + o_col_i; p->T.col_iq = t + o_col_i + ch;
@@ -865,9 +918,15 @@ int ntt_create(NttPlan **out, uint32_t m, uint32_t s, uint32_t k, const uint32_t
         p->T.row_stage_i = reinterpret_cast<const uint2 *>(t + o_rs_i);
         p->T.col_stage_f = reinterpret_cast<const uint2 *>(t + o_cs_f);
         p->T.col_stage_i = reinterpret_cast<const uint2 *>(t + o_cs_i);
-        if ((e = cudaMalloc(&p->buf, (size_t)p->G * p->N * 4)) != cudaSuccess) { rc = cuda_error(e, "ntt buffer"); break; }
-        if ((e = cudaMalloc(&p->S, (size_t)p->N * 4)) != cudaSuccess) { rc = cuda_error(e, "ntt spectrum"); break; }
-        if ((e = cudaMalloc(&p->Sq, (size_t)p->N * 4)) != cudaSuccess) { rc = cuda_error(e, "ntt spectrum"); break; }
+        if (work) {
+            p->buf = work;
+            p->own_buf = false;
+        } else if ((e = cudaMallocAsync(&p->buf, (size_t)p->G * p->N * 4, st)) != cudaSuccess) {
+            rc = cuda_error(e, "ntt buffer");
+            break;
+        }
+        if ((e = cudaMallocAsync(&p->S, (size_t)p->N * 4, st)) != cudaSuccess) { rc = cuda_error(e, "ntt spectrum"); break; }
+        if ((e = cudaMallocAsync(&p->Sq, (size_t)p->N * 4, st)) != cudaSuccess) { rc = cuda_error(e, "ntt spectrum"); break; }
         const size_t smem = smem_generic(R1);
         if ((e = cudaFuncSetAttribute(ntt_pass_a_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess ||
             (e = cudaFuncSetAttribute(ntt_pass_a_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess ||
@@ -892,6 +951,13 @@ int ntt_create(NttPlan **out, uint32_t m, uint32_t s, uint32_t k, const uint32_t
             EX_SET_SMEM(64, ntt_cols_fwd_t_kernel, ntt_cols_inv_t_kernel, smem_transposed(R1))
 #undef EX_SET_SMEM
             if (e != cudaSuccess) { rc = cuda_error(e, "ntt smem attribute"); break; }
+        }
+        if (R1 >= 1024) {
+            if ((e = cudaMallocAsync(&p->twist, (size_t)2 * p->N * 4, st)) != cudaSuccess) { rc = cuda_error(e, "ntt twist tables"); break; }
+            p->T.twist_f = p->twist;
+            p->T.twist_i = p->twist + p->N;
+            ntt_twist_table_kernel<<<(uint32_t)std::min<uint64_t>(ceil_div(p->N, 256), 8192), 256, 0, st>>>(
+                p->twist, p->twist + p->N, R1, p->r1_log, p->T);
         }
         // twiddles of the distance < 32 stages, as constant-bank operands
         {
@@ -933,6 +999,28 @@ int ntt_hash(const NttPlan *p, const uint32_t *arev, uint32_t w_pad, uint32_t m,
     for (uint32_t j0 = 0; j0 < m; j0 += p->G) {
         const uint32_t g = std::min(p->G, m - j0);
         if (int rc = ntt_launch_a(p, arev + (size_t)j0 * w_pad, w_pad, s, true, g, p->buf, st)) return rc;
+        ntt_launch_rows(p, p->buf, g, p->S, p->Sq, true, st);
+        if (int rc = ntt_launch_a_inv(p, g, j0, s, k, out, st)) return rc;
+    }
+    EX_LAUNCH("ntt kernels");
+    return EXTRACT_OK;
+}
+
+int ntt_run_overlapped(const NttPlan *p, const uint32_t *in, const uint32_t *perm, uint32_t *arev, uint32_t w_pad,
+                       uint32_t m, uint32_t s, uint32_t k, uint32_t *out, cudaStream_t st, cudaStream_t aux,
+                       cudaEvent_t ev_fork, cudaEvent_t ev_group, int num_sms)
+{
+    EX_CUDA(cudaEventRecord(ev_fork, st));
+    EX_CUDA(cudaStreamWaitEvent(aux, ev_fork, 0));
+    EX_CUDA(cudaMemsetAsync(out, 0, ceil_div((uint64_t)m * k, 32) * 4, st));
+    for (uint32_t j0 = 0; j0 < m; j0 += p->G) {
+        const uint32_t g = std::min(p->G, m - j0);
+        uint32_t *ar = arev + (size_t)j0 * w_pad;
+        if (int rc = launch_gather(in, perm, g, s, w_pad, ar, aux, num_sms, (uint64_t)j0 * s)) return rc;
+        // each wait binds to the record just before it, so one event serves every group
+        EX_CUDA(cudaEventRecord(ev_group, aux));
+        EX_CUDA(cudaStreamWaitEvent(st, ev_group, 0));
+        if (int rc = ntt_launch_a(p, ar, w_pad, s, true, g, p->buf, st)) return rc;
         ntt_launch_rows(p, p->buf, g, p->S, p->Sq, true, st);
         if (int rc = ntt_launch_a_inv(p, g, j0, s, k, out, st)) return rc;
     }

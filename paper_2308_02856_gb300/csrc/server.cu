@@ -63,6 +63,10 @@ struct SJob {
     JobState state = kQueued;
     int rc = EXTRACT_OK;
     cudaEvent_t setup_ev = nullptr;
+    // NTT method: hashed whole on the NTT lane
+    bool use_ntt = false, hashed = false;
+    NttPlan *ntt = nullptr;
+    cudaEvent_t done_ev = nullptr;
     Clock::time_point t_submit, t_done;
 };
 using JobPtr = std::shared_ptr<SJob>;
@@ -123,6 +127,10 @@ struct extract_server {
     uint64_t next_ticket = 1;
     cudaStream_t setup_st = nullptr;
     Wave waves[kWaveSlots];
+    // NTT lane: one job at a time (shared work buffer), concurrent with the waves
+    cudaStream_t ntt_st = nullptr;
+    uint32_t *ntt_work = nullptr;
+    JobPtr ntt_cur;
     std::thread sched_thread, setup_thread;
     // statistics
     uint64_t submitted = 0, admitted = 0, completed = 0, failed = 0, rejected = 0, nwaves = 0;
@@ -150,6 +158,8 @@ int setup_job(extract_server *S, SJob &J)
     }
     if (int rc = launch_gather(J.in, J.perm, J.m, J.s, J.w_pad, J.arev, st, S->sms)) return rc;
     EX_CUDA(cudaMemsetAsync(J.out, 0, ceil_div((uint64_t)J.m * J.k, 32) * 4, st));
+    if (J.use_ntt)  // tables and the seed spectrum (synchronous on the setup stream)
+        if (int rc = ntt_create(&J.ntt, J.m, J.s, J.k, J.seed, st, S->ntt_work)) return rc;
     // the order is only needed by the gather: give its memory back now
     if (J.perm) {
         EX_CUDA(cudaFreeAsync(J.perm, st));
@@ -194,6 +204,10 @@ void release_job(extract_server *S, SJob &J)
     if (J.arev) cudaFreeAsync(J.arev, st);
     if (J.seed) cudaFreeAsync(J.seed, st);
     J.perm = J.arev = J.seed = nullptr;
+    if (J.ntt) {
+        ntt_destroy_async(J.ntt, st);
+        J.ntt = nullptr;
+    }
     S->in_use -= J.bytes;
 }
 
@@ -246,7 +260,22 @@ bool schedule_step(extract_server *S)
             }
             else if (e != cudaErrorNotReady) { j->rc = cuda_error(e, "setup"); j->state = kFailed; }
         }
-        const bool finished = j->state == kReady && j->next_tile == j->tiles.size() && j->outstanding_waves == 0;
+        bool finished;
+        if (j->use_ntt) {
+            finished = false;
+            if (j->state == kReady && j->hashed) {
+                const cudaError_t e = cudaEventQuery(j->done_ev);
+                if (e == cudaSuccess) {
+                    finished = true;
+                } else if (e != cudaErrorNotReady) {
+                    j->rc = cuda_error(e, "ntt job");
+                    j->state = kFailed;
+                }
+            }
+            if ((finished || j->state == kFailed) && S->ntt_cur == j) S->ntt_cur.reset();
+        } else {
+            finished = j->state == kReady && j->next_tile == j->tiles.size() && j->outstanding_waves == 0;
+        }
         const bool dead = j->state == kFailed && j->outstanding_waves == 0;
         if (finished || dead) {
             release_job(S, *j);
@@ -267,7 +296,27 @@ bool schedule_step(extract_server *S)
         }
         ++i;
     }
-    // 4. a new wave on a free slot: shortest remaining work first
+    // 4. the NTT lane: the ready NTT job with the least predicted time
+    if (!S->ntt_cur) {
+        JobPtr best;
+        for (JobPtr &j : S->active)
+            if (j->use_ntt && j->state == kReady && !j->hashed && (!best || j->remaining_ns < best->remaining_ns))
+                best = j;
+        if (best) {
+            int rc = ntt_hash(best->ntt, best->arev, best->w_pad, best->m, best->s, best->k, best->out, S->ntt_st);
+            cudaError_t e = rc == EXTRACT_OK ? cudaEventRecord(best->done_ev, S->ntt_st) : cudaSuccess;
+            if (rc == EXTRACT_OK && e != cudaSuccess) rc = cuda_error(e, "ntt event");
+            best->hashed = true;
+            if (rc != EXTRACT_OK) {
+                best->rc = rc;
+                best->state = kFailed;
+            } else {
+                S->ntt_cur = best;
+            }
+            progress = true;
+        }
+    }
+    // 5. a new wave on a free slot: shortest remaining work first
     for (Wave &w : S->waves) {
         if (w.busy) continue;
         std::vector<JobPtr> ready;
@@ -352,8 +401,12 @@ void destroy_server(extract_server *S)
         if (w.st) cudaStreamDestroy(w.st);
     }
     if (S->setup_st) cudaStreamDestroy(S->setup_st);
-    for (auto &kv : S->by_ticket)
+    if (S->ntt_st) cudaStreamDestroy(S->ntt_st);
+    cudaFree(S->ntt_work);
+    for (auto &kv : S->by_ticket) {
         if (kv.second->setup_ev) cudaEventDestroy(kv.second->setup_ev);
+        if (kv.second->done_ev) cudaEventDestroy(kv.second->done_ev);
+    }
     delete S;
 }
 
@@ -381,6 +434,9 @@ int extract_server_create(extract_server **out, uint64_t hbm_budget_bytes, uint3
     int rc = EXTRACT_OK;
     do {
         if ((e = cudaStreamCreateWithFlags(&S->setup_st, cudaStreamNonBlocking)) != cudaSuccess) { rc = cuda_error(e, "stream"); break; }
+        if ((e = cudaStreamCreateWithFlags(&S->ntt_st, cudaStreamNonBlocking)) != cudaSuccess) { rc = cuda_error(e, "stream"); break; }
+        // the largest NTT work buffer any job can need (2^22-point transforms)
+        if ((e = cudaMalloc(&S->ntt_work, ntt_work_words(1u << 16, 1u << 21, 1u << 21) * 4)) != cudaSuccess) { rc = cuda_error(e, "ntt work"); break; }
         for (Wave &w : S->waves) {
             if ((e = cudaStreamCreateWithFlags(&w.st, cudaStreamNonBlocking)) != cudaSuccess) { rc = cuda_error(e, "stream"); break; }
             if ((e = cudaEventCreateWithFlags(&w.ev, cudaEventDisableTiming)) != cudaSuccess) { rc = cuda_error(e, "event"); break; }
@@ -412,6 +468,14 @@ int extract_server_submit(extract_server *S, const extract_job_desc *d, const ui
     const bool per_sub = (d->flags & EXTRACT_SEED_PER_SUBBLOCK) != 0;
     j->w_pad = (uint32_t)round_up(ceil_div(d->s, 32), kWordChunk);
     j->variant = (uint32_t)choose_variant(d->m, d->k, j->w_pad, per_sub, S->costs);
+    {
+        const double tiles = (double)ceil_div(d->k, variant_rows((int)j->variant)) *
+                             (double)ceil_div(d->m, (uint32_t)variant_j((int)j->variant));
+        const double direct_ns = tiles * (j->w_pad / kWordChunk) * S->costs[j->variant];
+        const double ntt_ns = predict_ntt_s(d->m, d->s, d->k) * 1e9;
+        j->use_ntt = !per_sub && ntt_eligible(d->s, d->k) && ntt_ns < direct_ns;
+        if (j->use_ntt) j->remaining_ns = ntt_ns;
+    }
     HashPlan vp;
     vp.q = variant_q(j->variant);
     vp.j = variant_j(j->variant);
@@ -431,14 +495,14 @@ int extract_server_submit(extract_server *S, const extract_job_desc *d, const ui
     // budget charge: order (freed early, still charged) + sub-blocks + seed + the job's input and output
     const uint64_t order_b = (d->flags & EXTRACT_IDENTITY_PERM) ? 0 : d->n * 4;
     j->bytes = order_b + (uint64_t)d->m * j->w_pad * 4 + (uint64_t)j->seed_host.size() * 4 + ceil_div(d->n, 32) * 4 +
-               ceil_div((uint64_t)d->m * d->k, 32) * 4;
+               ceil_div((uint64_t)d->m * d->k, 32) * 4 + (j->use_ntt ? ntt_plan_bytes(d->s, d->k) : 0);
     // tiles: every (row tile, sub-block tile, word range), each about tile_cap of one SM
     const uint32_t rows = vp.rows(), J = (uint32_t)vp.j, nchunks = j->w_pad / kWordChunk;
     const double ns_chunk = S->costs[j->variant];  // GPU ns per CTA-chunk
     const uint32_t cps = (uint32_t)std::max<double>(1.0, std::min<double>(nchunks,
                                                         S->tile_cap_sm_ns / (ns_chunk * S->sms)));
     const uint32_t gx = (uint32_t)ceil_div(d->k, rows), gy = (uint32_t)ceil_div(d->m, J);
-    for (uint32_t by = 0; by < gy; ++by)
+    for (uint32_t by = 0; by < gy && !j->use_ntt; ++by)
         for (uint32_t bx = 0; bx < gx; ++bx)
             for (uint32_t c = 0; c < nchunks; c += cps) {
                 const uint32_t ce = std::min(nchunks, c + cps);
@@ -447,12 +511,21 @@ int extract_server_submit(extract_server *S, const extract_job_desc *d, const ui
                 j->remaining_ns += (ce - c) * ns_chunk;
             }
     cudaError_t e = cudaEventCreateWithFlags(&j->setup_ev, cudaEventDisableTiming);
-    if (e != cudaSuccess) return cuda_error(e, "event");
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&j->done_ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        if (j->setup_ev) cudaEventDestroy(j->setup_ev);
+        return cuda_error(e, "event");
+    }
     std::lock_guard<std::mutex> lk(S->mu);
-    if (S->stop) { cudaEventDestroy(j->setup_ev); return set_error(EXTRACT_EBUSY, "server is stopping"); }
+    if (S->stop) {
+        cudaEventDestroy(j->setup_ev);
+        cudaEventDestroy(j->done_ev);
+        return set_error(EXTRACT_EBUSY, "server is stopping");
+    }
     if (j->bytes > S->budget) {
         ++S->rejected;
         cudaEventDestroy(j->setup_ev);
+        cudaEventDestroy(j->done_ev);
         return set_error(EXTRACT_EBUDGET, "job needs %llu bytes, budget is %llu", (unsigned long long)j->bytes,
                          (unsigned long long)S->budget);
     }
@@ -481,6 +554,7 @@ int extract_server_wait(extract_server *S, uint64_t ticket, uint32_t timeout_ms,
     if (latency_ms) *latency_ms = std::chrono::duration<double, std::milli>(j->t_done - j->t_submit).count();
     const int rc = j->rc;
     if (j->setup_ev) { cudaEventDestroy(j->setup_ev); j->setup_ev = nullptr; }
+    if (j->done_ev) { cudaEventDestroy(j->done_ev); j->done_ev = nullptr; }
     S->by_ticket.erase(it);
     if (j->state == kFailed) return set_error(rc ? rc : EXTRACT_EINTERNAL, "ticket %llu failed",
                                               (unsigned long long)ticket);

@@ -47,6 +47,7 @@ EXPORTED = [
 
 EXTRACT_BATCH_NO_GRAPH = 0x1
 EXTRACT_BATCH_NO_TUNE = 0x2
+EXTRACT_BATCH_DIRECT_ONLY = 0x4
 
 
 class extract_job_desc(ctypes.Structure):

@@ -155,3 +155,31 @@ def test_batch_of_256_uneven_blocks_full_size():
     for i in (order[0], order[1], order[-1]):
         j = jobs[i]
         _check_rows_against_oracle(j, ins[i], _host(outs[i]), sorted({0, j["m"] - 1, j["m"] // 2}), 24, rng)
+
+
+def test_batch_mixes_ntt_and_direct_jobs():
+    """Large-s jobs go to the NTT method on a concurrent stream, small ones
+    to the persistent direct launch; every output equals the direct-only
+    batch's and the oracle's (sampled rows)."""
+    shapes = []
+    for i, (n, s, k) in enumerate([(1 << 20, 1 << 18, 1 << 17), (1 << 14, 1 << 12, 500), (1 << 21, 1 << 20, 1 << 19),
+                                   (3 << 18, 1 << 18, 70_001), (1 << 16, 1 << 13, 4000), (1 << 20, 1 << 20, 104858)]):
+        shapes.append({"n": n, "m": n // s, "s": s, "k": k, "flags": 0, "p": 0.6 + 0.05 * i,
+                       "in_seed": 500 + i, "seed_seed": 600 + i, "key": 700 + i})
+    jobs, ins = _materialise(shapes)
+    d_in = [_dev(w) for w in ins]
+    with X.Batch(jobs) as b, X.Batch(jobs, X.EXTRACT_BATCH_DIRECT_ONLY) as bd:
+        desc = b.describe()
+        assert "NTT" in desc and "(0 NTT" not in desc, desc
+        assert "(0 NTT" in bd.describe()
+        outs, ref = _outs(jobs), _outs(jobs, fill=3)
+        for _ in range(2):
+            b.run(d_in, outs)
+        bd.run(d_in, ref)
+        torch.cuda.synchronize()
+        for i in range(len(jobs)):
+            assert torch.equal(outs[i], ref[i]), "job %d" % i
+    rng = np.random.default_rng(2)
+    for i in (0, 2, 5):
+        j = jobs[i]
+        _check_rows_against_oracle(j, ins[i], _host(outs[i]), sorted({0, j["m"] - 1}), 16, rng)

@@ -156,3 +156,25 @@ def test_concurrent_submitters_and_bad_jobs():
     for j, d, o in zip(jobs, ins, outs):
         with X.Extractor(j["n"], j["m"], j["s"], j["k"], j["seed"], j["key"]) as ex:
             assert np.array_equal(_host(o), _host(ex.run(d)))
+
+
+def test_server_ntt_lane_and_waves_give_the_same_bits():
+    """Large-s jobs take the NTT lane, small ones the direct waves; all run
+    at once and every output equals extract_run's."""
+    shapes = synth.job_shapes(16, 81, 2 ** 18, 2 ** 22, s_set=(1 << 12, 1 << 18, 1 << 20))
+    jobs, ins = [], []
+    for j in shapes:
+        j = dict(j)
+        j["seed"] = synth.uniform_bits(j["s"] + j["k"] - 1, j["seed_seed"])
+        jobs.append(j)
+        ins.append(_dev(synth.bernoulli_bits(j["n"], j["p"], j["in_seed"])))
+    assert any(j["s"] >= (1 << 18) for j in jobs) and any(j["s"] < (1 << 18) for j in jobs)
+    outs = [_out(j) for j in jobs]
+    with X.Server(16 << 30, max_slots=16, wave_us=500) as srv:
+        tickets = [srv.submit(j, d, o) for j, d, o in zip(jobs, ins, outs)]
+        for t in tickets:
+            srv.wait(t)
+        assert srv.stats()["completed"] == len(jobs)
+    for j, d, o in zip(jobs, ins, outs):
+        with X.Extractor(j["n"], j["m"], j["s"], j["k"], j["seed"], j["key"], X.EXTRACT_METHOD_DIRECT) as ex:
+            assert np.array_equal(_host(o), _host(ex.run(d)))
