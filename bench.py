@@ -217,12 +217,14 @@ def ntt_roofline(n, m, s, k, hash_ms, plan, sms=152):
     it at SMs x 64 / 4 butterflies per clock."""
     import math
     N = int(plan.split("N=")[1].split(" ")[0])
-    bfly = m * 2 * (N // 2) * math.log2(N)
+    P = int(plan.split("P=")[1].split(" ")[0]) if "P=" in plan else 1
+    bfly = m * (P + 1) * (N // 2) * math.log2(N)
     achieved = bfly / (hash_ms / 1e3) / 1e12
     peak = sms * 64 / 4.0 * 2070e6 / 1e12
     return {"bound": "alu", "achieved": achieved, "unit": "Tbutterfly/s", "peak": peak, "frac": achieved / peak,
             "traffic": None, "kernel": "ntt_cols_fwd_t / ntt_rows / ntt_cols_inv_t (one hash)",
-            "work_per_launch": "m x 2 x N/2 log2 N = %.4g radix-2 butterflies mod p (N=%d)" % (bfly, N),
+            "work_per_launch": "m x (P+1) x N/2 log2 N = %.4g radix-2 butterflies mod p (N=%d, P=%d pieces "
+                               "per sub-block)" % (bfly, N, P),
             "peak_basis": "%d SMs x 64 ALU lanes / 4 ALU ops per lazy butterfly x 2070 MHz" % sms,
             "note": "does %.0fx less work than the direct m*k*s product" % ((m * k * s / 32.0) / bfly)}
 

@@ -63,12 +63,18 @@ extern "C" {
 /* Hashing method.  Default (neither flag): the library picks the faster of
    the two exact methods for the shape.  EXTRACT_METHOD_DIRECT forces the
    direct GF(2) product (bit-sliced AND/XOR, work m*k*s); EXTRACT_METHOD_NTT
-   forces the number-theoretic-transform middle product (work about
-   m * N log N with N the power of two >= s+k-1), which needs a shared seed
-   and 2^11 < s+k-1 <= 2^22 (EXTRACT_EINVAL otherwise).  Both give the same
-   bits. */
+   forces the number-theoretic-transform middle product modulo the prime
+   7*2^26+1.  It splits each sub-block into P = 2^l pieces of h bits (h = s
+   for P = 1, else ceil(s/P) rounded up to a multiple of 32) and costs P + 1
+   transforms of the power of two N >= h+k-1 per sub-block; it needs a
+   shared seed, s+k-1 > 2^11, s < 7*2^26+1 and N <= 2^22 for some P <= 16
+   (EXTRACT_EINVAL otherwise).  Both methods give the same bits. */
 #define EXTRACT_METHOD_DIRECT     0x4u
 #define EXTRACT_METHOD_NTT        0x8u
+/* NTT method: use P = 2^l pieces per sub-block (l = 0 .. 4) instead of the
+   split with the least predicted work; EXTRACT_EINVAL if that split has no
+   transform length <= 2^22 or leaves a piece empty.  Tuning and test hook. */
+#define EXTRACT_NTT_SPLIT(l)      ((((uint32_t)(l) + 1u) & 0x7u) << 16)
 /* Test hook: keep only the top b (1..63) bits of every sampling label, which
    forces many equal labels so that the index tie-break is exercised. */
 #define EXTRACT_KEY_BITS(b)       ((((uint32_t)(b)) & 0x3fu) << 8)

@@ -211,6 +211,18 @@ struct BatchJobHost {
     uint32_t *perm = nullptr, *arev = nullptr, *seed = nullptr;
     NttPlan *ntt = nullptr;  // set when this job is hashed by the NTT method
     int table_index = -1;    // row of the device job table (direct-method jobs)
+    int lane = -1;           // NTT lane of an NTT-method job
+};
+
+// NTT jobs run on a few concurrent lanes (stream + work buffer each), so
+// small transforms fill the GPU together; jobs are assigned longest first
+// to the least loaded lane.
+constexpr int kNttLanes = 4;
+struct NttLane {
+    cudaStream_t st = nullptr;
+    uint32_t *work = nullptr;
+    cudaEvent_t join = nullptr;
+    double load_ns = 0;
 };
 
 }  // namespace
@@ -230,9 +242,9 @@ struct extract_batch {
     uint64_t total_groups = 0, total_out_words = 0;
     double predicted_ms = 0;
     uint32_t ndirect = 0, nntt = 0;
-    uint32_t *ntt_work = nullptr;  // shared by the NTT jobs, which run one after another
-    cudaStream_t aux = nullptr;    // the NTT jobs' stream, concurrent with the persistent launch
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    NttLane lanes[kNttLanes];      // concurrent with the persistent launch
+    std::vector<uint32_t> ntt_order;  // NTT jobs, longest predicted first
+    cudaEvent_t ev_fork = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     std::string desc;
@@ -251,10 +263,12 @@ void free_batch(extract_batch *b)
         cudaFree(j.seed);
         ntt_destroy(j.ntt);
     }
-    cudaFree(b->ntt_work);
+    for (NttLane &L : b->lanes) {
+        cudaFree(L.work);
+        if (L.join) cudaEventDestroy(L.join);
+        if (L.st) cudaStreamDestroy(L.st);
+    }
     if (b->ev_fork) cudaEventDestroy(b->ev_fork);
-    if (b->ev_join) cudaEventDestroy(b->ev_join);
-    if (b->aux) cudaStreamDestroy(b->aux);
     cudaFree(b->d_jobs);
     cudaFree(b->d_tiles);
     cudaFree(b->d_counter);
@@ -388,16 +402,35 @@ int extract_batch_create(extract_batch **out, const extract_job_desc *jobs, uint
         if ((e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) != cudaSuccess) { rc = cuda_error(e, "stream"); break; }
         b->table.resize(b->ndirect);
         uint64_t groups = 0, outw = 0, work = 0;
+        std::vector<std::pair<double, uint32_t>> nj_cost;
         for (uint32_t i = 0; i < njobs; ++i)
-            if (b->jobs[i].table_index == -2) work = std::max(work, ntt_work_words(jobs[i].m, jobs[i].s, jobs[i].k));
-        if (work) {
-            if ((e = cudaMalloc(&b->ntt_work, work * 4)) != cudaSuccess) { rc = cuda_error(e, "cudaMalloc(ntt work)"); break; }
-            if ((e = cudaStreamCreateWithFlags(&b->aux, cudaStreamNonBlocking)) != cudaSuccess ||
-                (e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming)) != cudaSuccess ||
-                (e = cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming)) != cudaSuccess) {
-                rc = cuda_error(e, "ntt stream");
+            if (b->jobs[i].table_index == -2) {
+                work = std::max(work, ntt_work_words(jobs[i].m, jobs[i].s, jobs[i].k));
+                nj_cost.push_back({predict_ntt_s(jobs[i].m, jobs[i].s, jobs[i].k), i});
+            }
+        std::stable_sort(nj_cost.begin(), nj_cost.end(), [](const auto &x, const auto &y) { return x.first > y.first; });
+        const int nlanes = (int)std::min<size_t>(kNttLanes, nj_cost.size());
+        for (auto &c : nj_cost) {  // longest first onto the least loaded lane
+            int best = 0;
+            for (int l = 1; l < nlanes; ++l)
+                if (b->lanes[l].load_ns < b->lanes[best].load_ns) best = l;
+            b->lanes[best].load_ns += c.first;
+            b->jobs[c.second].lane = best;
+            b->ntt_order.push_back(c.second);
+        }
+        for (int l = 0; l < nlanes && rc == EXTRACT_OK; ++l) {
+            NttLane &L = b->lanes[l];
+            if ((e = cudaMalloc(&L.work, work * 4)) != cudaSuccess) { rc = cuda_error(e, "cudaMalloc(ntt work)"); break; }
+            if ((e = cudaStreamCreateWithFlags(&L.st, cudaStreamNonBlocking)) != cudaSuccess ||
+                (e = cudaEventCreateWithFlags(&L.join, cudaEventDisableTiming)) != cudaSuccess) {
+                rc = cuda_error(e, "ntt lane");
                 break;
             }
+        }
+        if (rc != EXTRACT_OK) break;
+        if (nlanes && (e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming)) != cudaSuccess) {
+            rc = cuda_error(e, "ntt fork event");
+            break;
         }
         for (uint32_t i = 0; i < njobs && rc == EXTRACT_OK; ++i) {
             const extract_job_desc &d = jobs[i];
@@ -418,7 +451,7 @@ int extract_batch_create(extract_batch **out, const extract_job_desc *jobs, uint
                 if ((rc = build_perm(d.n, d.sampling_key, mask, J.perm, st, b->num_sms)) != EXTRACT_OK) break;
             }
             if (J.table_index == -2) {
-                if ((rc = ntt_create(&J.ntt, d.m, d.s, d.k, J.seed, st, b->ntt_work)) != EXTRACT_OK) break;
+                if ((rc = ntt_create(&J.ntt, d.m, d.s, d.k, J.seed, st, b->lanes[J.lane].work)) != EXTRACT_OK) break;
                 continue;
             }
             BatchJobDev &T = b->table[J.table_index];
@@ -458,7 +491,7 @@ int extract_batch_create(extract_batch **out, const extract_job_desc *jobs, uint
         if (!J.ntt) counts[J.variant]++;
     char buf[1024];
     int len = snprintf(buf, sizeof(buf),
-                       "batch: %u jobs (%u NTT on a concurrent stream, %u direct), %u tiles, graph=%s, tuned=%s, "
+                       "batch: %u jobs (%u NTT on concurrent lanes, %u direct), %u tiles, graph=%s, tuned=%s, "
                        "direct part predicted %.3f ms; variants",
                        njobs, b->nntt, b->ndirect, b->ntiles, b->exec ? "yes" : "no",
                        (flags & EXTRACT_BATCH_NO_TUNE) ? "no" : "yes", b->predicted_ms);
@@ -490,14 +523,16 @@ int extract_batch_run(extract_batch *b, void *stream, const uint32_t *const *in_
     // share one work buffer), concurrent with the persistent launch below
     if (b->nntt) {
         EX_CUDA(cudaEventRecord(b->ev_fork, st));
-        EX_CUDA(cudaStreamWaitEvent(b->aux, b->ev_fork, 0));
-        for (size_t i = 0; i < nj; ++i) {
+        for (NttLane &L : b->lanes)
+            if (L.st) EX_CUDA(cudaStreamWaitEvent(L.st, b->ev_fork, 0));
+        for (uint32_t i : b->ntt_order) {
             const BatchJobHost &J = b->jobs[i];
-            if (!J.ntt) continue;
-            if (int rc = launch_gather(in_bits_dev[i], J.perm, J.m, J.s, J.w_pad, J.arev, b->aux, b->num_sms)) return rc;
-            if (int rc = ntt_hash(J.ntt, J.arev, J.w_pad, J.m, J.s, J.k, out_bits_dev[i], b->aux)) return rc;
+            const NttLane &L = b->lanes[J.lane];
+            if (int rc = launch_gather(in_bits_dev[i], J.perm, J.m, J.s, J.w_pad, J.arev, L.st, b->num_sms)) return rc;
+            if (int rc = ntt_hash(J.ntt, J.arev, J.w_pad, J.m, J.s, J.k, out_bits_dev[i], L.st, L.work)) return rc;
         }
-        EX_CUDA(cudaEventRecord(b->ev_join, b->aux));
+        for (NttLane &L : b->lanes)
+            if (L.st) EX_CUDA(cudaEventRecord(L.join, L.st));
     }
     if (b->ndirect) {
         // pageable source: the copy is staged before the call returns, so the
@@ -510,7 +545,8 @@ int extract_batch_run(extract_batch *b, void *stream, const uint32_t *const *in_
             return rc;
         }
     }
-    if (b->nntt) EX_CUDA(cudaStreamWaitEvent(st, b->ev_join, 0));
+    for (NttLane &L : b->lanes)
+        if (L.st) EX_CUDA(cudaStreamWaitEvent(st, L.join, 0));
     return EXTRACT_OK;
 }
 

@@ -34,10 +34,11 @@ double predict_direct_s(uint32_t m, uint32_t k, uint32_t s)
     return (double)m * k * ((s + 31) / 32) / 19e12;
 }
 
-double predict_ntt_s(uint32_t m, uint32_t s, uint32_t k)
+double predict_ntt_s(uint32_t m, uint32_t s, uint32_t k, int split_log2)
 {
-    const double N = (double)ntt_length(s, k);
-    return (double)m * N * (std::log2(N) + 4.0) * 0.65e-12;
+    const NttShape sh = ntt_shape(s, k, split_log2);
+    const double N = (double)sh.N;
+    return (double)m * (sh.P + 1) * N * (std::log2(N) + 4.0) * 0.325e-12;
 }
 
 }  // namespace ex
@@ -66,7 +67,7 @@ struct extract_ctx {
 namespace {
 
 constexpr uint32_t kKnownFlags = EXTRACT_SEED_PER_SUBBLOCK | EXTRACT_IDENTITY_PERM | EXTRACT_METHOD_DIRECT |
-                                  EXTRACT_METHOD_NTT | (0x3fu << 8);
+                                  EXTRACT_METHOD_NTT | (0x3fu << 8) | (0x7u << 16);
 
 void free_ctx(extract_ctx *h)
 {
@@ -131,11 +132,16 @@ int extract_create(extract_ctx **out, uint64_t n, uint32_t m, uint32_t s, uint32
     const bool ident = (flags & EXTRACT_IDENTITY_PERM) != 0;
     if ((flags & EXTRACT_METHOD_DIRECT) && (flags & EXTRACT_METHOD_NTT))
         return set_error(EXTRACT_EINVAL, "EXTRACT_METHOD_DIRECT and EXTRACT_METHOD_NTT are exclusive");
-    const bool ntt_ok = !per_sub && ntt_eligible(s, k);
+    const uint32_t split_field = (flags >> 16) & 0x7u;
+    if (split_field > 5) return set_error(EXTRACT_EINVAL, "EXTRACT_NTT_SPLIT takes 0 .. 4");
+    const int split = (int)split_field - 1;  // -1: automatic
+    const bool ntt_ok = !per_sub && ntt_shape(s, k, split).N != 0;
     if ((flags & EXTRACT_METHOD_NTT) && !ntt_ok)
-        return set_error(EXTRACT_EINVAL, "the NTT method needs a shared seed and 2^11 < s+k-1 <= 2^22 (s=%u k=%u)", s, k);
+        return set_error(EXTRACT_EINVAL,
+                         "the NTT method needs a shared seed, s+k-1 > 2^11, s < 7*2^26+1 and a split with "
+                         "transform length <= 2^22 (s=%u k=%u split=%d)", s, k, split);
     const bool use_ntt = ntt_ok && !(flags & EXTRACT_METHOD_DIRECT) &&
-                         ((flags & EXTRACT_METHOD_NTT) || predict_ntt_s(m, s, k) < predict_direct_s(m, k, s));
+                         ((flags & EXTRACT_METHOD_NTT) || predict_ntt_s(m, s, k, split) < predict_direct_s(m, k, s));
 
     extract_ctx *h = new (std::nothrow) extract_ctx();
     if (!h) return set_error(EXTRACT_ENOMEM, "host allocation failed");
@@ -174,7 +180,7 @@ int extract_create(extract_ctx **out, uint64_t n, uint32_t m, uint32_t s, uint32
     if (use_ntt) {
         cudaStream_t st;
         if ((e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) != cudaSuccess) { free_ctx(h); return cuda_error(e, "stream"); }
-        int rc = ntt_create(&h->ntt, m, s, k, h->seed, st);
+        int rc = ntt_create(&h->ntt, m, s, k, h->seed, st, nullptr, split);
         cudaStreamDestroy(st);
         if (rc != EXTRACT_OK) { free_ctx(h); return rc; }
         if ((e = cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking)) != cudaSuccess ||
@@ -288,8 +294,10 @@ int extract_describe(extract_ctx *h, char *buf, uint32_t buflen)
     if (!buf || !buflen) return set_error(EXTRACT_EINVAL, "empty buffer");
     const HashPlan &p = h->plan;
     if (h->ntt) {
-        snprintf(buf, buflen, "ntt: N=%u (%u x 2048), %u sub-blocks per launch group, prime 7*2^26+1; sms=%d",
-                 ntt_size(h->ntt), ntt_size(h->ntt) / 2048, ntt_group(h->ntt), h->num_sms);
+        snprintf(buf, buflen,
+                 "ntt: N=%u (%u x 2048) P=%u pieces per sub-block, %u sub-blocks per launch group, "
+                 "prime 7*2^26+1; sms=%d",
+                 ntt_size(h->ntt), ntt_size(h->ntt) / 2048, ntt_pieces(h->ntt), ntt_group(h->ntt), h->num_sms);
         return EXTRACT_OK;
     }
     snprintf(buf, buflen,

@@ -91,18 +91,30 @@ int launch_batch_hash(const BatchJobDev *jobs, const BatchTileDev *tiles, uint32
 
 // ---- exact NTT middle product (ntt.cu) -----------------------------------
 struct NttPlan;
-bool ntt_eligible(uint32_t s, uint32_t k);  // 2^11 < s + k - 1 <= 2^22
-uint32_t ntt_length(uint32_t s, uint32_t k);
-// Words of the work buffer a plan for (m, s, k) uses.
-uint64_t ntt_work_words(uint32_t m, uint32_t s, uint32_t k);
-// Builds the twiddle tables and the seed spectrum (synchronous on st).  work:
+// Transform length N, pieces per sub-block P and coefficients per piece h.
+// split_log2 < 0 picks P = 2^l (l <= 4) with the least predicted work; N = 0
+// when no shape exists (s + k - 1 <= 2^11, s >= the prime, N > 2^22 or
+// P N > ntt_max_work_words()).
+struct NttShape {
+    uint32_t N = 0, P = 1, h = 0;
+};
+NttShape ntt_shape(uint32_t s, uint32_t k, int split_log2 = -1);
+bool ntt_eligible(uint32_t s, uint32_t k);
+// Words of the work buffer a plan for (m, s, k) uses, and the most any uses.
+uint64_t ntt_work_words(uint32_t m, uint32_t s, uint32_t k, int split_log2 = -1);
+uint64_t ntt_max_work_words();
+// Radix-2 butterflies of one hash of m sub-blocks ((P + 1) transforms each).
+double ntt_work_butterflies(uint32_t m, uint32_t s, uint32_t k, int split_log2 = -1);
+// Builds the twiddle tables and the seed spectra (synchronous on st).  work:
 // a caller-owned buffer of ntt_work_words() words shared by plans that never
 // run concurrently, or null to allocate one.
 int ntt_create(NttPlan **out, uint32_t m, uint32_t s, uint32_t k, const uint32_t *seed_dev, cudaStream_t st,
-               uint32_t *work = nullptr);
-// Hashes all m gathered sub-blocks; zeroes and fills out.
+               uint32_t *work = nullptr, int split_log2 = -1);
+// Hashes all m gathered sub-blocks; zeroes and fills out.  work: a buffer
+// of ntt_work_words() words to use instead of the plan's own (null: the
+// plan's).
 int ntt_hash(const NttPlan *p, const uint32_t *arev, uint32_t w_pad, uint32_t m, uint32_t s, uint32_t k,
-             uint32_t *out, cudaStream_t st);
+             uint32_t *out, cudaStream_t st, uint32_t *work = nullptr);
 // Gather and hash with the gather of each launch group on `aux` overlapping
 // the transforms of the previous group on `st`; ordered after prior work on
 // st and fully ordered before later work on st.  ev_fork, ev_group: events
@@ -114,13 +126,14 @@ void ntt_destroy(NttPlan *p);
 // Stream-ordered release (no device-wide synchronisation).
 void ntt_destroy_async(NttPlan *p, cudaStream_t st);
 // Device bytes a plan holds besides the shared work buffer.
-uint64_t ntt_plan_bytes(uint32_t s, uint32_t k);
+uint64_t ntt_plan_bytes(uint32_t s, uint32_t k, int split_log2 = -1);
 // Predicted seconds of the two hashing methods for m sub-blocks (direct: the
 // LOP3 rate the tiled kernel reaches; NTT: the measured cost per transformed
 // element and stage).
 double predict_direct_s(uint32_t m, uint32_t k, uint32_t s);
-double predict_ntt_s(uint32_t m, uint32_t s, uint32_t k);
+double predict_ntt_s(uint32_t m, uint32_t s, uint32_t k, int split_log2 = -1);
 uint32_t ntt_group(const NttPlan *p);
 uint32_t ntt_size(const NttPlan *p);
+uint32_t ntt_pieces(const NttPlan *p);
 
 }  // namespace ex

@@ -35,6 +35,8 @@
 #include "internal.h"
 
 #include <algorithm>
+#include <cmath>
+#include <mutex>
 #include <vector>
 
 namespace ex {
@@ -49,6 +51,8 @@ constexpr int kCW = 16;               // columns per pass-A CTA
 constexpr int kCS = kCW + 1;          // padded smem row (no bank conflicts)
 constexpr int kRowsB = 2;             // rows per pass-B CTA
 constexpr int kThreads = 256;
+constexpr int kMaxSplitLog2 = 4;      // at most 16 pieces per sub-block
+constexpr uint64_t kMaxWorkWords = 16ull << 20;  // one launch group's buffer, <= 64 MB
 
 // -p^{-1} mod 2^32 by Newton iteration
 constexpr uint32_t neg_inv32(uint32_t p)
@@ -135,6 +139,63 @@ struct Tables {
     const uint32_t *twist_f, *twist_i;
 };
 
+// Where pass A finds the bits of virtual block v = g P + q: piece q of
+// source row g.  A piece holds len coefficients; only its first lim(q) =
+// min(len, total - q len) positions are data, the rest read as 0.
+struct Pieces {
+    uint64_t stride;  // words between source rows
+    uint32_t P;       // pieces per row
+    uint32_t step;    // words between pieces (len / 32 when P > 1)
+    uint32_t len;     // coefficients per piece
+    uint32_t total;   // data bits per row
+};
+
+__device__ __forceinline__ const uint32_t *piece_src(const uint32_t *bits, const Pieces &pc, uint32_t v,
+                                                     uint32_t &lim)
+{
+    const uint32_t q = v % pc.P;
+    lim = min(pc.len, pc.total - q * pc.len);
+    return bits + (size_t)(v / pc.P) * pc.stride + (size_t)q * pc.step;
+}
+
+// The bits a pass-A CTA loads, staged once per CTA: rb[t1] bit c is element
+// t = t1 R2 + c0 + c, read from position len - 1 - t (kReversed) or t of b,
+// and 0 where t >= len or the position is >= lim.  The CTA's 16 columns of
+// one row are 16 adjacent bits of the source (at most two words), so a row
+// costs one or two word loads instead of one load per column.
+template <bool kReversed>
+__device__ __forceinline__ void stage_row_bits(uint32_t *rb, const uint32_t *__restrict__ b, uint32_t len,
+                                               uint32_t lim, uint32_t R1, uint32_t c0)
+{
+    for (uint32_t t1 = threadIdx.x; t1 < R1; t1 += blockDim.x) {
+        const uint32_t t0 = t1 * kR2 + c0;  // element of column c0
+        uint32_t f = 0;
+        if (t0 < len) {
+            if (kReversed) {
+                // element t0 + c sits at position hi - c; keep positions <= top
+                const int32_t hi = (int32_t)(len - 1 - t0), lo = hi - (kCW - 1);
+                const int32_t top = min(hi, (int32_t)lim - 1);
+                if (top >= max(lo, 0)) {
+                    const int32_t w0 = lo >> 5, w1 = top >> 5;  // floor; w1 >= 0
+                    const uint32_t a = w0 >= 0 ? __ldg(b + w0) : 0u;
+                    const uint32_t c = w1 != w0 ? __ldg(b + w1) : 0u;
+                    const uint64_t v = ((uint64_t)c << 32) | a;
+                    const int32_t nb = top - lo + 1;  // 1 .. 16 positions kept
+                    const uint32_t f16 = (uint32_t)(v >> (lo - 32 * w0)) & (nb >= 16 ? 0xffffu : (1u << nb) - 1u);
+                    f = __brev(f16 << 16);  // position lo + i -> column 15 - i
+                }
+            } else {
+                const uint32_t end = min(len, lim);
+                if (t0 < end) {
+                    f = (__ldg(b + (t0 >> 5)) >> (t0 & 31u)) & 0xffffu;  // c0 % 16 == 0: one word
+                    if (end - t0 < (uint32_t)kCW) f &= (1u << (end - t0)) - 1u;
+                }
+            }
+        }
+        rb[t1] = f;
+    }
+}
+
 __device__ __forceinline__ uint32_t twist_mont(const uint32_t *lo, const uint32_t *hi, uint32_t x)
 {
     return mul_mont(__ldg(lo + (x & (kR2 - 1))), __ldg(hi + (x >> kR2Log)));
@@ -176,30 +237,26 @@ __device__ __forceinline__ void dit_cols(uint32_t *x, uint32_t R, const uint32_t
     }
 }
 
-// Pass A: bits -> column DIF -> twist -> buf (row-major R1 x R2).
+// Pass A: bits -> column DIF -> twist -> buf (row-major R1 x R2), one
+// virtual block (piece) per blockIdx.y.
 // kReversed: bits are a gathered sub-block stored reversed (bit s-1-t of
 // row j holds A_j[t]); else bit t holds coefficient t (the seed).
 template <bool kReversed>
 __global__ void __launch_bounds__(kThreads)
-ntt_pass_a_kernel(const uint32_t *__restrict__ bits, uint64_t bits_stride, uint32_t len, uint32_t R1, int r1_log,
-                  uint32_t N, Tables T, uint32_t *__restrict__ buf)
+ntt_pass_a_kernel(const uint32_t *__restrict__ bits, Pieces pc, uint32_t R1, int r1_log, uint32_t N, Tables T,
+                  uint32_t *__restrict__ buf)
 {
-    extern __shared__ uint32_t x[];  // R1 * kCS
+    extern __shared__ uint32_t x[];  // R1 * kCS + R1
     const uint32_t g = blockIdx.y;
     const uint32_t c0 = blockIdx.x * kCW;
-    const uint32_t *b = bits + (size_t)g * bits_stride;
-    for (uint32_t t1 = threadIdx.x; t1 < R1; t1 += blockDim.x) {
-        const uint32_t base = t1 * kR2 + c0;
-#pragma unroll
-        for (int c = 0; c < kCW; ++c) {
-            const uint32_t t = base + c;
-            uint32_t v = 0;
-            if (t < len) {
-                const uint32_t pos = kReversed ? (len - 1 - t) : t;
-                v = (__ldg(b + (pos >> 5)) >> (pos & 31u)) & 1u;
-            }
-            x[t1 * kCS + c] = v;
-        }
+    uint32_t lim;
+    const uint32_t *b = piece_src(bits, pc, g, lim);
+    uint32_t *rb = x + R1 * kCS;
+    stage_row_bits<kReversed>(rb, b, pc.len, lim, R1, c0);
+    __syncthreads();
+    for (uint32_t it = threadIdx.x; it < R1 * kCW; it += blockDim.x) {
+        const uint32_t c = it % kCW, t1 = it / kCW;
+        x[t1 * kCS + c] = (rb[t1] >> c) & 1u;
     }
     __syncthreads();
     dif_cols(x, R1, T.col_f, T.col_fq);
@@ -218,15 +275,16 @@ ntt_pass_a_kernel(const uint32_t *__restrict__ bits, uint64_t bits_stride, uint3
 }
 
 // Pass A': untwist, column inverse DIT, parity of coefficients
-// [s-1, s+k-1) into output bits j k + t - (s-1).
+// [len-1, len+k-1) (len: coefficients per piece) into output bits
+// j k + t - (len-1).  Sub-block g's summed rows start g sub_stride words in.
 __global__ void __launch_bounds__(kThreads)
-ntt_pass_a_inv_kernel(const uint32_t *__restrict__ buf, uint32_t N, uint32_t R1, int r1_log, Tables T, uint32_t j0,
-                      uint32_t s, uint32_t k, uint32_t *__restrict__ out)
+ntt_pass_a_inv_kernel(const uint32_t *__restrict__ buf, uint64_t sub_stride, uint32_t R1, int r1_log, Tables T, uint32_t j0,
+                      uint32_t len, uint32_t k, uint32_t *__restrict__ out)
 {
     extern __shared__ uint32_t x[];  // R1 * kCS
     const uint32_t g = blockIdx.y;
     const uint32_t c0 = blockIdx.x * kCW;
-    const uint32_t *in = buf + (size_t)g * N;
+    const uint32_t *in = buf + (size_t)g * sub_stride;
     for (uint32_t it = threadIdx.x; it < R1 * kCW; it += blockDim.x) {
         const uint32_t c = it % kCW, r = it / kCW;
         const uint32_t e = bitrev(r, r1_log) * (c0 + c);
@@ -235,7 +293,7 @@ ntt_pass_a_inv_kernel(const uint32_t *__restrict__ buf, uint32_t N, uint32_t R1,
     __syncthreads();
     dit_cols(x, R1, T.col_i, T.col_iq);
     const uint64_t jk = (uint64_t)(j0 + g) * k;
-    const uint32_t lo_t = s - 1, hi_t = s - 1 + k;  // wanted coefficients
+    const uint32_t lo_t = len - 1, hi_t = len - 1 + k;  // wanted coefficients
     for (uint32_t t1 = threadIdx.x; t1 < R1; t1 += blockDim.x) {
         const uint32_t base = t1 * kR2 + c0;
         if (base + kCW <= lo_t || base >= hi_t) continue;
@@ -353,6 +411,7 @@ __constant__ uint2 c_low_i[31];
 
 __device__ __forceinline__ uint32_t swz(uint32_t t) { return (t & ~31u) | ((t ^ (t >> 5)) & 31u); }
 
+
 // DIF: layout A in (e[j] = position 32 j + l), layout B out (e[32 q + i] =
 // position 32 (l + 32 q) + i).  sw: this warp's 32 EPL-word scratch.
 template <int EPL>
@@ -423,18 +482,16 @@ __device__ __forceinline__ void dit_warp_t(uint32_t (&e)[EPL], uint32_t *sw, con
 // Pass B: one CTA of two warps per 2048-word row; warp w owns half
 // [1024 w, 1024 w + 1024).  The distance-1024 DIF stage is done while
 // loading (each warp reads both halves), the distance-1024 DIT stage by an
-// exchange through shared memory.  kInverse false: forward DIF only (the
-// seed spectrum), stored in layout B order.
-template <bool kInverse>
-__global__ void __launch_bounds__(64)
-ntt_rows_kernel(uint32_t *__restrict__ buf, uint32_t N, uint32_t R1, const uint32_t *__restrict__ S,
-                const uint32_t *__restrict__ Sq, Tables T)
+// exchange through shared memory.
+//   kInverse false: forward DIF only (the seed spectrum), stored in layout B.
+//   kInverse true:  for each of the P pieces q of a sub-block (its rows
+//                   q N words after piece 0's), DIF and multiply by
+//                   spectrum q; the products are summed, transformed back,
+//                   and the row is stored in piece 0's place.  kMulti
+//                   false is the P = 1 form.
+__device__ __forceinline__ void row_dif(uint32_t (&e)[32], const uint32_t *x, uint32_t *sw, const Tables &T,
+                                        int lane, int w)
 {
-    __shared__ __align__(16) uint32_t sw[2][1024];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const uint32_t row = blockIdx.x, g = row / R1, r = row % R1;
-    uint32_t *x = buf + (size_t)g * N + (size_t)r * kR2;
-    uint32_t e[32];
 #pragma unroll
     for (int j = 0; j < 32; ++j) {
         const uint32_t pos = 32u * j + lane;
@@ -446,23 +503,37 @@ ntt_rows_kernel(uint32_t *__restrict__ buf, uint32_t N, uint32_t R1, const uint3
             e[j] = shoup_lazy(a - b + k2P, tw.x, tw.y);
         }
     }
-    dif_warp_t<32>(e, sw[w], T.row_stage_f, lane);
-    const uint32_t base = 1024u * w + 32u * lane;  // layout B: e[i] at base + i
-    if (!kInverse) {
-#pragma unroll
-        for (int i = 0; i < 32; i += 4)
-            *reinterpret_cast<uint4 *>(x + base + i) = make_uint4(e[i], e[i + 1], e[i + 2], e[i + 3]);
-        return;
-    }
-    const uint32_t *sv = S + (size_t)r * kR2 + base, *sq = Sq + (size_t)r * kR2 + base;
+    dif_warp_t<32>(e, sw, T.row_stage_f, lane);
+}
+
+// e[i] (layout B, from base) times the spectrum; kAcc: added to acc
+template <bool kAcc>
+__device__ __forceinline__ void row_mul(uint32_t (&e)[32], uint32_t (&acc)[32], const uint32_t *sv,
+                                        const uint32_t *sq)
+{
 #pragma unroll
     for (int i = 0; i < 32; i += 4) {
         const uint4 a = __ldg(reinterpret_cast<const uint4 *>(sv + i)), b = __ldg(reinterpret_cast<const uint4 *>(sq + i));
-        e[i] = shoup_lazy(e[i], a.x, b.x);
-        e[i + 1] = shoup_lazy(e[i + 1], a.y, b.y);
-        e[i + 2] = shoup_lazy(e[i + 2], a.z, b.z);
-        e[i + 3] = shoup_lazy(e[i + 3], a.w, b.w);
+        const uint32_t m0 = shoup_lazy(e[i], a.x, b.x), m1 = shoup_lazy(e[i + 1], a.y, b.y);
+        const uint32_t m2 = shoup_lazy(e[i + 2], a.z, b.z), m3 = shoup_lazy(e[i + 3], a.w, b.w);
+        if (kAcc) {
+            acc[i] = red2p(acc[i] + m0);
+            acc[i + 1] = red2p(acc[i + 1] + m1);
+            acc[i + 2] = red2p(acc[i + 2] + m2);
+            acc[i + 3] = red2p(acc[i + 3] + m3);
+        } else {
+            acc[i] = m0;
+            acc[i + 1] = m1;
+            acc[i + 2] = m2;
+            acc[i + 3] = m3;
+        }
     }
+}
+
+// inverse DIT of acc (layout B) and the distance-1024 stage, stored to x
+__device__ __forceinline__ void row_dit_store(uint32_t (&e)[32], uint32_t *x, uint32_t (*sw)[1024], const Tables &T,
+                                              int lane, int w)
+{
     dit_warp_t<32>(e, sw[w], T.row_stage_i, lane);
     // distance-1024 DIT stage: x' = x + w y, y' = x - w y (w = w_2048^-pos)
 #pragma unroll
@@ -484,31 +555,60 @@ ntt_rows_kernel(uint32_t *__restrict__ buf, uint32_t N, uint32_t R1, const uint3
     }
 }
 
+template <bool kInverse, bool kMulti>
+__global__ void __launch_bounds__(64, kMulti ? 8 : 12)
+ntt_rows_kernel(uint32_t *__restrict__ buf, uint32_t N, uint32_t R1, uint32_t P, const uint32_t *__restrict__ S,
+                const uint32_t *__restrict__ Sq, Tables T)
+{
+    __shared__ __align__(16) uint32_t sw[2][1024];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const uint32_t row = blockIdx.x, g = row / R1, r = row % R1;
+    uint32_t *x = buf + (size_t)g * P * N + (size_t)r * kR2;
+    const uint32_t base = 1024u * w + 32u * lane;  // layout B: e[i] at base + i
+    const size_t so = (size_t)r * kR2 + base;
+    uint32_t e[32];
+    row_dif(e, x, sw[w], T, lane, w);
+    if (!kInverse) {
+#pragma unroll
+        for (int i = 0; i < 32; i += 4)
+            *reinterpret_cast<uint4 *>(x + base + i) = make_uint4(e[i], e[i + 1], e[i + 2], e[i + 3]);
+        return;
+    }
+    if (!kMulti) {
+        row_mul<false>(e, e, S + so, Sq + so);
+        row_dit_store(e, x, sw, T, lane, w);
+        return;
+    }
+    uint32_t acc[32];
+    row_mul<false>(e, acc, S + so, Sq + so);
+    for (uint32_t q = 1; q < P; ++q) {
+        row_dif(e, x + (size_t)q * N, sw[w], T, lane, w);
+        row_mul<true>(e, acc, S + (size_t)q * N + so, Sq + (size_t)q * N + so);
+    }
+    row_dit_store(acc, x, sw, T, lane, w);
+}
+
 // Pass A with transposed warps (R1 = 32 EPL, EPL in {32, 64}): one warp per
 // column; the CTA's 16 columns are staged (column-major, swizzled) in shared
 // memory for coalesced row-major stores.
 template <int EPL, bool kReversed>
 __global__ void __launch_bounds__(kCW * 32)
-ntt_cols_fwd_t_kernel(const uint32_t *__restrict__ bits, uint64_t bits_stride, uint32_t len, int r1_log, uint32_t N,
-                      Tables T, uint32_t *__restrict__ buf)
+ntt_cols_fwd_t_kernel(const uint32_t *__restrict__ bits, Pieces pc, int r1_log, uint32_t N, Tables T,
+                      uint32_t *__restrict__ buf)
 {
     constexpr uint32_t R1 = 32u * EPL, kStr = R1 + 1;
-    extern __shared__ uint32_t xs[];  // kCW * kStr
+    extern __shared__ uint32_t xs[];  // kCW * kStr + R1
     const int lane = threadIdx.x & 31, c = threadIdx.x >> 5;
     const uint32_t g = blockIdx.y, c0 = blockIdx.x * kCW, t2 = c0 + c;
     uint32_t *col = xs + c * kStr;
-    const uint32_t *b = bits + (size_t)g * bits_stride;
+    uint32_t *rb = xs + kCW * kStr;  // R1 staged row bits
+    uint32_t lim;
+    const uint32_t *b = piece_src(bits, pc, g, lim);
+    stage_row_bits<kReversed>(rb, b, pc.len, lim, R1, c0);
+    __syncthreads();
     uint32_t e[EPL];
 #pragma unroll
-    for (int j = 0; j < EPL; ++j) {
-        const uint32_t t = (32u * j + lane) * kR2 + t2;
-        uint32_t v = 0;
-        if (t < len) {
-            const uint32_t pos = kReversed ? (len - 1 - t) : t;
-            v = (__ldg(b + (pos >> 5)) >> (pos & 31u)) & 1u;
-        }
-        e[j] = v;
-    }
+    for (int j = 0; j < EPL; ++j) e[j] = (rb[32u * j + lane] >> c) & 1u;
     dif_warp_t<EPL>(e, col, T.col_stage_f, lane);
     // layout B: e[32 q + i] is row r = 32 (lane + 32 q) + i, frequency bitrev(r)
     const uint32_t *twr = T.twist_f + (size_t)t2 * R1;
@@ -534,8 +634,8 @@ ntt_cols_fwd_t_kernel(const uint32_t *__restrict__ bits, uint64_t bits_stride, u
 // Pass A' with transposed warps: coalesced tile load, untwist, inverse DIT
 // along t1, parity of the wanted coefficients into the output.
 template <int EPL>
-__global__ void __launch_bounds__(kCW * 32)
-ntt_cols_inv_t_kernel(const uint32_t *__restrict__ buf, uint32_t N, int r1_log, Tables T, uint32_t j0, uint32_t s,
+__global__ void __launch_bounds__(kCW * 32, EPL <= 32 ? 2 : 1)
+ntt_cols_inv_t_kernel(const uint32_t *__restrict__ buf, uint64_t sub_stride, int r1_log, Tables T, uint32_t j0, uint32_t len,
                       uint32_t k, uint32_t *__restrict__ out)
 {
     constexpr uint32_t R1 = 32u * EPL, kStr = R1 + 1;
@@ -543,7 +643,7 @@ ntt_cols_inv_t_kernel(const uint32_t *__restrict__ buf, uint32_t N, int r1_log, 
     const int lane = threadIdx.x & 31, c = threadIdx.x >> 5;
     const uint32_t g = blockIdx.y, c0 = blockIdx.x * kCW, t2 = c0 + c;
     uint32_t *col = xs + c * kStr;
-    const uint32_t *in = buf + (size_t)g * N;
+    const uint32_t *in = buf + (size_t)g * sub_stride;
     for (uint32_t it = threadIdx.x; it < R1 * kCW; it += blockDim.x) {
         const uint32_t cc = it % kCW, rr = it / kCW;
         xs[cc * kStr + swz(rr)] = in[(size_t)rr * kR2 + c0 + cc];
@@ -568,7 +668,7 @@ ntt_cols_inv_t_kernel(const uint32_t *__restrict__ buf, uint32_t N, int r1_log, 
     for (int j = 0; j < EPL; ++j) col[swz(32u * j + lane)] = redp(red2p(e[j])) & 1u;
     __syncthreads();
     const uint64_t jk = (uint64_t)(j0 + g) * k;
-    const uint32_t lo_t = s - 1, hi_t = s - 1 + k;
+    const uint32_t lo_t = len - 1, hi_t = len - 1 + k;
     for (uint32_t t1 = threadIdx.x; t1 < R1; t1 += blockDim.x) {
         const uint32_t base = t1 * kR2 + c0;
         if (base + kCW <= lo_t || base >= hi_t) continue;
@@ -596,25 +696,21 @@ ntt_cols_inv_t_kernel(const uint32_t *__restrict__ buf, uint32_t N, int r1_log, 
 // staged through shared memory so the row-major stores are coalesced.
 template <int EPL, bool kReversed>
 __global__ void __launch_bounds__(kCW * 32)
-ntt_cols_fwd_kernel(const uint32_t *__restrict__ bits, uint64_t bits_stride, uint32_t len, int r1_log, uint32_t N,
-                    Tables T, uint32_t *__restrict__ buf)
+ntt_cols_fwd_kernel(const uint32_t *__restrict__ bits, Pieces pc, int r1_log, uint32_t N, Tables T,
+                    uint32_t *__restrict__ buf)
 {
     constexpr uint32_t R1 = 32u * EPL;
-    extern __shared__ uint32_t x[];  // R1 * kCS
+    extern __shared__ uint32_t x[];  // R1 * kCS + R1
     const int lane = threadIdx.x & 31, c = threadIdx.x >> 5;
     const uint32_t g = blockIdx.y, c0 = blockIdx.x * kCW, t2 = c0 + c;
-    const uint32_t *b = bits + (size_t)g * bits_stride;
+    uint32_t *rb = x + R1 * kCS;  // R1 staged row bits
+    uint32_t lim;
+    const uint32_t *b = piece_src(bits, pc, g, lim);
+    stage_row_bits<kReversed>(rb, b, pc.len, lim, R1, c0);
+    __syncthreads();
     uint32_t e[EPL];
 #pragma unroll
-    for (int j = 0; j < EPL; ++j) {
-        const uint32_t t = (lane + 32u * j) * kR2 + t2;
-        uint32_t v = 0;
-        if (t < len) {
-            const uint32_t pos = kReversed ? (len - 1 - t) : t;
-            v = (__ldg(b + (pos >> 5)) >> (pos & 31u)) & 1u;
-        }
-        e[j] = v;
-    }
+    for (int j = 0; j < EPL; ++j) e[j] = (rb[lane + 32u * j] >> c) & 1u;
     warp_dif<EPL>(e, T.col_stage_f, lane);
 #pragma unroll
     for (int j = 0; j < EPL; ++j) {
@@ -634,14 +730,14 @@ ntt_cols_fwd_kernel(const uint32_t *__restrict__ bits, uint64_t bits_stride, uin
 // untwist, inverse DIT along t1, parity of the wanted coefficients.
 template <int EPL>
 __global__ void __launch_bounds__(kCW * 32)
-ntt_cols_inv_kernel(const uint32_t *__restrict__ buf, uint32_t N, int r1_log, Tables T, uint32_t j0, uint32_t s,
+ntt_cols_inv_kernel(const uint32_t *__restrict__ buf, uint64_t sub_stride, int r1_log, Tables T, uint32_t j0, uint32_t len,
                     uint32_t k, uint32_t *__restrict__ out)
 {
     constexpr uint32_t R1 = 32u * EPL;
     extern __shared__ uint32_t x[];  // R1 * kCS
     const int lane = threadIdx.x & 31, c = threadIdx.x >> 5;
     const uint32_t g = blockIdx.y, c0 = blockIdx.x * kCW, t2 = c0 + c;
-    const uint32_t *in = buf + (size_t)g * N;
+    const uint32_t *in = buf + (size_t)g * sub_stride;
     for (uint32_t it = threadIdx.x; it < R1 * kCW; it += blockDim.x) {
         const uint32_t cc = it % kCW, r = it / kCW;
         x[r * kCS + cc] = in[(size_t)r * kR2 + c0 + cc];
@@ -659,7 +755,7 @@ ntt_cols_inv_kernel(const uint32_t *__restrict__ buf, uint32_t N, int r1_log, Ta
     for (int j = 0; j < EPL; ++j) x[(lane + 32u * j) * kCS + c] = e[j] & 1u;
     __syncthreads();
     const uint64_t jk = (uint64_t)(j0 + g) * k;
-    const uint32_t lo_t = s - 1, hi_t = s - 1 + k;
+    const uint32_t lo_t = len - 1, hi_t = len - 1 + k;
     for (uint32_t t1 = threadIdx.x; t1 < R1; t1 += blockDim.x) {
         const uint32_t base = t1 * kR2 + c0;
         if (base + kCW <= lo_t || base >= hi_t) continue;
@@ -703,6 +799,7 @@ uint32_t to_mont(uint32_t w) { return (uint32_t)(((uint64_t)w << 32) % kP); }
 struct NttPlan {
     int e = 0, r1_log = 0;
     uint32_t N = 0, R1 = 0, G = 0;
+    uint32_t P = 1, h = 0;  // pieces per sub-block and coefficients per piece
     uint32_t *buf = nullptr, *S = nullptr, *Sq = nullptr, *tables = nullptr, *twist = nullptr;
     bool own_buf = true;
     Tables T{};
@@ -710,29 +807,30 @@ struct NttPlan {
 
 namespace {
 
-size_t smem_generic(uint32_t R1) { return (size_t)R1 * kCS * 4; }      // R1 < 1024 kernels
-size_t smem_transposed(uint32_t R1) { return (size_t)kCW * (R1 + 1) * 4; }  // R1 >= 1024 kernels
+// dynamic shared memory of the column kernels (+ R1 words of staged row bits)
+size_t smem_generic(uint32_t R1) { return (size_t)R1 * (kCS + 1) * 4; }         // R1 < 1024 kernels
+size_t smem_transposed(uint32_t R1) { return ((size_t)kCW * (R1 + 1) + R1) * 4; }  // R1 >= 1024 kernels
 
-// pass A for g sub-blocks (bits stride bits_stride words) into dst
-int ntt_launch_a(const NttPlan *p, const uint32_t *bits, uint64_t bits_stride, uint32_t len, bool reversed, uint32_t g,
-                 uint32_t *dst, cudaStream_t st)
+// pass A for the g * pc.P pieces of g source rows into dst (N words each)
+int ntt_launch_a(const NttPlan *p, const uint32_t *bits, const Pieces &pc, bool reversed, uint32_t g, uint32_t *dst,
+                 cudaStream_t st)
 {
-    const dim3 grid(kR2 / kCW, g);
+    const dim3 grid(kR2 / kCW, g * pc.P);
     const uint32_t R1 = p->R1;
     if (R1 < 32) {
         const size_t smem = smem_generic(R1);
         if (reversed)
-            ntt_pass_a_kernel<true><<<grid, kThreads, smem, st>>>(bits, bits_stride, len, R1, p->r1_log, p->N, p->T, dst);
+            ntt_pass_a_kernel<true><<<grid, kThreads, smem, st>>>(bits, pc, R1, p->r1_log, p->N, p->T, dst);
         else
-            ntt_pass_a_kernel<false><<<grid, kThreads, smem, st>>>(bits, bits_stride, len, R1, p->r1_log, p->N, p->T, dst);
+            ntt_pass_a_kernel<false><<<grid, kThreads, smem, st>>>(bits, pc, R1, p->r1_log, p->N, p->T, dst);
         return EXTRACT_OK;
     }
     const int epl = (int)(R1 / 32);
-#define EX_COLS_FWD(E, K, SMEM)                                                                               \
-    if (epl == E) {                                                                                           \
-        if (reversed) K<E, true><<<grid, kCW * 32, SMEM, st>>>(bits, bits_stride, len, p->r1_log, p->N, p->T, dst); \
-        else K<E, false><<<grid, kCW * 32, SMEM, st>>>(bits, bits_stride, len, p->r1_log, p->N, p->T, dst);       \
-        return EXTRACT_OK;                                                                                    \
+#define EX_COLS_FWD(E, K, SMEM)                                                                 \
+    if (epl == E) {                                                                             \
+        if (reversed) K<E, true><<<grid, kCW * 32, SMEM, st>>>(bits, pc, p->r1_log, p->N, p->T, dst); \
+        else K<E, false><<<grid, kCW * 32, SMEM, st>>>(bits, pc, p->r1_log, p->N, p->T, dst);       \
+        return EXTRACT_OK;                                                                      \
     }
     EX_COLS_FWD(1, ntt_cols_fwd_kernel, smem_generic(R1))
     EX_COLS_FWD(2, ntt_cols_fwd_kernel, smem_generic(R1))
@@ -745,30 +843,35 @@ int ntt_launch_a(const NttPlan *p, const uint32_t *bits, uint64_t bits_stride, u
     return set_error(EXTRACT_EINTERNAL, "ntt: no column kernel for R1=%u", R1);
 }
 
-// pass B over the g * R1 rows of dst (inverse: times S and back); one CTA of
-// two warps per row
-void ntt_launch_rows(const NttPlan *p, uint32_t *dst, uint32_t g, const uint32_t *S, const uint32_t *Sq, bool inverse,
-                     cudaStream_t st)
+// pass B over the g * R1 output rows of dst; one CTA of two warps per row.
+// inverse: the P pieces of each sub-block times their spectra, summed and
+// transformed back; else the forward DIF of one piece (P = 1).
+void ntt_launch_rows(const NttPlan *p, uint32_t *dst, uint32_t g, uint32_t P, const uint32_t *S, const uint32_t *Sq,
+                     bool inverse, cudaStream_t st)
 {
     const uint32_t rows = p->R1 * g;
-    if (inverse) ntt_rows_kernel<true><<<rows, 64, 0, st>>>(dst, p->N, p->R1, S, Sq, p->T);
-    else ntt_rows_kernel<false><<<rows, 64, 0, st>>>(dst, p->N, p->R1, S, Sq, p->T);
+    if (!inverse) ntt_rows_kernel<false, false><<<rows, 64, 0, st>>>(dst, p->N, p->R1, 1, S, Sq, p->T);
+    else if (P == 1) ntt_rows_kernel<true, false><<<rows, 64, 0, st>>>(dst, p->N, p->R1, 1, S, Sq, p->T);
+    else ntt_rows_kernel<true, true><<<rows, 64, 0, st>>>(dst, p->N, p->R1, P, S, Sq, p->T);
 }
 
-// pass A' for g sub-blocks, output bits of sub-blocks j0 .. j0+g-1
-int ntt_launch_a_inv(const NttPlan *p, uint32_t g, uint32_t j0, uint32_t s, uint32_t k, uint32_t *out, cudaStream_t st)
+// pass A' for g sub-blocks of buf (P N words apart), output bits of
+// sub-blocks j0 .. j0+g-1
+int ntt_launch_a_inv(const NttPlan *p, const uint32_t *buf, uint32_t g, uint32_t j0, uint32_t k, uint32_t *out,
+                     cudaStream_t st)
 {
     const dim3 grid(kR2 / kCW, g);
     const uint32_t R1 = p->R1;
+    const uint64_t sub = (uint64_t)p->P * p->N;
     if (R1 < 32) {
-        ntt_pass_a_inv_kernel<<<grid, kThreads, smem_generic(R1), st>>>(p->buf, p->N, R1, p->r1_log, p->T, j0, s, k, out);
+        ntt_pass_a_inv_kernel<<<grid, kThreads, smem_generic(R1), st>>>(buf, sub, R1, p->r1_log, p->T, j0, p->h, k, out);
         return EXTRACT_OK;
     }
     const int epl = (int)(R1 / 32);
-#define EX_COLS_INV(E, K, SMEM)                                                                        \
-    if (epl == E) {                                                                                    \
-        K<E><<<grid, kCW * 32, SMEM, st>>>(p->buf, p->N, p->r1_log, p->T, j0, s, k, out);            \
-        return EXTRACT_OK;                                                                             \
+#define EX_COLS_INV(E, K, SMEM)                                                          \
+    if (epl == E) {                                                                      \
+        K<E><<<grid, kCW * 32, SMEM, st>>>(buf, sub, p->r1_log, p->T, j0, p->h, k, out); \
+        return EXTRACT_OK;                                                               \
     }
     EX_COLS_INV(1, ntt_cols_inv_kernel, smem_generic(R1))
     EX_COLS_INV(2, ntt_cols_inv_kernel, smem_generic(R1))
@@ -783,18 +886,35 @@ int ntt_launch_a_inv(const NttPlan *p, uint32_t g, uint32_t j0, uint32_t s, uint
 
 }  // namespace
 
-bool ntt_eligible(uint32_t s, uint32_t k)
+// Split of a sub-block into P = 2^l pieces of h coefficients (h a multiple
+// of 32 when P > 1, so pieces start on word boundaries): each piece is its
+// own middle product with seed window q h .. q h + h + k - 2, and the P
+// products add up in the frequency domain, so one inverse transform serves
+// them all.  Length N = 2^e >= h + k - 1 (2^12 .. 2^22); work (P + 1)
+// transforms of N instead of 2 of the length for s + k - 1.
+NttShape ntt_shape(uint32_t s, uint32_t k, int split_log2)
 {
-    const uint64_t need = (uint64_t)s + k - 1;
-    return need > kR2 && need <= (1ull << (kR2Log + 11));  // 2^12 <= N <= 2^22
+    NttShape best{};
+    if ((uint64_t)s + k - 1 <= kR2 || s >= kP) return best;
+    double best_cost = 0;
+    for (int l = 0; l <= kMaxSplitLog2; ++l) {
+        if (split_log2 >= 0 && l != split_log2) continue;
+        const uint32_t P = 1u << l;
+        const uint64_t h = P == 1 ? s : (((uint64_t)s + P - 1) / P + 31) / 32 * 32;
+        if ((uint64_t)(P - 1) * h >= s) break;  // the last piece would be empty
+        uint64_t N = 2 * kR2;
+        while (N < h + k - 1) N <<= 1;
+        if (N > (1ull << 22) || P * N > kMaxWorkWords) continue;
+        const double cost = (double)(P + 1) * (double)N * (std::log2((double)N) + 4.0);
+        if (best.N == 0 || cost < best_cost) {
+            best = NttShape{(uint32_t)N, P, (uint32_t)h};
+            best_cost = cost;
+        }
+    }
+    return best;
 }
 
-uint32_t ntt_length(uint32_t s, uint32_t k)
-{
-    uint32_t N = kR2;
-    while ((uint64_t)N < (uint64_t)s + k - 1) N <<= 1;
-    return N;
-}
+bool ntt_eligible(uint32_t s, uint32_t k) { return ntt_shape(s, k).N != 0; }
 
 void ntt_destroy_async(NttPlan *p, cudaStream_t st)
 {
@@ -819,33 +939,100 @@ void ntt_destroy(NttPlan *p)
 }
 
 
-// seed: realigned seed bits (bit t = seed[t]), L = s + k - 1 bits.
-uint64_t ntt_plan_bytes(uint32_t s, uint32_t k)
+uint64_t ntt_plan_bytes(uint32_t s, uint32_t k, int split_log2)
 {
-    const uint64_t N = ntt_length(s, k);
-    return 4 * N * 4 + 64 * 1024;  // spectrum + quotients, twist tables, stage tables
+    const NttShape sh = ntt_shape(s, k, split_log2);
+    // P spectra + quotients, twist tables, stage tables
+    return (2ull * sh.P + 2) * sh.N * 4 + 64 * 1024;
 }
 
-uint64_t ntt_work_words(uint32_t m, uint32_t s, uint32_t k)
+// sub-blocks per launch group: keep the working buffer near 64 MB (L2-sized)
+static uint32_t group_size(uint32_t m, const NttShape &sh)
 {
-    const uint64_t N = ntt_length(s, k);
-    const uint64_t G = std::max<uint64_t>(1, std::min<uint64_t>(m, (16ull << 20) / N));
-    return G * N;
+    return (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(m, kMaxWorkWords / ((uint64_t)sh.P * sh.N)));
 }
 
+uint64_t ntt_max_work_words() { return kMaxWorkWords; }
+
+uint64_t ntt_work_words(uint32_t m, uint32_t s, uint32_t k, int split_log2)
+{
+    const NttShape sh = ntt_shape(s, k, split_log2);
+    return (uint64_t)group_size(m, sh) * sh.P * sh.N;
+}
+
+double ntt_work_butterflies(uint32_t m, uint32_t s, uint32_t k, int split_log2)
+{
+    const NttShape sh = ntt_shape(s, k, split_log2);
+    return (double)m * (sh.P + 1) * (sh.N / 2) * std::log2((double)std::max<uint32_t>(sh.N, 2));
+}
+
+// Once per device: every column kernel's dynamic shared-memory limit (set
+// to the most any plan launches it with, so plans of different lengths can
+// share the kernels) and the distance < 32 twiddles in the constant bank
+// (they depend only on the prime).  Complete before it returns.
+static int device_setup(cudaStream_t st)
+{
+    static std::mutex mu;
+    static uint64_t done = 0;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_error(e, "ntt device");
+    std::lock_guard<std::mutex> lock(mu);
+    if (dev < 64 && ((done >> dev) & 1u)) return EXTRACT_OK;
+    auto attr = [&](const void *f, size_t bytes) {
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    };
+    const size_t small = smem_generic(16);  // R1 < 32
+    attr((const void *)ntt_pass_a_kernel<false>, small);
+    attr((const void *)ntt_pass_a_kernel<true>, small);
+    attr((const void *)ntt_pass_a_inv_kernel, small);
+#define EX_SET_SMEM(E, KF, KI, SMEM)          \
+    attr((const void *)KF<E, true>, SMEM);  \
+    attr((const void *)KF<E, false>, SMEM); \
+    attr((const void *)KI<E>, SMEM);
+    EX_SET_SMEM(1, ntt_cols_fwd_kernel, ntt_cols_inv_kernel, smem_generic(32))
+    EX_SET_SMEM(2, ntt_cols_fwd_kernel, ntt_cols_inv_kernel, smem_generic(64))
+    EX_SET_SMEM(4, ntt_cols_fwd_kernel, ntt_cols_inv_kernel, smem_generic(128))
+    EX_SET_SMEM(8, ntt_cols_fwd_kernel, ntt_cols_inv_kernel, smem_generic(256))
+    EX_SET_SMEM(16, ntt_cols_fwd_kernel, ntt_cols_inv_kernel, smem_generic(512))
+    EX_SET_SMEM(32, ntt_cols_fwd_t_kernel, ntt_cols_inv_t_kernel, smem_transposed(1024))
+    EX_SET_SMEM(64, ntt_cols_fwd_t_kernel, ntt_cols_inv_t_kernel, smem_transposed(2048))
+#undef EX_SET_SMEM
+    if (e != cudaSuccess) return cuda_error(e, "ntt smem attribute");
+    uint2 lf[31], li[31];
+    for (uint32_t hh = 1; hh <= 16; hh <<= 1) {
+        const uint32_t wf = powmod(kGen, (kP - 1) / (2 * hh)), wi = powmod(wf, kP - 2);
+        for (uint32_t r = 0; r < hh; ++r) {
+            const uint32_t a = powmod(wf, r), b = powmod(wi, r);
+            lf[hh - 1 + r] = make_uint2(a, shoup_q(a));
+            li[hh - 1 + r] = make_uint2(b, shoup_q(b));
+        }
+    }
+    // complete before the flag is set: another thread may launch at once
+    if ((e = cudaMemcpyToSymbolAsync(c_low_f, lf, sizeof(lf), 0, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+        (e = cudaMemcpyToSymbolAsync(c_low_i, li, sizeof(li), 0, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)
+        return cuda_error(e, "ntt constant twiddles");
+    if (dev < 64) done |= 1ull << dev;
+    return EXTRACT_OK;
+}
+
+// seed_dev: realigned seed bits (bit t = seed[t]), L = s + k - 1 bits.
 int ntt_create(NttPlan **out, uint32_t m, uint32_t s, uint32_t k, const uint32_t *seed_dev, cudaStream_t st,
-               uint32_t *work)
+               uint32_t *work, int split_log2)
 {
     *out = nullptr;
-    if (!ntt_eligible(s, k)) return set_error(EXTRACT_EINVAL, "NTT path needs 2^11 < s+k-1 <= 2^22");
+    const NttShape sh = ntt_shape(s, k, split_log2);
+    if (!sh.N) return set_error(EXTRACT_EINVAL, "no NTT shape for s=%u k=%u (split %d)", s, k, split_log2);
     NttPlan *p = new NttPlan();
-    p->N = ntt_length(s, k);
+    p->N = sh.N;
+    p->P = sh.P;
+    p->h = sh.h;
     p->e = 0;
     while ((1u << p->e) < p->N) ++p->e;
     p->R1 = p->N / kR2;
     p->r1_log = p->e - kR2Log;
-    // sub-blocks per launch: keep the working buffer near 64 MB (L2-sized)
-    p->G = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(m, (16ull << 20) / p->N));
+    p->G = group_size(m, sh);
     const uint32_t R1 = p->R1;
     // table layout (words): col_f, col_fq, col_i, col_iq (R1/2 each, >= 1),
     // row_f, row_fq, row_i, row_iq (1024 each), tw_lo_f, tw_lo_i (2048),
@@ -918,40 +1105,16 @@ int ntt_create(NttPlan **out, uint32_t m, uint32_t s, uint32_t k, const uint32_t
         p->T.row_stage_i = reinterpret_cast<const uint2 *>(t + o_rs_i);
         p->T.col_stage_f = reinterpret_cast<const uint2 *>(t + o_cs_f);
         p->T.col_stage_i = reinterpret_cast<const uint2 *>(t + o_cs_i);
+        const size_t spec = (size_t)p->P * p->N;
         if (work) {
             p->buf = work;
             p->own_buf = false;
-        } else if ((e = cudaMallocAsync(&p->buf, (size_t)p->G * p->N * 4, st)) != cudaSuccess) {
+        } else if ((e = cudaMallocAsync(&p->buf, (size_t)p->G * spec * 4, st)) != cudaSuccess) {
             rc = cuda_error(e, "ntt buffer");
             break;
         }
-        if ((e = cudaMallocAsync(&p->S, (size_t)p->N * 4, st)) != cudaSuccess) { rc = cuda_error(e, "ntt spectrum"); break; }
-        if ((e = cudaMallocAsync(&p->Sq, (size_t)p->N * 4, st)) != cudaSuccess) { rc = cuda_error(e, "ntt spectrum"); break; }
-        const size_t smem = smem_generic(R1);
-        if ((e = cudaFuncSetAttribute(ntt_pass_a_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess ||
-            (e = cudaFuncSetAttribute(ntt_pass_a_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess ||
-            (e = cudaFuncSetAttribute(ntt_pass_a_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) {
-            rc = cuda_error(e, "ntt smem attribute");
-            break;
-        }
-        if (R1 >= 32) {
-            const int epl = (int)(R1 / 32);
-#define EX_SET_SMEM(E, KF, KI, SMEM)                                                                            \
-    if (epl == E) {                                                                                            \
-        e = cudaFuncSetAttribute(KF<E, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(SMEM));         \
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(KF<E, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(SMEM)); \
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(KI<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(SMEM)); \
-    }
-            EX_SET_SMEM(1, ntt_cols_fwd_kernel, ntt_cols_inv_kernel, smem_generic(R1))
-            EX_SET_SMEM(2, ntt_cols_fwd_kernel, ntt_cols_inv_kernel, smem_generic(R1))
-            EX_SET_SMEM(4, ntt_cols_fwd_kernel, ntt_cols_inv_kernel, smem_generic(R1))
-            EX_SET_SMEM(8, ntt_cols_fwd_kernel, ntt_cols_inv_kernel, smem_generic(R1))
-            EX_SET_SMEM(16, ntt_cols_fwd_kernel, ntt_cols_inv_kernel, smem_generic(R1))
-            EX_SET_SMEM(32, ntt_cols_fwd_t_kernel, ntt_cols_inv_t_kernel, smem_transposed(R1))
-            EX_SET_SMEM(64, ntt_cols_fwd_t_kernel, ntt_cols_inv_t_kernel, smem_transposed(R1))
-#undef EX_SET_SMEM
-            if (e != cudaSuccess) { rc = cuda_error(e, "ntt smem attribute"); break; }
-        }
+        if ((e = cudaMallocAsync(&p->S, spec * 4, st)) != cudaSuccess) { rc = cuda_error(e, "ntt spectrum"); break; }
+        if ((e = cudaMallocAsync(&p->Sq, spec * 4, st)) != cudaSuccess) { rc = cuda_error(e, "ntt spectrum"); break; }
         if (R1 >= 1024) {
             if ((e = cudaMallocAsync(&p->twist, (size_t)2 * p->N * 4, st)) != cudaSuccess) { rc = cuda_error(e, "ntt twist tables"); break; }
             p->T.twist_f = p->twist;
@@ -959,30 +1122,22 @@ int ntt_create(NttPlan **out, uint32_t m, uint32_t s, uint32_t k, const uint32_t
             ntt_twist_table_kernel<<<(uint32_t)std::min<uint64_t>(ceil_div(p->N, 256), 8192), 256, 0, st>>>(
                 p->twist, p->twist + p->N, R1, p->r1_log, p->T);
         }
-        // twiddles of the distance < 32 stages, as constant-bank operands
-        {
-            uint2 lf[31], li[31];
-            for (uint32_t hh = 1; hh <= 16; hh <<= 1) {
-                const uint32_t wf = powmod(kGen, (kP - 1) / (2 * hh)), wi = powmod(wf, kP - 2);
-                for (uint32_t r = 0; r < hh; ++r) {
-                    const uint32_t a = powmod(wf, r), b = powmod(wi, r);
-                    lf[hh - 1 + r] = make_uint2(a, shoup_q(a));
-                    li[hh - 1 + r] = make_uint2(b, shoup_q(b));
-                }
-            }
-            if ((e = cudaMemcpyToSymbol(c_low_f, lf, sizeof(lf))) != cudaSuccess ||
-                (e = cudaMemcpyToSymbol(c_low_i, li, sizeof(li))) != cudaSuccess) {
-                rc = cuda_error(e, "ntt constant twiddles");
-                break;
-            }
-        }
-        // seed spectrum: pass A (forward bits) + row DIF into S, then scale by 1/N
+        if ((rc = device_setup(st)) != EXTRACT_OK) break;
+        // seed spectra: for piece q, the window seed[q h .. q h + h + k - 1)
+        // (zero past L = s + k - 1) through pass A + row DIF into S + q N;
+        // then all are scaled by 1/N
         const uint32_t L = s + k - 1;
-        if (int lrc = ntt_launch_a(p, seed_dev, 0, L, false, 1, p->S, st)) { rc = lrc; break; }
-        ntt_launch_rows(p, p->S, 1, nullptr, nullptr, false, st);
+        for (uint32_t q = 0; q < p->P && rc == EXTRACT_OK; ++q) {
+            const uint32_t off = q * p->h;  // a multiple of 32 when P > 1
+            const uint32_t len = std::min(p->h + k - 1, L - off);
+            const Pieces pc{0, 1, 0, len, len};
+            if (int lrc = ntt_launch_a(p, seed_dev + off / 32, pc, false, 1, p->S + (size_t)q * p->N, st)) rc = lrc;
+            else ntt_launch_rows(p, p->S + (size_t)q * p->N, 1, 1, nullptr, nullptr, false, st);
+        }
+        if (rc != EXTRACT_OK) break;
         const uint32_t ninv = powmod(p->N, kP - 2);
-        ntt_finish_spectrum_kernel<<<(uint32_t)std::min<uint64_t>(ceil_div(p->N, 256), 4096), 256, 0, st>>>(
-            p->S, p->Sq, p->N, ninv, shoup_q(ninv));
+        ntt_finish_spectrum_kernel<<<(uint32_t)std::min<uint64_t>(ceil_div(spec, 256), 4096), 256, 0, st>>>(
+            p->S, p->Sq, (uint32_t)spec, ninv, shoup_q(ninv));
         if ((e = cudaGetLastError()) != cudaSuccess) { rc = cuda_error(e, "ntt spectrum kernels"); break; }
         if ((e = cudaStreamSynchronize(st)) != cudaSuccess) { rc = cuda_error(e, "ntt spectrum"); break; }
     } while (0);
@@ -991,16 +1146,26 @@ int ntt_create(NttPlan **out, uint32_t m, uint32_t s, uint32_t k, const uint32_t
     return EXTRACT_OK;
 }
 
+// The pieces of stored sub-blocks: row g at g w_pad words, piece q from
+// row bit q h (the reversed row's bit b holds A[s-1-b], so piece q holds
+// coefficients s-(q+1)h .. s-q h-1, and bits past s read as 0).
+static Pieces sub_block_pieces(const NttPlan *p, uint32_t w_pad, uint32_t s)
+{
+    return Pieces{w_pad, p->P, p->P > 1 ? p->h / 32 : 0u, p->h, s};
+}
+
 // Hash every sub-block: out (zeroed here) gets K_j at bit j*k.
 int ntt_hash(const NttPlan *p, const uint32_t *arev, uint32_t w_pad, uint32_t m, uint32_t s, uint32_t k,
-             uint32_t *out, cudaStream_t st)
+             uint32_t *out, cudaStream_t st, uint32_t *work)
 {
+    uint32_t *buf = work ? work : p->buf;
     EX_CUDA(cudaMemsetAsync(out, 0, ceil_div((uint64_t)m * k, 32) * 4, st));
+    const Pieces pc = sub_block_pieces(p, w_pad, s);
     for (uint32_t j0 = 0; j0 < m; j0 += p->G) {
         const uint32_t g = std::min(p->G, m - j0);
-        if (int rc = ntt_launch_a(p, arev + (size_t)j0 * w_pad, w_pad, s, true, g, p->buf, st)) return rc;
-        ntt_launch_rows(p, p->buf, g, p->S, p->Sq, true, st);
-        if (int rc = ntt_launch_a_inv(p, g, j0, s, k, out, st)) return rc;
+        if (int rc = ntt_launch_a(p, arev + (size_t)j0 * w_pad, pc, true, g, buf, st)) return rc;
+        ntt_launch_rows(p, buf, g, p->P, p->S, p->Sq, true, st);
+        if (int rc = ntt_launch_a_inv(p, buf, g, j0, k, out, st)) return rc;
     }
     EX_LAUNCH("ntt kernels");
     return EXTRACT_OK;
@@ -1013,6 +1178,7 @@ int ntt_run_overlapped(const NttPlan *p, const uint32_t *in, const uint32_t *per
     EX_CUDA(cudaEventRecord(ev_fork, st));
     EX_CUDA(cudaStreamWaitEvent(aux, ev_fork, 0));
     EX_CUDA(cudaMemsetAsync(out, 0, ceil_div((uint64_t)m * k, 32) * 4, st));
+    const Pieces pc = sub_block_pieces(p, w_pad, s);
     for (uint32_t j0 = 0; j0 < m; j0 += p->G) {
         const uint32_t g = std::min(p->G, m - j0);
         uint32_t *ar = arev + (size_t)j0 * w_pad;
@@ -1020,9 +1186,9 @@ int ntt_run_overlapped(const NttPlan *p, const uint32_t *in, const uint32_t *per
         // each wait binds to the record just before it, so one event serves every group
         EX_CUDA(cudaEventRecord(ev_group, aux));
         EX_CUDA(cudaStreamWaitEvent(st, ev_group, 0));
-        if (int rc = ntt_launch_a(p, ar, w_pad, s, true, g, p->buf, st)) return rc;
-        ntt_launch_rows(p, p->buf, g, p->S, p->Sq, true, st);
-        if (int rc = ntt_launch_a_inv(p, g, j0, s, k, out, st)) return rc;
+        if (int rc = ntt_launch_a(p, ar, pc, true, g, p->buf, st)) return rc;
+        ntt_launch_rows(p, p->buf, g, p->P, p->S, p->Sq, true, st);
+        if (int rc = ntt_launch_a_inv(p, p->buf, g, j0, k, out, st)) return rc;
     }
     EX_LAUNCH("ntt kernels");
     return EXTRACT_OK;
@@ -1030,5 +1196,6 @@ int ntt_run_overlapped(const NttPlan *p, const uint32_t *in, const uint32_t *per
 
 uint32_t ntt_group(const NttPlan *p) { return p->G; }
 uint32_t ntt_size(const NttPlan *p) { return p->N; }
+uint32_t ntt_pieces(const NttPlan *p) { return p->P; }
 
 }  // namespace ex

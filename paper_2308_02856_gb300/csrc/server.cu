@@ -43,6 +43,7 @@ using Clock = std::chrono::steady_clock;
 enum JobState { kQueued, kAdmitted, kSetupLaunched, kReady, kDone, kFailed };
 
 constexpr int kWaveSlots = 2;
+constexpr int kNttLanes = 2;
 constexpr uint32_t kMaxWaveTiles = 1u << 16;
 
 struct SJob {
@@ -70,6 +71,12 @@ struct SJob {
     Clock::time_point t_submit, t_done;
 };
 using JobPtr = std::shared_ptr<SJob>;
+
+struct NttLane {
+    cudaStream_t st = nullptr;
+    uint32_t *work = nullptr;
+    JobPtr cur;
+};
 
 struct Wave {
     bool busy = false;
@@ -127,10 +134,9 @@ struct extract_server {
     uint64_t next_ticket = 1;
     cudaStream_t setup_st = nullptr;
     Wave waves[kWaveSlots];
-    // NTT lane: one job at a time (shared work buffer), concurrent with the waves
-    cudaStream_t ntt_st = nullptr;
-    uint32_t *ntt_work = nullptr;
-    JobPtr ntt_cur;
+    // NTT lanes: one job at a time each (own stream and work buffer),
+    // concurrent with the waves and with each other
+    NttLane lanes[kNttLanes];
     std::thread sched_thread, setup_thread;
     // statistics
     uint64_t submitted = 0, admitted = 0, completed = 0, failed = 0, rejected = 0, nwaves = 0;
@@ -159,7 +165,7 @@ int setup_job(extract_server *S, SJob &J)
     if (int rc = launch_gather(J.in, J.perm, J.m, J.s, J.w_pad, J.arev, st, S->sms)) return rc;
     EX_CUDA(cudaMemsetAsync(J.out, 0, ceil_div((uint64_t)J.m * J.k, 32) * 4, st));
     if (J.use_ntt)  // tables and the seed spectrum (synchronous on the setup stream)
-        if (int rc = ntt_create(&J.ntt, J.m, J.s, J.k, J.seed, st, S->ntt_work)) return rc;
+        if (int rc = ntt_create(&J.ntt, J.m, J.s, J.k, J.seed, st, S->lanes[0].work)) return rc;
     // the order is only needed by the gather: give its memory back now
     if (J.perm) {
         EX_CUDA(cudaFreeAsync(J.perm, st));
@@ -272,7 +278,9 @@ bool schedule_step(extract_server *S)
                     j->state = kFailed;
                 }
             }
-            if ((finished || j->state == kFailed) && S->ntt_cur == j) S->ntt_cur.reset();
+            if (finished || j->state == kFailed)
+                for (NttLane &L : S->lanes)
+                    if (L.cur == j) L.cur.reset();
         } else {
             finished = j->state == kReady && j->next_tile == j->tiles.size() && j->outstanding_waves == 0;
         }
@@ -296,25 +304,25 @@ bool schedule_step(extract_server *S)
         }
         ++i;
     }
-    // 4. the NTT lane: the ready NTT job with the least predicted time
-    if (!S->ntt_cur) {
+    // 4. each free NTT lane takes the ready NTT job with the least predicted time
+    for (NttLane &L : S->lanes) {
+        if (L.cur) continue;
         JobPtr best;
         for (JobPtr &j : S->active)
             if (j->use_ntt && j->state == kReady && !j->hashed && (!best || j->remaining_ns < best->remaining_ns))
                 best = j;
-        if (best) {
-            int rc = ntt_hash(best->ntt, best->arev, best->w_pad, best->m, best->s, best->k, best->out, S->ntt_st);
-            cudaError_t e = rc == EXTRACT_OK ? cudaEventRecord(best->done_ev, S->ntt_st) : cudaSuccess;
-            if (rc == EXTRACT_OK && e != cudaSuccess) rc = cuda_error(e, "ntt event");
-            best->hashed = true;
-            if (rc != EXTRACT_OK) {
-                best->rc = rc;
-                best->state = kFailed;
-            } else {
-                S->ntt_cur = best;
-            }
-            progress = true;
+        if (!best) break;
+        int rc = ntt_hash(best->ntt, best->arev, best->w_pad, best->m, best->s, best->k, best->out, L.st, L.work);
+        cudaError_t e = rc == EXTRACT_OK ? cudaEventRecord(best->done_ev, L.st) : cudaSuccess;
+        if (rc == EXTRACT_OK && e != cudaSuccess) rc = cuda_error(e, "ntt event");
+        best->hashed = true;
+        if (rc != EXTRACT_OK) {
+            best->rc = rc;
+            best->state = kFailed;
+        } else {
+            L.cur = best;
         }
+        progress = true;
     }
     // 5. a new wave on a free slot: shortest remaining work first
     for (Wave &w : S->waves) {
@@ -401,8 +409,10 @@ void destroy_server(extract_server *S)
         if (w.st) cudaStreamDestroy(w.st);
     }
     if (S->setup_st) cudaStreamDestroy(S->setup_st);
-    if (S->ntt_st) cudaStreamDestroy(S->ntt_st);
-    cudaFree(S->ntt_work);
+    for (NttLane &L : S->lanes) {
+        if (L.st) cudaStreamDestroy(L.st);
+        cudaFree(L.work);
+    }
     for (auto &kv : S->by_ticket) {
         if (kv.second->setup_ev) cudaEventDestroy(kv.second->setup_ev);
         if (kv.second->done_ev) cudaEventDestroy(kv.second->done_ev);
@@ -434,9 +444,12 @@ int extract_server_create(extract_server **out, uint64_t hbm_budget_bytes, uint3
     int rc = EXTRACT_OK;
     do {
         if ((e = cudaStreamCreateWithFlags(&S->setup_st, cudaStreamNonBlocking)) != cudaSuccess) { rc = cuda_error(e, "stream"); break; }
-        if ((e = cudaStreamCreateWithFlags(&S->ntt_st, cudaStreamNonBlocking)) != cudaSuccess) { rc = cuda_error(e, "stream"); break; }
-        // the largest NTT work buffer any job can need (2^22-point transforms)
-        if ((e = cudaMalloc(&S->ntt_work, ntt_work_words(1u << 16, 1u << 21, 1u << 21) * 4)) != cudaSuccess) { rc = cuda_error(e, "ntt work"); break; }
+        // each lane holds the largest NTT work buffer any job can need
+        for (NttLane &L : S->lanes) {
+            if ((e = cudaStreamCreateWithFlags(&L.st, cudaStreamNonBlocking)) != cudaSuccess) { rc = cuda_error(e, "stream"); break; }
+            if ((e = cudaMalloc(&L.work, ntt_max_work_words() * 4)) != cudaSuccess) { rc = cuda_error(e, "ntt work"); break; }
+        }
+        if (rc != EXTRACT_OK) break;
         for (Wave &w : S->waves) {
             if ((e = cudaStreamCreateWithFlags(&w.st, cudaStreamNonBlocking)) != cudaSuccess) { rc = cuda_error(e, "stream"); break; }
             if ((e = cudaEventCreateWithFlags(&w.ev, cudaEventDisableTiming)) != cudaSuccess) { rc = cuda_error(e, "event"); break; }

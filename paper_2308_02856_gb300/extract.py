@@ -34,6 +34,11 @@ def EXTRACT_KEY_BITS(b: int) -> int:
     return (int(b) & 0x3F) << 8
 
 
+def EXTRACT_NTT_SPLIT(l: int) -> int:
+    """NTT method: 2^l pieces per sub-block (l = 0 .. 4) instead of the automatic split."""
+    return ((int(l) + 1) & 0x7) << 16
+
+
 # Every symbol include/extract.h declares (checked by the CPU test suite).
 EXPORTED = [
     "extract_create", "extract_run", "extract_run_host", "extract_gather", "extract_hash", "extract_run_plain",

@@ -1,6 +1,7 @@
 """The exact NTT middle product (the FFT direction of Sec. I / Sec. V, done in
 integers modulo a prime): bit-exact against the CPU oracle and against the
-direct GF(2) kernel, over transform lengths 2^12 .. 2^22."""
+direct GF(2) kernel, over transform lengths 2^12 .. 2^22 and every split of
+a sub-block into 2^l pieces."""
 import numpy as np
 import pytest
 
@@ -83,6 +84,31 @@ def test_ntt_matches_direct_kernel(n, m, s, k, p):
             assert got[j * k + i] == oracle.toeplitz_bit(seed, s, A, int(i)), (j, i)
 
 
+@pytest.mark.parametrize("n,m,s,k", [
+    (8192, 2, 4000, 1000),            # last piece ragged (4000 = 2016 + 1984 at P = 2)
+    (1 << 18, 8, 1 << 15, 1 << 13),   # pieces of whole words at every P
+    (70_001, 5, 14_000, 7_000),
+    (3 * 40_001, 3, 40_001, 333),     # small k: up to 16 pieces; s odd
+])
+def test_ntt_every_split_matches_oracle(n, m, s, k):
+    """Each sub-block split into 2^l pieces (one middle product per piece,
+    summed before the inverse transform) gives the oracle's bits."""
+    in_w = synth.bernoulli_bits(n, 0.65, 31)
+    seed = synth.uniform_bits(s + k - 1, 32)
+    want = oracle.extract(n, m, s, k, in_w, seed, 2)
+    ran = []
+    for l in range(5):
+        try:
+            got, desc = _run(n, m, s, k, X.EXTRACT_METHOD_NTT | X.EXTRACT_NTT_SPLIT(l), in_w, seed)
+        except X.ExtractError as e:
+            assert e.code == X.EXTRACT_EINVAL  # no transform length for this split
+            continue
+        assert " P=%d " % (1 << l) in desc, desc
+        assert np.array_equal(got, want), "split 2^%d" % l
+        ran.append(l)
+    assert len(ran) >= 3, ran
+
+
 def test_ntt_flag_rejections():
     seed = np.zeros(10000, dtype=np.uint32)
     for n, m, s, k, fl in [
@@ -90,6 +116,8 @@ def test_ntt_flag_rejections():
         (1 << 24, 1, 1 << 23, 1 << 22, 0),                       # s + k - 1 > 2^22
         (2 ** 14, 2, 4096, 100, X.EXTRACT_SEED_PER_SUBBLOCK),     # one seed per sub-block
         (2 ** 14, 2, 4096, 100, X.EXTRACT_METHOD_DIRECT),         # both methods
+        (4096 * 2, 2, 2049, 1000, X.EXTRACT_NTT_SPLIT(4)),        # 16 pieces would leave one empty
+        (4096 * 2, 2, 2049, 1000, 6 << 16),                       # split field out of range
     ]:
         with pytest.raises(X.ExtractError) as e:
             X.extract_create(n, m, s, k, seed, 1, fl | X.EXTRACT_METHOD_NTT)
