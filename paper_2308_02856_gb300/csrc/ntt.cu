@@ -9,22 +9,29 @@
 // cyclic convolution of length N = 2^e >= s + k - 1 leaves coefficients
 // s-1 .. s+k-2 free of wrap-around (no index pair reaches N + s - 1).
 //
+// Splitting: a sub-block may be cut into P = 2^l pieces of h coefficients;
+// piece q is its own middle product against the seed window starting at
+// q h, the P products add up in the frequency domain, and one inverse
+// transform of length N >= h + k - 1 gives their sum (work P + 1 transforms
+// of N instead of 2 of the length for s + k - 1).
+//
 // Four-step layout, N = R1 x R2 with R2 = 2048 (element t = t1 R2 + t2):
-//   pass A  (16 columns t2 of one sub-block per CTA): load the bits, R1-point
-//           DIF NTT along t1, multiply by w_N^(k1 t2);
-//   pass B  (two warps per row): 2048-point DIF NTT of the row, multiply by
-//           the seed spectrum (laid out the same way, 1/N folded in),
-//           2048-point inverse DIT NTT;
-//   pass A' (16 columns per CTA): multiply by w_N^(-k1 t2), R1-point inverse
+//   pass A  (columns t2 of one piece per CTA): load the bits, R1-point DIF
+//           NTT along t1, multiply by w_N^(k1 t2);
+//   pass B  (two warps per row): 2048-point DIF NTT of each piece's row,
+//           multiply by that piece's seed spectrum (laid out the same way,
+//           1/N folded in), sum over pieces, 2048-point inverse DIT NTT;
+//   pass A' (columns per CTA): multiply by w_N^(-k1 t2), R1-point inverse
 //           DIT NTT along t1, then the parity of every coefficient t in
-//           [s-1, s+k-1) goes straight to output bit j k + t - (s-1).
+//           [h-1, h+k-1) goes straight to output bit j k + t - (h-1).
 // DIF leaves bit-reversed order and DIT consumes it, so nothing is permuted.
 //
 // Warp transforms: a warp holds 32 EPL values, lane l / register j at
-// position 32 j + l; stages with pair distance >= 32 run inside registers,
-// then a swizzled shared-memory transpose (word 32 j + (l ^ j)) gives each
-// lane whole rows of 32 and the distance < 32 stages run in registers too,
-// with their twiddles as constant-bank operands.
+// position 32 j + l (for R1 < 1024, 32 / E whole columns of 32 E); stages
+// with pair distance >= 32 run inside registers, then a swizzled
+// shared-memory transpose (word 32 j + (l ^ j)) gives each lane whole rows
+// of 32 and the distance < 32 stages run in registers too, with their
+// twiddles as constant-bank operands.
 //
 // Arithmetic (Harvey's lazy butterflies): 4p < 2^31, so DIF values stay in
 // [0, 2p) and DIT values in [0, 4p) with one conditional subtraction per
@@ -134,7 +141,7 @@ struct Tables {
     // (w_2h^r, Shoup quotient) for r < h, every h = 1, 2, 4, ... < R
     const uint2 *row_stage_f, *row_stage_i;  // R = 2048
     const uint2 *col_stage_f, *col_stage_i;  // R = R1
-    // full twist tables for R1 >= 1024 (Montgomery form): entry t2 * R1 + r
+    // full twist tables for R1 >= 32 (Montgomery form): entry t2 * R1 + r
     // is w_N^(+-bitrev(r) t2)
     const uint32_t *twist_f, *twist_i;
 };
@@ -340,70 +347,6 @@ __global__ void ntt_finish_spectrum_kernel(uint32_t *S, uint32_t *Sq, uint32_t N
 }
 
 
-// ---- warp-resident transforms --------------------------------------------
-// A warp holds R = 32 EPL values; lane l, register j holds position l + 32 j.
-// Stages whose pair distance h is >= 32 pair two registers of one lane;
-// stages with h <= 16 pair lanes l and l ^ h through a shuffle.
-constexpr uint32_t kOneQ = (uint32_t)(((uint64_t)1 << 32) / kP);  // Shoup quotient of 1
-
-// DIF (natural positions in, bit-reversed out), twiddles w_2h^(i mod 2h).
-template <int EPL>
-__device__ __forceinline__ void warp_dif(uint32_t (&e)[EPL], const uint2 *__restrict__ tw, int lane)
-{
-#pragma unroll
-    for (int hp = EPL / 2; hp >= 1; hp >>= 1) {
-        const int h = hp * 32;
-#pragma unroll
-        for (int j = 0; j < EPL; ++j) {
-            if (j & hp) continue;
-            const uint2 w = __ldg(tw + (h - 1) + lane + 32 * (j & (hp - 1)));
-            const uint32_t u = e[j], v = e[j + hp];
-            e[j] = add_p(u, v);
-            e[j + hp] = mul_shoup(sub_p(u, v), w.x, w.y);
-        }
-    }
-#pragma unroll
-    for (int h = 16; h >= 1; h >>= 1) {
-        const bool upper = (lane & h) != 0;
-        const uint2 w = upper ? __ldg(tw + (h - 1) + (lane & (h - 1))) : make_uint2(1u, kOneQ);
-#pragma unroll
-        for (int j = 0; j < EPL; ++j) {
-            const uint32_t p = __shfl_xor_sync(0xffffffffu, e[j], h);
-            const uint32_t d = upper ? sub_p(p, e[j]) : add_p(e[j], p);
-            e[j] = mul_shoup(d, w.x, w.y);
-        }
-    }
-}
-
-// DIT (bit-reversed positions in, natural out), twiddles w_2h^-(i mod 2h).
-template <int EPL>
-__device__ __forceinline__ void warp_dit(uint32_t (&e)[EPL], const uint2 *__restrict__ tw, int lane)
-{
-#pragma unroll
-    for (int h = 1; h <= 16; h <<= 1) {
-        const bool upper = (lane & h) != 0;
-        const uint2 w = __ldg(tw + (h - 1) + (lane & (h - 1)));
-#pragma unroll
-        for (int j = 0; j < EPL; ++j) {
-            const uint32_t p = __shfl_xor_sync(0xffffffffu, e[j], h);
-            const uint32_t m = mul_shoup(upper ? e[j] : p, w.x, w.y);  // w * (upper element)
-            e[j] = upper ? sub_p(p, m) : add_p(e[j], m);
-        }
-    }
-#pragma unroll
-    for (int hp = 1; hp <= EPL / 2; hp <<= 1) {
-        const int h = hp * 32;
-#pragma unroll
-        for (int j = 0; j < EPL; ++j) {
-            if (j & hp) continue;
-            const uint2 w = __ldg(tw + (h - 1) + lane + 32 * (j & (hp - 1)));
-            const uint32_t u = e[j], v = mul_shoup(e[j + hp], w.x, w.y);
-            e[j] = add_p(u, v);
-            e[j + hp] = sub_p(u, v);
-        }
-    }
-}
-
 // ---- transposed warp transforms (32 EPL values, EPL in {32, 64}) ---------
 // distance < 32 stages: twiddle w_2h^r for r < h at (h - 1) + r, h = 1..16
 __constant__ uint2 c_low_f[31];
@@ -413,12 +356,15 @@ __device__ __forceinline__ uint32_t swz(uint32_t t) { return (t & ~31u) | ((t ^ 
 
 
 // DIF: layout A in (e[j] = position 32 j + l), layout B out (e[32 q + i] =
-// position 32 (l + 32 q) + i).  sw: this warp's 32 EPL-word scratch.
-template <int EPL>
+// position 32 (l + 32 q) + i).  sw: this warp's 32 EPL-word scratch.  HP0:
+// the largest register-stage distance / 32 (EPL / 2 for one column; E / 2
+// when the 32 EPL positions are 32 / E columns of 32 E, which the register
+// stages then never mix).
+template <int EPL, int HP0 = EPL / 2>
 __device__ __forceinline__ void dif_warp_t(uint32_t (&e)[EPL], uint32_t *sw, const uint2 *__restrict__ tw, int lane)
 {
 #pragma unroll
-    for (int hp = EPL / 2; hp >= 1; hp >>= 1) {
+    for (int hp = HP0; hp >= 1; hp >>= 1) {
 #pragma unroll
         for (int j = 0; j < EPL; ++j) {
             if (j & hp) continue;
@@ -447,7 +393,7 @@ __device__ __forceinline__ void dif_warp_t(uint32_t (&e)[EPL], uint32_t *sw, con
 }
 
 // DIT: layout B in, layout A out (the exact reverse of dif_warp_t).
-template <int EPL>
+template <int EPL, int HP0 = EPL / 2>
 __device__ __forceinline__ void dit_warp_t(uint32_t (&e)[EPL], uint32_t *sw, const uint2 *__restrict__ tw, int lane)
 {
 #pragma unroll
@@ -469,7 +415,7 @@ __device__ __forceinline__ void dit_warp_t(uint32_t (&e)[EPL], uint32_t *sw, con
     for (int j = 0; j < EPL; ++j) e[j] = sw[swz(32u * j + lane)];
     __syncwarp();
 #pragma unroll
-    for (int hp = 1; hp <= EPL / 2; hp <<= 1) {
+    for (int hp = 1; hp <= HP0; hp <<= 1) {
 #pragma unroll
         for (int j = 0; j < EPL; ++j) {
             if (j & hp) continue;
@@ -692,90 +638,166 @@ ntt_cols_inv_t_kernel(const uint32_t *__restrict__ buf, uint64_t sub_stride, int
     }
 }
 
-// Pass A, one warp per column (16 per CTA): bits -> DIF along t1 -> twist,
-// staged through shared memory so the row-major stores are coalesced.
-template <int EPL, bool kReversed>
-__global__ void __launch_bounds__(kCW * 32)
-ntt_cols_fwd_kernel(const uint32_t *__restrict__ bits, Pieces pc, int r1_log, uint32_t N, Tables T,
-                    uint32_t *__restrict__ buf)
+// ---- multi-column warps (R1 = 32 E, E in {1, 2, 4, 8, 16}) ---------------
+// A warp transforms COLS = 32 / E columns at once: lane l, register j holds
+// element 32 (j % E) + l of column j / E (layout A).  The distance >= 32
+// stages pair registers of one column; the swizzled transpose then gives
+// lane l the 32 consecutive elements 32 (l % E) .. 32 (l % E) + 31 of column
+// l / E (layout B), where the distance < 32 stages run: no shuffles.  A CTA
+// of 16 warps covers CW = 16 COLS adjacent columns; its R1 x CW tile sits in
+// shared memory row-major, the column of row r XOR-ed with COLS (r / 32) so
+// that both the per-lane column writes and the row-wise copies are
+// conflict-free.
+constexpr uint32_t kTileWords = 16384;  // R1 x CW = 32 E x 16 (32 / E)
+size_t smem_multi() { return (size_t)(kTileWords + 1024) * 4; }
+
+template <int E>
+__device__ __forceinline__ uint32_t tile_at(uint32_t r, uint32_t c)
 {
-    constexpr uint32_t R1 = 32u * EPL;
-    extern __shared__ uint32_t x[];  // R1 * kCS + R1
-    const int lane = threadIdx.x & 31, c = threadIdx.x >> 5;
-    const uint32_t g = blockIdx.y, c0 = blockIdx.x * kCW, t2 = c0 + c;
-    uint32_t *rb = x + R1 * kCS;  // R1 staged row bits
-    uint32_t lim;
-    const uint32_t *b = piece_src(bits, pc, g, lim);
-    stage_row_bits<kReversed>(rb, b, pc.len, lim, R1, c0);
-    __syncthreads();
-    uint32_t e[EPL];
-#pragma unroll
-    for (int j = 0; j < EPL; ++j) e[j] = (rb[lane + 32u * j] >> c) & 1u;
-    warp_dif<EPL>(e, T.col_stage_f, lane);
-#pragma unroll
-    for (int j = 0; j < EPL; ++j) {
-        const uint32_t r = lane + 32u * j;
-        e[j] = mul_mont(e[j], twist_mont(T.tw_lo_f, T.tw_hi_f, bitrev(r, r1_log) * t2));
-        x[r * kCS + c] = e[j];
-    }
-    __syncthreads();
-    uint32_t *o = buf + (size_t)g * N;
-    for (uint32_t it = threadIdx.x; it < R1 * kCW; it += blockDim.x) {
-        const uint32_t cc = it % kCW, r = it / kCW;
-        o[(size_t)r * kR2 + c0 + cc] = x[r * kCS + cc];
+    constexpr uint32_t COLS = 32u / E, CW = 16u * COLS;
+    return r * CW + (c ^ (COLS * (r >> 5)));
+}
+
+// Staged bits for CW >= 32 columns: rb[t1 * CW/32 + w] bit c is element
+// t = t1 R2 + c0 + 32 w + c, read as in stage_row_bits (c0 % 32 == 0).
+template <bool kReversed, uint32_t WPR>
+__device__ __forceinline__ void stage_row_words(uint32_t *rb, const uint32_t *__restrict__ b, uint32_t len,
+                                                uint32_t lim, uint32_t R1, uint32_t c0)
+{
+    for (uint32_t it = threadIdx.x; it < R1 * WPR; it += blockDim.x) {
+        const uint32_t t1 = it / WPR, wi = it % WPR;
+        const uint32_t t0 = t1 * kR2 + c0 + 32u * wi;
+        uint32_t f = 0;
+        if (t0 < len) {
+            if (kReversed) {
+                const int32_t hi = (int32_t)(len - 1 - t0), lo = hi - 31;
+                const int32_t top = min(hi, (int32_t)lim - 1);
+                if (top >= max(lo, 0)) {
+                    const int32_t w0 = lo >> 5, w1 = top >> 5;  // floor; w1 >= 0
+                    const uint32_t a = w0 >= 0 ? __ldg(b + w0) : 0u;
+                    const uint32_t c = w1 != w0 ? __ldg(b + w1) : 0u;
+                    const uint64_t v = ((uint64_t)c << 32) | a;
+                    const int32_t nb = top - lo + 1;  // 1 .. 32 positions kept
+                    const uint32_t f32 = (uint32_t)(v >> (lo - 32 * w0)) & (nb >= 32 ? ~0u : (1u << nb) - 1u);
+                    f = __brev(f32);  // position lo + i -> column 31 - i
+                }
+            } else {
+                const uint32_t end = min(len, lim);
+                if (t0 < end) {
+                    f = __ldg(b + (t0 >> 5));
+                    if (end - t0 < 32u) f &= (1u << (end - t0)) - 1u;
+                }
+            }
+        }
+        rb[it] = f;
     }
 }
 
-// Pass A', one warp per column: coalesced load through shared memory,
-// untwist, inverse DIT along t1, parity of the wanted coefficients.
-template <int EPL>
-__global__ void __launch_bounds__(kCW * 32)
-ntt_cols_inv_kernel(const uint32_t *__restrict__ buf, uint64_t sub_stride, int r1_log, Tables T, uint32_t j0, uint32_t len,
-                    uint32_t k, uint32_t *__restrict__ out)
+// Pass A: bits -> DIF along t1 -> twist -> buf, for CW columns per CTA.
+template <int E, bool kReversed>
+__global__ void __launch_bounds__(512, 2)
+ntt_cols_fwd_m_kernel(const uint32_t *__restrict__ bits, Pieces pc, uint32_t N, Tables T, uint32_t *__restrict__ buf)
 {
-    constexpr uint32_t R1 = 32u * EPL;
-    extern __shared__ uint32_t x[];  // R1 * kCS
-    const int lane = threadIdx.x & 31, c = threadIdx.x >> 5;
-    const uint32_t g = blockIdx.y, c0 = blockIdx.x * kCW, t2 = c0 + c;
+    constexpr uint32_t COLS = 32u / E, R1 = 32u * E, CW = 16u * COLS, WPR = CW / 32;
+    extern __shared__ uint32_t xs[];  // tile (and warp scratch), then R1 * WPR staged bit words
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const uint32_t g = blockIdx.y, c0 = blockIdx.x * CW;
+    uint32_t *rb = xs + kTileWords;
+    uint32_t lim;
+    const uint32_t *b = piece_src(bits, pc, g, lim);
+    stage_row_words<kReversed, WPR>(rb, b, pc.len, lim, R1, c0);
+    __syncthreads();
+    uint32_t e[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+        const uint32_t cc = w * COLS + j / E, t1 = 32u * (j % E) + lane;
+        e[j] = (rb[t1 * WPR + (cc >> 5)] >> (cc & 31u)) & 1u;
+    }
+    dif_warp_t<32, E / 2>(e, xs + w * 1024, T.col_stage_f, lane);
+    // layout B: e[i] is frequency row r = 32 a + i of column cc
+    const uint32_t a = lane % E, cc = w * COLS + lane / E;
+    const uint32_t *twr = T.twist_f + (size_t)(c0 + cc) * R1 + 32u * a;
+#pragma unroll
+    for (int i = 0; i < 32; i += 4) {
+        const uint4 tw = __ldg(reinterpret_cast<const uint4 *>(twr + i));
+        e[i] = mont_lazy(e[i], tw.x);
+        e[i + 1] = mont_lazy(e[i + 1], tw.y);
+        e[i + 2] = mont_lazy(e[i + 2], tw.z);
+        e[i + 3] = mont_lazy(e[i + 3], tw.w);
+    }
+    __syncthreads();  // every warp is done with its scratch
+#pragma unroll
+    for (int i = 0; i < 32; ++i) xs[tile_at<E>(32u * a + i, cc)] = e[i];
+    __syncthreads();
+    uint32_t *o = buf + (size_t)g * N;
+    for (uint32_t it = threadIdx.x; it < R1 * CW; it += blockDim.x) {
+        const uint32_t r = it / CW, c = it % CW;
+        o[(size_t)r * kR2 + c0 + c] = xs[tile_at<E>(r, c)];
+    }
+}
+
+// Pass A': coalesced tile load, untwist, inverse DIT along t1, parity of the
+// wanted coefficients [len-1, len+k-1) into output bits j k + t - (len-1).
+// The parities of a column are ballot-packed per 32 rows, then transposed
+// through shared memory into row words of 32 adjacent columns.
+template <int E>
+__global__ void __launch_bounds__(512, 2)
+ntt_cols_inv_m_kernel(const uint32_t *__restrict__ buf, uint64_t sub_stride, Tables T, uint32_t j0, uint32_t len,
+                      uint32_t k, uint32_t *__restrict__ out)
+{
+    constexpr uint32_t COLS = 32u / E, R1 = 32u * E, CW = 16u * COLS, WPR = CW / 32;
+    extern __shared__ uint32_t xs[];  // tile (and warp scratch), then CW x (E + 1) column words
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const uint32_t g = blockIdx.y, c0 = blockIdx.x * CW;
+    uint32_t *colw = xs + kTileWords;
     const uint32_t *in = buf + (size_t)g * sub_stride;
-    for (uint32_t it = threadIdx.x; it < R1 * kCW; it += blockDim.x) {
-        const uint32_t cc = it % kCW, r = it / kCW;
-        x[r * kCS + cc] = in[(size_t)r * kR2 + c0 + cc];
+    for (uint32_t it = threadIdx.x; it < R1 * CW; it += blockDim.x) {
+        const uint32_t r = it / CW, c = it % CW;
+        xs[tile_at<E>(r, c)] = in[(size_t)r * kR2 + c0 + c];
     }
     __syncthreads();
-    uint32_t e[EPL];
+    const uint32_t a = lane % E, cc = w * COLS + lane / E;
+    const uint32_t *twr = T.twist_i + (size_t)(c0 + cc) * R1 + 32u * a;
+    uint32_t e[32];
 #pragma unroll
-    for (int j = 0; j < EPL; ++j) {
-        const uint32_t r = lane + 32u * j;
-        e[j] = mul_mont(x[r * kCS + c], twist_mont(T.tw_lo_i, T.tw_hi_i, bitrev(r, r1_log) * t2));
+    for (int i = 0; i < 32; i += 4) {
+        const uint4 tw = __ldg(reinterpret_cast<const uint4 *>(twr + i));
+        e[i] = mont_lazy(xs[tile_at<E>(32u * a + i, cc)], tw.x);
+        e[i + 1] = mont_lazy(xs[tile_at<E>(32u * a + i + 1, cc)], tw.y);
+        e[i + 2] = mont_lazy(xs[tile_at<E>(32u * a + i + 2, cc)], tw.z);
+        e[i + 3] = mont_lazy(xs[tile_at<E>(32u * a + i + 3, cc)], tw.w);
     }
-    warp_dit<EPL>(e, T.col_stage_i, lane);
-    __syncthreads();
+    __syncthreads();  // the tile is consumed; warps reuse it as scratch
+    dit_warp_t<32, E / 2>(e, xs + w * 1024, T.col_stage_i, lane);
+    // layout A: e[j] is coefficient row 32 (j % E) + lane of column w COLS + j / E
+    uint32_t mine = 0;
 #pragma unroll
-    for (int j = 0; j < EPL; ++j) x[(lane + 32u * j) * kCS + c] = e[j] & 1u;
+    for (int j = 0; j < 32; ++j) {
+        const uint32_t word = __ballot_sync(0xffffffffu, redp(red2p(e[j])) & 1u);
+        if (lane == j) mine = word;
+    }
+    colw[(w * COLS + lane / E) * (E + 1) + lane % E] = mine;  // column, 32-row block
     __syncthreads();
     const uint64_t jk = (uint64_t)(j0 + g) * k;
     const uint32_t lo_t = len - 1, hi_t = len - 1 + k;
-    for (uint32_t t1 = threadIdx.x; t1 < R1; t1 += blockDim.x) {
-        const uint32_t base = t1 * kR2 + c0;
-        if (base + kCW <= lo_t || base >= hi_t) continue;
-        uint32_t bits16 = 0;
-#pragma unroll
-        for (int cc = 0; cc < kCW; ++cc) {
-            const uint32_t t = base + cc;
-            if (t >= lo_t && t < hi_t) bits16 |= x[t1 * kCS + cc] << cc;
-        }
-        uint64_t P;
+    for (uint32_t task = w; task < R1 * WPR; task += 16) {
+        const uint32_t t1 = task / WPR, wi = task % WPR;
+        const uint32_t base = t1 * kR2 + c0 + 32u * wi;  // element of bit 0
+        if (base + 32 <= lo_t || base >= hi_t) continue;
+        const uint32_t t = base + lane;
+        const uint32_t cw = colw[(32u * wi + lane) * (E + 1) + (t1 >> 5)];
+        uint32_t word = __ballot_sync(0xffffffffu, ((cw >> (t1 & 31u)) & 1u) && t >= lo_t && t < hi_t);
+        if (lane != 0 || !word) continue;
+        uint64_t P;  // output bit of element base (or of lo_t)
         if (base < lo_t) {
-            bits16 >>= (lo_t - base);
+            word >>= (lo_t - base);
             P = jk;
         } else {
             P = jk + (base - lo_t);
         }
-        if (!bits16) continue;
         const uint32_t sh = (uint32_t)(P & 31u);
-        atomicXor(out + (P >> 5), bits16 << sh);
-        if (sh > 16 && (bits16 >> (32u - sh))) atomicXor(out + (P >> 5) + 1, bits16 >> (32u - sh));
+        atomicXor(out + (P >> 5), word << sh);
+        if (sh && (word >> (32u - sh))) atomicXor(out + (P >> 5) + 1, word >> (32u - sh));
     }
 }
 
@@ -807,8 +829,9 @@ struct NttPlan {
 
 namespace {
 
-// dynamic shared memory of the column kernels (+ R1 words of staged row bits)
-size_t smem_generic(uint32_t R1) { return (size_t)R1 * (kCS + 1) * 4; }         // R1 < 1024 kernels
+// dynamic shared memory of the column kernels (+ R1 words of staged row
+// bits); 32 <= R1 < 1024 kernels take smem_multi()
+size_t smem_generic(uint32_t R1) { return (size_t)R1 * (kCS + 1) * 4; }         // R1 < 32 kernels
 size_t smem_transposed(uint32_t R1) { return ((size_t)kCW * (R1 + 1) + R1) * 4; }  // R1 >= 1024 kernels
 
 // pass A for the g * pc.P pieces of g source rows into dst (N words each)
@@ -826,19 +849,27 @@ int ntt_launch_a(const NttPlan *p, const uint32_t *bits, const Pieces &pc, bool 
         return EXTRACT_OK;
     }
     const int epl = (int)(R1 / 32);
+#define EX_COLS_FWD_M(E)                                                                                     \
+    if (epl == E) {                                                                                          \
+        const dim3 gm(kR2 / (512 / E), g * pc.P);                                                            \
+        if (reversed) ntt_cols_fwd_m_kernel<E, true><<<gm, 512, smem_multi(), st>>>(bits, pc, p->N, p->T, dst); \
+        else ntt_cols_fwd_m_kernel<E, false><<<gm, 512, smem_multi(), st>>>(bits, pc, p->N, p->T, dst);       \
+        return EXTRACT_OK;                                                                                   \
+    }
 #define EX_COLS_FWD(E, K, SMEM)                                                                 \
     if (epl == E) {                                                                             \
         if (reversed) K<E, true><<<grid, kCW * 32, SMEM, st>>>(bits, pc, p->r1_log, p->N, p->T, dst); \
         else K<E, false><<<grid, kCW * 32, SMEM, st>>>(bits, pc, p->r1_log, p->N, p->T, dst);       \
         return EXTRACT_OK;                                                                      \
     }
-    EX_COLS_FWD(1, ntt_cols_fwd_kernel, smem_generic(R1))
-    EX_COLS_FWD(2, ntt_cols_fwd_kernel, smem_generic(R1))
-    EX_COLS_FWD(4, ntt_cols_fwd_kernel, smem_generic(R1))
-    EX_COLS_FWD(8, ntt_cols_fwd_kernel, smem_generic(R1))
-    EX_COLS_FWD(16, ntt_cols_fwd_kernel, smem_generic(R1))
+    EX_COLS_FWD_M(1)
+    EX_COLS_FWD_M(2)
+    EX_COLS_FWD_M(4)
+    EX_COLS_FWD_M(8)
+    EX_COLS_FWD_M(16)
     EX_COLS_FWD(32, ntt_cols_fwd_t_kernel, smem_transposed(R1))
     EX_COLS_FWD(64, ntt_cols_fwd_t_kernel, smem_transposed(R1))
+#undef EX_COLS_FWD_M
 #undef EX_COLS_FWD
     return set_error(EXTRACT_EINTERNAL, "ntt: no column kernel for R1=%u", R1);
 }
@@ -868,18 +899,25 @@ int ntt_launch_a_inv(const NttPlan *p, const uint32_t *buf, uint32_t g, uint32_t
         return EXTRACT_OK;
     }
     const int epl = (int)(R1 / 32);
+#define EX_COLS_INV_M(E)                                                                                 \
+    if (epl == E) {                                                                                      \
+        const dim3 gm(kR2 / (512 / E), g);                                                               \
+        ntt_cols_inv_m_kernel<E><<<gm, 512, smem_multi(), st>>>(buf, sub, p->T, j0, p->h, k, out);       \
+        return EXTRACT_OK;                                                                               \
+    }
 #define EX_COLS_INV(E, K, SMEM)                                                          \
     if (epl == E) {                                                                      \
         K<E><<<grid, kCW * 32, SMEM, st>>>(buf, sub, p->r1_log, p->T, j0, p->h, k, out); \
         return EXTRACT_OK;                                                               \
     }
-    EX_COLS_INV(1, ntt_cols_inv_kernel, smem_generic(R1))
-    EX_COLS_INV(2, ntt_cols_inv_kernel, smem_generic(R1))
-    EX_COLS_INV(4, ntt_cols_inv_kernel, smem_generic(R1))
-    EX_COLS_INV(8, ntt_cols_inv_kernel, smem_generic(R1))
-    EX_COLS_INV(16, ntt_cols_inv_kernel, smem_generic(R1))
+    EX_COLS_INV_M(1)
+    EX_COLS_INV_M(2)
+    EX_COLS_INV_M(4)
+    EX_COLS_INV_M(8)
+    EX_COLS_INV_M(16)
     EX_COLS_INV(32, ntt_cols_inv_t_kernel, smem_transposed(R1))
     EX_COLS_INV(64, ntt_cols_inv_t_kernel, smem_transposed(R1))
+#undef EX_COLS_INV_M
 #undef EX_COLS_INV
     return set_error(EXTRACT_EINTERNAL, "ntt: no column kernel for R1=%u", R1);
 }
@@ -990,11 +1028,11 @@ static int device_setup(cudaStream_t st)
     attr((const void *)KF<E, true>, SMEM);  \
     attr((const void *)KF<E, false>, SMEM); \
     attr((const void *)KI<E>, SMEM);
-    EX_SET_SMEM(1, ntt_cols_fwd_kernel, ntt_cols_inv_kernel, smem_generic(32))
-    EX_SET_SMEM(2, ntt_cols_fwd_kernel, ntt_cols_inv_kernel, smem_generic(64))
-    EX_SET_SMEM(4, ntt_cols_fwd_kernel, ntt_cols_inv_kernel, smem_generic(128))
-    EX_SET_SMEM(8, ntt_cols_fwd_kernel, ntt_cols_inv_kernel, smem_generic(256))
-    EX_SET_SMEM(16, ntt_cols_fwd_kernel, ntt_cols_inv_kernel, smem_generic(512))
+    EX_SET_SMEM(1, ntt_cols_fwd_m_kernel, ntt_cols_inv_m_kernel, smem_multi())
+    EX_SET_SMEM(2, ntt_cols_fwd_m_kernel, ntt_cols_inv_m_kernel, smem_multi())
+    EX_SET_SMEM(4, ntt_cols_fwd_m_kernel, ntt_cols_inv_m_kernel, smem_multi())
+    EX_SET_SMEM(8, ntt_cols_fwd_m_kernel, ntt_cols_inv_m_kernel, smem_multi())
+    EX_SET_SMEM(16, ntt_cols_fwd_m_kernel, ntt_cols_inv_m_kernel, smem_multi())
     EX_SET_SMEM(32, ntt_cols_fwd_t_kernel, ntt_cols_inv_t_kernel, smem_transposed(1024))
     EX_SET_SMEM(64, ntt_cols_fwd_t_kernel, ntt_cols_inv_t_kernel, smem_transposed(2048))
 #undef EX_SET_SMEM
@@ -1115,7 +1153,7 @@ int ntt_create(NttPlan **out, uint32_t m, uint32_t s, uint32_t k, const uint32_t
         }
         if ((e = cudaMallocAsync(&p->S, spec * 4, st)) != cudaSuccess) { rc = cuda_error(e, "ntt spectrum"); break; }
         if ((e = cudaMallocAsync(&p->Sq, spec * 4, st)) != cudaSuccess) { rc = cuda_error(e, "ntt spectrum"); break; }
-        if (R1 >= 1024) {
+        if (R1 >= 32) {
             if ((e = cudaMallocAsync(&p->twist, (size_t)2 * p->N * 4, st)) != cudaSuccess) { rc = cuda_error(e, "ntt twist tables"); break; }
             p->T.twist_f = p->twist;
             p->T.twist_i = p->twist + p->N;
