@@ -39,6 +39,7 @@ WORKLOADS = {
     "qrng_n2^30_m1024_s2^20_k2^19": (1 << 30, 1024, 1 << 20, 1 << 19, 0.6),
     # smaller shapes of the same kind, for profiling and quick checks only
     "mid_n2^27_m128_s2^20_k2^16": (1 << 27, 128, 1 << 20, 1 << 16, 0.6),
+    "qrng128_n2^27_m128_s2^20_k2^19": (1 << 27, 128, 1 << 20, 1 << 19, 0.6),
     "small_n2^24_m64_s2^18_k2^17": (1 << 24, 64, 1 << 18, 1 << 17, 0.6),
 }
 DEFAULT_WORKLOAD = "qrng_n2^30_m1024_s2^20_k2^19"

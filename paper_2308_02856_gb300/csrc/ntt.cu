@@ -638,6 +638,21 @@ ntt_cols_inv_t_kernel(const uint32_t *__restrict__ buf, uint64_t sub_stride, int
     }
 }
 
+// 32 x 32 bit transpose across a warp: on return bit c of lane r is bit r
+// of lane c's input (five exchange rounds of swapping off-diagonal blocks).
+__device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane)
+{
+    const uint32_t masks[5] = {0x0000ffffu, 0x00ff00ffu, 0x0f0f0f0fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        const int sft = 16 >> k;
+        const uint32_t m = masks[k];
+        const uint32_t y = __shfl_xor_sync(0xffffffffu, x, sft);
+        x = (lane & sft) ? ((x & ~m) | ((y >> sft) & m)) : ((x & m) | ((y << sft) & ~m));
+    }
+    return x;
+}
+
 // ---- multi-column warps (R1 = 32 E, E in {1, 2, 4, 8, 16}) ---------------
 // A warp transforms COLS = 32 / E columns at once: lane l, register j holds
 // element 32 (j % E) + l of column j / E (layout A).  The distance >= 32
@@ -729,17 +744,20 @@ ntt_cols_fwd_m_kernel(const uint32_t *__restrict__ bits, Pieces pc, uint32_t N, 
 #pragma unroll
     for (int i = 0; i < 32; ++i) xs[tile_at<E>(32u * a + i, cc)] = e[i];
     __syncthreads();
+    // column pairs stay adjacent under the swizzle (COLS >= 2): 8-byte moves
     uint32_t *o = buf + (size_t)g * N;
-    for (uint32_t it = threadIdx.x; it < R1 * CW; it += blockDim.x) {
-        const uint32_t r = it / CW, c = it % CW;
-        o[(size_t)r * kR2 + c0 + c] = xs[tile_at<E>(r, c)];
+    for (uint32_t it = threadIdx.x; it < R1 * CW / 2; it += blockDim.x) {
+        const uint32_t r = it / (CW / 2), c = 2u * (it % (CW / 2));
+        *reinterpret_cast<uint2 *>(o + (size_t)r * kR2 + c0 + c) =
+            *reinterpret_cast<const uint2 *>(xs + tile_at<E>(r, c));
     }
 }
 
 // Pass A': coalesced tile load, untwist, inverse DIT along t1, parity of the
 // wanted coefficients [len-1, len+k-1) into output bits j k + t - (len-1).
-// The parities of a column are ballot-packed per 32 rows, then transposed
-// through shared memory into row words of 32 adjacent columns.
+// The parities of a column are ballot-packed per 32 rows into column words
+// (through shared memory), and each warp turns one 32 x 32 block of them
+// into row words of 32 adjacent columns with a shuffle transpose.
 template <int E>
 __global__ void __launch_bounds__(512, 2)
 ntt_cols_inv_m_kernel(const uint32_t *__restrict__ buf, uint64_t sub_stride, Tables T, uint32_t j0, uint32_t len,
@@ -751,9 +769,10 @@ ntt_cols_inv_m_kernel(const uint32_t *__restrict__ buf, uint64_t sub_stride, Tab
     const uint32_t g = blockIdx.y, c0 = blockIdx.x * CW;
     uint32_t *colw = xs + kTileWords;
     const uint32_t *in = buf + (size_t)g * sub_stride;
-    for (uint32_t it = threadIdx.x; it < R1 * CW; it += blockDim.x) {
-        const uint32_t r = it / CW, c = it % CW;
-        xs[tile_at<E>(r, c)] = in[(size_t)r * kR2 + c0 + c];
+    for (uint32_t it = threadIdx.x; it < R1 * CW / 2; it += blockDim.x) {
+        const uint32_t r = it / (CW / 2), c = 2u * (it % (CW / 2));
+        *reinterpret_cast<uint2 *>(xs + tile_at<E>(r, c)) =
+            __ldg(reinterpret_cast<const uint2 *>(in + (size_t)r * kR2 + c0 + c));
     }
     __syncthreads();
     const uint32_t a = lane % E, cc = w * COLS + lane / E;
@@ -778,27 +797,23 @@ ntt_cols_inv_m_kernel(const uint32_t *__restrict__ buf, uint64_t sub_stride, Tab
     }
     colw[(w * COLS + lane / E) * (E + 1) + lane % E] = mine;  // column, 32-row block
     __syncthreads();
-    const uint64_t jk = (uint64_t)(j0 + g) * k;
+    // one 32 x 32 bit block per warp (E * CW / 32 = 16 blocks): rows
+    // 32 b .. 32 b + 31 of columns 32 wi .. 32 wi + 31
+    const uint32_t b = w % E, wi = w / E;
+    uint32_t x = colw[(32u * wi + lane) * (E + 1) + b];  // lane c: column 32 wi + c
+    x = transpose32(x, lane);                              // lane r: row 32 b + r
+    const uint32_t t1 = 32u * b + lane;
+    const uint32_t base = t1 * kR2 + c0 + 32u * wi;  // element of bit 0
     const uint32_t lo_t = len - 1, hi_t = len - 1 + k;
-    for (uint32_t task = w; task < R1 * WPR; task += 16) {
-        const uint32_t t1 = task / WPR, wi = task % WPR;
-        const uint32_t base = t1 * kR2 + c0 + 32u * wi;  // element of bit 0
-        if (base + 32 <= lo_t || base >= hi_t) continue;
-        const uint32_t t = base + lane;
-        const uint32_t cw = colw[(32u * wi + lane) * (E + 1) + (t1 >> 5)];
-        uint32_t word = __ballot_sync(0xffffffffu, ((cw >> (t1 & 31u)) & 1u) && t >= lo_t && t < hi_t);
-        if (lane != 0 || !word) continue;
-        uint64_t P;  // output bit of element base (or of lo_t)
-        if (base < lo_t) {
-            word >>= (lo_t - base);
-            P = jk;
-        } else {
-            P = jk + (base - lo_t);
-        }
-        const uint32_t sh = (uint32_t)(P & 31u);
-        atomicXor(out + (P >> 5), word << sh);
-        if (sh && (word >> (32u - sh))) atomicXor(out + (P >> 5) + 1, word >> (32u - sh));
-    }
+    if (base + 32 <= lo_t || base >= hi_t) return;
+    if (hi_t - base < 32u) x &= (1u << (hi_t - base)) - 1u;
+    uint64_t P = (uint64_t)(j0 + g) * k;  // output bit of element base (or of lo_t)
+    if (base < lo_t) x >>= (lo_t - base);
+    else P += base - lo_t;
+    if (!x) return;
+    const uint32_t sh = (uint32_t)(P & 31u);
+    atomicXor(out + (P >> 5), x << sh);
+    if (sh && (x >> (32u - sh))) atomicXor(out + (P >> 5) + 1, x >> (32u - sh));
 }
 
 // ---- host side -----------------------------------------------------------
