@@ -13,6 +13,11 @@ compiles it with gcc and marshals numpy arrays through ctypes.  Definitions
   the stable argsort of the labels; sub-block j = sorted ranks [j*s, (j+1)*s);
 * ``K_j[i] = XOR_c seed_j[i - c + s - 1] AND A_j[c]`` for i < k;
 * output bit ``j*k + i = K_j[i]``, LSB-first in uint32 words, tail bits 0.
+
+With ``SAMPLING_IID`` the paper's own law replaces the sorted order: position
+i joins sub-block ``V_i = floor(label_i * m / 2^64)``; sub-block j is the input
+at ``{i : V_i = j}`` in increasing position order, zero-padded to s (the block
+size limit L_S^UB of Eq. 7), and the run aborts when a sub-block exceeds s.
 """
 from __future__ import annotations
 
@@ -28,6 +33,12 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 
 SEED_PER_SUBBLOCK = 0x1
 IDENTITY_PERM = 0x2
+SAMPLING_IID = 0x10
+NO_POS = 0xFFFFFFFF
+
+
+class Abort(Exception):
+    """The i.i.d. law aborts: some sub-block is larger than the limit s."""
 
 
 def KEY_BITS(b: int) -> int:
@@ -42,7 +53,7 @@ def build(force: bool = False) -> str:
                                               os.path.getmtime(os.path.join(_HERE, "oracle.h")))):
         return _LIB
     tmp = _LIB + ".tmp%d" % os.getpid()
-    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-pthread", "-o", tmp, _SRC]
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-pthread", "-o", tmp, _SRC, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB)
     return _LIB
@@ -77,6 +88,16 @@ def load_library(path: str) -> ctypes.CDLL:
     L.oracle_extract.restype = i32
     L.oracle_extract_window.argtypes = [vp, vp, u64, u64, vp, u32, u64, u64, u64, u64, vp, i32]
     L.oracle_extract_window.restype = None
+    L.oracle_subblock_padded.argtypes = [vp, vp, u64, vp]
+    L.oracle_subblock_padded.restype = None
+    L.oracle_iid_label.argtypes = [u64, u64]
+    L.oracle_iid_label.restype = u32
+    L.oracle_iid_order.argtypes = [u64, vp, u64, u64, vp, vp]
+    L.oracle_iid_order.restype = u64
+    L.oracle_size_tail_bound.argtypes = [u64, u64, ctypes.c_double]
+    L.oracle_size_tail_bound.restype = ctypes.c_double
+    L.oracle_block_limit.argtypes = [u64, u64, ctypes.c_double, ctypes.c_double]
+    L.oracle_block_limit.restype = u64
     return L
 
 
@@ -179,9 +200,47 @@ def extract(n, m, s, k, in_bits, seed_bits, sampling_key_, flags=0, nthreads=Non
     out = np.zeros((m * k + 31) // 32, dtype=np.uint32)
     rc = lib().oracle_extract(n, m, s, k, _ptr(in_bits), _ptr(seed_bits), sampling_key_, flags,
                               _ptr(out), _threads(nthreads))
+    if rc == -3:
+        raise Abort("a sub-block exceeds the limit s = %d" % s)
     if rc:
         raise ValueError("oracle_extract rejected the arguments (%d)" % rc)
     return out
+
+
+def iid_label(key: int, m: int) -> int:
+    """Sub-block of a position with sampling label ``key`` under the i.i.d. law."""
+    return int(lib().oracle_iid_label(key, m))
+
+
+def iid_order(keys: np.ndarray, m: int, s: int):
+    """(sizes, order, largest): sizes[j] = |S_j|; order (m*s entries, NO_POS
+    padding) is None when the largest sub-block exceeds s (the abort case)."""
+    keys = np.ascontiguousarray(keys, dtype=np.uint64)
+    sizes = np.zeros(m, dtype=np.uint64)
+    order = np.empty(max(m * s, 1), dtype=np.uint32)
+    largest = int(lib().oracle_iid_order(keys.shape[0], _ptr(keys) if keys.shape[0] else 0, m, s,
+                                         _ptr(sizes), _ptr(order)))
+    if largest == 2**64 - 1:
+        raise MemoryError("oracle_iid_order")
+    return sizes, (order[:m * s] if largest <= s else None), largest
+
+
+def subblock_padded(in_bits: np.ndarray, pos: np.ndarray) -> np.ndarray:
+    in_bits = np.ascontiguousarray(in_bits, dtype=np.uint32)
+    pos = np.ascontiguousarray(pos, dtype=np.uint32)
+    A = np.empty(max(pos.shape[0], 1), dtype=np.uint8)
+    lib().oracle_subblock_padded(_ptr(in_bits), _ptr(pos), pos.shape[0], _ptr(A))
+    return A[:pos.shape[0]]
+
+
+def size_tail_bound(N: int, L: int, p: float) -> float:
+    """Eq. 7's bound on P(a binomial(N, p) sub-block size exceeds L)."""
+    return float(lib().oracle_size_tail_bound(N, L, p))
+
+
+def block_limit(N: int, m: int, eps: float, p: float) -> int:
+    """Eq. 7: the smallest L with m * size_tail_bound(N, L, p) <= eps."""
+    return int(lib().oracle_block_limit(N, m, eps, p))
 
 
 def extract_window(in_bits, pos, s, k, seed_bits, flags, j0, nj, i0, ni, nthreads=None) -> np.ndarray:

@@ -8,6 +8,7 @@
  */
 #include "oracle.h"
 
+#include <math.h>
 #include <pthread.h>
 #include <stdlib.h>
 #include <string.h>
@@ -223,6 +224,83 @@ void oracle_subblock(const uint32_t *in, const uint32_t *pos, uint64_t s, uint8_
         A[c] = bit(in, pos[c]);
 }
 
+void oracle_subblock_padded(const uint32_t *in, const uint32_t *pos, uint64_t s, uint8_t *A)
+{
+    for (uint64_t c = 0; c < s; ++c)
+        A[c] = pos[c] == ORACLE_NO_POS ? 0 : bit(in, pos[c]);
+}
+
+/* ---------------------------------------------------------------------- */
+/* The paper's own sampling law (Sec. III.B step 1): every position draws  */
+/* an i.i.d. uniform label V_i in [0, m) and S_j = {i : V_i = j}, so the   */
+/* sub-block sizes are binomial.  V_i is the integer part of key_i m/2^64  */
+/* for the 64-bit label key_i of definition 1.  A sub-block is the input   */
+/* restricted to S_j in increasing position order (the order in which the  */
+/* paper's hardware stores the sampled bits, Sec. IV), zero-padded to the  */
+/* block size limit s = L_S^UB; the protocol aborts when some |S_j| > s    */
+/* (Sec. III.D).                                                           */
+/* ---------------------------------------------------------------------- */
+uint32_t oracle_iid_label(uint64_t key, uint64_t m)
+{
+    return (uint32_t)(((unsigned __int128)key * m) >> 64);
+}
+
+uint64_t oracle_iid_order(uint64_t n, const uint64_t *keys, uint64_t m, uint64_t s,
+                          uint64_t *sizes, uint32_t *order)
+{
+    memset(sizes, 0, (size_t)m * sizeof(uint64_t));
+    for (uint64_t i = 0; i < n; ++i)
+        sizes[oracle_iid_label(keys[i], m)]++;
+    uint64_t largest = 0;
+    for (uint64_t j = 0; j < m; ++j)
+        if (sizes[j] > largest) largest = sizes[j];
+    if (largest > s || !order) return largest;
+    for (uint64_t t = 0; t < m * s; ++t)
+        order[t] = ORACLE_NO_POS;
+    uint64_t *fill = (uint64_t *)calloc((size_t)m, sizeof(uint64_t));
+    if (!fill) return UINT64_MAX;
+    for (uint64_t i = 0; i < n; ++i) {  /* increasing positions */
+        uint32_t j = oracle_iid_label(keys[i], m);
+        order[(uint64_t)j * s + fill[j]++] = (uint32_t)i;
+    }
+    free(fill);
+    return largest;
+}
+
+/* Eq. 7 (Sec. III.D): with H(x, p) = x ln(x/p) + (1-x) ln((1-x)/(1-p)) and
+   Phi the standard normal CDF, the chance that one binomial(N, p) sub-block
+   size exceeds L is at most 1 - Phi(sqrt(2 N H(L/N, p))) for L >= N p (the
+   Zubkov-Serov bound); the limit is the smallest L at which m times that
+   bound is at most eps.  For L < N p the bound's argument changes sign. */
+static double binary_relative_entropy(double x, double p)
+{
+    double a = x > 0.0 ? x * log(x / p) : 0.0;
+    double b = x < 1.0 ? (1.0 - x) * log((1.0 - x) / (1.0 - p)) : 0.0;
+    return a + b;
+}
+
+double oracle_size_tail_bound(uint64_t N, uint64_t L, double p)
+{
+    double x = (double)L / (double)N;
+    double z = sqrt(2.0 * (double)N * binary_relative_entropy(x, p));
+    if (x < p) z = -z;
+    return 0.5 * erfc(z / sqrt(2.0));  /* 1 - Phi(z) */
+}
+
+uint64_t oracle_block_limit(uint64_t N, uint64_t m, double eps, double p)
+{
+    if (N == 0 || m == 0 || !(p > 0.0 && p < 1.0) || !(eps > 0.0)) return N;
+    double target = eps / (double)m;
+    if (oracle_size_tail_bound(N, N, p) > target) return N;  /* no size can exceed N */
+    uint64_t lo = 0, hi = N;  /* the bound fails at lo - 1 ... holds at hi */
+    while (lo < hi) {
+        uint64_t mid = lo + (hi - lo) / 2;
+        if (oracle_size_tail_bound(N, mid, p) <= target) hi = mid;
+        else lo = mid + 1;
+    }
+    return lo;
+}
+
 uint8_t oracle_toeplitz_bit(const uint32_t *seed, uint64_t off, uint64_t s,
                             const uint8_t *A, uint64_t i)
 {
@@ -254,7 +332,10 @@ static void *window_worker(void *arg)
     uint8_t *A = (uint8_t *)malloc((size_t)(w->s ? w->s : 1));
     if (!A) return (void *)1;
     for (uint64_t j = w->jlo; j < w->jhi; ++j) {
-        oracle_subblock(w->in, w->pos + (j - w->j0) * w->s, w->s, A);
+        if (w->flags & ORACLE_SAMPLING_IID)
+            oracle_subblock_padded(w->in, w->pos + (j - w->j0) * w->s, w->s, A);
+        else
+            oracle_subblock(w->in, w->pos + (j - w->j0) * w->s, w->s, A);
         uint64_t off = (w->flags & ORACLE_SEED_PER_SUBBLOCK) ? j * (w->s + w->k - 1) : 0;
         oracle_toeplitz(w->seed, off, w->s, A, w->i0, w->ni, w->out + (j - w->j0) * w->ni);
     }
@@ -301,11 +382,23 @@ int oracle_extract(uint64_t n, uint64_t m, uint64_t s, uint64_t k,
                    const uint32_t *in, const uint32_t *seed, uint64_t sampling_key,
                    uint32_t flags, uint32_t *out, int nthreads)
 {
-    if (m < 1 || s < 1 || k < 1 || k > s || m * s > n || n > (1ull << 32)) return -1;
-    uint32_t *perm = (uint32_t *)malloc((size_t)n * sizeof(uint32_t));
+    const int iid = (flags & ORACLE_SAMPLING_IID) != 0;
+    if (m < 1 || s < 1 || k < 1 || k > s || n > (1ull << 32)) return -1;
+    if (iid ? (n >= (1ull << 32) || (flags & ORACLE_IDENTITY_PERM)) : m * s > n) return -1;
+    uint32_t *perm = (uint32_t *)malloc((size_t)(iid ? m * s : n) * sizeof(uint32_t));
     uint8_t *K = (uint8_t *)malloc((size_t)(m * k));
     if (!perm || !K) { free(perm); free(K); return -2; }
-    if (flags & ORACLE_IDENTITY_PERM) {
+    if (iid) {
+        uint64_t *keys = (uint64_t *)malloc((size_t)(n ? n : 1) * sizeof(uint64_t));
+        uint64_t *sizes = (uint64_t *)malloc((size_t)m * sizeof(uint64_t));
+        if (!keys || !sizes) { free(keys); free(sizes); free(perm); free(K); return -2; }
+        oracle_sampling_keys(n, sampling_key, flags, keys, nthreads);
+        uint64_t largest = oracle_iid_order(n, keys, m, s, sizes, perm);
+        free(keys);
+        free(sizes);
+        if (largest == UINT64_MAX) { free(perm); free(K); return -2; }
+        if (largest > s) { free(perm); free(K); return -3; }  /* the protocol aborts */
+    } else if (flags & ORACLE_IDENTITY_PERM) {
         for (uint64_t i = 0; i < n; ++i) perm[i] = (uint32_t)i;
     } else {
         uint64_t *keys = (uint64_t *)malloc((size_t)n * sizeof(uint64_t));

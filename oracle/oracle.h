@@ -25,6 +25,11 @@
  *      seed_j is the shared seed (s + k - 1 bits), or, with
  *      ORACLE_SEED_PER_SUBBLOCK, the j-th consecutive (s + k - 1)-bit span
  *      of the seed string.
+ *   1b. With ORACLE_SAMPLING_IID, the paper's own law instead: position i
+ *      joins sub-block V_i = floor(key_i * m / 2^64) (i.i.d. uniform on
+ *      [0, m)); sub-block j is the input at S_j = {i : V_i = j} in
+ *      increasing position order, zero-padded to s = L_S^UB, and the run
+ *      aborts (returns -3) when some |S_j| > s (Sec. III.D).
  *   3. Concatenation (Sec. III.B step 4): output bit j*k + i = K_j[i]; the
  *      tail bits of the last output word are 0.
  */
@@ -39,6 +44,10 @@ extern "C" {
 /* Flags, same meaning as the library's create flags. */
 #define ORACLE_SEED_PER_SUBBLOCK 0x1u
 #define ORACLE_IDENTITY_PERM     0x2u
+/* The paper's i.i.d. sampling law (definition 1b). */
+#define ORACLE_SAMPLING_IID      0x10u
+/* Order entry of a padding slot (reads as a 0 bit). */
+#define ORACLE_NO_POS            0xffffffffu
 /* Test hook: keep only the top b (1..63) bits of every sampling key. */
 #define ORACLE_KEY_BITS(b)       (((uint32_t)(b) & 0x3fu) << 8)
 
@@ -70,6 +79,26 @@ int64_t oracle_check_order(uint64_t n, const uint64_t *keys, const uint32_t *per
 
 /* Sub-block assembly: A[c] = bit(in, pos[c]) for c < s (one byte per bit). */
 void oracle_subblock(const uint32_t *in, const uint32_t *pos, uint64_t s, uint8_t *A);
+/* The same with ORACLE_NO_POS entries read as 0 (padded i.i.d. sub-blocks). */
+void oracle_subblock_padded(const uint32_t *in, const uint32_t *pos, uint64_t s, uint8_t *A);
+
+/* i.i.d. law (definition 1b): the sub-block of a position with label key. */
+uint32_t oracle_iid_label(uint64_t key, uint64_t m);
+
+/* sizes[j] = |S_j| for j < m; returns the largest size.  When it is <= s
+   and order is not NULL, order[j*s + c] = the c-th smallest position of S_j
+   for c < sizes[j] and ORACLE_NO_POS for sizes[j] <= c < s.  UINT64_MAX on
+   allocation failure. */
+uint64_t oracle_iid_order(uint64_t n, const uint64_t *keys, uint64_t m, uint64_t s,
+                          uint64_t *sizes, uint32_t *order);
+
+/* Eq. 7: 1 - Phi(sign(L - N p) sqrt(2 N H(L/N, p))), the Zubkov-Serov bound
+   on the chance that a binomial(N, p) sub-block size exceeds L. */
+double oracle_size_tail_bound(uint64_t N, uint64_t L, double p);
+
+/* Eq. 7: the smallest L with m * oracle_size_tail_bound(N, L, p) <= eps
+   (N when no L below N qualifies or the arguments are degenerate). */
+uint64_t oracle_block_limit(uint64_t N, uint64_t m, double eps, double p);
 
 /* One Toeplitz output bit: XOR_{c<s} bit(seed, off + i - c + s - 1) AND A[c]. */
 uint8_t oracle_toeplitz_bit(const uint32_t *seed, uint64_t off, uint64_t s,
@@ -80,7 +109,8 @@ void oracle_toeplitz(const uint32_t *seed, uint64_t off, uint64_t s,
                      const uint8_t *A, uint64_t i0, uint64_t cnt, uint8_t *K);
 
 /* The whole method (definitions 1-3): out gets ceil(m*k/32) words.
-   Sub-blocks are processed on nthreads threads.  0 = ok, <0 = bad args. */
+   Sub-blocks are processed on nthreads threads.  0 = ok, -1 = bad args,
+   -2 = out of memory, -3 = the i.i.d. law aborts (a sub-block exceeds s). */
 int oracle_extract(uint64_t n, uint64_t m, uint64_t s, uint64_t k,
                    const uint32_t *in, const uint32_t *seed, uint64_t sampling_key,
                    uint32_t flags, uint32_t *out, int nthreads);

@@ -27,6 +27,13 @@ MUTANTS = {
     "tie-break reversed": ("if (x->idx != y->idx) return x->idx < y->idx ? -1 : 1;", "if (x->idx != y->idx) return x->idx < y->idx ? 1 : -1;"),
     "sub-block taken from the wrong rank": ("A[c] = bit(in, pos[c]);", "A[c] = bit(in, pos[s - 1 - c]);"),
     "output packed at the wrong bit": ("out[t >> 5] |= (uint32_t)K[t] << (t & 31u);", "out[t >> 5] |= (uint32_t)K[t] << (31u - (t & 31u));"),
+    "iid label from the low bits": ("return (uint32_t)(((unsigned __int128)key * m) >> 64);", "return (uint32_t)(key % m);"),
+    "iid positions in decreasing order": ("for (uint64_t i = 0; i < n; ++i) {  /* increasing positions */",
+                                          "for (uint64_t i = n; i-- > 0;) {  /* increasing positions */"),
+    "iid padding not zero": ("A[c] = pos[c] == ORACLE_NO_POS ? 0 : bit(in, pos[c]);", "A[c] = bit(in, pos[c] % 64u);"),
+    "eq7 without the factor 2": ("double z = sqrt(2.0 * (double)N * ", "double z = sqrt((double)N * "),
+    "eq7 relative entropy sign": ("double b = x < 1.0 ? (1.0 - x) * log((1.0 - x) / (1.0 - p)) : 0.0;",
+                                  "double b = x < 1.0 ? (1.0 - x) * log((1.0 - p) / (1.0 - x)) : 0.0;"),
 }
 
 
@@ -38,7 +45,7 @@ def _compile(src):
     with open(os.path.join(d, "oracle.h"), "w") as f:
         f.write(open(os.path.join(ROOT, "oracle", "oracle.h")).read())
     so = os.path.join(d, "liboracle_mutant.so")
-    subprocess.run(["gcc", "-O1", "-std=c11", "-fPIC", "-shared", "-pthread", "-o", so, c], check=True)
+    subprocess.run(["gcc", "-O1", "-std=c11", "-fPIC", "-shared", "-pthread", "-o", so, c, "-lm"], check=True)
     return oracle.load_library(so)
 
 
@@ -87,6 +94,37 @@ def _pins():
     want = np.packbits(np.concatenate([bits, np.zeros((-bits.size) % 32, np.uint8)]), bitorder="little").view("<u4")
     if not np.array_equal(oracle.extract(n, m, s2, k2, inw, sd, 3), want):
         failed.append("composition")
+    # i.i.d. law against numpy grouping and convolve, Eq. 7 against the exact tail
+    keys = oracle.sampling_keys(n, 4)
+    V = np.array([(int(x) * m) >> 64 for x in keys], dtype=np.int64)
+    s3 = int(np.bincount(V, minlength=m).max()) + 5
+    sizes, order, _ = oracle.iid_order(keys, m, s3)
+    if order is None or not np.array_equal(sizes, np.bincount(V, minlength=m)) or any(
+            not np.array_equal(order[j * s3:j * s3 + sizes[j]], np.flatnonzero(V == j)) for j in range(m)):
+        failed.append("iid order")
+    sd3 = _words(rng, s3 + k2 - 1)
+    sb3 = oracle.bits_of(sd3, s3 + k2 - 1).astype(np.int64)
+    bits3 = []
+    for j in range(m):
+        A = np.zeros(s3, dtype=np.int64)
+        rows = np.flatnonzero(V == j)
+        A[:rows.size] = oracle.bits_of(inw, n).astype(np.int64)[rows]
+        bits3.append(np.convolve(sb3, A)[s3 - 1:s3 - 1 + k2] % 2)
+    b3 = np.concatenate(bits3).astype(np.uint8)
+    want3 = np.packbits(np.concatenate([b3, np.zeros((-b3.size) % 32, np.uint8)]), bitorder="little").view("<u4")
+    try:
+        if not np.array_equal(oracle.extract(n, m, s3, k2, inw, sd3, 4, oracle.SAMPLING_IID), want3):
+            failed.append("iid composition")
+    except (ValueError, oracle.Abort):
+        failed.append("iid composition")
+    try:
+        from scipy import stats
+        for N, mm in ((2**20, 64), (10**6, 17)):
+            L = oracle.block_limit(N, mm, 1e-8, 1.0 / mm)
+            if not (mm * stats.binom.sf(L, N, 1.0 / mm) <= 1e-8 < mm * stats.binom.sf(L - 2, N, 1.0 / mm)):
+                failed.append("eq7 bracket")
+    except ImportError:
+        pass
     return failed
 
 
