@@ -44,6 +44,7 @@ WORKLOADS = {
 }
 DEFAULT_WORKLOAD = "qrng_n2^30_m1024_s2^20_k2^19"
 IN_SEED, SAMPLING_KEY, TOEPLITZ_SEED = 1, 2, 3
+IID_EPS = 1e-8  # abort probability eps_Omega' of the i.i.d. law's limit (the paper's Sec. IV value)
 
 # Integer-pipe roofline of the hashing kernel (bound "alu"): LOP3 results per
 # SM per clock x SMs x maximum SM clock.  The lane count is the one measured
@@ -69,6 +70,9 @@ def parse_args():
                     help="block: one large block (default); batch: 256 uneven blocks in one persistent "
                          "launch vs one launch per block; serve: Poisson job arrivals under an HBM budget")
     ap.add_argument("--jobs", type=int, default=0, help="jobs per serving trace (default 120)")
+    ap.add_argument("--sampling", choices=["sorted", "iid"], default="sorted",
+                    help="block mode: sorted order cut into equal sub-blocks (default), or the paper's i.i.d. "
+                         "labels with sub-blocks padded to Eq. 7's block size limit")
     ap.add_argument("--method", choices=["auto", "direct", "ntt"], default="auto",
                     help="hashing method of the block mode (auto: the library's choice)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -153,15 +157,20 @@ class OracleSample:
     assembly plus ni output rows of each, on nj host threads; scaled to the
     whole block by the share of Toeplitz rows it computed."""
 
-    def __init__(self, n, m, s, k, in_w, seed_w, target_s):
+    def __init__(self, n, m, s, k, in_w, seed_w, target_s, iid=False):
         import oracle
         self.oracle = oracle
         self.n, self.m, self.s, self.k = n, m, s, k
         self.in_w, self.seed_w = in_w, seed_w
         self.cores = os.cpu_count() or 1
         self.nj = min(self.cores, m)
+        self.flags = oracle.SAMPLING_IID if iid else 0
         keys = oracle.sampling_keys(n, SAMPLING_KEY)
-        self.pos = oracle.perm_range(keys, 0, self.nj * s)
+        if iid:  # the oracle's i.i.d. order (padded sub-blocks of s slots)
+            _, order, _ = oracle.iid_order(keys, m, s)
+            self.pos = np.ascontiguousarray(order[:self.nj * s])
+        else:
+            self.pos = oracle.perm_range(keys, 0, self.nj * s)
         del keys
         # calibrate the rows per sub-block to about target_s of wall time
         ni = 8
@@ -170,7 +179,7 @@ class OracleSample:
 
     def _time(self, ni):
         t0 = time.perf_counter()
-        self.oracle.extract_window(self.in_w, self.pos, self.s, self.k, self.seed_w, 0, 0, self.nj, 0, ni,
+        self.oracle.extract_window(self.in_w, self.pos, self.s, self.k, self.seed_w, self.flags, 0, self.nj, 0, ni,
                                    nthreads=self.nj)
         return time.perf_counter() - t0
 
@@ -293,9 +302,14 @@ def run_ours(args):
     sms = props.multi_processor_count
 
     X.load()  # fails loudly when the CUDA library is missing
+    iid = args.sampling == "iid"
+    if iid:  # the paper's law: s becomes Eq. 7's block size limit
+        s = X.extract_block_limit(n, m, IID_EPS, 1.0 / m)
     in_w, seed_w = make_inputs(n, m, s, k, p)
 
     method_flags = {"auto": 0, "direct": X.EXTRACT_METHOD_DIRECT, "ntt": X.EXTRACT_METHOD_NTT}[args.method]
+    if iid:
+        method_flags |= X.EXTRACT_SAMPLING_IID
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     ex = X.Extractor(n, m, s, k, seed_w, SAMPLING_KEY, method_flags)
@@ -385,7 +399,8 @@ def run_ours(args):
     if is_ntt:
         roofline = ntt_roofline(n, m, s, k, hash_ms, plan, sms)
         # the direct kernel on the same block, for the record (2 timed steps)
-        exd = X.Extractor(n, m, s, k, seed_w, SAMPLING_KEY, X.EXTRACT_METHOD_DIRECT)
+        exd = X.Extractor(n, m, s, k, seed_w, SAMPLING_KEY,
+                          X.EXTRACT_METHOD_DIRECT | (X.EXTRACT_SAMPLING_IID if iid else 0))
         exd.gather(d_in, stream=stream)
         exd.hash(d_out, stream=stream)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -404,7 +419,7 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
-            smp = OracleSample(n, m, s, k, in_w, seed_w, args.cpu_seconds)
+            smp = OracleSample(n, m, s, k, in_w, seed_w, args.cpu_seconds, iid=iid)
             cpu = smp.measure()
             cpu.pop("seconds", None)
         except Exception as e:  # the baseline is context; report why it is missing
@@ -416,7 +431,10 @@ def run_ours(args):
             "metric": "extracted input Gbit/s", "value": value, "unit": "Gbit/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32 (GF(2) bits)", "data": "synthetic",
-            "config": {"workload": args.workload, "n": n, "m": m, "s": s, "k": k, "bernoulli_p": p,
+            "config": {"workload": args.workload + ("_iid" if iid else ""), "n": n, "m": m, "s": s, "k": k,
+                       "bernoulli_p": p,
+                       "sampling": ("i.i.d. labels V_i in [0, m), sub-blocks padded to Eq. 7's limit s "
+                                    "(eps %g, p_sift 1/m)" % IID_EPS) if iid else "stable argsort, equal sub-blocks",
                        "seeds": {"input": IN_SEED, "sampling_key": SAMPLING_KEY, "toeplitz": TOEPLITZ_SEED},
                        "order": "resident (built once per sampling key; see create_ms)",
                        "l2": "inputs larger than L2: 4n-byte order + n/8-byte input read per step",
@@ -595,6 +613,9 @@ def run_compare(args):
             out = ex.new_output()
             ms = timed(lambda: ex.run(d_in, out, stream=st), reps)
             res["qkd_n2^32_" + name] = {"ms": ms, "gbit_per_s": n / (ms / 1e3) / 1e9, "plan": ex.describe()}
+            if name == "library_choice":  # the two steps alone
+                res["qkd_n2^32_" + name]["gather_ms"] = timed(lambda: ex.gather(d_in, stream=st), 2)
+                res["qkd_n2^32_" + name]["hash_ms"] = timed(lambda: ex.hash(out, stream=st), 2)
             if name == "direct_tiled":
                 pms = timed(lambda: ex.run_plain(d_in, out, stream=st), 1)
                 res["qkd_n2^32_plain_per_block"] = {"ms": pms, "gbit_per_s": n / (pms / 1e3) / 1e9,

@@ -50,6 +50,9 @@ extern "C" {
 #define EXTRACT_EBUDGET   (-5)  /* the job does not fit the memory budget     */
 #define EXTRACT_EBUSY     (-6)  /* no free slot / resource in use             */
 #define EXTRACT_EINTERNAL (-7)  /* an internal consistency check failed       */
+#define EXTRACT_EABORT    (-8)  /* i.i.d. sampling: a sub-block exceeds the
+                                   block size limit s, so the protocol aborts
+                                   (Sec. III.D); nothing is created        */
 
 /* ---- create flags ---------------------------------------------------- */
 /* seed_bits holds m consecutive (s + k - 1)-bit seeds, one independent
@@ -78,6 +81,17 @@ extern "C" {
 /* Test hook: keep only the top b (1..63) bits of every sampling label, which
    forces many equal labels so that the index tie-break is exercised. */
 #define EXTRACT_KEY_BITS(b)       ((((uint32_t)(b)) & 0x3fu) << 8)
+/* The paper's own sampling law (Sec. III.B step 1) instead of the sorted
+   order: position i joins sub-block V_i = floor(label_i * m / 2^64), an
+   i.i.d. uniform draw on [0, m), so sub-block sizes are binomial(n, 1/m).
+   Sub-block j is the input at S_j = {i : V_i = j} in increasing position
+   order, zero-padded to s, which now plays the block size limit L_S^UB
+   (extract_block_limit computes it from Eq. 7): the Toeplitz matrix is
+   k x s and the seed s + k - 1 bits as usual.  Every position is hashed
+   (m*s >= n is not required).  extract_create fails with EXTRACT_EABORT
+   when some |S_j| > s.  Needs n < 2^32 and m <= 2^16; not combinable with
+   EXTRACT_IDENTITY_PERM; not accepted by the batch and server forms. */
+#define EXTRACT_SAMPLING_IID      0x10u
 
 typedef struct extract_ctx extract_ctx;
 
@@ -86,7 +100,7 @@ typedef struct extract_ctx extract_ctx;
  * the sampled order (step 1) on the GPU, resident until extract_destroy.
  *
  *   out            receives the new context (owned by the library).
- *   n              input bits, m*s <= n <= 2^32.
+ *   n              input bits, m*s <= n <= 2^32 (i.i.d. law: n < 2^32).
  *   m, s, k        sub-blocks, bits per sub-block, output bits per sub-block;
  *                  1 <= m, 1 <= k <= s.
  *   seed_bits_host host pointer to ceil(L/32) words with L = s + k - 1 (or
@@ -96,8 +110,9 @@ typedef struct extract_ctx extract_ctx;
  *   flags          EXTRACT_* create flags.
  *
  * Synchronous: it returns once the order is built.  Device memory held:
- * 4n bytes of order (none with EXTRACT_IDENTITY_PERM) plus about n/8 bytes
- * of sub-block buffer and the seed.  Errors: EINVAL, ENOMEM, ECUDA.
+ * 4n bytes of order (4ms with EXTRACT_SAMPLING_IID, none with
+ * EXTRACT_IDENTITY_PERM) plus about n/8 bytes of sub-block buffer and the
+ * seed.  Errors: EINVAL, ENOMEM, ECUDA, EABORT (i.i.d. law only).
  */
 int extract_create(extract_ctx **out, uint64_t n, uint32_t m, uint32_t s, uint32_t k,
                    const uint32_t *seed_bits_host, uint64_t sampling_key, uint32_t flags);
@@ -150,8 +165,29 @@ int extract_run_plain(extract_ctx *h, void *stream, const uint32_t *in_bits_dev,
 
 /* extract_read_perm - copy ranks [start, start+count) of the sampled order
    to host memory (synchronous).  With EXTRACT_IDENTITY_PERM it writes the
-   identity.  Errors: EINVAL if start + count > n. */
+   identity.  With EXTRACT_SAMPLING_IID the order has m*s slots: slot
+   j*s + c is the c-th position of sub-block j, 0xffffffff past its size.
+   Errors: EINVAL if start + count exceeds the order. */
 int extract_read_perm(extract_ctx *h, uint64_t start, uint64_t count, uint32_t *dst_host);
+
+/* extract_subblock_sizes - sizes_host[j] = |S_j| for j < m: the number of
+   input bits in each sub-block (s for every j under the sorted order; the
+   binomial sizes under EXTRACT_SAMPLING_IID).  Host memory, synchronous. */
+int extract_subblock_sizes(extract_ctx *h, uint64_t *sizes_host);
+
+/*
+ * extract_block_limit - the block size limit of Eq. 7 (Sec. III.D): the
+ * smallest L with
+ *     m * (1 - Phi(sign(L - N p) sqrt(2 N H(L/N, p)))) <= eps,
+ * H(x, p) = x ln(x/p) + (1-x) ln((1-x)/(1-p)), Phi the standard normal CDF
+ * (the Zubkov-Serov bound on a binomial tail, union over the m
+ * sub-blocks).  N = n input bits, p = the chance that a bit lands in a given
+ * sub-block (1/m without sifting), eps = the allowed abort probability
+ * eps_Omega'.  Writes N when no smaller L qualifies.  Host only (no GPU).
+ * Errors: EINVAL for N = 0, m = 0, p outside (0, 1), eps <= 0 or a null
+ * limit_out.
+ */
+int extract_block_limit(uint64_t N, uint32_t m, double eps, double p, uint64_t *limit_out);
 
 /* extract_read_subblock - copy sub-block j as gathered by the last run or
    gather, ceil(s/32) words, to host memory (synchronous, waits for the

@@ -212,17 +212,18 @@ def iid_label(key: int, m: int) -> int:
     return int(lib().oracle_iid_label(key, m))
 
 
-def iid_order(keys: np.ndarray, m: int, s: int):
+def iid_order(keys: np.ndarray, m: int, s: int, with_order: bool = True):
     """(sizes, order, largest): sizes[j] = |S_j|; order (m*s entries, NO_POS
-    padding) is None when the largest sub-block exceeds s (the abort case)."""
+    padding) is None when the largest sub-block exceeds s (the abort case) or
+    when with_order is False (sizes only, nothing of size m*s allocated)."""
     keys = np.ascontiguousarray(keys, dtype=np.uint64)
     sizes = np.zeros(m, dtype=np.uint64)
-    order = np.empty(max(m * s, 1), dtype=np.uint32)
+    order = np.empty(max(m * s, 1), dtype=np.uint32) if with_order else None
     largest = int(lib().oracle_iid_order(keys.shape[0], _ptr(keys) if keys.shape[0] else 0, m, s,
-                                         _ptr(sizes), _ptr(order)))
+                                         _ptr(sizes), _ptr(order) if with_order else 0))
     if largest == 2**64 - 1:
         raise MemoryError("oracle_iid_order")
-    return sizes, (order[:m * s] if largest <= s else None), largest
+    return sizes, (order[:m * s] if with_order and largest <= s else None), largest
 
 
 def subblock_padded(in_bits: np.ndarray, pos: np.ndarray) -> np.ndarray:

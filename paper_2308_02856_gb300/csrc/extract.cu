@@ -53,7 +53,11 @@ struct extract_ctx {
     uint32_t w_pad = 0;        // words per stored sub-block (multiple of kWordChunk)
     uint32_t seed_stride = 0;  // words per realigned seed
     uint32_t nseeds = 0;
-    uint32_t *perm = nullptr;  // n entries (null with EXTRACT_IDENTITY_PERM)
+    uint32_t *perm = nullptr;  // n entries (null with EXTRACT_IDENTITY_PERM; m*s padded slots with
+                               // EXTRACT_SAMPLING_IID)
+    uint64_t perm_len = 0;     // entries of perm (n, or m*s)
+    bool iid = false;          // EXTRACT_SAMPLING_IID: padded order, kNoPos slots read as 0
+    std::vector<uint64_t> sizes;  // |S_j| (i.i.d. law; empty for the sorted order)
     uint32_t *arev = nullptr;  // m * w_pad words
     uint32_t *seed = nullptr;  // nseeds * seed_stride words
     uint32_t *stage_in = nullptr;   // extract_run_host staging, ceil(n/32) words
@@ -67,7 +71,7 @@ struct extract_ctx {
 namespace {
 
 constexpr uint32_t kKnownFlags = EXTRACT_SEED_PER_SUBBLOCK | EXTRACT_IDENTITY_PERM | EXTRACT_METHOD_DIRECT |
-                                  EXTRACT_METHOD_NTT | (0x3fu << 8) | (0x7u << 16);
+                                  EXTRACT_METHOD_NTT | EXTRACT_SAMPLING_IID | (0x3fu << 8) | (0x7u << 16);
 
 void free_ctx(extract_ctx *h)
 {
@@ -125,11 +129,17 @@ int extract_create(extract_ctx **out, uint64_t n, uint32_t m, uint32_t s, uint32
     if (m < 1 || s < 1 || k < 1 || k > s)
         return set_error(EXTRACT_EINVAL, "need m >= 1 and 1 <= k <= s (m=%u s=%u k=%u)", m, s, k);
     if (n > (1ull << 32)) return set_error(EXTRACT_EINVAL, "n = %llu exceeds 2^32", (unsigned long long)n);
-    if ((uint64_t)m * s > n)
-        return set_error(EXTRACT_EINVAL, "m*s = %llu exceeds n = %llu",
-                         (unsigned long long)((uint64_t)m * s), (unsigned long long)n);
     const bool per_sub = (flags & EXTRACT_SEED_PER_SUBBLOCK) != 0;
     const bool ident = (flags & EXTRACT_IDENTITY_PERM) != 0;
+    const bool iid = (flags & EXTRACT_SAMPLING_IID) != 0;
+    if (iid) {
+        if (ident) return set_error(EXTRACT_EINVAL, "EXTRACT_SAMPLING_IID and EXTRACT_IDENTITY_PERM are exclusive");
+        if (n >= (1ull << 32)) return set_error(EXTRACT_EINVAL, "the i.i.d. law needs n < 2^32");
+        if (m > (1u << 16)) return set_error(EXTRACT_EINVAL, "the i.i.d. law needs m <= 2^16 (m = %u)", m);
+    } else if ((uint64_t)m * s > n) {
+        return set_error(EXTRACT_EINVAL, "m*s = %llu exceeds n = %llu",
+                         (unsigned long long)((uint64_t)m * s), (unsigned long long)n);
+    }
     if ((flags & EXTRACT_METHOD_DIRECT) && (flags & EXTRACT_METHOD_NTT))
         return set_error(EXTRACT_EINVAL, "EXTRACT_METHOD_DIRECT and EXTRACT_METHOD_NTT are exclusive");
     const uint32_t split_field = (flags >> 16) & 0x7u;
@@ -146,6 +156,8 @@ int extract_create(extract_ctx **out, uint64_t n, uint32_t m, uint32_t s, uint32
     extract_ctx *h = new (std::nothrow) extract_ctx();
     if (!h) return set_error(EXTRACT_ENOMEM, "host allocation failed");
     h->n = n; h->m = m; h->s = s; h->k = k; h->flags = flags; h->sampling_key = sampling_key;
+    h->iid = iid;
+    h->perm_len = ident ? 0 : iid ? (uint64_t)m * s : n;
     cudaError_t e = cudaGetDevice(&h->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
     if (e != cudaSuccess) { delete h; return cuda_error(e, "device query"); }
@@ -193,12 +205,16 @@ int extract_create(extract_ctx **out, uint64_t n, uint32_t m, uint32_t s, uint32
     if ((e = cudaMalloc(&h->arev, (size_t)m * h->w_pad * 4)) != cudaSuccess) { free_ctx(h); return cuda_error(e, "cudaMalloc(sub-blocks)"); }
     if ((e = cudaMemset(h->arev, 0, (size_t)m * h->w_pad * 4)) != cudaSuccess) { free_ctx(h); return cuda_error(e, "memset(sub-blocks)"); }
     if (!ident) {
-        if ((e = cudaMalloc(&h->perm, (size_t)n * 4)) != cudaSuccess) { free_ctx(h); return cuda_error(e, "cudaMalloc(order)"); }
+        if ((e = cudaMalloc(&h->perm, (size_t)std::max<uint64_t>(h->perm_len, 1) * 4)) != cudaSuccess) {
+            free_ctx(h);
+            return cuda_error(e, "cudaMalloc(order)");
+        }
         const uint32_t kb = (flags >> 8) & 0x3fu;
         const uint64_t mask = kb ? ~((1ull << (64u - kb)) - 1ull) : ~0ull;
         cudaStream_t st;
         if ((e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) != cudaSuccess) { free_ctx(h); return cuda_error(e, "stream"); }
-        int rc = build_perm(n, sampling_key, mask, h->perm, st, h->num_sms);
+        int rc = iid ? build_iid_order(n, sampling_key, mask, m, s, h->perm, &h->sizes, st, h->num_sms)
+                     : build_perm(n, sampling_key, mask, h->perm, st, h->num_sms);
         cudaStreamDestroy(st);
         if (rc != EXTRACT_OK) { free_ctx(h); return rc; }
     }
@@ -212,7 +228,7 @@ int extract_gather(extract_ctx *h, void *stream, const uint32_t *in_bits_dev)
     if (int rc = check_ctx(h)) return rc;
     if (!in_bits_dev) return set_error(EXTRACT_EINVAL, "in_bits_dev is null");
     return launch_gather(in_bits_dev, h->perm, h->m, h->s, h->w_pad, h->arev, (cudaStream_t)stream,
-                         h->num_sms);
+                         h->num_sms, 0, h->iid);
 }
 
 int extract_hash(extract_ctx *h, void *stream, uint32_t *out_bits_dev)
@@ -231,7 +247,7 @@ int extract_run(extract_ctx *h, void *stream, const uint32_t *in_bits_dev, uint3
     if (h->ntt) {
         if (!in_bits_dev) return set_error(EXTRACT_EINVAL, "in_bits_dev is null");
         return ntt_run_overlapped(h->ntt, in_bits_dev, h->perm, h->arev, h->w_pad, h->m, h->s, h->k, out_bits_dev,
-                                  (cudaStream_t)stream, h->aux, h->ev_fork, h->ev_group, h->num_sms);
+                                  (cudaStream_t)stream, h->aux, h->ev_fork, h->ev_group, h->num_sms, h->iid);
     }
     if (int rc = extract_gather(h, stream, in_bits_dev)) return rc;
     return extract_hash(h, stream, out_bits_dev);
@@ -265,15 +281,56 @@ int extract_read_perm(extract_ctx *h, uint64_t start, uint64_t count, uint32_t *
 {
     if (int rc = check_ctx(h)) return rc;
     if (!dst_host && count) return set_error(EXTRACT_EINVAL, "dst_host is null");
-    if (start > h->n || count > h->n - start)
-        return set_error(EXTRACT_EINVAL, "range [%llu, +%llu) outside n = %llu", (unsigned long long)start,
-                         (unsigned long long)count, (unsigned long long)h->n);
+    const uint64_t len = h->perm ? h->perm_len : h->n;
+    if (start > len || count > len - start)
+        return set_error(EXTRACT_EINVAL, "range [%llu, +%llu) outside the order of %llu entries",
+                         (unsigned long long)start, (unsigned long long)count, (unsigned long long)len);
     if (!h->perm) {
         for (uint64_t t = 0; t < count; ++t) dst_host[t] = (uint32_t)(start + t);
         return EXTRACT_OK;
     }
     EX_CUDA(cudaDeviceSynchronize());
     EX_CUDA(cudaMemcpy(dst_host, h->perm + start, count * 4, cudaMemcpyDeviceToHost));
+    return EXTRACT_OK;
+}
+
+int extract_subblock_sizes(extract_ctx *h, uint64_t *sizes_host)
+{
+    if (int rc = check_ctx(h)) return rc;
+    if (!sizes_host) return set_error(EXTRACT_EINVAL, "sizes_host is null");
+    for (uint32_t j = 0; j < h->m; ++j) sizes_host[j] = h->iid ? h->sizes[j] : h->s;
+    return EXTRACT_OK;
+}
+
+// Eq. 7 (Sec. III.D), restated from the paper for the library: the chance
+// that a binomial(N, p) sub-block size exceeds L is at most
+// 1 - Phi(sign(L - N p) sqrt(2 N H(L/N, p))), H the binary relative entropy;
+// the limit is the smallest L at which m times that bound is <= eps.
+static double eq7_tail(uint64_t N, uint64_t L, double p)
+{
+    const double x = (double)L / (double)N;
+    const double h = (x > 0.0 ? x * std::log(x / p) : 0.0) + (x < 1.0 ? (1.0 - x) * std::log((1.0 - x) / (1.0 - p)) : 0.0);
+    const double z = (x < p ? -1.0 : 1.0) * std::sqrt(2.0 * (double)N * std::max(h, 0.0));
+    return 0.5 * std::erfc(z / std::sqrt(2.0));
+}
+
+int extract_block_limit(uint64_t N, uint32_t m, double eps, double p, uint64_t *limit_out)
+{
+    if (!limit_out) return set_error(EXTRACT_EINVAL, "limit_out is null");
+    if (N == 0 || m == 0 || !(p > 0.0 && p < 1.0) || !(eps > 0.0))
+        return set_error(EXTRACT_EINVAL, "need N > 0, m > 0, 0 < p < 1 and eps > 0");
+    const double target = eps / (double)m;
+    if (eq7_tail(N, N, p) > target) {
+        *limit_out = N;
+        return EXTRACT_OK;
+    }
+    uint64_t lo = 0, hi = N;  // smallest L in [lo, hi] with eq7_tail(L) <= target
+    while (lo < hi) {
+        const uint64_t mid = lo + (hi - lo) / 2;
+        if (eq7_tail(N, mid, p) <= target) hi = mid;
+        else lo = mid + 1;
+    }
+    *limit_out = lo;
     return EXTRACT_OK;
 }
 

@@ -22,7 +22,7 @@
 namespace ex {
 namespace {
 
-template <bool kIdentity>
+template <bool kIdentity, bool kPadded>
 __global__ void __launch_bounds__(256)
 gather_kernel(const uint32_t *__restrict__ in, const uint32_t *__restrict__ perm, uint32_t m,
               uint32_t s, uint32_t w_pad, uint64_t groups, uint32_t *__restrict__ arev, uint64_t rank0)
@@ -32,23 +32,26 @@ gather_kernel(const uint32_t *__restrict__ in, const uint32_t *__restrict__ perm
     const uint32_t gpr = w_pad >> 5;  // 32-word groups per sub-block
     for (uint64_t g = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; g < groups;
          g += gstride)
-        gather_group<kIdentity>(in, perm, s, w_pad, (uint32_t)(g / gpr), (uint32_t)(g % gpr) * 32u, lane, arev, rank0);
+        gather_group<kIdentity, kPadded>(in, perm, s, w_pad, (uint32_t)(g / gpr), (uint32_t)(g % gpr) * 32u, lane, arev,
+                                         rank0);
 }
 
 }  // namespace
 
 int launch_gather(const uint32_t *in, const uint32_t *perm, uint32_t m, uint32_t s,
-                  uint32_t w_pad, uint32_t *arev, cudaStream_t st, int num_sms, uint64_t rank0)
+                  uint32_t w_pad, uint32_t *arev, cudaStream_t st, int num_sms, uint64_t rank0, bool padded)
 {
     if (w_pad % 32u) return set_error(EXTRACT_EINTERNAL, "gather: w_pad %u not a multiple of 32", w_pad);
     const uint64_t groups = (uint64_t)m * (w_pad / 32u);
     if (groups == 0) return EXTRACT_OK;
     const uint64_t want = ceil_div(groups, 8);  // 8 warps per block
     const uint32_t grid = (uint32_t)std::min<uint64_t>(want, (uint64_t)num_sms * 64);
-    if (perm)
-        gather_kernel<false><<<grid, 256, 0, st>>>(in, perm, m, s, w_pad, groups, arev, rank0);
+    if (perm && padded)
+        gather_kernel<false, true><<<grid, 256, 0, st>>>(in, perm, m, s, w_pad, groups, arev, rank0);
+    else if (perm)
+        gather_kernel<false, false><<<grid, 256, 0, st>>>(in, perm, m, s, w_pad, groups, arev, rank0);
     else
-        gather_kernel<true><<<grid, 256, 0, st>>>(in, perm, m, s, w_pad, groups, arev, rank0);
+        gather_kernel<true, false><<<grid, 256, 0, st>>>(in, perm, m, s, w_pad, groups, arev, rank0);
     EX_LAUNCH("gather_kernel");
     return EXTRACT_OK;
 }

@@ -4,6 +4,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "internal.h"
 
 namespace ex {
 
@@ -13,7 +14,10 @@ namespace ex {
 // coalesced 128-byte loads of the order, then 32 independent input loads
 // per lane, packs each word with a ballot and stores the 32 words with one
 // coalesced store.  kIdentity: perm is the identity (perm unused).
-template <bool kIdentity>
+// kPadded: order entries equal to kNoPos are padding and read as 0 (the
+// i.i.d. law's sub-blocks shorter than s; n < 2^32 there, so no position
+// has that value).
+template <bool kIdentity, bool kPadded = false>
 __device__ __forceinline__ void gather_group(const uint32_t *__restrict__ in, const uint32_t *__restrict__ perm,
                                              uint32_t s, uint32_t w_pad, uint32_t j, uint32_t w0, uint32_t lane,
                                              uint32_t *__restrict__ arev, uint64_t rank0 = 0)
@@ -37,7 +41,7 @@ __device__ __forceinline__ void gather_group(const uint32_t *__restrict__ in, co
     for (int t = 0; t < 32; ++t) {
         const uint64_t cr = (uint64_t)(w0 + t) * 32u + lane;
         uint32_t bit = 0;
-        if (cr < s) bit = (__ldg(in + (pos[t] >> 5)) >> (pos[t] & 31u)) & 1u;
+        if (cr < s && (!kPadded || pos[t] != kNoPos)) bit = (__ldg(in + (pos[t] >> 5)) >> (pos[t] & 31u)) & 1u;
         const uint32_t word = __ballot_sync(0xffffffffu, bit);
         if (lane == (uint32_t)t) mine = word;
     }

@@ -3,6 +3,7 @@
 
 #include <cstdint>
 #include <cuda_runtime.h>
+#include <vector>
 
 namespace ex {
 
@@ -14,14 +15,30 @@ namespace ex {
 int build_perm(uint64_t n, uint64_t sampling_key, uint64_t mask, uint32_t *perm,
                cudaStream_t st, int num_sms);
 
+// start[0..nb) = exclusive prefix sums of cnt[0..nb), start[nb] = total
+// (which must equal the sum), on `st`.
+int exclusive_scan_counts(const uint32_t *cnt, uint32_t nb, uint64_t total, uint64_t *start, cudaStream_t st);
+
+// Order entry of a padding slot of the i.i.d. law (reads as a 0 bit).
+constexpr uint32_t kNoPos = 0xffffffffu;
+
+// The paper's i.i.d. sampling law (iid.cu): sub-block V_i =
+// floor(label_i * m / 2^64); order[j*s + c] = the c-th smallest position with
+// V_i = j, kNoPos past |S_j|; sizes_out[j] = |S_j|.  EXTRACT_EABORT (order
+// untouched) when some |S_j| > s.  Needs n < 2^32.  Synchronises `st`.
+int build_iid_order(uint64_t n, uint64_t sampling_key, uint64_t mask, uint32_t m, uint32_t s, uint32_t *order,
+                    std::vector<uint64_t> *sizes_out, cudaStream_t st, int num_sms);
+
 // ---- step 1 (gather) ----------------------------------------------------
 // arev[j * w_pad + w], for j < m and w < w_pad: bit b of the word is
 // in[perm[j*s + s-1-(32w+b)]] when 32w+b < s, else 0 (sub-block j reversed).
 // perm == nullptr means the identity order.
 // rank0: rank of the first position of sub-block 0 of this launch (arev
 // then holds sub-blocks starting at that rank).
+// padded: kNoPos entries of perm read as 0 (i.i.d. law).
 int launch_gather(const uint32_t *in, const uint32_t *perm, uint32_t m, uint32_t s,
-                  uint32_t w_pad, uint32_t *arev, cudaStream_t st, int num_sms, uint64_t rank0 = 0);
+                  uint32_t w_pad, uint32_t *arev, cudaStream_t st, int num_sms, uint64_t rank0 = 0,
+                  bool padded = false);
 
 // ---- steps 2-3: the Toeplitz product and concatenation ------------------
 struct HashPlan {
@@ -121,7 +138,7 @@ int ntt_hash(const NttPlan *p, const uint32_t *arev, uint32_t w_pad, uint32_t m,
 // owned by the caller.
 int ntt_run_overlapped(const NttPlan *p, const uint32_t *in, const uint32_t *perm, uint32_t *arev, uint32_t w_pad,
                        uint32_t m, uint32_t s, uint32_t k, uint32_t *out, cudaStream_t st, cudaStream_t aux,
-                       cudaEvent_t ev_fork, cudaEvent_t ev_group, int num_sms);
+                       cudaEvent_t ev_fork, cudaEvent_t ev_group, int num_sms, bool padded = false);
 void ntt_destroy(NttPlan *p);
 // Stream-ordered release (no device-wide synchronisation).
 void ntt_destroy_async(NttPlan *p, cudaStream_t st);

@@ -278,6 +278,20 @@ int ceil_log2_u64(uint64_t n)
 
 }  // namespace
 
+int exclusive_scan_counts(const uint32_t *cnt, uint32_t nb, uint64_t total, uint64_t *start, cudaStream_t st)
+{
+    const uint32_t nblk = (uint32_t)ceil_div(nb, kScanPerBlock);
+    uint64_t *bsum = nullptr;
+    cudaError_t e = cudaMallocAsync(&bsum, sizeof(uint64_t) * std::max<uint32_t>(nblk, 1), st);
+    if (e != cudaSuccess) return cuda_error(e, "cudaMalloc(scan)");
+    scan_blocks_kernel<<<nblk, 1024, 0, st>>>(cnt, nb, start, bsum);
+    scan_bsum_kernel<<<1, 1024, 0, st>>>(bsum, nblk);
+    scan_add_kernel<<<(uint32_t)ceil_div((uint64_t)nb + 1, 256), 256, 0, st>>>(start, nb, bsum, total);
+    e = cudaGetLastError();
+    cudaFreeAsync(bsum, st);
+    return e == cudaSuccess ? EXTRACT_OK : cuda_error(e, "scan kernels");
+}
+
 int build_perm(uint64_t n, uint64_t sampling_key, uint64_t mask, uint32_t *perm,
                cudaStream_t st, int num_sms)
 {

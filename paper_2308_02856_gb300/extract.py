@@ -23,11 +23,14 @@ EXTRACT_ETIMEDOUT = -4
 EXTRACT_EBUDGET = -5
 EXTRACT_EBUSY = -6
 EXTRACT_EINTERNAL = -7
+EXTRACT_EABORT = -8
 
 EXTRACT_SEED_PER_SUBBLOCK = 0x1
 EXTRACT_IDENTITY_PERM = 0x2
 EXTRACT_METHOD_DIRECT = 0x4
 EXTRACT_METHOD_NTT = 0x8
+EXTRACT_SAMPLING_IID = 0x10
+NO_POS = 0xFFFFFFFF  # padding slot of the i.i.d. law's order
 
 
 def EXTRACT_KEY_BITS(b: int) -> int:
@@ -43,6 +46,7 @@ def EXTRACT_NTT_SPLIT(l: int) -> int:
 EXPORTED = [
     "extract_create", "extract_run", "extract_run_host", "extract_gather", "extract_hash", "extract_run_plain",
     "extract_read_perm", "extract_read_subblock", "extract_describe", "extract_destroy",
+    "extract_subblock_sizes", "extract_block_limit",
     "extract_last_error", "extract_run_static",
     "extract_batch_create", "extract_batch_run", "extract_batch_run_sequential", "extract_batch_describe",
     "extract_batch_destroy",
@@ -98,6 +102,8 @@ def load() -> ctypes.CDLL:
     L.extract_run_plain.argtypes = [vp, vp, vp, vp]
     L.extract_read_perm.argtypes = [vp, u64, u64, vp]
     L.extract_read_subblock.argtypes = [vp, u32, vp]
+    L.extract_subblock_sizes.argtypes = [vp, vp]
+    L.extract_block_limit.argtypes = [u64, u32, ctypes.c_double, ctypes.c_double, ctypes.POINTER(u64)]
     L.extract_describe.argtypes = [vp, ctypes.c_char_p, u32]
     L.extract_destroy.argtypes = [vp]
     L.extract_run_static.argtypes = [u64, u32, u32, u32, vp, vp, vp, vp, vp]
@@ -191,6 +197,19 @@ def extract_read_perm(h, start: int, count: int) -> np.ndarray:
     out = np.empty(max(count, 1), dtype=np.uint32)
     _check(load().extract_read_perm(h, start, count, out.ctypes.data))
     return out[:count]
+
+
+def extract_subblock_sizes(h, m: int) -> np.ndarray:
+    out = np.empty(max(m, 1), dtype=np.uint64)
+    _check(load().extract_subblock_sizes(h, out.ctypes.data))
+    return out[:m]
+
+
+def extract_block_limit(N: int, m: int, eps: float, p: float) -> int:
+    """Eq. 7's block size limit (host computation in the library)."""
+    out = ctypes.c_uint64(0)
+    _check(load().extract_block_limit(N, m, float(eps), float(p), ctypes.byref(out)))
+    return int(out.value)
 
 
 def extract_read_subblock(h, j: int, s: int) -> np.ndarray:
@@ -368,7 +387,11 @@ class Extractor:
         return out_bits
 
     def read_perm(self, start=0, count=None):
-        return extract_read_perm(self.h, start, self.n - start if count is None else count)
+        length = self.m * self.s if self.flags & EXTRACT_SAMPLING_IID else self.n
+        return extract_read_perm(self.h, start, length - start if count is None else count)
+
+    def sizes(self) -> np.ndarray:
+        return extract_subblock_sizes(self.h, self.m)
 
     def read_subblock(self, j):
         return extract_read_subblock(self.h, j, self.s)

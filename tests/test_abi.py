@@ -11,6 +11,8 @@ import pytest
 from paper_2308_02856_gb300 import build as pkg_build
 from paper_2308_02856_gb300 import extract as X
 
+import oracle
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADERS = [os.path.join(ROOT, "include", f) for f in sorted(os.listdir(os.path.join(ROOT, "include")))
            if f.endswith(".h")]
@@ -90,3 +92,18 @@ def test_product_path_fails_loudly_without_the_library(monkeypatch, tmp_path):
     monkeypatch.setattr(X, "_lib", None)
     with pytest.raises(RuntimeError, match="not built"):
         X.load()
+
+
+def test_block_limit_matches_the_oracle_and_rejects_bad_arguments():
+    """extract_block_limit is host code: it runs without a GPU.  The library's
+    Eq. 7 and the oracle's give the same limit on a grid of parameters."""
+    for N in (1000, 10**6, 2**24, 2**30, 10**9, 2**32 - 1):
+        for m in (1, 2, 17, 64, 1024, 4096):
+            for eps in (1e-3, 1e-8, 1e-12):
+                p = 1.0 / m if m > 1 else 0.5
+                assert X.extract_block_limit(N, m, eps, p) == oracle.block_limit(N, m, eps, p), (N, m, eps)
+    for args in ((0, 4, 1e-8, 0.25), (100, 0, 1e-8, 0.25), (100, 4, 0.0, 0.25), (100, 4, 1e-8, 1.0),
+                 (100, 4, 1e-8, 0.0)):
+        with pytest.raises(X.ExtractError) as e:
+            X.extract_block_limit(*args)
+        assert e.value.code == X.EXTRACT_EINVAL
