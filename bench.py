@@ -210,13 +210,22 @@ def aggregate_rate(n_per_rank: int, world: int, ms_per_step: float) -> float:
     return world * n_per_rank / (ms_per_step / 1e3) / 1e9
 
 
-def launches_per_step(is_ntt, m, plan):
-    """Kernels of ours per step: gather + hash (direct), or per group of
-    sub-blocks a gather and three transform passes (NTT)."""
+GATHER_WINDOW_BITS = 1 << 29  # inputs longer than this are gathered in one pass per window
+
+
+def launches_per_step(is_ntt, m, plan, n=0):
+    """Kernels of ours per step: the gather pass(es) + the hash (direct); for
+    the NTT method the whole-block gather + three transform passes per group
+    of sub-blocks, or (inputs over two gather windows) a gather per group."""
+    passes = -(-n // GATHER_WINDOW_BITS)
+    passes = passes if passes == 2 else 1  # windows only when they take two passes
     if not is_ntt:
-        return 2
+        return passes + 1
     g = int(plan.split("sub-blocks per launch group")[0].split(",")[-1])
-    return 4 * ((m + g - 1) // g)
+    groups = (m + g - 1) // g
+    if n <= 2 * GATHER_WINDOW_BITS:
+        return passes + 3 * groups
+    return 4 * groups
 
 
 def ntt_roofline(n, m, s, k, hash_ms, plan, sms=152):
@@ -443,7 +452,7 @@ def run_ours(args):
             "method": "ntt" if is_ntt else "direct",
             "create_ms": create_ms,
             "gather_ms": gather_ms, "hash_ms": hash_ms,
-            "gpu_launches": launches_per_step(is_ntt, m, plan) * args.steps,
+            "gpu_launches": launches_per_step(is_ntt, m, plan, n) * args.steps,
             "direct_lop3": direct,
             "roofline": roofline,
             "cpu_baseline": cpu,

@@ -528,7 +528,8 @@ int extract_batch_run(extract_batch *b, void *stream, const uint32_t *const *in_
         for (uint32_t i : b->ntt_order) {
             const BatchJobHost &J = b->jobs[i];
             const NttLane &L = b->lanes[J.lane];
-            if (int rc = launch_gather(in_bits_dev[i], J.perm, J.m, J.s, J.w_pad, J.arev, L.st, b->num_sms)) return rc;
+            if (int rc = launch_gather(in_bits_dev[i], J.perm, J.m, J.s, J.w_pad, J.arev, L.st, b->num_sms, 0, false, J.n))
+                return rc;
             if (int rc = ntt_hash(J.ntt, J.arev, J.w_pad, J.m, J.s, J.k, out_bits_dev[i], L.st, L.work)) return rc;
         }
         for (NttLane &L : b->lanes)
@@ -559,7 +560,8 @@ int extract_batch_run_sequential(extract_batch *b, void *stream, const uint32_t 
     for (size_t i = 0; i < b->jobs.size(); ++i) {
         const BatchJobHost &J = b->jobs[i];
         if (!in_bits_dev[i] || !out_bits_dev[i]) return set_error(EXTRACT_EINVAL, "job %zu: null buffer", i);
-        if (int rc = launch_gather(in_bits_dev[i], J.perm, J.m, J.s, J.w_pad, J.arev, st, b->num_sms)) return rc;
+        if (int rc = launch_gather(in_bits_dev[i], J.perm, J.m, J.s, J.w_pad, J.arev, st, b->num_sms, 0, false, J.n))
+            return rc;
         if (J.ntt) {
             if (int rc = ntt_hash(J.ntt, J.arev, J.w_pad, J.m, J.s, J.k, out_bits_dev[i], st)) return rc;
         } else if (int rc = launch_hash(J.plain_plan, J.seed, J.nseeds > 1 ? J.seed_stride : 0u, J.arev, J.w_pad,

@@ -17,10 +17,15 @@ namespace ex {
 // kPadded: order entries equal to kNoPos are padding and read as 0 (the
 // i.i.d. law's sub-blocks shorter than s; n < 2^32 there, so no position
 // has that value).
-template <bool kIdentity, bool kPadded = false>
+// kWindowed: only positions in [wlo, wlo + wlen) are read (the others
+// count as 0) and, when `accumulate`, the words are OR-ed into what earlier
+// windows stored: passes over windows of the input that fit in L2 turn the
+// random input reads into L2 hits at the cost of re-reading the order.
+template <bool kIdentity, bool kPadded = false, bool kWindowed = false>
 __device__ __forceinline__ void gather_group(const uint32_t *__restrict__ in, const uint32_t *__restrict__ perm,
                                              uint32_t s, uint32_t w_pad, uint32_t j, uint32_t w0, uint32_t lane,
-                                             uint32_t *__restrict__ arev, uint64_t rank0 = 0)
+                                             uint32_t *__restrict__ arev, uint64_t rank0 = 0, uint32_t wlo = 0,
+                                             uint32_t wlen = 0, bool accumulate = false)
 {
     const uint64_t top = rank0 + (uint64_t)j * s + (s - 1);  // rank of A_j[s-1]
     uint32_t pos[32];
@@ -41,11 +46,15 @@ __device__ __forceinline__ void gather_group(const uint32_t *__restrict__ in, co
     for (int t = 0; t < 32; ++t) {
         const uint64_t cr = (uint64_t)(w0 + t) * 32u + lane;
         uint32_t bit = 0;
-        if (cr < s && (!kPadded || pos[t] != kNoPos)) bit = (__ldg(in + (pos[t] >> 5)) >> (pos[t] & 31u)) & 1u;
+        const bool in_window = !kWindowed || pos[t] - wlo < wlen;
+        if (cr < s && (!kPadded || pos[t] != kNoPos) && in_window)
+            bit = (__ldg(in + (pos[t] >> 5)) >> (pos[t] & 31u)) & 1u;
         const uint32_t word = __ballot_sync(0xffffffffu, bit);
         if (lane == (uint32_t)t) mine = word;
     }
-    __stcs(arev + (uint64_t)j * w_pad + w0 + lane, mine);
+    uint32_t *dst = arev + (uint64_t)j * w_pad + w0 + lane;
+    if (kWindowed && accumulate) mine |= *dst;
+    __stcs(dst, mine);
 }
 
 }  // namespace ex

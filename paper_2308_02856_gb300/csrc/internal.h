@@ -35,10 +35,15 @@ int build_iid_order(uint64_t n, uint64_t sampling_key, uint64_t mask, uint32_t m
 // perm == nullptr means the identity order.
 // rank0: rank of the first position of sub-block 0 of this launch (arev
 // then holds sub-blocks starting at that rank).
-// padded: kNoPos entries of perm read as 0 (i.i.d. law).
+// padded: kNoPos entries of perm read as 0 (i.i.d. law).  input_bits: the
+// input's length; sorted-order inputs of one to two half-L2 windows are
+// gathered in one pass per window (0: one pass).
 int launch_gather(const uint32_t *in, const uint32_t *perm, uint32_t m, uint32_t s,
                   uint32_t w_pad, uint32_t *arev, cudaStream_t st, int num_sms, uint64_t rank0 = 0,
-                  bool padded = false);
+                  bool padded = false, uint64_t input_bits = 0);
+// True when the gather of an input of this length runs best as one launch
+// (at most two windows); larger inputs are better overlapped with hashing.
+bool gather_prefers_whole_block(uint64_t input_bits);
 
 // ---- steps 2-3: the Toeplitz product and concatenation ------------------
 struct HashPlan {
@@ -138,7 +143,8 @@ int ntt_hash(const NttPlan *p, const uint32_t *arev, uint32_t w_pad, uint32_t m,
 // owned by the caller.
 int ntt_run_overlapped(const NttPlan *p, const uint32_t *in, const uint32_t *perm, uint32_t *arev, uint32_t w_pad,
                        uint32_t m, uint32_t s, uint32_t k, uint32_t *out, cudaStream_t st, cudaStream_t aux,
-                       cudaEvent_t ev_fork, cudaEvent_t ev_group, int num_sms, bool padded = false);
+                       cudaEvent_t ev_fork, cudaEvent_t ev_group, int num_sms, bool padded = false,
+                       uint64_t input_bits = 0);
 void ntt_destroy(NttPlan *p);
 // Stream-ordered release (no device-wide synchronisation).
 void ntt_destroy_async(NttPlan *p, cudaStream_t st);

@@ -1226,7 +1226,7 @@ int ntt_hash(const NttPlan *p, const uint32_t *arev, uint32_t w_pad, uint32_t m,
 
 int ntt_run_overlapped(const NttPlan *p, const uint32_t *in, const uint32_t *perm, uint32_t *arev, uint32_t w_pad,
                        uint32_t m, uint32_t s, uint32_t k, uint32_t *out, cudaStream_t st, cudaStream_t aux,
-                       cudaEvent_t ev_fork, cudaEvent_t ev_group, int num_sms, bool padded)
+                       cudaEvent_t ev_fork, cudaEvent_t ev_group, int num_sms, bool padded, uint64_t input_bits)
 {
     EX_CUDA(cudaEventRecord(ev_fork, st));
     EX_CUDA(cudaStreamWaitEvent(aux, ev_fork, 0));
@@ -1235,7 +1235,8 @@ int ntt_run_overlapped(const NttPlan *p, const uint32_t *in, const uint32_t *per
     for (uint32_t j0 = 0; j0 < m; j0 += p->G) {
         const uint32_t g = std::min(p->G, m - j0);
         uint32_t *ar = arev + (size_t)j0 * w_pad;
-        if (int rc = launch_gather(in, perm, g, s, w_pad, ar, aux, num_sms, (uint64_t)j0 * s, padded)) return rc;
+        if (int rc = launch_gather(in, perm, g, s, w_pad, ar, aux, num_sms, (uint64_t)j0 * s, padded, input_bits))
+            return rc;
         // each wait binds to the record just before it, so one event serves every group
         EX_CUDA(cudaEventRecord(ev_group, aux));
         EX_CUDA(cudaStreamWaitEvent(st, ev_group, 0));

@@ -162,7 +162,7 @@ int setup_job(extract_server *S, SJob &J)
         const uint64_t mask = kb ? ~((1ull << (64u - kb)) - 1ull) : ~0ull;
         if (int rc = build_perm(J.n, J.key, mask, J.perm, st, S->sms)) return rc;
     }
-    if (int rc = launch_gather(J.in, J.perm, J.m, J.s, J.w_pad, J.arev, st, S->sms)) return rc;
+    if (int rc = launch_gather(J.in, J.perm, J.m, J.s, J.w_pad, J.arev, st, S->sms, 0, false, J.n)) return rc;
     EX_CUDA(cudaMemsetAsync(J.out, 0, ceil_div((uint64_t)J.m * J.k, 32) * 4, st));
     if (J.use_ntt)  // tables and the seed spectrum (synchronous on the setup stream)
         if (int rc = ntt_create(&J.ntt, J.m, J.s, J.k, J.seed, st, S->lanes[0].work)) return rc;

@@ -96,6 +96,6 @@ extern "C" int extract_run_static(uint64_t n, uint32_t m, uint32_t s, uint32_t k
     stage_seed_kernel<<<(uint32_t)ceil_div(stride, 256), 256, 0, st>>>(seed_dev, (uint64_t)s + k - 1, stride,
                                                                        seed_stage);
     EX_LAUNCH("stage_seed_kernel");
-    if (int rc = launch_gather(in_bits_dev, perm_dev, m, s, w_pad, arev, st, sms)) return rc;
+    if (int rc = launch_gather(in_bits_dev, perm_dev, m, s, w_pad, arev, st, sms, 0, false, n)) return rc;
     return launch_hash(plan, seed_stage, 0u, arev, w_pad, m, k, out_bits_dev, st);
 }
