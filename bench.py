@@ -228,7 +228,16 @@ def launches_per_step(is_ntt, m, plan, n=0):
     return 4 * groups
 
 
-def ntt_roofline(n, m, s, k, hash_ms, plan, sms=152):
+# DRAM bytes (read + write) of one NTT hash: the ncu capture of one launch
+# group (8 sub-blocks, P = 2, N = 2^20: 139.4 MB over the three passes, cold
+# cache; profiles/ntt_kernels_qrng128_n2^27_m128_s2^20_k2^19.md) times the
+# groups of the block.  Set to None whenever the kernels change until they
+# are captured again.
+NTT_TRAFFIC_BYTES = {"qrng_n2^30_m1024_s2^20_k2^19": 139.4e6 * 128,
+                     "qrng128_n2^27_m128_s2^20_k2^19": 139.4e6 * 16}
+
+
+def ntt_roofline(n, m, s, k, hash_ms, plan, sms=152, workload=None):
     """NTT path: the transform work (forward + inverse, N/2 log2 N radix-2
     butterflies each, per sub-block) against the integer ALU pipe.  A lazy
     butterfly is 7 integer instructions, 4 of them (adds, subtracts, min) on
@@ -241,7 +250,8 @@ def ntt_roofline(n, m, s, k, hash_ms, plan, sms=152):
     achieved = bfly / (hash_ms / 1e3) / 1e12
     peak = sms * 64 / 4.0 * 2070e6 / 1e12
     return {"bound": "alu", "achieved": achieved, "unit": "Tbutterfly/s", "peak": peak, "frac": achieved / peak,
-            "traffic": None, "kernel": "ntt_cols_fwd_t / ntt_rows / ntt_cols_inv_t (one hash)",
+            "traffic": NTT_TRAFFIC_BYTES.get(workload),
+            "kernel": "the NTT hash: pass A (column DIF), pass B (rows), pass A' (column DIT) per launch group",
             "work_per_launch": "m x (P+1) x N/2 log2 N = %.4g radix-2 butterflies mod p (N=%d, P=%d pieces "
                                "per sub-block)" % (bfly, N, P),
             "peak_basis": "%d SMs x 64 ALU lanes / 4 ALU ops per lazy butterfly x 2070 MHz" % sms,
@@ -406,7 +416,7 @@ def run_ours(args):
 
     direct = None
     if is_ntt:
-        roofline = ntt_roofline(n, m, s, k, hash_ms, plan, sms)
+        roofline = ntt_roofline(n, m, s, k, hash_ms, plan, sms, None if iid else args.workload)
         # the direct kernel on the same block, for the record (2 timed steps)
         exd = X.Extractor(n, m, s, k, seed_w, SAMPLING_KEY,
                           X.EXTRACT_METHOD_DIRECT | (X.EXTRACT_SAMPLING_IID if iid else 0))
