@@ -66,10 +66,13 @@ struct extract_ctx {
     NttPlan *ntt = nullptr;  // set when the NTT method hashes this shape
     cudaStream_t aux = nullptr;                       // gather stream of the overlapped NTT run
     cudaEvent_t ev_fork = nullptr, ev_group = nullptr;
+    NttSecondLane lane2;                              // second lane of the NTT hash (own stream, buffer)
 };
 
 namespace {
 
+// NTT hash on two lanes (alternating launch groups)
+constexpr bool kNttTwoLanes = true;
 
 constexpr uint32_t kKnownFlags = EXTRACT_SEED_PER_SUBBLOCK | EXTRACT_IDENTITY_PERM | EXTRACT_METHOD_DIRECT |
                                   EXTRACT_METHOD_NTT | EXTRACT_SAMPLING_IID | (0x3fu << 8) | (0x7u << 16);
@@ -86,6 +89,10 @@ void free_ctx(extract_ctx *h)
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
     if (h->ev_group) cudaEventDestroy(h->ev_group);
     if (h->aux) cudaStreamDestroy(h->aux);
+    cudaFree(h->lane2.work);
+    if (h->lane2.ev_fork) cudaEventDestroy(h->lane2.ev_fork);
+    if (h->lane2.ev_join) cudaEventDestroy(h->lane2.ev_join);
+    if (h->lane2.st) cudaStreamDestroy(h->lane2.st);
     delete h;
 }
 
@@ -202,6 +209,16 @@ int extract_create(extract_ctx **out, uint64_t n, uint32_t m, uint32_t s, uint32
             free_ctx(h);
             return cuda_error(e, "overlap stream");
         }
+        if (kNttTwoLanes && m > ntt_group(h->ntt)) {
+            NttSecondLane &L = h->lane2;
+            if ((e = cudaStreamCreateWithFlags(&L.st, cudaStreamNonBlocking)) != cudaSuccess ||
+                (e = cudaEventCreateWithFlags(&L.ev_fork, cudaEventDisableTiming)) != cudaSuccess ||
+                (e = cudaEventCreateWithFlags(&L.ev_join, cudaEventDisableTiming)) != cudaSuccess ||
+                (e = cudaMalloc(&L.work, ntt_work_words(m, s, k, split) * 4)) != cudaSuccess) {
+                free_ctx(h);
+                return cuda_error(e, "second NTT lane");
+            }
+        }
     }
     if ((e = cudaMalloc(&h->arev, (size_t)m * h->w_pad * 4)) != cudaSuccess) { free_ctx(h); return cuda_error(e, "cudaMalloc(sub-blocks)"); }
     if ((e = cudaMemset(h->arev, 0, (size_t)m * h->w_pad * 4)) != cudaSuccess) { free_ctx(h); return cuda_error(e, "memset(sub-blocks)"); }
@@ -236,7 +253,9 @@ int extract_hash(extract_ctx *h, void *stream, uint32_t *out_bits_dev)
 {
     if (int rc = check_ctx(h)) return rc;
     if (!out_bits_dev) return set_error(EXTRACT_EINVAL, "out_bits_dev is null");
-    if (h->ntt) return ntt_hash(h->ntt, h->arev, h->w_pad, h->m, h->s, h->k, out_bits_dev, (cudaStream_t)stream);
+    if (h->ntt)
+        return ntt_hash(h->ntt, h->arev, h->w_pad, h->m, h->s, h->k, out_bits_dev, (cudaStream_t)stream, nullptr,
+                        kNttTwoLanes ? &h->lane2 : nullptr);
     return launch_hash(h->plan, h->seed, h->nseeds > 1 ? h->seed_stride : 0u, h->arev, h->w_pad, h->m,
                        h->k, out_bits_dev, (cudaStream_t)stream);
 }

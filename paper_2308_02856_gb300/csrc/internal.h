@@ -132,11 +132,20 @@ double ntt_work_butterflies(uint32_t m, uint32_t s, uint32_t k, int split_log2 =
 // run concurrently, or null to allocate one.
 int ntt_create(NttPlan **out, uint32_t m, uint32_t s, uint32_t k, const uint32_t *seed_dev, cudaStream_t st,
                uint32_t *work = nullptr, int split_log2 = -1);
+// A second stream and work buffer for ntt_hash: launch groups alternate
+// between the two, so one group's passes fill the other's last waves.
+// ev_fork / ev_join: events owned by the caller.
+struct NttSecondLane {
+    cudaStream_t st = nullptr;
+    uint32_t *work = nullptr;  // ntt_work_words() words
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+};
 // Hashes all m gathered sub-blocks; zeroes and fills out.  work: a buffer
 // of ntt_work_words() words to use instead of the plan's own (null: the
-// plan's).
+// plan's).  lane2: optional second lane (ordered after prior work on st and
+// joined back into st).
 int ntt_hash(const NttPlan *p, const uint32_t *arev, uint32_t w_pad, uint32_t m, uint32_t s, uint32_t k,
-             uint32_t *out, cudaStream_t st, uint32_t *work = nullptr);
+             uint32_t *out, cudaStream_t st, uint32_t *work = nullptr, const NttSecondLane *lane2 = nullptr);
 // Gather and hash with the gather of each launch group on `aux` overlapping
 // the transforms of the previous group on `st`; ordered after prior work on
 // st and fully ordered before later work on st.  ev_fork, ev_group: events

@@ -1209,16 +1209,29 @@ static Pieces sub_block_pieces(const NttPlan *p, uint32_t w_pad, uint32_t s)
 
 // Hash every sub-block: out (zeroed here) gets K_j at bit j*k.
 int ntt_hash(const NttPlan *p, const uint32_t *arev, uint32_t w_pad, uint32_t m, uint32_t s, uint32_t k,
-             uint32_t *out, cudaStream_t st, uint32_t *work)
+             uint32_t *out, cudaStream_t st, uint32_t *work, const NttSecondLane *lane2)
 {
     uint32_t *buf = work ? work : p->buf;
     EX_CUDA(cudaMemsetAsync(out, 0, ceil_div((uint64_t)m * k, 32) * 4, st));
     const Pieces pc = sub_block_pieces(p, w_pad, s);
-    for (uint32_t j0 = 0; j0 < m; j0 += p->G) {
+    const bool two = lane2 && lane2->st && lane2->work && m > p->G;
+    if (two) {  // odd groups on the second lane: its launches fill the first lane's last waves
+        EX_CUDA(cudaEventRecord(lane2->ev_fork, st));
+        EX_CUDA(cudaStreamWaitEvent(lane2->st, lane2->ev_fork, 0));
+    }
+    uint32_t gi = 0;
+    for (uint32_t j0 = 0; j0 < m; j0 += p->G, ++gi) {
         const uint32_t g = std::min(p->G, m - j0);
-        if (int rc = ntt_launch_a(p, arev + (size_t)j0 * w_pad, pc, true, g, buf, st)) return rc;
-        ntt_launch_rows(p, buf, g, p->P, p->S, p->Sq, true, st);
-        if (int rc = ntt_launch_a_inv(p, buf, g, j0, k, out, st)) return rc;
+        const bool second = two && (gi & 1u);
+        cudaStream_t gs = second ? lane2->st : st;
+        uint32_t *gb = second ? lane2->work : buf;
+        if (int rc = ntt_launch_a(p, arev + (size_t)j0 * w_pad, pc, true, g, gb, gs)) return rc;
+        ntt_launch_rows(p, gb, g, p->P, p->S, p->Sq, true, gs);
+        if (int rc = ntt_launch_a_inv(p, gb, g, j0, k, out, gs)) return rc;
+    }
+    if (two) {
+        EX_CUDA(cudaEventRecord(lane2->ev_join, lane2->st));
+        EX_CUDA(cudaStreamWaitEvent(st, lane2->ev_join, 0));
     }
     EX_LAUNCH("ntt kernels");
     return EXTRACT_OK;
