@@ -3,12 +3,18 @@
 // labels with the lower position first on equal labels.
 //
 // GPU design (no sort library): the labels are never stored; every pass
-// recomputes them from the position with Philox, which keeps the device
-// footprint at the 4n-byte order itself.
-//   1. histogram of the top b label bits (b = ceil(log2 n) - 10, so a bucket
-//      holds about 512-1024 positions);
-//   2. exclusive scan of the bucket counts;
-//   3. scatter of every position into its bucket (any order inside it);
+// recomputes them from the position with Philox.  The order is an MSD sort
+// on the top b = ceil(log2 n) - 10 label bits (buckets of about 512-1024
+// positions) finished by a sort inside each bucket:
+//   1. a histogram of the top C <= 10 label bits (coarse bins) in shared
+//      memory per CTA;
+//   2. coarse scatter: each CTA sorts a tile of 8192 positions by coarse bin
+//      in shared memory and writes one contiguous run per bin (coalesced),
+//      reserving its place in the bin with one atomic per (tile, bin);
+//   3. fine pass, one CTA per coarse bin: a shared-memory histogram of the
+//      next b - C bits, then the scatter of the bin's positions into their
+//      buckets; a coarse bin spans at most a few MB of the order, so these
+//      random writes stay in L2;
 //   4. one CTA per bucket sorts it in shared memory by (label, position):
 //      a counting pass on the next 10 label bits, then insertion sort of
 //      each of those small bins;
@@ -18,27 +24,16 @@
 #include "internal.h"
 
 #include <algorithm>
+#include <vector>
 
 namespace ex {
 namespace {
 
 constexpr int kSortCap = 2048;      // positions per bucket sorted in smem
-constexpr int kSubBits = 10;        // counting-pass digit inside a bucket
+constexpr int kSubBits = 8;         // counting-pass digit inside a bucket (== kSortThreads bins)
 constexpr int kSubBins = 1 << kSubBits;
 constexpr int kSortThreads = 256;
 constexpr int kScanPerBlock = 4096; // elements per scan block (1024 x 4)
-
-__device__ __forceinline__ uint32_t bucket_of(uint64_t label, int b)
-{
-    return b ? (uint32_t)(label >> (64 - b)) : 0u;
-}
-
-__global__ void perm_hist_kernel(uint64_t n, uint2 key, uint64_t mask, int b, uint32_t *cnt)
-{
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += stride)
-        atomicAdd(&cnt[bucket_of(sampling_label(i, key, mask), b)], 1u);
-}
 
 // Inclusive scan of one value per thread across a block of 1024 threads.
 __device__ __forceinline__ uint64_t block_inclusive_scan(uint64_t v, uint64_t *warp_tot)
@@ -114,14 +109,162 @@ __global__ void scan_add_kernel(uint64_t *start, uint32_t nb, const uint64_t *bs
     if (i == 0) start[nb] = n;
 }
 
-__global__ void perm_scatter_kernel(uint64_t n, uint2 key, uint64_t mask, int b,
-                                    const uint64_t *start, uint32_t *fill, uint32_t *perm)
+constexpr int kCoarseMax = 10;              // coarse bins: at most 1024
+constexpr uint32_t kCoarseBins = 1u << kCoarseMax;
+constexpr int kTileThreads = 512;
+constexpr int kTilePerThread = 16;
+constexpr uint32_t kTile = kTileThreads * kTilePerThread;  // positions per coarse-scatter tile
+constexpr int kFineThreads = 1024;
+
+__device__ __forceinline__ uint32_t coarse_of(uint64_t label, int C)
 {
+    return C ? (uint32_t)(label >> (64 - C)) : 0u;
+}
+__device__ __forceinline__ uint32_t fine_of(uint64_t label, int C, int F)
+{
+    return F ? (uint32_t)((label << C) >> (64 - F)) : 0u;
+}
+
+// ccnt[d] += #{i : coarse digit d}
+__global__ void __launch_bounds__(512) perm_coarse_hist_kernel(uint64_t n, uint2 key, uint64_t mask, int C,
+                                                               uint32_t *ccnt)
+{
+    __shared__ uint32_t h[kCoarseBins];
+    for (uint32_t d = threadIdx.x; d < kCoarseBins; d += blockDim.x) h[d] = 0;
+    __syncthreads();
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
-        const uint32_t bk = bucket_of(sampling_label(i, key, mask), b);
-        const uint64_t pos = start[bk] + atomicAdd(&fill[bk], 1u);
-        perm[pos] = (uint32_t)i;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += stride)
+        atomicAdd(&h[coarse_of(sampling_label(i, key, mask), C)], 1u);
+    __syncthreads();
+    for (uint32_t d = threadIdx.x; d < (1u << C); d += blockDim.x)
+        if (h[d]) atomicAdd(&ccnt[d], h[d]);
+}
+
+// Exclusive scan of kCoarseBins values (2 per thread, 512 threads) in place;
+// returns nothing, tot: scratch of 16 words.
+__device__ __forceinline__ void scan_coarse_bins(uint32_t *v, uint32_t *tot)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t a = v[2 * threadIdx.x], b = v[2 * threadIdx.x + 1];
+    uint32_t x = a + b;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t o = __shfl_up_sync(0xffffffffu, x, d);
+        if (lane >= d) x += o;
+    }
+    if (lane == 31) tot[warp] = x;
+    __syncthreads();
+    uint32_t base = 0;
+    for (int w = 0; w < warp; ++w) base += tot[w];
+    const uint32_t excl = base + x - (a + b);
+    __syncthreads();
+    v[2 * threadIdx.x] = excl;
+    v[2 * threadIdx.x + 1] = excl + a;
+    __syncthreads();
+}
+
+// Coarse scatter: tile t holds positions [t kTile, (t+1) kTile); they are
+// sorted by coarse digit in shared memory and each digit's run is written
+// to tmp[cstart[d] + (the run's reserved offset in bin d)].
+__global__ void __launch_bounds__(kTileThreads) perm_coarse_scatter_kernel(uint64_t n, uint2 key, uint64_t mask,
+                                                                           int C, const uint64_t *cstart,
+                                                                           uint32_t *cfill, uint32_t *tmp)
+{
+    __shared__ uint32_t cnt[kCoarseBins], tstart[kCoarseBins], gbase[kCoarseBins], tot[16];
+    extern __shared__ uint32_t sorted_pos[];  // kTile positions, then kTile 16-bit digits
+    uint16_t *sorted_dig = reinterpret_cast<uint16_t *>(sorted_pos + kTile);
+    const uint32_t nbins = 1u << C;
+    const uint64_t ntiles = (n + kTile - 1) / kTile;
+    for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const uint64_t i0 = t * kTile;
+        const uint32_t cnt_t = (uint32_t)min((uint64_t)kTile, n - i0);
+        for (uint32_t d = threadIdx.x; d < kCoarseBins; d += blockDim.x) cnt[d] = 0;
+        __syncthreads();
+        uint16_t dig[kTilePerThread], rnk[kTilePerThread];
+#pragma unroll
+        for (int q = 0; q < kTilePerThread; ++q) {
+            const uint32_t e = threadIdx.x + q * kTileThreads;
+            if (e < cnt_t) {
+                const uint32_t d = coarse_of(sampling_label(i0 + e, key, mask), C);
+                dig[q] = (uint16_t)d;
+                rnk[q] = (uint16_t)atomicAdd(&cnt[d], 1u);
+            }
+        }
+        __syncthreads();
+        for (uint32_t d = threadIdx.x; d < kCoarseBins; d += blockDim.x) {
+            tstart[d] = cnt[d];
+            gbase[d] = (d < nbins && cnt[d]) ? atomicAdd(&cfill[d], cnt[d]) : 0u;
+        }
+        __syncthreads();
+        scan_coarse_bins(tstart, tot);
+#pragma unroll
+        for (int q = 0; q < kTilePerThread; ++q) {
+            const uint32_t e = threadIdx.x + q * kTileThreads;
+            if (e < cnt_t) {
+                const uint32_t at = tstart[dig[q]] + rnk[q];
+                sorted_pos[at] = (uint32_t)(i0 + e);
+                sorted_dig[at] = dig[q];
+            }
+        }
+        __syncthreads();
+        for (uint32_t u = threadIdx.x; u < cnt_t; u += blockDim.x) {
+            const uint32_t d = sorted_dig[u];
+            tmp[cstart[d] + gbase[d] + (u - tstart[d])] = sorted_pos[u];
+        }
+        __syncthreads();
+    }
+}
+
+// Fine pass: CTA per coarse bin c (grid-stride).  The bin's positions
+// tmp[cstart[c] .. cstart[c+1]) go to their buckets (c << F) + f, whose
+// starts it also writes (start[bucket] = first rank of the bucket).
+__global__ void __launch_bounds__(kFineThreads) perm_fine_kernel(uint2 key, uint64_t mask, int C, int F,
+                                                                 const uint64_t *cstart, const uint32_t *tmp,
+                                                                 uint64_t *start, uint32_t *perm)
+{
+    extern __shared__ uint32_t fsm[];  // hist[1 << F], fill[1 << F]
+    __shared__ uint64_t warp_tot[32];
+    const uint32_t nf = 1u << F;
+    uint32_t *hist = fsm, *fill = fsm + nf;
+    for (uint32_t c = blockIdx.x; c < (1u << C); c += gridDim.x) {
+        const uint64_t lo = cstart[c], L = cstart[c + 1] - lo;
+        for (uint32_t f = threadIdx.x; f < nf; f += blockDim.x) {
+            hist[f] = 0;
+            fill[f] = 0;
+        }
+        __syncthreads();
+        for (uint64_t e = threadIdx.x; e < L; e += blockDim.x)
+            atomicAdd(&hist[fine_of(sampling_label(tmp[lo + e], key, mask), C, F)], 1u);
+        __syncthreads();
+        // exclusive scan of nf (<= 4 * blockDim) counts, 4 per thread
+        {
+            uint32_t v[4], tsum = 0;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const uint32_t f = threadIdx.x * 4 + q;
+                v[q] = f < nf ? hist[f] : 0u;
+                tsum += v[q];
+            }
+            const uint64_t incl = block_inclusive_scan(tsum, warp_tot);
+            uint32_t run = (uint32_t)(incl - tsum);
+            __syncthreads();
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const uint32_t f = threadIdx.x * 4 + q;
+                if (f < nf) {
+                    hist[f] = run;
+                    start[((uint64_t)c << F) + f] = lo + run;
+                }
+                run += v[q];
+            }
+        }
+        __syncthreads();
+        for (uint64_t e = threadIdx.x; e < L; e += blockDim.x) {
+            const uint32_t pos = tmp[lo + e];
+            const uint32_t f = fine_of(sampling_label(pos, key, mask), C, F);
+            perm[lo + hist[f] + atomicAdd(&fill[f], 1u)] = pos;
+        }
+        __syncthreads();
     }
 }
 
@@ -135,21 +278,23 @@ __device__ __forceinline__ uint32_t sub_digit(uint64_t label, int b)
     return (uint32_t)((label << b) >> (64 - kSubBits));
 }
 
-// One CTA per bucket (grid-stride over buckets).  Shared memory:
-//   k1, k2: labels (2 x cap x 8 B), i1, i2: positions (2 x cap x 4 B),
-//   hist, cur: counting-pass bins.
+// One CTA per bucket (grid-stride over buckets).  Each thread keeps its
+// (up to kSortCap / kSortThreads) entries in registers; shared memory holds
+// only the counting-pass bins and the sorted copy k2 / i2, so 8 CTAs fit on
+// an SM.  A counting pass on the next kSubBits label bits leaves about 4
+// entries per bin, then each thread insertion-sorts one bin by (label,
+// position).
 __global__ void __launch_bounds__(kSortThreads)
 perm_local_sort_kernel(uint32_t nb, int b, uint2 key, uint64_t mask, const uint64_t *start,
                        uint32_t *perm, uint32_t *big_list, uint32_t *big_count)
 {
+    constexpr int kPer = kSortCap / kSortThreads;
     extern __shared__ __align__(16) uint8_t smem[];
-    uint64_t *k1 = reinterpret_cast<uint64_t *>(smem);
-    uint64_t *k2 = k1 + kSortCap;
-    uint32_t *i1 = reinterpret_cast<uint32_t *>(k2 + kSortCap);
-    uint32_t *i2 = i1 + kSortCap;
+    uint64_t *k2 = reinterpret_cast<uint64_t *>(smem);
+    uint32_t *i2 = reinterpret_cast<uint32_t *>(k2 + kSortCap);
     uint32_t *hist = i2 + kSortCap;         // kSubBins + 1
     uint32_t *cur = hist + kSubBins + 1;    // kSubBins
-    __shared__ uint64_t warp_tot[32];
+    __shared__ uint32_t warp_tot[kSortThreads / 32];
 
     for (uint32_t bk = blockIdx.x; bk < nb; bk += gridDim.x) {
         const uint64_t lo = start[bk];
@@ -164,25 +309,23 @@ perm_local_sort_kernel(uint32_t nb, int b, uint2 key, uint64_t mask, const uint6
             cur[t] = 0;
         }
         __syncthreads();
-        for (uint32_t e = threadIdx.x; e < L; e += blockDim.x) {
-            const uint32_t idx = perm[lo + e];
-            const uint64_t lab = sampling_label(idx, key, mask);
-            k1[e] = lab;
-            i1[e] = idx;
-            atomicAdd(&hist[sub_digit(lab, b)], 1u);
+        uint64_t lab[kPer];
+        uint32_t idx[kPer];
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+            const uint32_t e = threadIdx.x + q * kSortThreads;
+            if (e < L) {
+                idx[q] = perm[lo + e];
+                lab[q] = sampling_label(idx[q], key, mask);
+                atomicAdd(&hist[sub_digit(lab[q], b)], 1u);
+            }
         }
         __syncthreads();
-        // exclusive scan of the kSubBins counts, 4 per thread
+        // exclusive scan of the kSubBins (== kSortThreads) counts
         {
-            uint32_t v[4];
-            uint32_t tsum = 0;
-#pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                v[t] = hist[threadIdx.x * 4 + t];
-                tsum += v[t];
-            }
             const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-            uint32_t x = tsum;
+            const uint32_t v = hist[threadIdx.x];
+            uint32_t x = v;
 #pragma unroll
             for (int d = 1; d < 32; d <<= 1) {
                 const uint32_t o = __shfl_up_sync(0xffffffffu, x, d);
@@ -191,27 +334,25 @@ perm_local_sort_kernel(uint32_t nb, int b, uint2 key, uint64_t mask, const uint6
             if (lane == 31) warp_tot[warp] = x;
             __syncthreads();
             uint32_t wbase = 0;
-            for (int w = 0; w < warp; ++w) wbase += (uint32_t)warp_tot[w];
-            uint32_t run = wbase + x - tsum;
+            for (int w = 0; w < warp; ++w) wbase += warp_tot[w];
             __syncthreads();
-#pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                hist[threadIdx.x * 4 + t] = run;
-                run += v[t];
-            }
+            hist[threadIdx.x] = wbase + x - v;
             if (threadIdx.x == 0) hist[kSubBins] = (uint32_t)L;
         }
         __syncthreads();
-        for (uint32_t e = threadIdx.x; e < L; e += blockDim.x) {
-            const uint64_t lab = k1[e];
-            const uint32_t d = sub_digit(lab, b);
-            const uint32_t p = hist[d] + atomicAdd(&cur[d], 1u);
-            k2[p] = lab;
-            i2[p] = i1[e];
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+            const uint32_t e = threadIdx.x + q * kSortThreads;
+            if (e < L) {
+                const uint32_t d = sub_digit(lab[q], b);
+                const uint32_t p = hist[d] + atomicAdd(&cur[d], 1u);
+                k2[p] = lab[q];
+                i2[p] = idx[q];
+            }
         }
         __syncthreads();
-        for (int d = threadIdx.x; d < kSubBins; d += blockDim.x) {
-            const uint32_t a = hist[d], z = hist[d + 1];
+        {
+            const uint32_t a = hist[threadIdx.x], z = hist[threadIdx.x + 1];
             for (uint32_t x = a + 1; x < z; ++x) {
                 const uint64_t kx = k2[x];
                 const uint32_t ix = i2[x];
@@ -299,39 +440,63 @@ int build_perm(uint64_t n, uint64_t sampling_key, uint64_t mask, uint32_t *perm,
     int b = ceil_log2_u64(n) - 10;
     if (b < 0) b = 0;
     if (b > 22) b = 22;
-    const uint32_t nb = 1u << b;
+    const int C = std::min(b, kCoarseMax), F = b - C;
+    const uint32_t nb = 1u << b, ncb = 1u << C;
     const uint2 key = make_uint2((uint32_t)sampling_key, (uint32_t)(sampling_key >> 32));
-    const uint32_t nblk = (uint32_t)ceil_div(nb, kScanPerBlock);
 
-    uint32_t *cnt = nullptr, *big_list = nullptr, *big_count = nullptr;
-    uint64_t *start = nullptr, *bsum = nullptr;
+    uint32_t *ccnt = nullptr, *cfill = nullptr, *tmp = nullptr, *big_list = nullptr, *big_count = nullptr;
+    uint64_t *start = nullptr, *cstart = nullptr;
     int rc = EXTRACT_OK;
     auto fail = [&](int code) { rc = code; };
     do {
         cudaError_t e;
-        if ((e = cudaMallocAsync(&cnt, sizeof(uint32_t) * nb, st)) != cudaSuccess) { fail(cuda_error(e, "cudaMalloc(perm hist)")); break; }
+        if ((e = cudaMallocAsync(&ccnt, sizeof(uint32_t) * kCoarseBins * 2, st)) != cudaSuccess) { fail(cuda_error(e, "cudaMalloc(perm coarse)")); break; }
+        cfill = ccnt + kCoarseBins;
+        if ((e = cudaMallocAsync(&cstart, sizeof(uint64_t) * (kCoarseBins + 1), st)) != cudaSuccess) { fail(cuda_error(e, "cudaMalloc(perm cstart)")); break; }
         if ((e = cudaMallocAsync(&start, sizeof(uint64_t) * (nb + 1), st)) != cudaSuccess) { fail(cuda_error(e, "cudaMalloc(perm start)")); break; }
-        if ((e = cudaMallocAsync(&bsum, sizeof(uint64_t) * nblk, st)) != cudaSuccess) { fail(cuda_error(e, "cudaMalloc(perm bsum)")); break; }
+        if ((e = cudaMallocAsync(&tmp, sizeof(uint32_t) * n, st)) != cudaSuccess) { fail(cuda_error(e, "cudaMalloc(perm tmp)")); break; }
         if ((e = cudaMallocAsync(&big_list, sizeof(uint32_t) * nb, st)) != cudaSuccess) { fail(cuda_error(e, "cudaMalloc(perm big)")); break; }
         if ((e = cudaMallocAsync(&big_count, sizeof(uint32_t), st)) != cudaSuccess) { fail(cuda_error(e, "cudaMalloc(perm bigc)")); break; }
-        if ((e = cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * nb, st)) != cudaSuccess) { fail(cuda_error(e, "memset")); break; }
+        if ((e = cudaMemsetAsync(ccnt, 0, sizeof(uint32_t) * kCoarseBins * 2, st)) != cudaSuccess) { fail(cuda_error(e, "memset")); break; }
         if ((e = cudaMemsetAsync(big_count, 0, sizeof(uint32_t), st)) != cudaSuccess) { fail(cuda_error(e, "memset")); break; }
 
-        const uint32_t grid = (uint32_t)std::min<uint64_t>(ceil_div(n, 256), (uint64_t)num_sms * 16);
-        perm_hist_kernel<<<grid, 256, 0, st>>>(n, key, mask, b, cnt);
-        if ((e = cudaGetLastError()) != cudaSuccess) { fail(cuda_error(e, "perm_hist_kernel")); break; }
-        scan_blocks_kernel<<<nblk, 1024, 0, st>>>(cnt, nb, start, bsum);
-        scan_bsum_kernel<<<1, 1024, 0, st>>>(bsum, nblk);
-        scan_add_kernel<<<(uint32_t)ceil_div(nb, 256), 256, 0, st>>>(start, nb, bsum, n);
-        if ((e = cudaGetLastError()) != cudaSuccess) { fail(cuda_error(e, "perm scan")); break; }
-        if ((e = cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * nb, st)) != cudaSuccess) { fail(cuda_error(e, "memset")); break; }
-        perm_scatter_kernel<<<grid, 256, 0, st>>>(n, key, mask, b, start, cnt, perm);
-        if ((e = cudaGetLastError()) != cudaSuccess) { fail(cuda_error(e, "perm_scatter_kernel")); break; }
+        // 1. coarse histogram, scanned on the host (1024 values)
+        const uint32_t hgrid = (uint32_t)std::min<uint64_t>(ceil_div(n, 512), (uint64_t)num_sms * 4);
+        perm_coarse_hist_kernel<<<hgrid, 512, 0, st>>>(n, key, mask, C, ccnt);
+        if ((e = cudaGetLastError()) != cudaSuccess) { fail(cuda_error(e, "perm_coarse_hist_kernel")); break; }
+        std::vector<uint32_t> hc(ncb);
+        std::vector<uint64_t> hs(kCoarseBins + 1, n);
+        if ((e = cudaMemcpyAsync(hc.data(), ccnt, sizeof(uint32_t) * ncb, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(st)) != cudaSuccess) { fail(cuda_error(e, "perm coarse counts")); break; }
+        uint64_t run = 0;
+        for (uint32_t d = 0; d < ncb; ++d) {
+            hs[d] = run;
+            run += hc[d];
+        }
+        if (run != n) { fail(set_error(EXTRACT_EINTERNAL, "perm: coarse counts sum to %llu, not n", (unsigned long long)run)); break; }
+        if ((e = cudaMemcpyAsync(cstart, hs.data(), sizeof(uint64_t) * (kCoarseBins + 1), cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(start + nb, &n, sizeof(uint64_t), cudaMemcpyHostToDevice, st)) != cudaSuccess) {
+            fail(cuda_error(e, "perm coarse starts"));
+            break;
+        }
+        // 2. coarse scatter in tiles
+        const size_t tsmem = (size_t)kTile * (4 + 2);
+        if ((e = cudaFuncSetAttribute(perm_coarse_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)tsmem)) != cudaSuccess) { fail(cuda_error(e, "smem attr")); break; }
+        const uint32_t tgrid = (uint32_t)std::min<uint64_t>(ceil_div(n, kTile), (uint64_t)num_sms * 3);
+        perm_coarse_scatter_kernel<<<tgrid, kTileThreads, tsmem, st>>>(n, key, mask, C, cstart, cfill, tmp);
+        if ((e = cudaGetLastError()) != cudaSuccess) { fail(cuda_error(e, "perm_coarse_scatter_kernel")); break; }
+        // 3. fine pass, one CTA per coarse bin
+        perm_fine_kernel<<<ncb, kFineThreads, sizeof(uint32_t) * 2 * (1u << F), st>>>(key, mask, C, F, cstart, tmp,
+                                                                                      start, perm);
+        if ((e = cudaGetLastError()) != cudaSuccess) { fail(cuda_error(e, "perm_fine_kernel")); break; }
+        cudaFreeAsync(tmp, st);
+        tmp = nullptr;
 
-        const size_t smem = (size_t)kSortCap * (8 + 8 + 4 + 4) + (size_t)(2 * kSubBins + 1) * 4;
+        const size_t smem = (size_t)kSortCap * (8 + 4) + (size_t)(2 * kSubBins + 1) * 4;
         if ((e = cudaFuncSetAttribute(perm_local_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem)) != cudaSuccess) { fail(cuda_error(e, "smem attr")); break; }
-        const uint32_t sgrid = std::min<uint32_t>(nb, (uint32_t)num_sms * 8);
+        const uint32_t sgrid = std::min<uint32_t>(nb, (uint32_t)num_sms * 16);
         perm_local_sort_kernel<<<sgrid, kSortThreads, smem, st>>>(nb, b, key, mask, start, perm,
                                                                   big_list, big_count);
         if ((e = cudaGetLastError()) != cudaSuccess) { fail(cuda_error(e, "perm_local_sort_kernel")); break; }
@@ -377,9 +542,10 @@ int build_perm(uint64_t n, uint64_t sampling_key, uint64_t mask, uint32_t *perm,
     } while (0);
     // stream-ordered frees: no device-wide synchronisation, so an order can
     // be built while other streams keep hashing
-    if (cnt) cudaFreeAsync(cnt, st);
+    if (ccnt) cudaFreeAsync(ccnt, st);
+    if (cstart) cudaFreeAsync(cstart, st);
+    if (tmp) cudaFreeAsync(tmp, st);
     if (start) cudaFreeAsync(start, st);
-    if (bsum) cudaFreeAsync(bsum, st);
     if (big_list) cudaFreeAsync(big_list, st);
     if (big_count) cudaFreeAsync(big_count, st);
     cudaError_t fe = cudaStreamSynchronize(st);
