@@ -67,6 +67,7 @@ struct extract_ctx {
     cudaStream_t aux = nullptr;                       // gather stream of the overlapped NTT run
     cudaEvent_t ev_fork = nullptr, ev_group = nullptr;
     NttSecondLane lane2;                              // second lane of the NTT hash (own stream, buffer)
+    GatherWindows gw;                                 // window-major order for inputs far above L2
 };
 
 namespace {
@@ -89,6 +90,7 @@ void free_ctx(extract_ctx *h)
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
     if (h->ev_group) cudaEventDestroy(h->ev_group);
     if (h->aux) cudaStreamDestroy(h->aux);
+    gather_windows_free(&h->gw);
     cudaFree(h->lane2.work);
     if (h->lane2.ev_fork) cudaEventDestroy(h->lane2.ev_fork);
     if (h->lane2.ev_join) cudaEventDestroy(h->lane2.ev_join);
@@ -233,6 +235,8 @@ int extract_create(extract_ctx **out, uint64_t n, uint32_t m, uint32_t s, uint32
         if ((e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) != cudaSuccess) { free_ctx(h); return cuda_error(e, "stream"); }
         int rc = iid ? build_iid_order(n, sampling_key, mask, m, s, h->perm, &h->sizes, st, h->num_sms)
                      : build_perm(n, sampling_key, mask, h->perm, st, h->num_sms);
+        if (rc == EXTRACT_OK && !iid && gather_windows_wanted(n))
+            rc = gather_windows_build(h->perm, m, s, h->w_pad, n, &h->gw, st, h->num_sms);
         cudaStreamDestroy(st);
         if (rc != EXTRACT_OK) { free_ctx(h); return rc; }
     }
@@ -245,6 +249,7 @@ int extract_gather(extract_ctx *h, void *stream, const uint32_t *in_bits_dev)
 {
     if (int rc = check_ctx(h)) return rc;
     if (!in_bits_dev) return set_error(EXTRACT_EINVAL, "in_bits_dev is null");
+    if (h->gw.pos) return gather_windows_run(h->gw, in_bits_dev, h->w_pad, h->arev, (cudaStream_t)stream, h->num_sms);
     return launch_gather(in_bits_dev, h->perm, h->m, h->s, h->w_pad, h->arev, (cudaStream_t)stream,
                          h->num_sms, 0, h->iid, h->n);
 }
@@ -264,12 +269,11 @@ int extract_run(extract_ctx *h, void *stream, const uint32_t *in_bits_dev, uint3
 {
     if (int rc = check_ctx(h)) return rc;
     if (!out_bits_dev) return set_error(EXTRACT_EINVAL, "out_bits_dev is null");
-    // NTT method: inputs up to two gather windows gather the whole block
-    // first (the windowed gather is fastest in one piece: 2^30-bit block
-    // 25.4 ms/step against 26.7 overlapped); larger inputs, whose gather
-    // waits on DRAM, gather each launch group on a second stream while the
-    // previous group transforms (2^32-bit block 123.5 ms against 132.3).
-    if (h->ntt && !gather_prefers_whole_block(h->n)) {
+    // NTT method: the whole block is gathered first (2^30-bit block 25.4
+    // ms/step against 26.7 overlapped), except for large inputs without the
+    // window-major order (the i.i.d. law), whose gather waits on DRAM and is
+    // overlapped group by group with the transforms.
+    if (h->ntt && !h->gw.pos && !gather_prefers_whole_block(h->n)) {
         if (!in_bits_dev) return set_error(EXTRACT_EINVAL, "in_bits_dev is null");
         return ntt_run_overlapped(h->ntt, in_bits_dev, h->perm, h->arev, h->w_pad, h->m, h->s, h->k, out_bits_dev,
                                   (cudaStream_t)stream, h->aux, h->ev_fork, h->ev_group, h->num_sms, h->iid, h->n);

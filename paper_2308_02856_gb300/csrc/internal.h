@@ -45,6 +45,25 @@ int launch_gather(const uint32_t *in, const uint32_t *perm, uint32_t m, uint32_t
 // (at most two windows); larger inputs are better overlapped with hashing.
 bool gather_prefers_whole_block(uint64_t input_bits);
 
+// Gather for inputs of more than two 64 MiB windows (gather_windows.cu): the
+// order entries of every 1024-bit group of stored sub-block words re-laid by
+// input window, so a run takes one pass per window with all random reads in
+// L2.  Same words as launch_gather.
+struct GatherWindows {
+    uint32_t *pos = nullptr;   // groups x 1024 positions, window-major per group
+    uint16_t *slot = nullptr;  // their slots in the group (32 t + lane)
+    uint16_t *off = nullptr;   // groups x (R + 1) window starts
+    uint32_t R = 0;            // windows
+    uint64_t groups = 0;       // m * w_pad / 32
+};
+bool gather_windows_wanted(uint64_t input_bits);
+// Builds the re-laid order from the sorted order perm (on st, asynchronous).
+int gather_windows_build(const uint32_t *perm, uint32_t m, uint32_t s, uint32_t w_pad, uint64_t input_bits,
+                         GatherWindows *gw, cudaStream_t st, int num_sms);
+int gather_windows_run(const GatherWindows &gw, const uint32_t *in, uint32_t w_pad, uint32_t *arev, cudaStream_t st,
+                       int num_sms);
+void gather_windows_free(GatherWindows *gw);
+
 // ---- steps 2-3: the Toeplitz product and concatenation ------------------
 struct HashPlan {
     int variant = 7;      // tile variant (see hash_tile.cuh)

@@ -4,7 +4,8 @@
   and checks that the GPU order increases strictly in (label, position)
   order with every entry < n, which makes it a bijection and the unique
   stable argsort.
-* The hash is checked on sampled outputs: the oracle selects sub-blocks by
+* The gather is checked on whole sub-blocks (every bit, as stored for the
+  hash) and the hash on sampled outputs: the oracle selects sub-blocks by
   rank from its own labels and computes sampled rows one bit at a time.
 """
 import numpy as np
@@ -35,6 +36,7 @@ def _full_size_case(n, m, s, k, p, rows_per_block, blocks):
         d_in = torch.from_numpy(in_w.view(np.int32)).cuda()
         out = ex.run(d_in)
         got = oracle.bits_of(out.cpu().numpy().view(np.uint32), m * k)
+        stored = {j: oracle.bits_of(ex.read_subblock(j), s)[::-1] for j in blocks}  # stored reversed
         del d_in, out
         perm = ex.read_perm()
     keys = oracle.sampling_keys(n, 2)
@@ -44,6 +46,7 @@ def _full_size_case(n, m, s, k, p, rows_per_block, blocks):
     for j in blocks:
         pos = oracle.perm_range(keys, j * s, s)
         A = oracle.subblock(in_w, pos)
+        assert np.array_equal(stored[j], A), "gathered sub-block %d" % j
         rows = np.unique(np.concatenate([np.arange(16), np.arange(k - 16, k),
                                          rng.choice(k, rows_per_block, replace=False)]))
         want = np.array([oracle.toeplitz_bit(seed, s, A, int(i)) for i in rows], dtype=np.uint8)
