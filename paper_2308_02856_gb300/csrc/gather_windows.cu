@@ -28,6 +28,7 @@ namespace {
 constexpr int kWindowLog2 = 29;
 constexpr uint32_t kGroupSlots = 1024;
 constexpr int kPassWarps = 8;
+constexpr int kUnroll = 4;  // rounds of 32 entries in flight per warp
 
 // One warp per group: its 1024 slots' windows, counts, then the stable
 // placement of the entries (slot order inside each window).
@@ -98,13 +99,21 @@ gw_pass_kernel(const uint32_t *__restrict__ in, const uint32_t *__restrict__ pos
         __syncwarp();
         const uint32_t a = off[g * (R + 1) + r], b = off[g * (R + 1) + r + 1];
         const uint64_t ebase = g * kGroupSlots;
-        for (uint32_t e0 = a; e0 < b; e0 += 32) {
-            const uint32_t e = e0 + lane;
-            if (e < b) {
-                const uint32_t q = __ldcs(pos + ebase + e);
-                const uint32_t u = __ldcs(slot + ebase + e);
-                if ((__ldg(in + (q >> 5)) >> (q & 31u)) & 1u) atomicOr(&words[w][u >> 5], 1u << (u & 31u));
+        // kUnroll rounds of 32 entries at a time: all their loads are issued
+        // before the first bit is used
+        for (uint32_t e0 = a; e0 < b; e0 += 32 * kUnroll) {
+            uint32_t q[kUnroll], u[kUnroll], v[kUnroll];
+#pragma unroll
+            for (int k = 0; k < kUnroll; ++k) {
+                const uint32_t e = e0 + 32u * k + lane;
+                q[k] = e < b ? __ldcs(pos + ebase + e) : 0u;
+                u[k] = e < b ? __ldcs(slot + ebase + e) : 0u;
             }
+#pragma unroll
+            for (int k = 0; k < kUnroll; ++k) v[k] = e0 + 32u * k + lane < b ? __ldg(in + (q[k] >> 5)) : 0u;
+#pragma unroll
+            for (int k = 0; k < kUnroll; ++k)
+                if ((v[k] >> (q[k] & 31u)) & 1u) atomicOr(&words[w][u[k] >> 5], 1u << (u[k] & 31u));
         }
         __syncwarp();
         __stcs(dst + lane, words[w][lane]);
