@@ -89,8 +89,9 @@ extern "C" {
    (extract_block_limit computes it from Eq. 7): the Toeplitz matrix is
    k x s and the seed s + k - 1 bits as usual.  Every position is hashed
    (m*s >= n is not required).  extract_create fails with EXTRACT_EABORT
-   when some |S_j| > s.  Needs n < 2^32 and m <= 2^16; not combinable with
-   EXTRACT_IDENTITY_PERM; not accepted by the batch and server forms. */
+   when some |S_j| > s (a batch fails to create, naming the job; a served
+   job fails and extract_server_wait returns EXTRACT_EABORT).  Needs
+   n < 2^32 and m <= 2^16; not combinable with EXTRACT_IDENTITY_PERM. */
 #define EXTRACT_SAMPLING_IID      0x10u
 
 typedef struct extract_ctx extract_ctx;

@@ -66,7 +66,8 @@ batch_gather_kernel(const BatchJobDev *__restrict__ jobs, uint32_t njobs, uint64
         const uint64_t local = g - J.groups_before;
         const uint32_t gpr = J.w_pad >> 5;
         const uint32_t j = (uint32_t)(local / gpr), w0 = (uint32_t)(local % gpr) * 32u;
-        if (J.perm) gather_group<false>(J.in, J.perm, J.s, J.w_pad, j, w0, lane, J.arev);
+        if (J.perm && J.padded) gather_group<false, true>(J.in, J.perm, J.s, J.w_pad, j, w0, lane, J.arev);
+        else if (J.perm) gather_group<false>(J.in, J.perm, J.s, J.w_pad, j, w0, lane, J.arev);
         else gather_group<true>(J.in, J.perm, J.s, J.w_pad, j, w0, lane, J.arev);
     }
 }
@@ -315,14 +316,17 @@ int extract_batch_create(extract_batch **out, const extract_job_desc *jobs, uint
     if (!jobs || njobs == 0) return set_error(EXTRACT_EINVAL, "empty job list");
     if (flags & ~(EXTRACT_BATCH_NO_GRAPH | EXTRACT_BATCH_NO_TUNE | EXTRACT_BATCH_DIRECT_ONLY))
         return set_error(EXTRACT_EINVAL, "unknown batch flags 0x%x", flags);
-    const uint32_t known = EXTRACT_SEED_PER_SUBBLOCK | EXTRACT_IDENTITY_PERM | (0x3fu << 8);
+    const uint32_t known = EXTRACT_SEED_PER_SUBBLOCK | EXTRACT_IDENTITY_PERM | EXTRACT_SAMPLING_IID | (0x3fu << 8);
     for (uint32_t i = 0; i < njobs; ++i) {
         const extract_job_desc &d = jobs[i];
         if (!d.seed_bits_host) return set_error(EXTRACT_EINVAL, "job %u: null seed", i);
         if (d.flags & ~known) return set_error(EXTRACT_EINVAL, "job %u: unknown flags 0x%x", i, d.flags);
-        if (d.m < 1 || d.s < 1 || d.k < 1 || d.k > d.s || d.n > (1ull << 32) || (uint64_t)d.m * d.s > d.n)
+        const bool iid = (d.flags & EXTRACT_SAMPLING_IID) != 0;
+        if (d.m < 1 || d.s < 1 || d.k < 1 || d.k > d.s || d.n > (1ull << 32) || (!iid && (uint64_t)d.m * d.s > d.n))
             return set_error(EXTRACT_EINVAL, "job %u: bad shape n=%llu m=%u s=%u k=%u", i,
                              (unsigned long long)d.n, d.m, d.s, d.k);
+        if (iid && ((d.flags & EXTRACT_IDENTITY_PERM) || d.n >= (1ull << 32) || d.m > (1u << 16)))
+            return set_error(EXTRACT_EINVAL, "job %u: the i.i.d. law needs n < 2^32, m <= 2^16, no identity order", i);
     }
     extract_batch *b = new (std::nothrow) extract_batch();
     if (!b) return set_error(EXTRACT_ENOMEM, "host allocation failed");
@@ -445,10 +449,24 @@ int extract_batch_create(extract_batch **out, const extract_job_desc *jobs, uint
             if ((e = cudaMemcpy(J.seed, host.data(), host.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess) { rc = cuda_error(e, "seed copy"); break; }
             if ((e = cudaMalloc(&J.arev, (size_t)d.m * J.w_pad * 4)) != cudaSuccess) { rc = cuda_error(e, "cudaMalloc(sub-blocks)"); break; }
             if (!(d.flags & EXTRACT_IDENTITY_PERM)) {
-                if ((e = cudaMalloc(&J.perm, (size_t)d.n * 4)) != cudaSuccess) { rc = cuda_error(e, "cudaMalloc(order)"); break; }
+                const bool iid = (d.flags & EXTRACT_SAMPLING_IID) != 0;
+                const uint64_t len = iid ? (uint64_t)d.m * d.s : d.n;
+                if ((e = cudaMalloc(&J.perm, (size_t)std::max<uint64_t>(len, 1) * 4)) != cudaSuccess) { rc = cuda_error(e, "cudaMalloc(order)"); break; }
                 const uint32_t kb = (d.flags >> 8) & 0x3fu;
                 const uint64_t mask = kb ? ~((1ull << (64u - kb)) - 1ull) : ~0ull;
-                if ((rc = build_perm(d.n, d.sampling_key, mask, J.perm, st, b->num_sms)) != EXTRACT_OK) break;
+                if (iid) {
+                    std::vector<uint64_t> sizes;
+                    if ((rc = build_iid_order(d.n, d.sampling_key, mask, d.m, d.s, J.perm, &sizes, st, b->num_sms)) !=
+                        EXTRACT_OK) {
+                        if (rc == EXTRACT_EABORT) {
+                            const std::string why = extract_last_error();
+                            rc = set_error(EXTRACT_EABORT, "job %u: %s", i, why.c_str());
+                        }
+                        break;
+                    }
+                } else if ((rc = build_perm(d.n, d.sampling_key, mask, J.perm, st, b->num_sms)) != EXTRACT_OK) {
+                    break;
+                }
             }
             if (J.table_index == -2) {
                 if ((rc = ntt_create(&J.ntt, d.m, d.s, d.k, J.seed, st, b->lanes[J.lane].work)) != EXTRACT_OK) break;
@@ -459,6 +477,7 @@ int extract_batch_create(extract_batch **out, const extract_job_desc *jobs, uint
             T.groups_before = groups; T.outw_before = outw;
             T.seed_stride = J.nseeds > 1 ? J.seed_stride : 0u;
             T.m = d.m; T.s = d.s; T.k = d.k; T.w_pad = J.w_pad;
+            T.padded = (d.flags & EXTRACT_SAMPLING_IID) ? 1u : 0u;
             groups += (uint64_t)d.m * (J.w_pad / 32);
             outw += ceil_div((uint64_t)d.m * d.k, 32);
         }
@@ -528,7 +547,8 @@ int extract_batch_run(extract_batch *b, void *stream, const uint32_t *const *in_
         for (uint32_t i : b->ntt_order) {
             const BatchJobHost &J = b->jobs[i];
             const NttLane &L = b->lanes[J.lane];
-            if (int rc = launch_gather(in_bits_dev[i], J.perm, J.m, J.s, J.w_pad, J.arev, L.st, b->num_sms, 0, false, J.n))
+            if (int rc = launch_gather(in_bits_dev[i], J.perm, J.m, J.s, J.w_pad, J.arev, L.st, b->num_sms, 0,
+                                       (J.flags & EXTRACT_SAMPLING_IID) != 0, J.n))
                 return rc;
             if (int rc = ntt_hash(J.ntt, J.arev, J.w_pad, J.m, J.s, J.k, out_bits_dev[i], L.st, L.work)) return rc;
         }
@@ -560,7 +580,8 @@ int extract_batch_run_sequential(extract_batch *b, void *stream, const uint32_t 
     for (size_t i = 0; i < b->jobs.size(); ++i) {
         const BatchJobHost &J = b->jobs[i];
         if (!in_bits_dev[i] || !out_bits_dev[i]) return set_error(EXTRACT_EINVAL, "job %zu: null buffer", i);
-        if (int rc = launch_gather(in_bits_dev[i], J.perm, J.m, J.s, J.w_pad, J.arev, st, b->num_sms, 0, false, J.n))
+        if (int rc = launch_gather(in_bits_dev[i], J.perm, J.m, J.s, J.w_pad, J.arev, st, b->num_sms, 0,
+                                   (J.flags & EXTRACT_SAMPLING_IID) != 0, J.n))
             return rc;
         if (J.ntt) {
             if (int rc = ntt_hash(J.ntt, J.arev, J.w_pad, J.m, J.s, J.k, out_bits_dev[i], st)) return rc;

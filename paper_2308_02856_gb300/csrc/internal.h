@@ -111,6 +111,7 @@ struct BatchJobDev {
     uint64_t outw_before;    // prefix of output words
     uint32_t seed_stride;    // 0: one shared seed
     uint32_t m, s, k, w_pad;
+    uint32_t padded;         // 1: the i.i.d. law's padded order (kNoPos reads as 0)
 };
 
 // One CTA work item: rows [r0, r0 + rows(variant)) x sub-blocks

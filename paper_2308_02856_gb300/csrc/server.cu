@@ -103,6 +103,14 @@ void realign_seed(const uint32_t *src, uint64_t src_words, uint64_t off, uint64_
     if (len % 32 && nw - 1 < dst_words) dst[nw - 1] &= (1u << (len % 32)) - 1u;
 }
 
+// entries of a job's order: n (sorted order), m s (the i.i.d. law's padded
+// order) or none (identity)
+uint64_t order_entries(uint64_t n, uint32_t m, uint32_t s, uint32_t flags)
+{
+    if (flags & EXTRACT_IDENTITY_PERM) return 0;
+    return (flags & EXTRACT_SAMPLING_IID) ? (uint64_t)m * s : n;
+}
+
 double percentile(std::vector<double> v, double q)
 {
     if (v.empty()) return 0.0;
@@ -156,13 +164,19 @@ int setup_job(extract_server *S, SJob &J)
     EX_CUDA(cudaMallocAsync(&J.seed, J.seed_host.size() * 4, st));
     EX_CUDA(cudaMemcpyAsync(J.seed, J.seed_host.data(), J.seed_host.size() * 4, cudaMemcpyHostToDevice, st));
     EX_CUDA(cudaMallocAsync(&J.arev, (size_t)J.m * J.w_pad * 4, st));
+    const bool iid = (J.flags & EXTRACT_SAMPLING_IID) != 0;
     if (!(J.flags & EXTRACT_IDENTITY_PERM)) {
-        EX_CUDA(cudaMallocAsync(&J.perm, (size_t)J.n * 4, st));
+        EX_CUDA(cudaMallocAsync(&J.perm, (size_t)order_entries(J.n, J.m, J.s, J.flags) * 4, st));
         const uint32_t kb = (J.flags >> 8) & 0x3fu;
         const uint64_t mask = kb ? ~((1ull << (64u - kb)) - 1ull) : ~0ull;
-        if (int rc = build_perm(J.n, J.key, mask, J.perm, st, S->sms)) return rc;
+        if (iid) {
+            std::vector<uint64_t> sizes;  // EXTRACT_EABORT fails the job
+            if (int rc = build_iid_order(J.n, J.key, mask, J.m, J.s, J.perm, &sizes, st, S->sms)) return rc;
+        } else if (int rc = build_perm(J.n, J.key, mask, J.perm, st, S->sms)) {
+            return rc;
+        }
     }
-    if (int rc = launch_gather(J.in, J.perm, J.m, J.s, J.w_pad, J.arev, st, S->sms, 0, false, J.n)) return rc;
+    if (int rc = launch_gather(J.in, J.perm, J.m, J.s, J.w_pad, J.arev, st, S->sms, 0, iid, J.n)) return rc;
     EX_CUDA(cudaMemsetAsync(J.out, 0, ceil_div((uint64_t)J.m * J.k, 32) * 4, st));
     if (J.use_ntt)  // tables and the seed spectrum (synchronous on the setup stream)
         if (int rc = ntt_create(&J.ntt, J.m, J.s, J.k, J.seed, st, S->lanes[0].work)) return rc;
@@ -258,7 +272,7 @@ bool schedule_step(extract_server *S)
             const cudaError_t e = cudaEventQuery(j->setup_ev);
             if (e == cudaSuccess) {
                 // the order was freed after the gather: return its share of the budget
-                const uint64_t order_b = (j->flags & EXTRACT_IDENTITY_PERM) ? 0 : j->n * 4;
+                const uint64_t order_b = order_entries(j->n, j->m, j->s, j->flags) * 4;
                 S->in_use -= order_b;
                 j->bytes -= order_b;
                 j->state = kReady;
@@ -470,10 +484,13 @@ int extract_server_submit(extract_server *S, const extract_job_desc *d, const ui
 {
     if (!S || !d || !ticket) return set_error(EXTRACT_EINVAL, "null argument");
     if (!in_bits_dev || !out_bits_dev || !d->seed_bits_host) return set_error(EXTRACT_EINVAL, "null buffer");
-    const uint32_t known = EXTRACT_SEED_PER_SUBBLOCK | EXTRACT_IDENTITY_PERM | (0x3fu << 8);
+    const uint32_t known = EXTRACT_SEED_PER_SUBBLOCK | EXTRACT_IDENTITY_PERM | EXTRACT_SAMPLING_IID | (0x3fu << 8);
     if (d->flags & ~known) return set_error(EXTRACT_EINVAL, "unknown flags 0x%x", d->flags);
-    if (d->m < 1 || d->s < 1 || d->k < 1 || d->k > d->s || d->n > (1ull << 32) || (uint64_t)d->m * d->s > d->n)
+    const bool iid = (d->flags & EXTRACT_SAMPLING_IID) != 0;
+    if (d->m < 1 || d->s < 1 || d->k < 1 || d->k > d->s || d->n > (1ull << 32) || (!iid && (uint64_t)d->m * d->s > d->n))
         return set_error(EXTRACT_EINVAL, "bad shape n=%llu m=%u s=%u k=%u", (unsigned long long)d->n, d->m, d->s, d->k);
+    if (iid && ((d->flags & EXTRACT_IDENTITY_PERM) || d->n >= (1ull << 32) || d->m > (1u << 16)))
+        return set_error(EXTRACT_EINVAL, "the i.i.d. law needs n < 2^32, m <= 2^16 and no identity order");
     JobPtr j = std::make_shared<SJob>();
     j->n = d->n; j->m = d->m; j->s = d->s; j->k = d->k; j->flags = d->flags; j->key = d->sampling_key;
     j->in = in_bits_dev;
@@ -506,7 +523,7 @@ int extract_server_submit(extract_server *S, const extract_job_desc *d, const ui
         realign_seed(d->seed_bits_host, src_words, (uint64_t)q * L, L, j->seed_host.data() + (size_t)q * j->stride,
                      j->stride);
     // budget charge: order (freed early, still charged) + sub-blocks + seed + the job's input and output
-    const uint64_t order_b = (d->flags & EXTRACT_IDENTITY_PERM) ? 0 : d->n * 4;
+    const uint64_t order_b = order_entries(d->n, d->m, d->s, d->flags) * 4;
     j->bytes = order_b + (uint64_t)d->m * j->w_pad * 4 + (uint64_t)j->seed_host.size() * 4 + ceil_div(d->n, 32) * 4 +
                ceil_div((uint64_t)d->m * d->k, 32) * 4 + (j->use_ntt ? ntt_plan_bytes(d->s, d->k) : 0);
     // tiles: every (row tile, sub-block tile, word range), each about tile_cap of one SM

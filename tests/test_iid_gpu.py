@@ -96,10 +96,89 @@ def test_rejections():
         with pytest.raises(X.ExtractError) as e:
             X.extract_create(n, m, s, k, seed, 1, fl | X.EXTRACT_SAMPLING_IID)
         assert e.value.code == X.EXTRACT_EINVAL
-    job = {"n": 4096, "m": 2, "s": 2100, "k": 8, "key": 1, "flags": X.EXTRACT_SAMPLING_IID,
-           "seed": synth.uniform_bits(2107, 1)}
-    with pytest.raises(X.ExtractError):
+    job = {"n": 4096, "m": 2, "s": 2100, "k": 8, "key": 1,
+           "flags": X.EXTRACT_SAMPLING_IID | X.EXTRACT_IDENTITY_PERM, "seed": synth.uniform_bits(2107, 1)}
+    with pytest.raises(X.ExtractError) as e:
         X.Batch([job])
+    assert e.value.code == X.EXTRACT_EINVAL
+
+
+def _iid_jobs():
+    """i.i.d.-law jobs (both methods) mixed with sorted-order jobs."""
+    jobs = []
+    for i, (n, m, k, slack, fl) in enumerate([
+            (100_000, 7, 3000, 3, X.EXTRACT_SAMPLING_IID),
+            (1 << 18, 8, 1 << 13, 40, X.EXTRACT_SAMPLING_IID),
+            (50_000, 5, 777, 0, X.EXTRACT_SAMPLING_IID | X.EXTRACT_SEED_PER_SUBBLOCK),
+            (1 << 16, 4, 1 << 12, 0, 0),
+            (70_000, 20_000, 2, 1, X.EXTRACT_SAMPLING_IID),
+            (1 << 20, 2, 1 << 18, 100, X.EXTRACT_SAMPLING_IID)]):
+        key = 40 + i
+        if fl & X.EXTRACT_SAMPLING_IID:
+            s = _largest(n, m, key) + slack
+        else:
+            s = n // m
+        L = (s + k - 1) * (m if fl & X.EXTRACT_SEED_PER_SUBBLOCK else 1)
+        jobs.append({"n": n, "m": m, "s": s, "k": k, "key": key, "flags": fl,
+                     "seed": synth.uniform_bits(L, 50 + i), "in": synth.bernoulli_bits(n, 0.6, 60 + i)})
+    return jobs
+
+
+def _out(j, fill=-1):
+    return torch.full(((j["m"] * j["k"] + 31) // 32,), fill, dtype=torch.int32, device="cuda")
+
+
+def test_batch_with_iid_jobs_matches_single_contexts_and_the_oracle():
+    jobs = _iid_jobs()
+    d_in = [_dev(j["in"]) for j in jobs]
+    with X.Batch(jobs) as b:
+        outs = [_out(j) for j in jobs]
+        b.run(d_in, outs)
+        seq = [_out(j, 7) for j in jobs]
+        b.run_sequential(d_in, seq)
+        torch.cuda.synchronize()
+    for i, (j, d) in enumerate(zip(jobs, d_in)):
+        with X.Extractor(j["n"], j["m"], j["s"], j["k"], j["seed"], j["key"], j["flags"]) as ex:
+            want = _host(ex.run(d))
+        assert np.array_equal(_host(outs[i]), want), "job %d" % i
+        assert np.array_equal(_host(seq[i]), want), "sequential job %d" % i
+    for i in (0, 2, 4):
+        j = jobs[i]
+        fl = oracle.SAMPLING_IID | (oracle.SEED_PER_SUBBLOCK if j["flags"] & X.EXTRACT_SEED_PER_SUBBLOCK else 0)
+        want = oracle.extract(j["n"], j["m"], j["s"], j["k"], j["in"], j["seed"], j["key"], fl)
+        assert np.array_equal(_host(outs[i]), want), "job %d vs oracle" % i
+
+
+def test_batch_aborts_naming_the_job():
+    jobs = _iid_jobs()[:2]
+    jobs[1] = dict(jobs[1])
+    jobs[1]["s"] -= 41  # one below its largest sub-block
+    jobs[1]["seed"] = synth.uniform_bits(jobs[1]["s"] + jobs[1]["k"] - 1, 5)
+    with pytest.raises(X.ExtractError) as e:
+        X.Batch(jobs)
+    assert e.value.code == X.EXTRACT_EABORT and "job 1" in str(e.value)
+
+
+def test_server_serves_iid_jobs_and_fails_an_aborting_one():
+    jobs = _iid_jobs()
+    bad = dict(jobs[0])
+    bad["s"] = _largest(bad["n"], bad["m"], bad["key"]) - 1
+    bad["seed"] = synth.uniform_bits(bad["s"] + bad["k"] - 1, 9)
+    d_in = [_dev(j["in"]) for j in jobs]
+    outs = [_out(j) for j in jobs]
+    with X.Server(8 << 30, max_slots=8, wave_us=500) as srv:
+        tickets = [srv.submit(j, d, o) for j, d, o in zip(jobs, d_in, outs)]
+        bt = srv.submit(bad, _dev(bad["in"]), _out(bad))
+        for t in tickets:
+            srv.wait(t)
+        with pytest.raises(X.ExtractError) as e:
+            srv.wait(bt)
+        assert e.value.code == X.EXTRACT_EABORT
+        st = srv.stats()
+        assert st["completed"] == len(jobs) and st["failed"] == 1
+    for i, (j, d) in enumerate(zip(jobs, d_in)):
+        with X.Extractor(j["n"], j["m"], j["s"], j["k"], j["seed"], j["key"], j["flags"]) as ex:
+            assert np.array_equal(_host(outs[i]), _host(ex.run(d))), "job %d" % i
 
 
 def test_qrng_shaped_block_with_the_eq7_limit():
