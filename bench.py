@@ -70,6 +70,9 @@ def parse_args():
                     help="block: one large block (default); batch: 256 uneven blocks in one persistent "
                          "launch vs one launch per block; serve: Poisson job arrivals under an HBM budget")
     ap.add_argument("--jobs", type=int, default=0, help="jobs per serving trace (default 120)")
+    ap.add_argument("--seeds", choices=["shared", "per-subblock"], default="shared",
+                    help="block mode: one Toeplitz seed for all sub-blocks (default), or an independent seed per "
+                         "sub-block (the paper's f_RE,j)")
     ap.add_argument("--sampling", choices=["sorted", "iid"], default="sorted",
                     help="block mode: sorted order cut into equal sub-blocks (default), or the paper's i.i.d. "
                          "labels with sub-blocks padded to Eq. 7's block size limit")
@@ -157,14 +160,14 @@ class OracleSample:
     assembly plus ni output rows of each, on nj host threads; scaled to the
     whole block by the share of Toeplitz rows it computed."""
 
-    def __init__(self, n, m, s, k, in_w, seed_w, target_s, iid=False):
+    def __init__(self, n, m, s, k, in_w, seed_w, target_s, iid=False, per_sub=False):
         import oracle
         self.oracle = oracle
         self.n, self.m, self.s, self.k = n, m, s, k
         self.in_w, self.seed_w = in_w, seed_w
         self.cores = os.cpu_count() or 1
         self.nj = min(self.cores, m)
-        self.flags = oracle.SAMPLING_IID if iid else 0
+        self.flags = (oracle.SAMPLING_IID if iid else 0) | (oracle.SEED_PER_SUBBLOCK if per_sub else 0)
         keys = oracle.sampling_keys(n, SAMPLING_KEY)
         if iid:  # the oracle's i.i.d. order (padded sub-blocks of s slots)
             _, order, _ = oracle.iid_order(keys, m, s)
@@ -258,10 +261,10 @@ def ntt_roofline(n, m, s, k, hash_ms, plan, sms=152, workload=None):
             "note": "does %.0fx less work than the direct m*k*s product" % ((m * k * s / 32.0) / bfly)}
 
 
-def make_inputs(n, m, s, k, p):
+def make_inputs(n, m, s, k, p, nseeds=1):
     from paper_2308_02856_gb300 import synth
     in_w = synth.bernoulli_bits(n, p, IN_SEED)
-    seed_w = synth.uniform_bits(s + k - 1, TOEPLITZ_SEED)
+    seed_w = synth.uniform_bits((s + k - 1) * nseeds, TOEPLITZ_SEED)
     return in_w, seed_w
 
 
@@ -322,13 +325,16 @@ def run_ours(args):
 
     X.load()  # fails loudly when the CUDA library is missing
     iid = args.sampling == "iid"
+    per_sub = args.seeds == "per-subblock"
     if iid:  # the paper's law: s becomes Eq. 7's block size limit
         s = X.extract_block_limit(n, m, IID_EPS, 1.0 / m)
-    in_w, seed_w = make_inputs(n, m, s, k, p)
+    in_w, seed_w = make_inputs(n, m, s, k, p, m if per_sub else 1)
 
     method_flags = {"auto": 0, "direct": X.EXTRACT_METHOD_DIRECT, "ntt": X.EXTRACT_METHOD_NTT}[args.method]
     if iid:
         method_flags |= X.EXTRACT_SAMPLING_IID
+    if per_sub:
+        method_flags |= X.EXTRACT_SEED_PER_SUBBLOCK
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     ex = X.Extractor(n, m, s, k, seed_w, SAMPLING_KEY, method_flags)
@@ -419,7 +425,7 @@ def run_ours(args):
         roofline = ntt_roofline(n, m, s, k, hash_ms, plan, sms, None if iid else args.workload)
         # the direct kernel on the same block, for the record (2 timed steps)
         exd = X.Extractor(n, m, s, k, seed_w, SAMPLING_KEY,
-                          X.EXTRACT_METHOD_DIRECT | (X.EXTRACT_SAMPLING_IID if iid else 0))
+                          X.EXTRACT_METHOD_DIRECT | (method_flags & (X.EXTRACT_SAMPLING_IID | X.EXTRACT_SEED_PER_SUBBLOCK)))
         exd.gather(d_in, stream=stream)
         exd.hash(d_out, stream=stream)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -438,7 +444,7 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
-            smp = OracleSample(n, m, s, k, in_w, seed_w, args.cpu_seconds, iid=iid)
+            smp = OracleSample(n, m, s, k, in_w, seed_w, args.cpu_seconds, iid=iid, per_sub=per_sub)
             cpu = smp.measure()
             cpu.pop("seconds", None)
         except Exception as e:  # the baseline is context; report why it is missing
@@ -450,7 +456,9 @@ def run_ours(args):
             "metric": "extracted input Gbit/s", "value": value, "unit": "Gbit/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32 (GF(2) bits)", "data": "synthetic",
-            "config": {"workload": args.workload + ("_iid" if iid else ""), "n": n, "m": m, "s": s, "k": k,
+            "config": {"workload": args.workload + ("_iid" if iid else "") + ("_seed_per_subblock" if per_sub else ""),
+                       "n": n, "m": m, "s": s, "k": k,
+                       "toeplitz_seeds": "one per sub-block" if per_sub else "shared",
                        "bernoulli_p": p,
                        "sampling": ("i.i.d. labels V_i in [0, m), sub-blocks padded to Eq. 7's limit s "
                                     "(eps %g, p_sift 1/m)" % IID_EPS) if iid else "stable argsort, equal sub-blocks",

@@ -69,9 +69,11 @@ extern "C" {
    forces the number-theoretic-transform middle product modulo the prime
    7*2^26+1.  It splits each sub-block into P = 2^l pieces of h bits (h = s
    for P = 1, else ceil(s/P) rounded up to a multiple of 32) and costs P + 1
-   transforms of the power of two N >= h+k-1 per sub-block; it needs a
-   shared seed, s+k-1 > 2^11, s < 7*2^26+1 and N <= 2^22 for some P <= 16
-   (EXTRACT_EINVAL otherwise).  Both methods give the same bits. */
+   transforms of the power of two N >= h+k-1 per sub-block (2P + 1 with
+   EXTRACT_SEED_PER_SUBBLOCK, whose seed windows are transformed in every
+   run; then N >= 2^16); it needs s+k-1 > 2^11, s < 7*2^26+1 and
+   N <= 2^22 for some P <= 16 (EXTRACT_EINVAL otherwise).  Both methods
+   give the same bits. */
 #define EXTRACT_METHOD_DIRECT     0x4u
 #define EXTRACT_METHOD_NTT        0x8u
 /* NTT method: use P = 2^l pieces per sub-block (l = 0 .. 4) instead of the

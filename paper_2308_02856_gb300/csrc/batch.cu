@@ -362,8 +362,8 @@ int extract_batch_create(extract_batch **out, const extract_job_desc *jobs, uint
         const uint64_t tiles = ceil_div(d.k, (uint64_t)kHashWarps * 32 * variant_q(J.variant)) *
                                ceil_div(d.m, (uint64_t)variant_j(J.variant));
         const double direct_ns = (double)tiles * nchunks * tt->ns_per_chunk[J.variant];
-        const bool want_ntt = !(flags & EXTRACT_BATCH_DIRECT_ONLY) && !per_sub && ntt_eligible(d.s, d.k) &&
-                              predict_ntt_s(d.m, d.s, d.k) * 1e9 < direct_ns;
+        const bool want_ntt = !(flags & EXTRACT_BATCH_DIRECT_ONLY) && ntt_shape(d.s, d.k, -1, per_sub).N != 0 &&
+                              predict_ntt_s(d.m, d.s, d.k, -1, per_sub) * 1e9 < direct_ns;
         if (want_ntt) J.table_index = -2;  // marks an NTT job until its plan exists
         else total_ns += direct_ns;
         HashPlan vp;
@@ -409,8 +409,9 @@ int extract_batch_create(extract_batch **out, const extract_job_desc *jobs, uint
         std::vector<std::pair<double, uint32_t>> nj_cost;
         for (uint32_t i = 0; i < njobs; ++i)
             if (b->jobs[i].table_index == -2) {
-                work = std::max(work, ntt_work_words(jobs[i].m, jobs[i].s, jobs[i].k));
-                nj_cost.push_back({predict_ntt_s(jobs[i].m, jobs[i].s, jobs[i].k), i});
+                const bool ps = (jobs[i].flags & EXTRACT_SEED_PER_SUBBLOCK) != 0;
+                work = std::max(work, ntt_work_words(jobs[i].m, jobs[i].s, jobs[i].k, -1, ps));
+                nj_cost.push_back({predict_ntt_s(jobs[i].m, jobs[i].s, jobs[i].k, -1, ps), i});
             }
         std::stable_sort(nj_cost.begin(), nj_cost.end(), [](const auto &x, const auto &y) { return x.first > y.first; });
         const int nlanes = (int)std::min<size_t>(kNttLanes, nj_cost.size());
@@ -469,7 +470,9 @@ int extract_batch_create(extract_batch **out, const extract_job_desc *jobs, uint
                 }
             }
             if (J.table_index == -2) {
-                if ((rc = ntt_create(&J.ntt, d.m, d.s, d.k, J.seed, st, b->lanes[J.lane].work)) != EXTRACT_OK) break;
+                if ((rc = ntt_create(&J.ntt, d.m, d.s, d.k, J.seed, st, b->lanes[J.lane].work, -1,
+                                     J.nseeds > 1 ? J.seed_stride : 0)) != EXTRACT_OK)
+                    break;
                 continue;
             }
             BatchJobDev &T = b->table[J.table_index];

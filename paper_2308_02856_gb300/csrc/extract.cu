@@ -34,11 +34,12 @@ double predict_direct_s(uint32_t m, uint32_t k, uint32_t s)
     return (double)m * k * ((s + 31) / 32) / 19e12;
 }
 
-double predict_ntt_s(uint32_t m, uint32_t s, uint32_t k, int split_log2)
+double predict_ntt_s(uint32_t m, uint32_t s, uint32_t k, int split_log2, bool per_block_seeds)
 {
-    const NttShape sh = ntt_shape(s, k, split_log2);
+    const NttShape sh = ntt_shape(s, k, split_log2, per_block_seeds);
     const double N = (double)sh.N;
-    return (double)m * (sh.P + 1) * N * (std::log2(N) + 4.0) * 0.325e-12;
+    const double transforms = (per_block_seeds ? 2.0 : 1.0) * sh.P + 1.0;
+    return (double)m * transforms * N * (std::log2(N) + 4.0) * 0.325e-12;
 }
 
 }  // namespace ex
@@ -155,13 +156,14 @@ int extract_create(extract_ctx **out, uint64_t n, uint32_t m, uint32_t s, uint32
     const uint32_t split_field = (flags >> 16) & 0x7u;
     if (split_field > 5) return set_error(EXTRACT_EINVAL, "EXTRACT_NTT_SPLIT takes 0 .. 4");
     const int split = (int)split_field - 1;  // -1: automatic
-    const bool ntt_ok = !per_sub && ntt_shape(s, k, split).N != 0;
+    const bool ntt_ok = ntt_shape(s, k, split, per_sub).N != 0;
     if ((flags & EXTRACT_METHOD_NTT) && !ntt_ok)
         return set_error(EXTRACT_EINVAL,
-                         "the NTT method needs a shared seed, s+k-1 > 2^11, s < 7*2^26+1 and a split with "
-                         "transform length <= 2^22 (s=%u k=%u split=%d)", s, k, split);
+                         "the NTT method needs s+k-1 > 2^11, s < 7*2^26+1 and a split with transform length "
+                         "<= 2^22 (>= 2^16 with one seed per sub-block) (s=%u k=%u split=%d)", s, k, split);
     const bool use_ntt = ntt_ok && !(flags & EXTRACT_METHOD_DIRECT) &&
-                         ((flags & EXTRACT_METHOD_NTT) || predict_ntt_s(m, s, k, split) < predict_direct_s(m, k, s));
+                         ((flags & EXTRACT_METHOD_NTT) ||
+                          predict_ntt_s(m, s, k, split, per_sub) < predict_direct_s(m, k, s));
 
     extract_ctx *h = new (std::nothrow) extract_ctx();
     if (!h) return set_error(EXTRACT_ENOMEM, "host allocation failed");
@@ -202,7 +204,7 @@ int extract_create(extract_ctx **out, uint64_t n, uint32_t m, uint32_t s, uint32
     if (use_ntt) {
         cudaStream_t st;
         if ((e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) != cudaSuccess) { free_ctx(h); return cuda_error(e, "stream"); }
-        int rc = ntt_create(&h->ntt, m, s, k, h->seed, st, nullptr, split);
+        int rc = ntt_create(&h->ntt, m, s, k, h->seed, st, nullptr, split, per_sub ? h->seed_stride : 0);
         cudaStreamDestroy(st);
         if (rc != EXTRACT_OK) { free_ctx(h); return rc; }
         if ((e = cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking)) != cudaSuccess ||
@@ -216,7 +218,7 @@ int extract_create(extract_ctx **out, uint64_t n, uint32_t m, uint32_t s, uint32
             if ((e = cudaStreamCreateWithFlags(&L.st, cudaStreamNonBlocking)) != cudaSuccess ||
                 (e = cudaEventCreateWithFlags(&L.ev_fork, cudaEventDisableTiming)) != cudaSuccess ||
                 (e = cudaEventCreateWithFlags(&L.ev_join, cudaEventDisableTiming)) != cudaSuccess ||
-                (e = cudaMalloc(&L.work, ntt_work_words(m, s, k, split) * 4)) != cudaSuccess) {
+                (e = cudaMalloc(&L.work, ntt_work_words(m, s, k, split, per_sub) * 4)) != cudaSuccess) {
                 free_ctx(h);
                 return cuda_error(e, "second NTT lane");
             }
@@ -382,8 +384,10 @@ int extract_describe(extract_ctx *h, char *buf, uint32_t buflen)
     if (h->ntt) {
         snprintf(buf, buflen,
                  "ntt: N=%u (%u x 2048) P=%u pieces per sub-block, %u sub-blocks per launch group, "
-                 "prime 7*2^26+1; sms=%d",
-                 ntt_size(h->ntt), ntt_size(h->ntt) / 2048, ntt_pieces(h->ntt), ntt_group(h->ntt), h->num_sms);
+                 "prime 7*2^26+1, %s; sms=%d",
+                 ntt_size(h->ntt), ntt_size(h->ntt) / 2048, ntt_pieces(h->ntt), ntt_group(h->ntt),
+                 h->nseeds > 1 ? "seed windows transformed per run (one seed per sub-block)" : "shared seed spectrum",
+                 h->num_sms);
         return EXTRACT_OK;
     }
     snprintf(buf, buflen,

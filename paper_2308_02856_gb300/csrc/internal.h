@@ -140,18 +140,21 @@ struct NttPlan;
 struct NttShape {
     uint32_t N = 0, P = 1, h = 0;
 };
-NttShape ntt_shape(uint32_t s, uint32_t k, int split_log2 = -1);
+// per_block_seeds: one seed per sub-block (its windows are transformed in
+// every run: 2P + 1 transforms per sub-block; N >= 2^16).
+NttShape ntt_shape(uint32_t s, uint32_t k, int split_log2 = -1, bool per_block_seeds = false);
 bool ntt_eligible(uint32_t s, uint32_t k);
 // Words of the work buffer a plan for (m, s, k) uses, and the most any uses.
-uint64_t ntt_work_words(uint32_t m, uint32_t s, uint32_t k, int split_log2 = -1);
+uint64_t ntt_work_words(uint32_t m, uint32_t s, uint32_t k, int split_log2 = -1, bool per_block_seeds = false);
 uint64_t ntt_max_work_words();
 // Radix-2 butterflies of one hash of m sub-blocks ((P + 1) transforms each).
-double ntt_work_butterflies(uint32_t m, uint32_t s, uint32_t k, int split_log2 = -1);
+double ntt_work_butterflies(uint32_t m, uint32_t s, uint32_t k, int split_log2 = -1, bool per_block_seeds = false);
 // Builds the twiddle tables and the seed spectra (synchronous on st).  work:
 // a caller-owned buffer of ntt_work_words() words shared by plans that never
 // run concurrently, or null to allocate one.
+// seed_stride > 0: one seed per sub-block, seed_stride words apart.
 int ntt_create(NttPlan **out, uint32_t m, uint32_t s, uint32_t k, const uint32_t *seed_dev, cudaStream_t st,
-               uint32_t *work = nullptr, int split_log2 = -1);
+               uint32_t *work = nullptr, int split_log2 = -1, uint64_t seed_stride = 0);
 // A second stream and work buffer for ntt_hash: launch groups alternate
 // between the two, so one group's passes fill the other's last waves.
 // ev_fork / ev_join: events owned by the caller.
@@ -178,12 +181,12 @@ void ntt_destroy(NttPlan *p);
 // Stream-ordered release (no device-wide synchronisation).
 void ntt_destroy_async(NttPlan *p, cudaStream_t st);
 // Device bytes a plan holds besides the shared work buffer.
-uint64_t ntt_plan_bytes(uint32_t s, uint32_t k, int split_log2 = -1);
+uint64_t ntt_plan_bytes(uint32_t s, uint32_t k, int split_log2 = -1, bool per_block_seeds = false);
 // Predicted seconds of the two hashing methods for m sub-blocks (direct: the
 // LOP3 rate the tiled kernel reaches; NTT: the measured cost per transformed
 // element and stage).
 double predict_direct_s(uint32_t m, uint32_t k, uint32_t s);
-double predict_ntt_s(uint32_t m, uint32_t s, uint32_t k, int split_log2 = -1);
+double predict_ntt_s(uint32_t m, uint32_t s, uint32_t k, int split_log2 = -1, bool per_block_seeds = false);
 uint32_t ntt_group(const NttPlan *p);
 uint32_t ntt_size(const NttPlan *p);
 uint32_t ntt_pieces(const NttPlan *p);

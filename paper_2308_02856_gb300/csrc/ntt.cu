@@ -147,12 +147,14 @@ struct Tables {
 };
 
 // Where pass A finds the bits of virtual block v = g P + q: piece q of
-// source row g.  A piece holds len coefficients; only its first lim(q) =
-// min(len, total - q len) positions are data, the rest read as 0.
+// source row g, starting 32 step q bits in.  A piece holds len coefficients;
+// only its first lim(q) = min(len, total - 32 step q) positions are data,
+// the rest read as 0.  Sub-block pieces have len = 32 step; a seed window of
+// a piece is longer (len = h + k - 1) and overlaps the next one.
 struct Pieces {
     uint64_t stride;  // words between source rows
     uint32_t P;       // pieces per row
-    uint32_t step;    // words between pieces (len / 32 when P > 1)
+    uint32_t step;    // words between pieces (h / 32 when P > 1)
     uint32_t len;     // coefficients per piece
     uint32_t total;   // data bits per row
 };
@@ -161,7 +163,7 @@ __device__ __forceinline__ const uint32_t *piece_src(const uint32_t *bits, const
                                                      uint32_t &lim)
 {
     const uint32_t q = v % pc.P;
-    lim = min(pc.len, pc.total - q * pc.len);
+    lim = min(pc.len, pc.total - q * pc.step * 32u);
     return bits + (size_t)(v / pc.P) * pc.stride + (size_t)q * pc.step;
 }
 
@@ -452,6 +454,31 @@ __device__ __forceinline__ void row_dif(uint32_t (&e)[32], const uint32_t *x, ui
     dif_warp_t<32>(e, sw, T.row_stage_f, lane);
 }
 
+// e[i] (layout B, from base) times a spectrum row computed in the same run
+// (no Shoup quotients): Montgomery products, e * s * 2^-32; the inverse
+// twist table of such a plan carries the factor 2^32 back.  kAcc: added.
+template <bool kAcc>
+__device__ __forceinline__ void row_mul_mont(uint32_t (&e)[32], uint32_t (&acc)[32], const uint32_t *sv)
+{
+#pragma unroll
+    for (int i = 0; i < 32; i += 4) {
+        const uint4 a = *reinterpret_cast<const uint4 *>(sv + i);
+        const uint32_t m0 = mont_lazy(e[i], a.x), m1 = mont_lazy(e[i + 1], a.y);
+        const uint32_t m2 = mont_lazy(e[i + 2], a.z), m3 = mont_lazy(e[i + 3], a.w);
+        if (kAcc) {
+            acc[i] = red2p(acc[i] + m0);
+            acc[i + 1] = red2p(acc[i + 1] + m1);
+            acc[i + 2] = red2p(acc[i + 2] + m2);
+            acc[i + 3] = red2p(acc[i + 3] + m3);
+        } else {
+            acc[i] = m0;
+            acc[i + 1] = m1;
+            acc[i + 2] = m2;
+            acc[i + 3] = m3;
+        }
+    }
+}
+
 // e[i] (layout B, from base) times the spectrum; kAcc: added to acc
 template <bool kAcc>
 __device__ __forceinline__ void row_mul(uint32_t (&e)[32], uint32_t (&acc)[32], const uint32_t *sv,
@@ -501,7 +528,10 @@ __device__ __forceinline__ void row_dit_store(uint32_t (&e)[32], uint32_t *x, ui
     }
 }
 
-template <bool kInverse, bool kMulti>
+// kPerBlock: the spectra are per sub-block (independent seeds), transformed
+// in the same run: piece q of sub-block g uses S + (g P + q) N, without
+// quotients (Montgomery products).
+template <bool kInverse, bool kMulti, bool kPerBlock = false>
 __global__ void __launch_bounds__(64, kMulti ? 8 : 12)
 ntt_rows_kernel(uint32_t *__restrict__ buf, uint32_t N, uint32_t R1, uint32_t P, const uint32_t *__restrict__ S,
                 const uint32_t *__restrict__ Sq, Tables T)
@@ -512,6 +542,7 @@ ntt_rows_kernel(uint32_t *__restrict__ buf, uint32_t N, uint32_t R1, uint32_t P,
     uint32_t *x = buf + (size_t)g * P * N + (size_t)r * kR2;
     const uint32_t base = 1024u * w + 32u * lane;  // layout B: e[i] at base + i
     const size_t so = (size_t)r * kR2 + base;
+    const uint32_t *Sb = kPerBlock ? S + (size_t)g * P * N : S;
     uint32_t e[32];
     row_dif(e, x, sw[w], T, lane, w);
     if (!kInverse) {
@@ -521,15 +552,18 @@ ntt_rows_kernel(uint32_t *__restrict__ buf, uint32_t N, uint32_t R1, uint32_t P,
         return;
     }
     if (!kMulti) {
-        row_mul<false>(e, e, S + so, Sq + so);
+        if (kPerBlock) row_mul_mont<false>(e, e, Sb + so);
+        else row_mul<false>(e, e, S + so, Sq + so);
         row_dit_store(e, x, sw, T, lane, w);
         return;
     }
     uint32_t acc[32];
-    row_mul<false>(e, acc, S + so, Sq + so);
+    if (kPerBlock) row_mul_mont<false>(e, acc, Sb + so);
+    else row_mul<false>(e, acc, S + so, Sq + so);
     for (uint32_t q = 1; q < P; ++q) {
         row_dif(e, x + (size_t)q * N, sw[w], T, lane, w);
-        row_mul<true>(e, acc, S + (size_t)q * N + so, Sq + (size_t)q * N + so);
+        if (kPerBlock) row_mul_mont<true>(e, acc, Sb + (size_t)q * N + so);
+        else row_mul<true>(e, acc, S + (size_t)q * N + so, Sq + (size_t)q * N + so);
     }
     row_dit_store(acc, x, sw, T, lane, w);
 }
@@ -839,6 +873,11 @@ struct NttPlan {
     uint32_t P = 1, h = 0;  // pieces per sub-block and coefficients per piece
     uint32_t *buf = nullptr, *S = nullptr, *Sq = nullptr, *tables = nullptr, *twist = nullptr;
     bool own_buf = true;
+    // independent seeds: every sub-block's windows are transformed per run
+    bool per_block = false;
+    const uint32_t *seed = nullptr;  // sub-block j's seed at seed + j seed_stride words
+    uint64_t seed_stride = 0;
+    uint32_t L = 0;                  // bits per seed (s + k - 1)
     Tables T{};
 };
 
@@ -893,10 +932,12 @@ int ntt_launch_a(const NttPlan *p, const uint32_t *bits, const Pieces &pc, bool 
 // inverse: the P pieces of each sub-block times their spectra, summed and
 // transformed back; else the forward DIF of one piece (P = 1).
 void ntt_launch_rows(const NttPlan *p, uint32_t *dst, uint32_t g, uint32_t P, const uint32_t *S, const uint32_t *Sq,
-                     bool inverse, cudaStream_t st)
+                     bool inverse, cudaStream_t st, bool per_block = false)
 {
     const uint32_t rows = p->R1 * g;
     if (!inverse) ntt_rows_kernel<false, false><<<rows, 64, 0, st>>>(dst, p->N, p->R1, 1, S, Sq, p->T);
+    else if (per_block && P == 1) ntt_rows_kernel<true, false, true><<<rows, 64, 0, st>>>(dst, p->N, p->R1, 1, S, Sq, p->T);
+    else if (per_block) ntt_rows_kernel<true, true, true><<<rows, 64, 0, st>>>(dst, p->N, p->R1, P, S, Sq, p->T);
     else if (P == 1) ntt_rows_kernel<true, false><<<rows, 64, 0, st>>>(dst, p->N, p->R1, 1, S, Sq, p->T);
     else ntt_rows_kernel<true, true><<<rows, 64, 0, st>>>(dst, p->N, p->R1, P, S, Sq, p->T);
 }
@@ -945,10 +986,11 @@ int ntt_launch_a_inv(const NttPlan *p, const uint32_t *buf, uint32_t g, uint32_t
 // products add up in the frequency domain, so one inverse transform serves
 // them all.  Length N = 2^e >= h + k - 1 (2^12 .. 2^22); work (P + 1)
 // transforms of N instead of 2 of the length for s + k - 1.
-NttShape ntt_shape(uint32_t s, uint32_t k, int split_log2)
+NttShape ntt_shape(uint32_t s, uint32_t k, int split_log2, bool per_block_seeds)
 {
     NttShape best{};
     if ((uint64_t)s + k - 1 <= kR2 || s >= kP) return best;
+    const uint32_t bufs = per_block_seeds ? 2u : 1u;  // data pieces (+ seed windows)
     double best_cost = 0;
     for (int l = 0; l <= kMaxSplitLog2; ++l) {
         if (split_log2 >= 0 && l != split_log2) continue;
@@ -957,8 +999,10 @@ NttShape ntt_shape(uint32_t s, uint32_t k, int split_log2)
         if ((uint64_t)(P - 1) * h >= s) break;  // the last piece would be empty
         uint64_t N = 2 * kR2;
         while (N < h + k - 1) N <<= 1;
-        if (N > (1ull << 22) || P * N > kMaxWorkWords) continue;
-        const double cost = (double)(P + 1) * (double)N * (std::log2((double)N) + 4.0);
+        if (N > (1ull << 22) || bufs * P * N > kMaxWorkWords) continue;
+        if (per_block_seeds && N < (1u << 16)) continue;  // needs the full twist tables (R1 >= 32)
+        // transforms per sub-block: P data pieces (+ P seed windows) + 1 inverse
+        const double cost = (double)(bufs * P + 1) * (double)N * (std::log2((double)N) + 4.0);
         if (best.N == 0 || cost < best_cost) {
             best = NttShape{(uint32_t)N, P, (uint32_t)h};
             best_cost = cost;
@@ -992,31 +1036,42 @@ void ntt_destroy(NttPlan *p)
 }
 
 
-uint64_t ntt_plan_bytes(uint32_t s, uint32_t k, int split_log2)
+uint64_t ntt_plan_bytes(uint32_t s, uint32_t k, int split_log2, bool per_block_seeds)
 {
-    const NttShape sh = ntt_shape(s, k, split_log2);
-    // P spectra + quotients, twist tables, stage tables
-    return (2ull * sh.P + 2) * sh.N * 4 + 64 * 1024;
+    const NttShape sh = ntt_shape(s, k, split_log2, per_block_seeds);
+    // P spectra + quotients (shared seed) or the scaled inverse twist table
+    // (independent seeds), twist tables, stage tables
+    return (per_block_seeds ? 3ull : 2ull * sh.P + 2) * sh.N * 4 + 64 * 1024;
 }
 
 // sub-blocks per launch group: keep the working buffer near 64 MB (L2-sized)
-static uint32_t group_size(uint32_t m, const NttShape &sh)
+static uint32_t group_size(uint32_t m, const NttShape &sh, bool per_block_seeds)
 {
-    return (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(m, kMaxWorkWords / ((uint64_t)sh.P * sh.N)));
+    const uint64_t per_sub = (per_block_seeds ? 2ull : 1ull) * sh.P * sh.N;
+    return (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(m, kMaxWorkWords / per_sub));
 }
 
 uint64_t ntt_max_work_words() { return kMaxWorkWords; }
 
-uint64_t ntt_work_words(uint32_t m, uint32_t s, uint32_t k, int split_log2)
+uint64_t ntt_work_words(uint32_t m, uint32_t s, uint32_t k, int split_log2, bool per_block_seeds)
 {
-    const NttShape sh = ntt_shape(s, k, split_log2);
-    return (uint64_t)group_size(m, sh) * sh.P * sh.N;
+    const NttShape sh = ntt_shape(s, k, split_log2, per_block_seeds);
+    return (uint64_t)group_size(m, sh, per_block_seeds) * (per_block_seeds ? 2u : 1u) * sh.P * sh.N;
 }
 
-double ntt_work_butterflies(uint32_t m, uint32_t s, uint32_t k, int split_log2)
+double ntt_work_butterflies(uint32_t m, uint32_t s, uint32_t k, int split_log2, bool per_block_seeds)
 {
-    const NttShape sh = ntt_shape(s, k, split_log2);
-    return (double)m * (sh.P + 1) * (sh.N / 2) * std::log2((double)std::max<uint32_t>(sh.N, 2));
+    const NttShape sh = ntt_shape(s, k, split_log2, per_block_seeds);
+    const uint32_t transforms = (per_block_seeds ? 2u : 1u) * sh.P + 1;
+    return (double)m * transforms * (sh.N / 2) * std::log2((double)std::max<uint32_t>(sh.N, 2));
+}
+
+// tw'[i] = tw[i] c 2^-32 (Montgomery product): the per-block plans' inverse
+// twist, scaled by 1/N and by 2^32 to undo their Montgomery row products.
+__global__ void ntt_scale_table_kernel(const uint32_t *tw, uint32_t *out, uint32_t n, uint32_t c)
+{
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        out[i] = mul_mont(tw[i], c);
 }
 
 // Once per device: every column kernel's dynamic shared-memory limit (set
@@ -1070,22 +1125,28 @@ static int device_setup(cudaStream_t st)
     return EXTRACT_OK;
 }
 
-// seed_dev: realigned seed bits (bit t = seed[t]), L = s + k - 1 bits.
+// seed_dev: realigned seed bits (bit t = seed[t]), L = s + k - 1 bits; with
+// seed_stride > 0 one seed per sub-block, seed_stride words apart.
 int ntt_create(NttPlan **out, uint32_t m, uint32_t s, uint32_t k, const uint32_t *seed_dev, cudaStream_t st,
-               uint32_t *work, int split_log2)
+               uint32_t *work, int split_log2, uint64_t seed_stride)
 {
     *out = nullptr;
-    const NttShape sh = ntt_shape(s, k, split_log2);
+    const bool per_block = seed_stride > 0;
+    const NttShape sh = ntt_shape(s, k, split_log2, per_block);
     if (!sh.N) return set_error(EXTRACT_EINVAL, "no NTT shape for s=%u k=%u (split %d)", s, k, split_log2);
     NttPlan *p = new NttPlan();
     p->N = sh.N;
     p->P = sh.P;
     p->h = sh.h;
+    p->per_block = per_block;
+    p->seed = seed_dev;
+    p->seed_stride = seed_stride;
+    p->L = s + k - 1;
     p->e = 0;
     while ((1u << p->e) < p->N) ++p->e;
     p->R1 = p->N / kR2;
     p->r1_log = p->e - kR2Log;
-    p->G = group_size(m, sh);
+    p->G = group_size(m, sh, per_block);
     const uint32_t R1 = p->R1;
     // table layout (words): col_f, col_fq, col_i, col_iq (R1/2 each, >= 1),
     // row_f, row_fq, row_i, row_iq (1024 each), tw_lo_f, tw_lo_i (2048),
@@ -1162,20 +1223,35 @@ int ntt_create(NttPlan **out, uint32_t m, uint32_t s, uint32_t k, const uint32_t
         if (work) {
             p->buf = work;
             p->own_buf = false;
-        } else if ((e = cudaMallocAsync(&p->buf, (size_t)p->G * spec * 4, st)) != cudaSuccess) {
+        } else if ((e = cudaMallocAsync(&p->buf, (size_t)p->G * spec * (per_block ? 2 : 1) * 4, st)) != cudaSuccess) {
             rc = cuda_error(e, "ntt buffer");
             break;
         }
-        if ((e = cudaMallocAsync(&p->S, spec * 4, st)) != cudaSuccess) { rc = cuda_error(e, "ntt spectrum"); break; }
-        if ((e = cudaMallocAsync(&p->Sq, spec * 4, st)) != cudaSuccess) { rc = cuda_error(e, "ntt spectrum"); break; }
         if (R1 >= 32) {
-            if ((e = cudaMallocAsync(&p->twist, (size_t)2 * p->N * 4, st)) != cudaSuccess) { rc = cuda_error(e, "ntt twist tables"); break; }
+            if ((e = cudaMallocAsync(&p->twist, (size_t)(per_block ? 3 : 2) * p->N * 4, st)) != cudaSuccess) { rc = cuda_error(e, "ntt twist tables"); break; }
             p->T.twist_f = p->twist;
             p->T.twist_i = p->twist + p->N;
             ntt_twist_table_kernel<<<(uint32_t)std::min<uint64_t>(ceil_div(p->N, 256), 8192), 256, 0, st>>>(
                 p->twist, p->twist + p->N, R1, p->r1_log, p->T);
+            if (per_block) {  // inverse twist x 1/N x 2^32 (the row products are Montgomery)
+                const uint64_t two32 = (1ull << 32) % kP, two64 = two32 * two32 % kP;
+                const uint32_t c = (uint32_t)((uint64_t)powmod(p->N, kP - 2) * two64 % kP);
+                ntt_scale_table_kernel<<<(uint32_t)std::min<uint64_t>(ceil_div(p->N, 256), 8192), 256, 0, st>>>(
+                    p->twist + p->N, p->twist + 2 * (size_t)p->N, p->N, c);
+                p->T.twist_i = p->twist + 2 * (size_t)p->N;
+            }
+        } else if (per_block) {
+            rc = set_error(EXTRACT_EINVAL, "independent seeds need N >= 2^16");
+            break;
         }
         if ((rc = device_setup(st)) != EXTRACT_OK) break;
+        if (per_block) {
+            if ((e = cudaGetLastError()) != cudaSuccess) { rc = cuda_error(e, "ntt tables"); break; }
+            if ((e = cudaStreamSynchronize(st)) != cudaSuccess) { rc = cuda_error(e, "ntt tables"); break; }
+            break;  // no shared spectrum
+        }
+        if ((e = cudaMallocAsync(&p->S, spec * 4, st)) != cudaSuccess) { rc = cuda_error(e, "ntt spectrum"); break; }
+        if ((e = cudaMallocAsync(&p->Sq, spec * 4, st)) != cudaSuccess) { rc = cuda_error(e, "ntt spectrum"); break; }
         // seed spectra: for piece q, the window seed[q h .. q h + h + k - 1)
         // (zero past L = s + k - 1) through pass A + row DIF into S + q N;
         // then all are scaled by 1/N
@@ -1207,6 +1283,31 @@ static Pieces sub_block_pieces(const NttPlan *p, uint32_t w_pad, uint32_t s)
     return Pieces{w_pad, p->P, p->P > 1 ? p->h / 32 : 0u, p->h, s};
 }
 
+// The seed windows of sub-blocks j0 .. (independent seeds): window q of
+// sub-block j starts at bit q h of its seed and holds h + k - 1 coefficients
+// (0 past L): the seed window that meets piece q of the sub-block.
+static Pieces seed_pieces(const NttPlan *p, uint32_t k)
+{
+    return Pieces{p->seed_stride, p->P, p->P > 1 ? p->h / 32 : 0u, std::min(p->h + k - 1, p->L), p->L};
+}
+
+// One launch group: the g sub-blocks from j0, in gb (the group's buffer).
+static int ntt_group_run(const NttPlan *p, const uint32_t *arev, uint32_t w_pad, uint32_t j0, uint32_t g,
+                         uint32_t k, const Pieces &pc, uint32_t *gb, uint32_t *out, cudaStream_t gs)
+{
+    if (int rc = ntt_launch_a(p, arev + (size_t)j0 * w_pad, pc, true, g, gb, gs)) return rc;
+    if (!p->per_block) {
+        ntt_launch_rows(p, gb, g, p->P, p->S, p->Sq, true, gs);
+    } else {
+        // the seed windows' spectra, transformed into the second half
+        uint32_t *sb = gb + (size_t)p->G * p->P * p->N;
+        if (int rc = ntt_launch_a(p, p->seed + (size_t)j0 * p->seed_stride, seed_pieces(p, k), false, g, sb, gs)) return rc;
+        ntt_launch_rows(p, sb, g * p->P, 1, nullptr, nullptr, false, gs);
+        ntt_launch_rows(p, gb, g, p->P, sb, nullptr, true, gs, true);
+    }
+    return ntt_launch_a_inv(p, gb, g, j0, k, out, gs);
+}
+
 // Hash every sub-block: out (zeroed here) gets K_j at bit j*k.
 int ntt_hash(const NttPlan *p, const uint32_t *arev, uint32_t w_pad, uint32_t m, uint32_t s, uint32_t k,
              uint32_t *out, cudaStream_t st, uint32_t *work, const NttSecondLane *lane2)
@@ -1225,9 +1326,7 @@ int ntt_hash(const NttPlan *p, const uint32_t *arev, uint32_t w_pad, uint32_t m,
         const bool second = two && (gi & 1u);
         cudaStream_t gs = second ? lane2->st : st;
         uint32_t *gb = second ? lane2->work : buf;
-        if (int rc = ntt_launch_a(p, arev + (size_t)j0 * w_pad, pc, true, g, gb, gs)) return rc;
-        ntt_launch_rows(p, gb, g, p->P, p->S, p->Sq, true, gs);
-        if (int rc = ntt_launch_a_inv(p, gb, g, j0, k, out, gs)) return rc;
+        if (int rc = ntt_group_run(p, arev, w_pad, j0, g, k, pc, gb, out, gs)) return rc;
     }
     if (two) {
         EX_CUDA(cudaEventRecord(lane2->ev_join, lane2->st));
@@ -1253,9 +1352,7 @@ int ntt_run_overlapped(const NttPlan *p, const uint32_t *in, const uint32_t *per
         // each wait binds to the record just before it, so one event serves every group
         EX_CUDA(cudaEventRecord(ev_group, aux));
         EX_CUDA(cudaStreamWaitEvent(st, ev_group, 0));
-        if (int rc = ntt_launch_a(p, ar, pc, true, g, p->buf, st)) return rc;
-        ntt_launch_rows(p, p->buf, g, p->P, p->S, p->Sq, true, st);
-        if (int rc = ntt_launch_a_inv(p, p->buf, g, j0, k, out, st)) return rc;
+        if (int rc = ntt_group_run(p, arev, w_pad, j0, g, k, pc, p->buf, out, st)) return rc;
     }
     EX_LAUNCH("ntt kernels");
     return EXTRACT_OK;

@@ -179,7 +179,8 @@ int setup_job(extract_server *S, SJob &J)
     if (int rc = launch_gather(J.in, J.perm, J.m, J.s, J.w_pad, J.arev, st, S->sms, 0, iid, J.n)) return rc;
     EX_CUDA(cudaMemsetAsync(J.out, 0, ceil_div((uint64_t)J.m * J.k, 32) * 4, st));
     if (J.use_ntt)  // tables and the seed spectrum (synchronous on the setup stream)
-        if (int rc = ntt_create(&J.ntt, J.m, J.s, J.k, J.seed, st, S->lanes[0].work)) return rc;
+        if (int rc = ntt_create(&J.ntt, J.m, J.s, J.k, J.seed, st, S->lanes[0].work, -1, J.nseeds > 1 ? J.stride : 0))
+            return rc;
     // the order is only needed by the gather: give its memory back now
     if (J.perm) {
         EX_CUDA(cudaFreeAsync(J.perm, st));
@@ -502,8 +503,8 @@ int extract_server_submit(extract_server *S, const extract_job_desc *d, const ui
         const double tiles = (double)ceil_div(d->k, variant_rows((int)j->variant)) *
                              (double)ceil_div(d->m, (uint32_t)variant_j((int)j->variant));
         const double direct_ns = tiles * (j->w_pad / kWordChunk) * S->costs[j->variant];
-        const double ntt_ns = predict_ntt_s(d->m, d->s, d->k) * 1e9;
-        j->use_ntt = !per_sub && ntt_eligible(d->s, d->k) && ntt_ns < direct_ns;
+        const double ntt_ns = predict_ntt_s(d->m, d->s, d->k, -1, per_sub) * 1e9;
+        j->use_ntt = ntt_shape(d->s, d->k, -1, per_sub).N != 0 && ntt_ns < direct_ns;
         if (j->use_ntt) j->remaining_ns = ntt_ns;
     }
     HashPlan vp;
@@ -525,7 +526,7 @@ int extract_server_submit(extract_server *S, const extract_job_desc *d, const ui
     // budget charge: order (freed early, still charged) + sub-blocks + seed + the job's input and output
     const uint64_t order_b = order_entries(d->n, d->m, d->s, d->flags) * 4;
     j->bytes = order_b + (uint64_t)d->m * j->w_pad * 4 + (uint64_t)j->seed_host.size() * 4 + ceil_div(d->n, 32) * 4 +
-               ceil_div((uint64_t)d->m * d->k, 32) * 4 + (j->use_ntt ? ntt_plan_bytes(d->s, d->k) : 0);
+               ceil_div((uint64_t)d->m * d->k, 32) * 4 + (j->use_ntt ? ntt_plan_bytes(d->s, d->k, -1, per_sub) : 0);
     // tiles: every (row tile, sub-block tile, word range), each about tile_cap of one SM
     const uint32_t rows = vp.rows(), J = (uint32_t)vp.j, nchunks = j->w_pad / kWordChunk;
     const double ns_chunk = S->costs[j->variant];  // GPU ns per CTA-chunk

@@ -162,9 +162,11 @@ def test_batch_mixes_ntt_and_direct_jobs():
     to the persistent direct launch; every output equals the direct-only
     batch's and the oracle's (sampled rows)."""
     shapes = []
-    for i, (n, s, k) in enumerate([(1 << 20, 1 << 18, 1 << 17), (1 << 14, 1 << 12, 500), (1 << 21, 1 << 20, 1 << 19),
-                                   (3 << 18, 1 << 18, 70_001), (1 << 16, 1 << 13, 4000), (1 << 20, 1 << 20, 104858)]):
-        shapes.append({"n": n, "m": n // s, "s": s, "k": k, "flags": 0, "p": 0.6 + 0.05 * i,
+    for i, (n, s, k, fl) in enumerate([(1 << 20, 1 << 18, 1 << 17, 0), (1 << 14, 1 << 12, 500, 0),
+                                       (1 << 21, 1 << 20, 1 << 19, 0), (3 << 18, 1 << 18, 70_001, 0),
+                                       (1 << 16, 1 << 13, 4000, 0), (1 << 20, 1 << 20, 104858, 0),
+                                       (1 << 20, 1 << 17, 1 << 15, X.EXTRACT_SEED_PER_SUBBLOCK)]):
+        shapes.append({"n": n, "m": n // s, "s": s, "k": k, "flags": fl, "p": 0.6 + 0.05 * i,
                        "in_seed": 500 + i, "seed_seed": 600 + i, "key": 700 + i})
     jobs, ins = _materialise(shapes)
     d_in = [_dev(w) for w in ins]

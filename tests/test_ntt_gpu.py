@@ -109,12 +109,59 @@ def test_ntt_every_split_matches_oracle(n, m, s, k):
     assert len(ran) >= 3, ran
 
 
+@pytest.mark.parametrize("n,m,s,k", [
+    (1 << 18, 4, 1 << 15, 1 << 13),   # N = 2^16, P = 1
+    (1 << 20, 8, 1 << 17, 1 << 15),   # P = 2
+    (300_000, 3, 70_001, 9_999),      # P = 2, ragged last piece and seed windows
+])
+def test_ntt_independent_seeds_match_oracle(n, m, s, k):
+    """One seed per sub-block (the paper's independent f_RE,j): each
+    sub-block's seed windows are transformed in the run and multiplied into
+    its own pieces."""
+    in_w = synth.bernoulli_bits(n, 0.6, 41)
+    seed = synth.uniform_bits((s + k - 1) * m, 42)
+    got, desc = _run(n, m, s, k, X.EXTRACT_SEED_PER_SUBBLOCK | X.EXTRACT_METHOD_NTT, in_w, seed)
+    assert desc.startswith("ntt") and "one seed per sub-block" in desc, desc
+    want = oracle.extract(n, m, s, k, in_w, seed, 2, oracle.SEED_PER_SUBBLOCK)
+    assert np.array_equal(got, want)
+
+
+def test_ntt_independent_seeds_every_split():
+    n, m, s, k = 1 << 20, 8, 1 << 17, 1 << 15
+    in_w = synth.bernoulli_bits(n, 0.7, 43)
+    seed = synth.uniform_bits((s + k - 1) * m, 44)
+    want = oracle.extract(n, m, s, k, in_w, seed, 2, oracle.SEED_PER_SUBBLOCK)
+    for l in range(5):
+        got, desc = _run(n, m, s, k, X.EXTRACT_SEED_PER_SUBBLOCK | X.EXTRACT_METHOD_NTT | X.EXTRACT_NTT_SPLIT(l),
+                         in_w, seed)
+        assert " P=%d " % (1 << l) in desc, desc
+        assert np.array_equal(got, want), "split 2^%d" % l
+
+
+def test_ntt_independent_seeds_large_equal_direct():
+    n, m, s, k = 5_000_000, 9, 333_333, 77_777
+    in_w = synth.bernoulli_bits(n, 0.8, 45)
+    seed = synth.uniform_bits((s + k - 1) * m, 46)
+    a, da = _run(n, m, s, k, X.EXTRACT_SEED_PER_SUBBLOCK | X.EXTRACT_METHOD_NTT, in_w, seed)
+    b, db = _run(n, m, s, k, X.EXTRACT_SEED_PER_SUBBLOCK | X.EXTRACT_METHOD_DIRECT, in_w, seed)
+    assert da.startswith("ntt") and not db.startswith("ntt")
+    assert np.array_equal(a, b)
+    got = oracle.bits_of(a, m * k)
+    perm = oracle.perm(n, 2)
+    L = s + k - 1
+    rng = np.random.default_rng(5)
+    for j in (0, m - 1):
+        A = oracle.subblock(in_w, perm[j * s:(j + 1) * s])
+        for i in np.concatenate([[0, k - 1], rng.choice(k, 12, replace=False)]):
+            assert got[j * k + i] == oracle.toeplitz_bit(seed, s, A, int(i), off=j * L), (j, i)
+
+
 def test_ntt_flag_rejections():
     seed = np.zeros(10000, dtype=np.uint32)
     for n, m, s, k, fl in [
         (4096, 2, 1024, 512, 0),                                  # s + k - 1 <= 2^11
         (1 << 24, 1, 1 << 23, 1 << 22, 0),                       # s + k - 1 > 2^22
-        (2 ** 14, 2, 4096, 100, X.EXTRACT_SEED_PER_SUBBLOCK),     # one seed per sub-block
+        (2 ** 14, 2, 4096, 100, X.EXTRACT_SEED_PER_SUBBLOCK),     # one seed per sub-block needs N >= 2^16
         (2 ** 14, 2, 4096, 100, X.EXTRACT_METHOD_DIRECT),         # both methods
         (4096 * 2, 2, 2049, 1000, X.EXTRACT_NTT_SPLIT(4)),        # 16 pieces would leave one empty
         (4096 * 2, 2, 2049, 1000, 6 << 16),                       # split field out of range
