@@ -241,7 +241,8 @@ NTT_TRAFFIC_BYTES = {"qrng_n2^30_m1024_s2^20_k2^19": 139.4e6 * 128,
 
 
 def ntt_roofline(n, m, s, k, hash_ms, plan, sms=152, workload=None):
-    """NTT path: the transform work (forward + inverse, N/2 log2 N radix-2
+    """NTT path: the transform work (P forward pieces, P seed windows when
+    every sub-block has its own seed, one inverse; N/2 log2 N radix-2
     butterflies each, per sub-block) against the integer ALU pipe.  A lazy
     butterfly is 7 integer instructions, 4 of them (adds, subtracts, min) on
     the 64-lane ALU pipe and 3 IMAD on the FMA pipe, so the ALU pipe bounds
@@ -249,14 +250,17 @@ def ntt_roofline(n, m, s, k, hash_ms, plan, sms=152, workload=None):
     import math
     N = int(plan.split("N=")[1].split(" ")[0])
     P = int(plan.split("P=")[1].split(" ")[0]) if "P=" in plan else 1
-    bfly = m * (P + 1) * (N // 2) * math.log2(N)
+    transforms = (2 * P + 1) if "one seed per sub-block" in plan else (P + 1)
+    bfly = m * transforms * (N // 2) * math.log2(N)
     achieved = bfly / (hash_ms / 1e3) / 1e12
     peak = sms * 64 / 4.0 * 2070e6 / 1e12
     return {"bound": "alu", "achieved": achieved, "unit": "Tbutterfly/s", "peak": peak, "frac": achieved / peak,
             "traffic": NTT_TRAFFIC_BYTES.get(workload),
             "kernel": "the NTT hash: pass A (column DIF), pass B (rows), pass A' (column DIT) per launch group",
-            "work_per_launch": "m x (P+1) x N/2 log2 N = %.4g radix-2 butterflies mod p (N=%d, P=%d pieces "
-                               "per sub-block)" % (bfly, N, P),
+            "work_per_launch": "m x %d transforms x N/2 log2 N = %.4g radix-2 butterflies mod p (N=%d, P=%d "
+                               "pieces per sub-block%s)" % (transforms, bfly, N, P,
+                                                            ", seed windows transformed per run"
+                                                            if transforms == 2 * P + 1 else ""),
             "peak_basis": "%d SMs x 64 ALU lanes / 4 ALU ops per lazy butterfly x 2070 MHz" % sms,
             "note": "does %.0fx less work than the direct m*k*s product" % ((m * k * s / 32.0) / bfly)}
 
