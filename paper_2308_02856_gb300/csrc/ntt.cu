@@ -338,13 +338,18 @@ __global__ void ntt_twist_table_kernel(uint32_t *twf, uint32_t *twi, uint32_t R1
     }
 }
 
-// S = spectrum * N^-1 and its Shoup quotients.
-__global__ void ntt_finish_spectrum_kernel(uint32_t *S, uint32_t *Sq, uint32_t N, uint32_t ninv, uint32_t ninv_q)
+// The shared seed spectrum's pointwise products: Montgomery form (one word
+// per element) or Shoup form (value and quotient, two words).
+constexpr bool kSpectrumMont = true;
+
+// S = spectrum * N^-1 (Shoup: c = N^-1, with quotients Sq) or spectrum *
+// N^-1 * 2^32 (Montgomery form: c = N^-1 2^32, Sq unused).
+__global__ void ntt_finish_spectrum_kernel(uint32_t *S, uint32_t *Sq, uint32_t N, uint32_t c, uint32_t c_q)
 {
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
-        const uint32_t v = mul_shoup(S[i], ninv, ninv_q);
+        const uint32_t v = mul_shoup(S[i], c, c_q);
         S[i] = v;
-        Sq[i] = (uint32_t)(((uint64_t)v << 32) / kP);
+        if (!kSpectrumMont) Sq[i] = (uint32_t)(((uint64_t)v << 32) / kP);
     }
 }
 
@@ -551,18 +556,19 @@ ntt_rows_kernel(uint32_t *__restrict__ buf, uint32_t N, uint32_t R1, uint32_t P,
             *reinterpret_cast<uint4 *>(x + base + i) = make_uint4(e[i], e[i + 1], e[i + 2], e[i + 3]);
         return;
     }
+    constexpr bool kMont = kPerBlock || kSpectrumMont;
     if (!kMulti) {
-        if (kPerBlock) row_mul_mont<false>(e, e, Sb + so);
+        if (kMont) row_mul_mont<false>(e, e, Sb + so);
         else row_mul<false>(e, e, S + so, Sq + so);
         row_dit_store(e, x, sw, T, lane, w);
         return;
     }
     uint32_t acc[32];
-    if (kPerBlock) row_mul_mont<false>(e, acc, Sb + so);
+    if (kMont) row_mul_mont<false>(e, acc, Sb + so);
     else row_mul<false>(e, acc, S + so, Sq + so);
     for (uint32_t q = 1; q < P; ++q) {
         row_dif(e, x + (size_t)q * N, sw[w], T, lane, w);
-        if (kPerBlock) row_mul_mont<true>(e, acc, Sb + (size_t)q * N + so);
+        if (kMont) row_mul_mont<true>(e, acc, Sb + (size_t)q * N + so);
         else row_mul<true>(e, acc, S + (size_t)q * N + so, Sq + (size_t)q * N + so);
     }
     row_dit_store(acc, x, sw, T, lane, w);
@@ -1251,7 +1257,7 @@ int ntt_create(NttPlan **out, uint32_t m, uint32_t s, uint32_t k, const uint32_t
             break;  // no shared spectrum
         }
         if ((e = cudaMallocAsync(&p->S, spec * 4, st)) != cudaSuccess) { rc = cuda_error(e, "ntt spectrum"); break; }
-        if ((e = cudaMallocAsync(&p->Sq, spec * 4, st)) != cudaSuccess) { rc = cuda_error(e, "ntt spectrum"); break; }
+        if (!kSpectrumMont && (e = cudaMallocAsync(&p->Sq, spec * 4, st)) != cudaSuccess) { rc = cuda_error(e, "ntt spectrum"); break; }
         // seed spectra: for piece q, the window seed[q h .. q h + h + k - 1)
         // (zero past L = s + k - 1) through pass A + row DIF into S + q N;
         // then all are scaled by 1/N
@@ -1265,8 +1271,9 @@ int ntt_create(NttPlan **out, uint32_t m, uint32_t s, uint32_t k, const uint32_t
         }
         if (rc != EXTRACT_OK) break;
         const uint32_t ninv = powmod(p->N, kP - 2);
+        const uint32_t c = kSpectrumMont ? (uint32_t)((uint64_t)ninv * ((1ull << 32) % kP) % kP) : ninv;
         ntt_finish_spectrum_kernel<<<(uint32_t)std::min<uint64_t>(ceil_div(spec, 256), 4096), 256, 0, st>>>(
-            p->S, p->Sq, (uint32_t)spec, ninv, shoup_q(ninv));
+            p->S, p->Sq, (uint32_t)spec, c, shoup_q(c));
         if ((e = cudaGetLastError()) != cudaSuccess) { rc = cuda_error(e, "ntt spectrum kernels"); break; }
         if ((e = cudaStreamSynchronize(st)) != cudaSuccess) { rc = cuda_error(e, "ntt spectrum"); break; }
     } while (0);
