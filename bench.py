@@ -217,18 +217,25 @@ GATHER_WINDOW_BITS = 1 << 29  # inputs longer than this are gathered in one pass
 
 
 def launches_per_step(is_ntt, m, plan, n=0):
-    """Kernels of ours per step: the gather pass(es) + the hash (direct); for
-    the NTT method the whole-block gather + three transform passes per group
-    of sub-blocks, or (inputs over two gather windows) a gather per group."""
-    passes = -(-n // GATHER_WINDOW_BITS)
-    passes = passes if passes == 2 else 1  # windows only when they take two passes
+    """Kernels of ours per step: the gather (two stages with the bucket
+    tables, one pass per input window with the window-major order, else one
+    or two plain passes) + the hash (direct); for the NTT method three
+    transform passes per group of sub-blocks, and a plain gather per group
+    when the input is over two gather windows without tables."""
+    if "gather=buckets" in plan:
+        gather = 2
+    elif "gather=windows" in plan:
+        gather = int(plan.split("gather=windows (")[1].split(" ")[0])
+    else:
+        passes = -(-n // GATHER_WINDOW_BITS)
+        gather = passes if passes == 2 else 1  # windows only when they take two passes
     if not is_ntt:
-        return passes + 1
+        return gather + 1
     g = int(plan.split("sub-blocks per launch group")[0].split(",")[-1])
     groups = (m + g - 1) // g
-    if n <= 2 * GATHER_WINDOW_BITS:
-        return passes + 3 * groups
-    return 4 * groups
+    if "gather=plain" in plan and n > 2 * GATHER_WINDOW_BITS:
+        return 4 * groups
+    return gather + 3 * groups
 
 
 # DRAM bytes (read + write) of one NTT hash: the ncu capture of one launch
@@ -468,7 +475,9 @@ def run_ours(args):
                                     "(eps %g, p_sift 1/m)" % IID_EPS) if iid else "stable argsort, equal sub-blocks",
                        "seeds": {"input": IN_SEED, "sampling_key": SAMPLING_KEY, "toeplitz": TOEPLITZ_SEED},
                        "order": "resident (built once per sampling key; see create_ms)",
-                       "l2": "inputs larger than L2: 4n-byte order + n/8-byte input read per step",
+                       "l2": ("inputs larger than L2: bucket tables (2 B per sampled bit + 4 B per stored "
+                              "sub-block bit) + n/8-byte input read per step" if "gather=buckets" in plan else
+                              "inputs larger than L2: 4n-byte order + n/8-byte input read per step"),
                        "parallelism": "replicas" if world > 1 else "1 GPU",
                        "plan": plan},
             "method": "ntt" if is_ntt else "direct",

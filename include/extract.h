@@ -95,6 +95,20 @@ extern "C" {
    job fails and extract_server_wait returns EXTRACT_EABORT).  Needs
    n < 2^32 and m <= 2^16; not combinable with EXTRACT_IDENTITY_PERM. */
 #define EXTRACT_SAMPLING_IID      0x10u
+/* Gather (step 1's bit movement).  Default (neither flag): for inputs of at
+   least 2^22 bits the library compiles the order into bucket tables at
+   create time (a two-stage gather: each 2^16-bit input chunk regrouped by
+   sub-block in shared memory, then each sub-block permuted in shared
+   memory), which costs 2 bytes per sampled bit plus 4 bytes per stored
+   sub-block bit of extra device memory and makes no random global reads; it
+   needs m*s < 2^32, m <= 16384 and every sub-block's regrouped bits within
+   220 KiB, and otherwise (or without room) the plain gather is kept.
+   EXTRACT_GATHER_PLAIN keeps the plain gather (one random input read per
+   gathered bit); EXTRACT_GATHER_BUCKETS asks for the tables at any input
+   size (EXTRACT_EINVAL if the shape does not suit them).  Both give the
+   same sub-blocks.  Not combinable with EXTRACT_IDENTITY_PERM. */
+#define EXTRACT_GATHER_PLAIN      0x20u
+#define EXTRACT_GATHER_BUCKETS    0x40u
 
 typedef struct extract_ctx extract_ctx;
 

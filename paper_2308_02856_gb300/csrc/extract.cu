@@ -69,6 +69,7 @@ struct extract_ctx {
     cudaEvent_t ev_fork = nullptr, ev_group = nullptr;
     NttSecondLane lane2;                              // second lane of the NTT hash (own stream, buffer)
     GatherWindows gw;                                 // window-major order for inputs far above L2
+    GatherBuckets gb;                                 // bucketed two-stage gather tables
 };
 
 namespace {
@@ -77,7 +78,11 @@ namespace {
 constexpr bool kNttTwoLanes = true;
 
 constexpr uint32_t kKnownFlags = EXTRACT_SEED_PER_SUBBLOCK | EXTRACT_IDENTITY_PERM | EXTRACT_METHOD_DIRECT |
-                                  EXTRACT_METHOD_NTT | EXTRACT_SAMPLING_IID | (0x3fu << 8) | (0x7u << 16);
+                                  EXTRACT_METHOD_NTT | EXTRACT_SAMPLING_IID | EXTRACT_GATHER_PLAIN |
+                                  EXTRACT_GATHER_BUCKETS | (0x3fu << 8) | (0x7u << 16);
+
+// Smallest input that gets the bucketed gather by default
+constexpr uint64_t kBucketsMinBits = 1ull << 22;
 
 void free_ctx(extract_ctx *h)
 {
@@ -92,6 +97,7 @@ void free_ctx(extract_ctx *h)
     if (h->ev_group) cudaEventDestroy(h->ev_group);
     if (h->aux) cudaStreamDestroy(h->aux);
     gather_windows_free(&h->gw);
+    gather_buckets_free(&h->gb);
     cudaFree(h->lane2.work);
     if (h->lane2.ev_fork) cudaEventDestroy(h->lane2.ev_fork);
     if (h->lane2.ev_join) cudaEventDestroy(h->lane2.ev_join);
@@ -153,6 +159,10 @@ int extract_create(extract_ctx **out, uint64_t n, uint32_t m, uint32_t s, uint32
     }
     if ((flags & EXTRACT_METHOD_DIRECT) && (flags & EXTRACT_METHOD_NTT))
         return set_error(EXTRACT_EINVAL, "EXTRACT_METHOD_DIRECT and EXTRACT_METHOD_NTT are exclusive");
+    if ((flags & EXTRACT_GATHER_PLAIN) && (flags & EXTRACT_GATHER_BUCKETS))
+        return set_error(EXTRACT_EINVAL, "EXTRACT_GATHER_PLAIN and EXTRACT_GATHER_BUCKETS are exclusive");
+    if (ident && (flags & EXTRACT_GATHER_BUCKETS))
+        return set_error(EXTRACT_EINVAL, "EXTRACT_GATHER_BUCKETS needs a sampled order (not EXTRACT_IDENTITY_PERM)");
     const uint32_t split_field = (flags >> 16) & 0x7u;
     if (split_field > 5) return set_error(EXTRACT_EINVAL, "EXTRACT_NTT_SPLIT takes 0 .. 4");
     const int split = (int)split_field - 1;  // -1: automatic
@@ -237,7 +247,21 @@ int extract_create(extract_ctx **out, uint64_t n, uint32_t m, uint32_t s, uint32
         if ((e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) != cudaSuccess) { free_ctx(h); return cuda_error(e, "stream"); }
         int rc = iid ? build_iid_order(n, sampling_key, mask, m, s, h->perm, &h->sizes, st, h->num_sms)
                      : build_perm(n, sampling_key, mask, h->perm, st, h->num_sms);
-        if (rc == EXTRACT_OK && !iid && gather_windows_wanted(n))
+        const bool want_buckets = (flags & EXTRACT_GATHER_BUCKETS) ||
+                                  (!(flags & EXTRACT_GATHER_PLAIN) && n >= kBucketsMinBits);
+        bool have_buckets = false;
+        if (rc == EXTRACT_OK && want_buckets) {
+            rc = gather_buckets_build(h->perm, h->perm_len, n, m, s, h->w_pad, &h->gb, st, h->num_sms);
+            if (rc == kBucketsNotEligible) {
+                rc = (flags & EXTRACT_GATHER_BUCKETS)
+                         ? set_error(EXTRACT_EINVAL, "EXTRACT_GATHER_BUCKETS: the shape does not suit the bucket "
+                                                     "tables (m*s < 2^32, m <= 16384, regions within 220 KiB)")
+                         : EXTRACT_OK;
+            } else {
+                have_buckets = rc == EXTRACT_OK;
+            }
+        }
+        if (rc == EXTRACT_OK && !have_buckets && !iid && gather_windows_wanted(n))
             rc = gather_windows_build(h->perm, m, s, h->w_pad, n, &h->gw, st, h->num_sms);
         cudaStreamDestroy(st);
         if (rc != EXTRACT_OK) { free_ctx(h); return rc; }
@@ -251,6 +275,8 @@ int extract_gather(extract_ctx *h, void *stream, const uint32_t *in_bits_dev)
 {
     if (int rc = check_ctx(h)) return rc;
     if (!in_bits_dev) return set_error(EXTRACT_EINVAL, "in_bits_dev is null");
+    if (h->gb.pi)
+        return gather_buckets_run(h->gb, in_bits_dev, h->n, h->m, h->w_pad, h->arev, (cudaStream_t)stream, h->num_sms);
     if (h->gw.pos) return gather_windows_run(h->gw, in_bits_dev, h->w_pad, h->arev, (cudaStream_t)stream, h->num_sms);
     return launch_gather(in_bits_dev, h->perm, h->m, h->s, h->w_pad, h->arev, (cudaStream_t)stream,
                          h->num_sms, 0, h->iid, h->n);
@@ -275,7 +301,7 @@ int extract_run(extract_ctx *h, void *stream, const uint32_t *in_bits_dev, uint3
     // ms/step against 26.7 overlapped), except for large inputs without the
     // window-major order (the i.i.d. law), whose gather waits on DRAM and is
     // overlapped group by group with the transforms.
-    if (h->ntt && !h->gw.pos && !gather_prefers_whole_block(h->n)) {
+    if (h->ntt && !h->gw.pos && !h->gb.pi && !gather_prefers_whole_block(h->n)) {
         if (!in_bits_dev) return set_error(EXTRACT_EINVAL, "in_bits_dev is null");
         return ntt_run_overlapped(h->ntt, in_bits_dev, h->perm, h->arev, h->w_pad, h->m, h->s, h->k, out_bits_dev,
                                   (cudaStream_t)stream, h->aux, h->ev_fork, h->ev_group, h->num_sms, h->iid, h->n);
@@ -381,20 +407,27 @@ int extract_describe(extract_ctx *h, char *buf, uint32_t buflen)
     if (int rc = check_ctx(h)) return rc;
     if (!buf || !buflen) return set_error(EXTRACT_EINVAL, "empty buffer");
     const HashPlan &p = h->plan;
+    char gather[96];
+    if (h->gb.pi)
+        snprintf(gather, sizeof gather, "gather=buckets (2^16-bit chunks, %u-word sub-block regions)", h->gb.bstride);
+    else if (h->gw.pos)
+        snprintf(gather, sizeof gather, "gather=windows (%u input windows)", h->gw.R);
+    else
+        snprintf(gather, sizeof gather, "gather=plain");
     if (h->ntt) {
         snprintf(buf, buflen,
                  "ntt: N=%u (%u x 2048) P=%u pieces per sub-block, %u sub-blocks per launch group, "
-                 "prime 7*2^26+1, %s; sms=%d",
+                 "prime 7*2^26+1, %s; sms=%d; %s",
                  ntt_size(h->ntt), ntt_size(h->ntt) / 2048, ntt_pieces(h->ntt), ntt_group(h->ntt),
                  h->nseeds > 1 ? "seed windows transformed per run (one seed per sub-block)" : "shared seed spectrum",
-                 h->num_sms);
+                 h->num_sms, gather);
         return EXTRACT_OK;
     }
     snprintf(buf, buflen,
              "lop3 tile: rows=%u (q=%d x %d warps x 32) subblocks=%d words/chunk=%d grid=%ux%ux%u "
-             "(row tiles %u, sub-block tiles %u, split-K %u x %u chunks) w_pad=%u sms=%d",
+             "(row tiles %u, sub-block tiles %u, split-K %u x %u chunks) w_pad=%u sms=%d; %s",
              p.rows(), p.q, p.warps, p.j, p.wc, p.gx * p.gy, 1u, p.splits, p.gx, p.gy, p.splits, p.cps,
-             h->w_pad, h->num_sms);
+             h->w_pad, h->num_sms, gather);
     return EXTRACT_OK;
 }
 

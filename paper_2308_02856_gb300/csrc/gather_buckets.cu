@@ -1,0 +1,399 @@
+// Bucketed gather of the sub-blocks (Sec. III.B step 1), in two stages.
+//
+// The plain gather reads one random input bit per sub-block bit, and every
+// such read costs a whole 32-byte sector: the gather is bound by the sector
+// rate, not by bytes.  Here, once per sampling key, the fixed map from input
+// positions to sub-block slots is compiled into two tables so that a run
+// reads every input word once and does its random bit reads in shared
+// memory:
+//
+//   stage 1, per input chunk of kChunkBits positions (one CTA, the chunk's
+//     words in shared memory): the chunk's sampled bits are regrouped by
+//     sub-block, each sub-block's bits in increasing position order and
+//     padded to whole words ("runs"); every run word is stored into that
+//     sub-block's region of the run buffer B.  Table: for every run word, the
+//     32 in-chunk positions of its bits (16-bit, pairs in one 32-bit word)
+//     and the word's place in B.
+//   stage 2, per sub-block j (one CTA, B_j in shared memory): B_j holds the
+//     members of sub-block j, chunk by chunk; stored bit c of the sub-block
+//     is the member sigma_j[c] of B_j.  Table: sigma, one 32-bit index per
+//     stored bit (kNoPos: a zero bit, past s or past |S_j|).
+//
+// Both tables are read in order (each warp instruction loads 128 contiguous
+// bytes), the input and B move once each, and the stored words equal the
+// plain gather's: word w of sub-block j has bit l = in[perm[j s + s-1 - c]]
+// with c = 32 w + l (0 when c >= s or the slot is padding).
+//
+// Layouts (a group = 32 consecutive words, lane l = word 32 g + l):
+//   pi   [word group g][bit pair b2 < 16][lane]   (bit 2 b2 | bit 2 b2+1 << 16)
+//   dst  [run word]                                word index into B, or kNoPos
+//   qc   [chunk + 1]                               first run word of a chunk
+//                                                  (multiples of 32)
+//   sigma[j][word group g][bit b][lane]            member bit index in B_j
+//   B    [j][bstride words]
+#include "common.cuh"
+#include "internal.h"
+
+#include <algorithm>
+#include <cstdio>
+#include <vector>
+
+namespace ex {
+namespace {
+
+constexpr uint32_t kChunkBits = 1u << 16;
+constexpr uint32_t kChunkWords = kChunkBits / 32;
+constexpr uint32_t kMaxBuckets = 16384;          // sub-blocks with per-chunk counters in shared memory
+constexpr size_t kStage2SmemMax = 220 * 1024;    // bytes of B_j a stage-2 CTA holds
+constexpr int kStage1Warps = 8;
+constexpr int kStage2Warps = 32;
+
+__host__ __device__ __forceinline__ uint32_t words_of(uint32_t bits) { return (bits + 31u) >> 5; }
+
+// inv[perm[X]] = X for the slots X < len that hold a position.
+__global__ void bk_inv_kernel(const uint32_t *__restrict__ perm, uint64_t len, uint32_t *__restrict__ inv)
+{
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t X = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; X < len; X += stride) {
+        const uint32_t p = perm[X];
+        if (p != kNoPos) inv[p] = (uint32_t)X;
+    }
+}
+
+// cnt[c * m + j] = #{p in chunk c : inv[p] != kNoPos, inv[p] / s = j}
+__global__ void __launch_bounds__(512)
+bk_count_kernel(const uint32_t *__restrict__ inv, uint64_t n, uint32_t s, uint32_t m, uint32_t nch,
+                uint32_t *__restrict__ cnt)
+{
+    extern __shared__ uint32_t hist[];  // m
+    for (uint32_t c = blockIdx.x; c < nch; c += gridDim.x) {
+        for (uint32_t j = threadIdx.x; j < m; j += blockDim.x) hist[j] = 0;
+        __syncthreads();
+        const uint64_t p0 = (uint64_t)c * kChunkBits, p1 = min(n, p0 + kChunkBits);
+        for (uint64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+            const uint32_t X = inv[p];
+            if (X != kNoPos) atomicAdd(&hist[X / s], 1u);
+        }
+        __syncthreads();
+        for (uint32_t j = threadIdx.x; j < m; j += blockDim.x) cnt[(size_t)c * m + j] = hist[j];
+        __syncthreads();
+    }
+}
+
+// Per chunk (one CTA): wpre[c * (m + 1) + j] = run words of sub-blocks < j
+// in chunk c; chunk_words[c] = round_up(all of them, 32).
+__global__ void __launch_bounds__(1024)
+bk_chunk_scan_kernel(const uint32_t *__restrict__ cnt, uint32_t m, uint32_t nch, uint32_t *__restrict__ wpre,
+                     uint32_t *__restrict__ chunk_words)
+{
+    __shared__ uint32_t warp_tot[32];
+    __shared__ uint32_t carry;
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    for (uint32_t c = blockIdx.x; c < nch; c += gridDim.x) {
+        if (threadIdx.x == 0) carry = 0;
+        __syncthreads();
+        for (uint32_t j0 = 0; j0 < m; j0 += blockDim.x) {
+            const uint32_t j = j0 + threadIdx.x;
+            const uint32_t v = j < m ? words_of(cnt[(size_t)c * m + j]) : 0u;
+            uint32_t x = v;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t o = __shfl_up_sync(0xffffffffu, x, d);
+                if ((int)lane >= d) x += o;
+            }
+            if (lane == 31) warp_tot[warp] = x;
+            __syncthreads();
+            uint32_t wb = 0;
+            for (uint32_t w = 0; w < warp; ++w) wb += warp_tot[w];
+            const uint32_t base = carry;
+            if (j < m) wpre[(size_t)c * (m + 1) + j] = base + wb + x - v;
+            __syncthreads();
+            if (threadIdx.x == blockDim.x - 1) carry = base + wb + x;
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            wpre[(size_t)c * (m + 1) + m] = carry;
+            chunk_words[c] = (carry + 31u) & ~31u;
+        }
+        __syncthreads();
+    }
+}
+
+// Per sub-block (one thread): mw[c * m + j] = run words of sub-block j in
+// chunks < c; total[j] = all of them.  Loads go 16 chunks ahead.
+__global__ void bk_block_scan_kernel(const uint32_t *__restrict__ cnt, uint32_t m, uint32_t nch,
+                                     uint32_t *__restrict__ mw, uint32_t *__restrict__ total)
+{
+    constexpr uint32_t kAhead = 16;
+    const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= m) return;
+    uint32_t run = 0;
+    for (uint32_t c0 = 0; c0 < nch; c0 += kAhead) {
+        uint32_t v[kAhead];
+#pragma unroll
+        for (uint32_t t = 0; t < kAhead; ++t) v[t] = c0 + t < nch ? cnt[(size_t)(c0 + t) * m + j] : 0u;
+#pragma unroll
+        for (uint32_t t = 0; t < kAhead; ++t) {
+            if (c0 + t < nch) mw[(size_t)(c0 + t) * m + j] = run;
+            run += words_of(v[t]);
+        }
+    }
+    total[j] = run;
+}
+
+// dst of every run word: chunk c's run of sub-block j, word t -> j * bstride
+// + mw[c][j] + t (padding words of a chunk keep kNoPos from the memset).
+__global__ void __launch_bounds__(256)
+bk_dst_kernel(const uint32_t *__restrict__ cnt, const uint32_t *__restrict__ wpre, const uint32_t *__restrict__ mw,
+              const uint32_t *__restrict__ qc, uint32_t m, uint32_t nch, uint32_t bstride, uint32_t *__restrict__ dst)
+{
+    for (uint32_t c = blockIdx.x; c < nch; c += gridDim.x) {
+        const uint32_t q0 = qc[c];
+        for (uint32_t j = threadIdx.x; j < m; j += blockDim.x) {
+            const uint32_t nw = words_of(cnt[(size_t)c * m + j]);
+            const uint32_t at = q0 + wpre[(size_t)c * (m + 1) + j];
+            const uint32_t to = j * bstride + mw[(size_t)c * m + j];
+            for (uint32_t t = 0; t < nw; ++t) dst[at + t] = to + t;
+        }
+    }
+}
+
+// One warp per chunk walks its positions in increasing order, 32 at a time;
+// lanes of the same sub-block find each other with a match and a per-sub-block
+// counter in shared memory carries their rank r inside the chunk's run.
+// Member r of run (c, j) is bit r % 32 of run word r / 32:
+//   pi:    that bit's in-chunk position;
+//   sigma: stored bit s-1-x of sub-block j (x = its slot) -> 32 mw[c][j] + r.
+template <int kWarps>
+__global__ void __launch_bounds__(kWarps * 32)
+bk_fill_kernel(const uint32_t *__restrict__ inv, uint64_t n, uint32_t s, uint32_t m, uint32_t nch,
+               uint32_t w_pad, const uint32_t *__restrict__ wpre, const uint32_t *__restrict__ mw,
+               const uint32_t *__restrict__ qc, uint16_t *__restrict__ pi, uint32_t *__restrict__ sigma)
+{
+    extern __shared__ uint32_t ctr_all[];  // kWarps x m
+    const uint32_t lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
+    uint32_t *ctr = ctr_all + (size_t)w * m;
+    const uint32_t below = (1u << lane) - 1u;
+    const uint32_t gps = w_pad >> 5;  // word groups per stored sub-block
+    for (uint32_t c = blockIdx.x * kWarps + w; c < nch; c += gridDim.x * kWarps) {
+        for (uint32_t j = lane; j < m; j += 32) ctr[j] = 0;
+        __syncwarp();
+        const uint64_t p0 = (uint64_t)c * kChunkBits, p1 = min(n, p0 + kChunkBits);
+        const uint32_t q0 = qc[c];
+        for (uint64_t b = p0; b < p1; b += 32) {
+            const uint64_t p = b + lane;
+            const uint32_t X = p < p1 ? inv[p] : kNoPos;
+            const bool live = X != kNoPos;
+            // dead lanes take sub-block m, which no live lane has
+            const uint32_t j = live ? X / s : m;
+            const uint32_t peers = __match_any_sync(0xffffffffu, j);
+            const uint32_t base = live ? ctr[j] : 0u;
+            __syncwarp();
+            if (live) {
+                const uint32_t r = base + __popc(peers & below);
+                if ((peers & below) == 0) ctr[j] = base + __popc(peers);  // the lowest lane of each sub-block
+                const uint32_t q = q0 + wpre[(size_t)c * (m + 1) + j] + (r >> 5);  // run word
+                const uint32_t bit = r & 31u;
+                pi[((((size_t)(q >> 5) * 16u + (bit >> 1)) * 32u + (q & 31u)) << 1) | (bit & 1u)] =
+                    (uint16_t)(p - p0);
+                const uint32_t cs = s - 1u - (X - j * s);  // stored bit of the slot
+                const uint32_t wd = cs >> 5;
+                sigma[(((size_t)j * gps + (wd >> 5)) * 32u + (cs & 31u)) * 32u + (wd & 31u)] =
+                    (mw[(size_t)c * m + j] << 5) + r;
+            }
+            __syncwarp();
+        }
+        __syncwarp();
+    }
+}
+
+// Stage 1: one chunk per CTA iteration; one warp per group of 32 run words.
+__global__ void __launch_bounds__(kStage1Warps * 32)
+bk_stage1_kernel(const uint32_t *__restrict__ in, uint64_t in_words, const uint32_t *__restrict__ pi,
+                 const uint32_t *__restrict__ dst, const uint32_t *__restrict__ qc, uint32_t nch,
+                 uint32_t *__restrict__ B)
+{
+    __shared__ __align__(16) uint32_t cw[kChunkWords];
+    const uint32_t lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
+    const bool aligned = (reinterpret_cast<uintptr_t>(in) & 15u) == 0;
+    for (uint32_t c = blockIdx.x; c < nch; c += gridDim.x) {
+        const uint64_t w0 = (uint64_t)c * kChunkWords;
+        if (aligned && w0 + kChunkWords <= in_words) {
+            const uint4 *src = reinterpret_cast<const uint4 *>(in + w0);
+            for (uint32_t t = threadIdx.x; t < kChunkWords / 4; t += blockDim.x)
+                reinterpret_cast<uint4 *>(cw)[t] = __ldcs(src + t);
+        } else {
+            for (uint32_t t = threadIdx.x; t < kChunkWords; t += blockDim.x)
+                cw[t] = w0 + t < in_words ? __ldcs(in + w0 + t) : 0u;
+        }
+        __syncthreads();
+        const uint32_t g0 = qc[c] >> 5, g1 = qc[c + 1] >> 5;
+        for (uint32_t g = g0 + w; g < g1; g += kStage1Warps) {
+            const uint32_t *pg = pi + (size_t)g * 16u * 32u + lane;
+            uint32_t pr[16];
+#pragma unroll
+            for (int b2 = 0; b2 < 16; ++b2) pr[b2] = __ldcs(pg + b2 * 32);
+            const uint32_t to = __ldcs(dst + (size_t)g * 32u + lane);
+            uint32_t word = 0;
+#pragma unroll
+            for (int b2 = 0; b2 < 16; ++b2) {
+                const uint32_t lo = pr[b2] & 0xffffu, hi = pr[b2] >> 16;
+                word |= ((cw[lo >> 5] >> (lo & 31u)) & 1u) << (2 * b2);
+                word |= ((cw[hi >> 5] >> (hi & 31u)) & 1u) << (2 * b2 + 1);
+            }
+            if (to != kNoPos) B[to] = word;
+        }
+        __syncthreads();
+    }
+}
+
+// Stage 2: one sub-block per CTA iteration (B_j in shared memory); one warp
+// per group of 32 stored words.
+__global__ void __launch_bounds__(kStage2Warps * 32)
+bk_stage2_kernel(const uint32_t *__restrict__ B, uint32_t bstride, const uint32_t *__restrict__ sigma, uint32_t m,
+                 uint32_t w_pad, uint32_t *__restrict__ arev)
+{
+    extern __shared__ __align__(16) uint32_t bj[];  // bstride words
+    const uint32_t lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
+    const uint32_t gps = w_pad >> 5;
+    for (uint32_t j = blockIdx.x; j < m; j += gridDim.x) {
+        const uint4 *src = reinterpret_cast<const uint4 *>(B + (size_t)j * bstride);
+        for (uint32_t t = threadIdx.x; t < bstride / 4; t += blockDim.x) reinterpret_cast<uint4 *>(bj)[t] = __ldcs(src + t);
+        __syncthreads();
+        for (uint32_t g = w; g < gps; g += kStage2Warps) {
+            const uint32_t *sg = sigma + ((size_t)j * gps + g) * 1024u + lane;
+            uint32_t v[32];
+#pragma unroll
+            for (int b = 0; b < 32; ++b) v[b] = __ldcs(sg + b * 32);
+            uint32_t word = 0;
+#pragma unroll
+            for (int b = 0; b < 32; ++b)
+                if (v[b] != kNoPos) word |= ((bj[v[b] >> 5] >> (v[b] & 31u)) & 1u) << b;
+            __stcs(arev + (size_t)j * w_pad + (size_t)g * 32u + lane, word);
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+int gather_buckets_build(const uint32_t *perm, uint64_t perm_len, uint64_t n, uint32_t m, uint32_t s, uint32_t w_pad,
+                         GatherBuckets *gb, cudaStream_t st, int num_sms)
+{
+    gather_buckets_free(gb);
+    if ((uint64_t)m * s >= (1ull << 32) || n >= (1ull << 32) || m > kMaxBuckets || w_pad % 32u || n == 0)
+        return kBucketsNotEligible;
+    const uint32_t nch = (uint32_t)ceil_div(n, kChunkBits);
+    if ((uint64_t)nch * (m + 1) >= (1ull << 32)) return kBucketsNotEligible;
+    uint32_t *inv = nullptr, *cnt = nullptr, *wpre = nullptr, *mw = nullptr, *cwords = nullptr, *total = nullptr;
+    int rc = EXTRACT_OK;
+    cudaError_t e = cudaSuccess;
+    auto fail = [&](int code) { if (rc == EXTRACT_OK) rc = code; };
+    do {
+        if ((e = cudaMallocAsync(&inv, n * 4, st)) != cudaSuccess ||
+            (e = cudaMallocAsync(&cnt, (size_t)nch * m * 4, st)) != cudaSuccess ||
+            (e = cudaMallocAsync(&wpre, (size_t)nch * (m + 1) * 4, st)) != cudaSuccess ||
+            (e = cudaMallocAsync(&mw, (size_t)nch * m * 4, st)) != cudaSuccess ||
+            (e = cudaMallocAsync(&cwords, (size_t)(nch + 1) * 4, st)) != cudaSuccess ||
+            (e = cudaMallocAsync(&total, (size_t)m * 4, st)) != cudaSuccess) {
+            cudaGetLastError();
+            fail(kBucketsNotEligible);  // no room for the tables
+            break;
+        }
+        if ((e = cudaMemsetAsync(inv, 0xff, n * 4, st)) != cudaSuccess) { fail(cuda_error(e, "memset")); break; }
+        const uint64_t len = std::min<uint64_t>(perm_len, (uint64_t)m * s);
+        bk_inv_kernel<<<(uint32_t)std::min<uint64_t>(ceil_div(len, 256), (uint64_t)num_sms * 32), 256, 0, st>>>(perm, len, inv);
+        if ((e = cudaFuncSetAttribute(bk_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(m * 4))) !=
+            cudaSuccess) { fail(cuda_error(e, "smem attribute")); break; }
+        bk_count_kernel<<<std::min<uint32_t>(nch, (uint32_t)num_sms * 4), 512, m * 4, st>>>(inv, n, s, m, nch, cnt);
+        bk_chunk_scan_kernel<<<std::min<uint32_t>(nch, (uint32_t)num_sms * 2), 1024, 0, st>>>(cnt, m, nch, wpre, cwords);
+        bk_block_scan_kernel<<<(uint32_t)ceil_div(m, 128), 128, 0, st>>>(cnt, m, nch, mw, total);
+        if ((e = cudaGetLastError()) != cudaSuccess) { fail(cuda_error(e, "bucket scans")); break; }
+        // host: the chunk starts (qc) and the widest sub-block region
+        std::vector<uint32_t> hw(nch), ht(m);
+        if ((e = cudaMemcpyAsync(hw.data(), cwords, (size_t)nch * 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(ht.data(), total, (size_t)m * 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(st)) != cudaSuccess) { fail(cuda_error(e, "bucket sizes")); break; }
+        const uint32_t widest = *std::max_element(ht.begin(), ht.end());
+        const uint32_t bstride = std::max<uint32_t>(4, (widest + 3u) & ~3u);
+        if ((size_t)bstride * 4 > kStage2SmemMax) { fail(kBucketsNotEligible); break; }  // B_j too wide
+        std::vector<uint32_t> hq(nch + 1);
+        uint64_t q = 0;
+        for (uint32_t c = 0; c < nch; ++c) {
+            hq[c] = (uint32_t)q;
+            q += hw[c];
+        }
+        if (q >= (1ull << 32) || (uint64_t)m * bstride >= (1ull << 32)) { fail(kBucketsNotEligible); break; }
+        hq[nch] = (uint32_t)q;
+        gb->nch = nch;
+        gb->bstride = bstride;
+        gb->run_words = q;
+        const uint64_t sig_len = (uint64_t)m * w_pad * 32;
+        if ((e = cudaMalloc(&gb->qc, (size_t)(nch + 1) * 4)) != cudaSuccess ||
+            (e = cudaMalloc(&gb->pi, std::max<uint64_t>(q, 1) * 64)) != cudaSuccess ||
+            (e = cudaMalloc(&gb->dst, std::max<uint64_t>(q, 1) * 4)) != cudaSuccess ||
+            (e = cudaMalloc(&gb->sigma, sig_len * 4)) != cudaSuccess ||
+            (e = cudaMalloc(&gb->B, (size_t)m * bstride * 4)) != cudaSuccess) {
+            cudaGetLastError();
+            fail(kBucketsNotEligible);  // no room for the tables
+            break;
+        }
+        if ((e = cudaMemcpyAsync(gb->qc, hq.data(), (size_t)(nch + 1) * 4, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+            (e = cudaMemsetAsync(gb->pi, 0, std::max<uint64_t>(q, 1) * 64, st)) != cudaSuccess ||
+            (e = cudaMemsetAsync(gb->dst, 0xff, std::max<uint64_t>(q, 1) * 4, st)) != cudaSuccess ||
+            (e = cudaMemsetAsync(gb->sigma, 0xff, sig_len * 4, st)) != cudaSuccess ||
+            (e = cudaMemsetAsync(gb->B, 0, (size_t)m * bstride * 4, st)) != cudaSuccess) {
+            fail(cuda_error(e, "bucket tables init"));
+            break;
+        }
+        bk_dst_kernel<<<std::min<uint32_t>(nch, (uint32_t)num_sms * 8), 256, 0, st>>>(cnt, wpre, mw, gb->qc, m, nch,
+                                                                                 bstride, gb->dst);
+        if ((e = cudaGetLastError()) != cudaSuccess) { fail(cuda_error(e, "bk_dst_kernel")); break; }
+        const size_t per_warp = (size_t)m * 4;
+        const int warps = (int)std::min<size_t>(8, std::max<size_t>(1, (size_t)(96 * 1024) / per_warp));
+#define EX_BK_FILL(W)                                                                                               \
+    if (warps >= W) {                                                                                               \
+        const size_t smem = per_warp * W;                                                                           \
+        if ((e = cudaFuncSetAttribute(bk_fill_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != \
+            cudaSuccess) { fail(cuda_error(e, "smem attribute")); break; }                                           \
+        bk_fill_kernel<W><<<(uint32_t)std::min<uint64_t>(ceil_div(nch, W), (uint64_t)num_sms * 8), W * 32, smem, st>>>( \
+            inv, n, s, m, nch, w_pad, wpre, mw, gb->qc, reinterpret_cast<uint16_t *>(gb->pi), gb->sigma);        \
+    } else
+        EX_BK_FILL(8) EX_BK_FILL(4) EX_BK_FILL(2) EX_BK_FILL(1) {}
+#undef EX_BK_FILL
+        if (rc != EXTRACT_OK) break;
+        if ((e = cudaGetLastError()) != cudaSuccess) { fail(cuda_error(e, "bk_fill_kernel")); break; }
+        if ((e = cudaFuncSetAttribute(bk_stage2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)kStage2SmemMax)) != cudaSuccess) { fail(cuda_error(e, "smem attribute")); break; }
+    } while (0);
+    for (void *ptr : {(void *)inv, (void *)cnt, (void *)wpre, (void *)mw, (void *)cwords, (void *)total})
+        if (ptr) cudaFreeAsync(ptr, st);
+    const cudaError_t se = cudaStreamSynchronize(st);
+    if (rc == EXTRACT_OK && se != cudaSuccess) rc = cuda_error(se, "bucket gather build");
+    if (rc != EXTRACT_OK) gather_buckets_free(gb);
+    return rc;
+}
+
+int gather_buckets_run(const GatherBuckets &gb, const uint32_t *in, uint64_t n, uint32_t m, uint32_t w_pad,
+                       uint32_t *arev, cudaStream_t st, int num_sms)
+{
+    bk_stage1_kernel<<<std::min<uint32_t>(gb.nch, (uint32_t)num_sms * 8), kStage1Warps * 32, 0, st>>>(
+        in, ceil_div(n, 32), gb.pi, gb.dst, gb.qc, gb.nch, gb.B);
+    EX_LAUNCH("bk_stage1_kernel");
+    bk_stage2_kernel<<<std::min<uint32_t>(m, (uint32_t)num_sms), kStage2Warps * 32, (size_t)gb.bstride * 4, st>>>(
+        gb.B, gb.bstride, gb.sigma, m, w_pad, arev);
+    EX_LAUNCH("bk_stage2_kernel");
+    return EXTRACT_OK;
+}
+
+void gather_buckets_free(GatherBuckets *gb)
+{
+    cudaFree(gb->qc);
+    cudaFree(gb->pi);
+    cudaFree(gb->dst);
+    cudaFree(gb->sigma);
+    cudaFree(gb->B);
+    *gb = GatherBuckets{};
+}
+
+}  // namespace ex

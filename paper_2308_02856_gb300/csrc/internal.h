@@ -64,6 +64,31 @@ int gather_windows_run(const GatherWindows &gw, const uint32_t *in, uint32_t w_p
                        int num_sms);
 void gather_windows_free(GatherWindows *gw);
 
+// Bucketed two-stage gather (gather_buckets.cu): per sampling key, tables
+// that regroup every input chunk's bits by sub-block (stage 1) and then
+// permute each sub-block's members in shared memory (stage 2), so a run
+// reads the input once and makes no random global reads.  Same words as
+// launch_gather.
+struct GatherBuckets {
+    uint32_t *qc = nullptr;     // chunks + 1: first run word of each chunk
+    uint32_t *pi = nullptr;     // 16 words per run word: in-chunk positions of its 32 bits
+    uint32_t *dst = nullptr;    // run words: word index into B (kNoPos: padding)
+    uint32_t *sigma = nullptr;  // m * w_pad * 32: member bit of every stored bit
+    uint32_t *B = nullptr;      // m * bstride words: the runs of each sub-block
+    uint32_t nch = 0;           // input chunks
+    uint32_t bstride = 0;       // words per sub-block region of B
+    uint64_t run_words = 0;     // run words over all chunks
+};
+// Returned by gather_buckets_build when the shape does not suit the tables
+// (too many sub-blocks, a region wider than shared memory, no room); the
+// caller keeps the plain gather.
+constexpr int kBucketsNotEligible = 1;
+int gather_buckets_build(const uint32_t *perm, uint64_t perm_len, uint64_t n, uint32_t m, uint32_t s, uint32_t w_pad,
+                         GatherBuckets *gb, cudaStream_t st, int num_sms);
+int gather_buckets_run(const GatherBuckets &gb, const uint32_t *in, uint64_t n, uint32_t m, uint32_t w_pad,
+                       uint32_t *arev, cudaStream_t st, int num_sms);
+void gather_buckets_free(GatherBuckets *gb);
+
 // ---- steps 2-3: the Toeplitz product and concatenation ------------------
 struct HashPlan {
     int variant = 7;      // tile variant (see hash_tile.cuh)

@@ -30,6 +30,8 @@ EXTRACT_IDENTITY_PERM = 0x2
 EXTRACT_METHOD_DIRECT = 0x4
 EXTRACT_METHOD_NTT = 0x8
 EXTRACT_SAMPLING_IID = 0x10
+EXTRACT_GATHER_PLAIN = 0x20
+EXTRACT_GATHER_BUCKETS = 0x40
 NO_POS = 0xFFFFFFFF  # padding slot of the i.i.d. law's order
 
 
