@@ -67,15 +67,16 @@ struct extract_ctx {
     NttPlan *ntt = nullptr;  // set when the NTT method hashes this shape
     cudaStream_t aux = nullptr;                       // gather stream of the overlapped NTT run
     cudaEvent_t ev_fork = nullptr, ev_group = nullptr;
-    NttSecondLane lane2;                              // second lane of the NTT hash (own stream, buffer)
+    NttLanes lanes;                                   // extra lanes of the NTT hash (own streams, buffers)
     GatherWindows gw;                                 // window-major order for inputs far above L2
     GatherBuckets gb;                                 // bucketed two-stage gather tables
 };
 
 namespace {
 
-// NTT hash on two lanes (alternating launch groups)
-constexpr bool kNttTwoLanes = true;
+// NTT hash lanes (launch groups dealt round robin over streams)
+constexpr uint32_t kNttLanes = 2;
+static_assert(kNttLanes >= 1 && kNttLanes <= (uint32_t)kMaxNttLanes, "NTT lane count");
 
 constexpr uint32_t kKnownFlags = EXTRACT_SEED_PER_SUBBLOCK | EXTRACT_IDENTITY_PERM | EXTRACT_METHOD_DIRECT |
                                   EXTRACT_METHOD_NTT | EXTRACT_SAMPLING_IID | EXTRACT_GATHER_PLAIN |
@@ -98,10 +99,12 @@ void free_ctx(extract_ctx *h)
     if (h->aux) cudaStreamDestroy(h->aux);
     gather_windows_free(&h->gw);
     gather_buckets_free(&h->gb);
-    cudaFree(h->lane2.work);
-    if (h->lane2.ev_fork) cudaEventDestroy(h->lane2.ev_fork);
-    if (h->lane2.ev_join) cudaEventDestroy(h->lane2.ev_join);
-    if (h->lane2.st) cudaStreamDestroy(h->lane2.st);
+    for (int l = 0; l < kMaxNttLanes - 1; ++l) {
+        cudaFree(h->lanes.work[l]);
+        if (h->lanes.ev_join[l]) cudaEventDestroy(h->lanes.ev_join[l]);
+        if (h->lanes.st[l]) cudaStreamDestroy(h->lanes.st[l]);
+    }
+    if (h->lanes.ev_fork) cudaEventDestroy(h->lanes.ev_fork);
     delete h;
 }
 
@@ -223,16 +226,20 @@ int extract_create(extract_ctx **out, uint64_t n, uint32_t m, uint32_t s, uint32
             free_ctx(h);
             return cuda_error(e, "overlap stream");
         }
-        if (kNttTwoLanes && m > ntt_group(h->ntt)) {
-            NttSecondLane &L = h->lane2;
-            if ((e = cudaStreamCreateWithFlags(&L.st, cudaStreamNonBlocking)) != cudaSuccess ||
-                (e = cudaEventCreateWithFlags(&L.ev_fork, cudaEventDisableTiming)) != cudaSuccess ||
-                (e = cudaEventCreateWithFlags(&L.ev_join, cudaEventDisableTiming)) != cudaSuccess ||
-                (e = cudaMalloc(&L.work, ntt_work_words(m, s, k, split, per_sub) * 4)) != cudaSuccess) {
-                free_ctx(h);
-                return cuda_error(e, "second NTT lane");
-            }
+        const uint32_t groups = (uint32_t)ceil_div(m, ntt_group(h->ntt));
+        NttLanes &L = h->lanes;
+        L.n = (int)std::min<uint32_t>(kNttLanes - 1, groups - 1);
+        if (L.n > 0 && (e = cudaEventCreateWithFlags(&L.ev_fork, cudaEventDisableTiming)) != cudaSuccess) {
+            free_ctx(h);
+            return cuda_error(e, "NTT lanes");
         }
+        for (int l = 0; l < L.n; ++l)
+            if ((e = cudaStreamCreateWithFlags(&L.st[l], cudaStreamNonBlocking)) != cudaSuccess ||
+                (e = cudaEventCreateWithFlags(&L.ev_join[l], cudaEventDisableTiming)) != cudaSuccess ||
+                (e = cudaMalloc(&L.work[l], ntt_work_words(m, s, k, split, per_sub) * 4)) != cudaSuccess) {
+                free_ctx(h);
+                return cuda_error(e, "NTT lanes");
+            }
     }
     if ((e = cudaMalloc(&h->arev, (size_t)m * h->w_pad * 4)) != cudaSuccess) { free_ctx(h); return cuda_error(e, "cudaMalloc(sub-blocks)"); }
     if ((e = cudaMemset(h->arev, 0, (size_t)m * h->w_pad * 4)) != cudaSuccess) { free_ctx(h); return cuda_error(e, "memset(sub-blocks)"); }
@@ -255,7 +262,7 @@ int extract_create(extract_ctx **out, uint64_t n, uint32_t m, uint32_t s, uint32
             if (rc == kBucketsNotEligible) {
                 rc = (flags & EXTRACT_GATHER_BUCKETS)
                          ? set_error(EXTRACT_EINVAL, "EXTRACT_GATHER_BUCKETS: the shape does not suit the bucket "
-                                                     "tables (m*s < 2^32, m <= 16384, regions within 220 KiB)")
+                                                     "tables (m*s < 2^32, n <= 25600 * 2^16, regions within 220 KiB)")
                          : EXTRACT_OK;
             } else {
                 have_buckets = rc == EXTRACT_OK;
@@ -288,7 +295,7 @@ int extract_hash(extract_ctx *h, void *stream, uint32_t *out_bits_dev)
     if (!out_bits_dev) return set_error(EXTRACT_EINVAL, "out_bits_dev is null");
     if (h->ntt)
         return ntt_hash(h->ntt, h->arev, h->w_pad, h->m, h->s, h->k, out_bits_dev, (cudaStream_t)stream, nullptr,
-                        kNttTwoLanes ? &h->lane2 : nullptr);
+                        &h->lanes);
     return launch_hash(h->plan, h->seed, h->nseeds > 1 ? h->seed_stride : 0u, h->arev, h->w_pad, h->m,
                        h->k, out_bits_dev, (cudaStream_t)stream);
 }

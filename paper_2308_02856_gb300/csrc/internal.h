@@ -80,7 +80,7 @@ struct GatherBuckets {
     uint64_t run_words = 0;     // run words over all chunks
 };
 // Returned by gather_buckets_build when the shape does not suit the tables
-// (too many sub-blocks, a region wider than shared memory, no room); the
+// (too many input chunks, a region wider than shared memory, no room); the
 // caller keeps the plain gather.
 constexpr int kBucketsNotEligible = 1;
 int gather_buckets_build(const uint32_t *perm, uint64_t perm_len, uint64_t n, uint32_t m, uint32_t s, uint32_t w_pad,
@@ -180,20 +180,23 @@ double ntt_work_butterflies(uint32_t m, uint32_t s, uint32_t k, int split_log2 =
 // seed_stride > 0: one seed per sub-block, seed_stride words apart.
 int ntt_create(NttPlan **out, uint32_t m, uint32_t s, uint32_t k, const uint32_t *seed_dev, cudaStream_t st,
                uint32_t *work = nullptr, int split_log2 = -1, uint64_t seed_stride = 0);
-// A second stream and work buffer for ntt_hash: launch groups alternate
-// between the two, so one group's passes fill the other's last waves.
-// ev_fork / ev_join: events owned by the caller.
-struct NttSecondLane {
-    cudaStream_t st = nullptr;
-    uint32_t *work = nullptr;  // ntt_work_words() words
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+// Extra streams and work buffers for ntt_hash: launch group i runs on lane
+// i mod (1 + n) (lane 0 = the caller's stream and buffer), so one group's
+// passes fill the others' last waves.  Events owned by the caller.
+constexpr int kMaxNttLanes = 4;
+struct NttLanes {
+    int n = 0;  // extra lanes (0 .. kMaxNttLanes - 1)
+    cudaStream_t st[kMaxNttLanes - 1] = {};
+    uint32_t *work[kMaxNttLanes - 1] = {};  // ntt_work_words() words each
+    cudaEvent_t ev_fork = nullptr;
+    cudaEvent_t ev_join[kMaxNttLanes - 1] = {};
 };
 // Hashes all m gathered sub-blocks; zeroes and fills out.  work: a buffer
 // of ntt_work_words() words to use instead of the plan's own (null: the
-// plan's).  lane2: optional second lane (ordered after prior work on st and
+// plan's).  lanes: optional extra lanes (ordered after prior work on st and
 // joined back into st).
 int ntt_hash(const NttPlan *p, const uint32_t *arev, uint32_t w_pad, uint32_t m, uint32_t s, uint32_t k,
-             uint32_t *out, cudaStream_t st, uint32_t *work = nullptr, const NttSecondLane *lane2 = nullptr);
+             uint32_t *out, cudaStream_t st, uint32_t *work = nullptr, const NttLanes *lanes = nullptr);
 // Gather and hash with the gather of each launch group on `aux` overlapping
 // the transforms of the previous group on `st`; ordered after prior work on
 // st and fully ordered before later work on st.  ev_fork, ev_group: events

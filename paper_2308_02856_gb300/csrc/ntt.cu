@@ -367,7 +367,9 @@ __device__ __forceinline__ uint32_t swz(uint32_t t) { return (t & ~31u) | ((t ^ 
 // the largest register-stage distance / 32 (EPL / 2 for one column; E / 2
 // when the 32 EPL positions are 32 / E columns of 32 E, which the register
 // stages then never mix).
-template <int EPL, int HP0 = EPL / 2>
+// kZeroTop: e[j] are bits and the upper half of every column is zero, so the
+// first stage's butterflies (x, 0) -> (x, x w) are one multiply each.
+template <int EPL, int HP0 = EPL / 2, bool kZeroTop = false>
 __device__ __forceinline__ void dif_warp_t(uint32_t (&e)[EPL], uint32_t *sw, const uint2 *__restrict__ tw, int lane)
 {
 #pragma unroll
@@ -376,7 +378,8 @@ __device__ __forceinline__ void dif_warp_t(uint32_t (&e)[EPL], uint32_t *sw, con
         for (int j = 0; j < EPL; ++j) {
             if (j & hp) continue;
             const uint2 w = __ldg(tw + (32 * hp - 1) + lane + 32 * (j & (hp - 1)));
-            bf_dif(e[j], e[j + hp], w.x, w.y);
+            if (kZeroTop && hp == HP0) e[j + hp] = e[j] * w.x;
+            else bf_dif(e[j], e[j + hp], w.x, w.y);
         }
     }
 #pragma unroll
@@ -749,7 +752,8 @@ __device__ __forceinline__ void stage_row_words(uint32_t *rb, const uint32_t *__
 }
 
 // Pass A: bits -> DIF along t1 -> twist -> buf, for CW columns per CTA.
-template <int E, bool kReversed>
+// kZeroTop: pieces of at most N / 2 coefficients (rows t1 >= R1 / 2 zero).
+template <int E, bool kReversed, bool kZeroTop>
 __global__ void __launch_bounds__(512, 2)
 ntt_cols_fwd_m_kernel(const uint32_t *__restrict__ bits, Pieces pc, uint32_t N, Tables T, uint32_t *__restrict__ buf)
 {
@@ -768,7 +772,7 @@ ntt_cols_fwd_m_kernel(const uint32_t *__restrict__ bits, Pieces pc, uint32_t N, 
         const uint32_t cc = w * COLS + j / E, t1 = 32u * (j % E) + lane;
         e[j] = (rb[t1 * WPR + (cc >> 5)] >> (cc & 31u)) & 1u;
     }
-    dif_warp_t<32, E / 2>(e, xs + w * 1024, T.col_stage_f, lane);
+    dif_warp_t<32, E / 2, kZeroTop && (E >= 2)>(e, xs + w * 1024, T.col_stage_f, lane);
     // layout B: e[i] is frequency row r = 32 a + i of column cc
     const uint32_t a = lane % E, cc = w * COLS + lane / E;
     const uint32_t *twr = T.twist_f + (size_t)(c0 + cc) * R1 + 32u * a;
@@ -828,12 +832,16 @@ ntt_cols_inv_m_kernel(const uint32_t *__restrict__ buf, uint64_t sub_stride, Tab
     }
     __syncthreads();  // the tile is consumed; warps reuse it as scratch
     dit_warp_t<32, E / 2>(e, xs + w * 1024, T.col_stage_i, lane);
-    // layout A: e[j] is coefficient row 32 (j % E) + lane of column w COLS + j / E
+    // layout A: e[j] is coefficient row 32 (j % E) + lane of column w COLS + j / E;
+    // only row blocks holding a wanted coefficient [len-1, len+k-1) are packed
+    const uint32_t row_lo = (len - 1) / kR2, row_hi = (uint32_t)(((uint64_t)len + k - 2) / kR2);
     uint32_t mine = 0;
 #pragma unroll
     for (int j = 0; j < 32; ++j) {
-        const uint32_t word = __ballot_sync(0xffffffffu, redp(red2p(e[j])) & 1u);
-        if (lane == j) mine = word;
+        if (32u * (j % E) + 31u >= row_lo && 32u * (j % E) <= row_hi) {  // warp-uniform
+            const uint32_t word = __ballot_sync(0xffffffffu, redp(red2p(e[j])) & 1u);
+            if (lane == j) mine = word;
+        }
     }
     colw[(w * COLS + lane / E) * (E + 1) + lane % E] = mine;  // column, 32-row block
     __syncthreads();
@@ -912,8 +920,13 @@ int ntt_launch_a(const NttPlan *p, const uint32_t *bits, const Pieces &pc, bool 
 #define EX_COLS_FWD_M(E)                                                                                     \
     if (epl == E) {                                                                                          \
         const dim3 gm(kR2 / (512 / E), g * pc.P);                                                            \
-        if (reversed) ntt_cols_fwd_m_kernel<E, true><<<gm, 512, smem_multi(), st>>>(bits, pc, p->N, p->T, dst); \
-        else ntt_cols_fwd_m_kernel<E, false><<<gm, 512, smem_multi(), st>>>(bits, pc, p->N, p->T, dst);       \
+        if (2ull * pc.len <= p->N) {                                                                         \
+            if (reversed) ntt_cols_fwd_m_kernel<E, true, true><<<gm, 512, smem_multi(), st>>>(bits, pc, p->N, p->T, dst); \
+            else ntt_cols_fwd_m_kernel<E, false, true><<<gm, 512, smem_multi(), st>>>(bits, pc, p->N, p->T, dst); \
+        } else {                                                                                             \
+            if (reversed) ntt_cols_fwd_m_kernel<E, true, false><<<gm, 512, smem_multi(), st>>>(bits, pc, p->N, p->T, dst); \
+            else ntt_cols_fwd_m_kernel<E, false, false><<<gm, 512, smem_multi(), st>>>(bits, pc, p->N, p->T, dst); \
+        }                                                                                                    \
         return EXTRACT_OK;                                                                                   \
     }
 #define EX_COLS_FWD(E, K, SMEM)                                                                 \
@@ -1104,14 +1117,21 @@ static int device_setup(cudaStream_t st)
     attr((const void *)KF<E, true>, SMEM);  \
     attr((const void *)KF<E, false>, SMEM); \
     attr((const void *)KI<E>, SMEM);
-    EX_SET_SMEM(1, ntt_cols_fwd_m_kernel, ntt_cols_inv_m_kernel, smem_multi())
-    EX_SET_SMEM(2, ntt_cols_fwd_m_kernel, ntt_cols_inv_m_kernel, smem_multi())
-    EX_SET_SMEM(4, ntt_cols_fwd_m_kernel, ntt_cols_inv_m_kernel, smem_multi())
-    EX_SET_SMEM(8, ntt_cols_fwd_m_kernel, ntt_cols_inv_m_kernel, smem_multi())
-    EX_SET_SMEM(16, ntt_cols_fwd_m_kernel, ntt_cols_inv_m_kernel, smem_multi())
+#define EX_SET_SMEM_M(E)                                                            \
+    attr((const void *)ntt_cols_fwd_m_kernel<E, true, true>, smem_multi());    \
+    attr((const void *)ntt_cols_fwd_m_kernel<E, false, true>, smem_multi());   \
+    attr((const void *)ntt_cols_fwd_m_kernel<E, true, false>, smem_multi());   \
+    attr((const void *)ntt_cols_fwd_m_kernel<E, false, false>, smem_multi());  \
+    attr((const void *)ntt_cols_inv_m_kernel<E>, smem_multi());
+    EX_SET_SMEM_M(1)
+    EX_SET_SMEM_M(2)
+    EX_SET_SMEM_M(4)
+    EX_SET_SMEM_M(8)
+    EX_SET_SMEM_M(16)
     EX_SET_SMEM(32, ntt_cols_fwd_t_kernel, ntt_cols_inv_t_kernel, smem_transposed(1024))
     EX_SET_SMEM(64, ntt_cols_fwd_t_kernel, ntt_cols_inv_t_kernel, smem_transposed(2048))
 #undef EX_SET_SMEM
+#undef EX_SET_SMEM_M
     if (e != cudaSuccess) return cuda_error(e, "ntt smem attribute");
     uint2 lf[31], li[31];
     for (uint32_t hh = 1; hh <= 16; hh <<= 1) {
@@ -1317,27 +1337,29 @@ static int ntt_group_run(const NttPlan *p, const uint32_t *arev, uint32_t w_pad,
 
 // Hash every sub-block: out (zeroed here) gets K_j at bit j*k.
 int ntt_hash(const NttPlan *p, const uint32_t *arev, uint32_t w_pad, uint32_t m, uint32_t s, uint32_t k,
-             uint32_t *out, cudaStream_t st, uint32_t *work, const NttSecondLane *lane2)
+             uint32_t *out, cudaStream_t st, uint32_t *work, const NttLanes *lanes)
 {
     uint32_t *buf = work ? work : p->buf;
     EX_CUDA(cudaMemsetAsync(out, 0, ceil_div((uint64_t)m * k, 32) * 4, st));
     const Pieces pc = sub_block_pieces(p, w_pad, s);
-    const bool two = lane2 && lane2->st && lane2->work && m > p->G;
-    if (two) {  // odd groups on the second lane: its launches fill the first lane's last waves
-        EX_CUDA(cudaEventRecord(lane2->ev_fork, st));
-        EX_CUDA(cudaStreamWaitEvent(lane2->st, lane2->ev_fork, 0));
+    const uint32_t groups = (uint32_t)ceil_div(m, p->G);
+    // lanes past the group count stay idle
+    const uint32_t L = 1u + (lanes ? std::min<uint32_t>((uint32_t)lanes->n, groups - 1u) : 0u);
+    if (L > 1) {
+        EX_CUDA(cudaEventRecord(lanes->ev_fork, st));
+        for (uint32_t l = 1; l < L; ++l) EX_CUDA(cudaStreamWaitEvent(lanes->st[l - 1], lanes->ev_fork, 0));
     }
     uint32_t gi = 0;
     for (uint32_t j0 = 0; j0 < m; j0 += p->G, ++gi) {
         const uint32_t g = std::min(p->G, m - j0);
-        const bool second = two && (gi & 1u);
-        cudaStream_t gs = second ? lane2->st : st;
-        uint32_t *gb = second ? lane2->work : buf;
+        const uint32_t l = gi % L;
+        cudaStream_t gs = l ? lanes->st[l - 1] : st;
+        uint32_t *gb = l ? lanes->work[l - 1] : buf;
         if (int rc = ntt_group_run(p, arev, w_pad, j0, g, k, pc, gb, out, gs)) return rc;
     }
-    if (two) {
-        EX_CUDA(cudaEventRecord(lane2->ev_join, lane2->st));
-        EX_CUDA(cudaStreamWaitEvent(st, lane2->ev_join, 0));
+    for (uint32_t l = 1; l < L; ++l) {
+        EX_CUDA(cudaEventRecord(lanes->ev_join[l - 1], lanes->st[l - 1]));
+        EX_CUDA(cudaStreamWaitEvent(st, lanes->ev_join[l - 1], 0));
     }
     EX_LAUNCH("ntt kernels");
     return EXTRACT_OK;
