@@ -9,8 +9,8 @@
 //
 //   stage 1, per input chunk of kChunkBits positions (one CTA, the chunk's
 //     words in shared memory): the chunk's sampled bits are regrouped by
-//     sub-block, each sub-block's bits in increasing position order and
-//     padded to whole words ("runs"); every run word is stored into that
+//     sub-block into runs padded to whole words (the order inside a run is
+//     fixed when the tables are built); every run word is stored into that
 //     sub-block's region of the run buffer B.  Table: for every run word, the
 //     32 in-chunk positions of its bits (16-bit, pairs in one 32-bit word)
 //     and the word's place in B.
@@ -23,6 +23,11 @@
 // bytes), the input and B move once each, and the stored words equal the
 // plain gather's: word w of sub-block j has bit l = in[perm[j s + s-1 - c]]
 // with c = 32 w + l (0 when c >= s or the slot is padding).
+//
+// The tables come from the order in five steps: a per-(chunk, sub-block)
+// count, two scans (run offsets inside a chunk and inside B_j), the run
+// words' destinations, and one CTA per sub-block that places each slot's
+// position in its run (pi, first in B's layout) and records where (sigma).
 //
 // Layouts (a group = 32 consecutive words, lane l = word 32 g + l):
 //   pi   [word group g][bit pair b2 < 16][lane]   (bit 2 b2 | bit 2 b2+1 << 16)
@@ -43,39 +48,29 @@ namespace {
 
 constexpr uint32_t kChunkBits = 1u << 16;
 constexpr uint32_t kChunkWords = kChunkBits / 32;
-constexpr uint32_t kMaxBuckets = 16384;          // sub-blocks with per-chunk counters in shared memory
+constexpr size_t kAssignSmemMax = 200 * 1024;    // two counters per chunk in shared memory
 constexpr size_t kStage2SmemMax = 220 * 1024;    // bytes of B_j a stage-2 CTA holds
 constexpr int kStage1Warps = 8;
 constexpr int kStage2Warps = 32;
 
 __host__ __device__ __forceinline__ uint32_t words_of(uint32_t bits) { return (bits + 31u) >> 5; }
 
-// inv[perm[X]] = X for the slots X < len that hold a position.
-__global__ void bk_inv_kernel(const uint32_t *__restrict__ perm, uint64_t len, uint32_t *__restrict__ inv)
+// One CTA per sub-block: cnt[c * m + j] = #{slots of sub-block j whose
+// position lies in chunk c} (a shared-memory histogram over the chunks).
+__global__ void __launch_bounds__(1024)
+bk_count_kernel(const uint32_t *__restrict__ perm, uint32_t s, uint32_t m, uint32_t nch, uint32_t *__restrict__ cnt)
 {
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t X = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; X < len; X += stride) {
-        const uint32_t p = perm[X];
-        if (p != kNoPos) inv[p] = (uint32_t)X;
-    }
-}
-
-// cnt[c * m + j] = #{p in chunk c : inv[p] != kNoPos, inv[p] / s = j}
-__global__ void __launch_bounds__(512)
-bk_count_kernel(const uint32_t *__restrict__ inv, uint64_t n, uint32_t s, uint32_t m, uint32_t nch,
-                uint32_t *__restrict__ cnt)
-{
-    extern __shared__ uint32_t hist[];  // m
-    for (uint32_t c = blockIdx.x; c < nch; c += gridDim.x) {
-        for (uint32_t j = threadIdx.x; j < m; j += blockDim.x) hist[j] = 0;
+    extern __shared__ uint32_t hist[];  // nch
+    for (uint32_t j = blockIdx.x; j < m; j += gridDim.x) {
+        for (uint32_t c = threadIdx.x; c < nch; c += blockDim.x) hist[c] = 0;
         __syncthreads();
-        const uint64_t p0 = (uint64_t)c * kChunkBits, p1 = min(n, p0 + kChunkBits);
-        for (uint64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
-            const uint32_t X = inv[p];
-            if (X != kNoPos) atomicAdd(&hist[X / s], 1u);
+        const uint32_t *pj = perm + (size_t)j * s;
+        for (uint32_t x = threadIdx.x; x < s; x += blockDim.x) {
+            const uint32_t p = __ldcs(pj + x);
+            if (p != kNoPos) atomicAdd(&hist[p / kChunkBits], 1u);
         }
         __syncthreads();
-        for (uint32_t j = threadIdx.x; j < m; j += blockDim.x) cnt[(size_t)c * m + j] = hist[j];
+        for (uint32_t c = threadIdx.x; c < nch; c += blockDim.x) cnt[(size_t)c * m + j] = hist[c];
         __syncthreads();
     }
 }
@@ -158,52 +153,68 @@ bk_dst_kernel(const uint32_t *__restrict__ cnt, const uint32_t *__restrict__ wpr
     }
 }
 
-// One warp per chunk walks its positions in increasing order, 32 at a time;
-// lanes of the same sub-block find each other with a match and a per-sub-block
-// counter in shared memory carries their rank r inside the chunk's run.
-// Member r of run (c, j) is bit r % 32 of run word r / 32:
-//   pi:    that bit's in-chunk position;
-//   sigma: stored bit s-1-x of sub-block j (x = its slot) -> 32 mw[c][j] + r.
-template <int kWarps>
-__global__ void __launch_bounds__(kWarps * 32)
-bk_fill_kernel(const uint32_t *__restrict__ inv, uint64_t n, uint32_t s, uint32_t m, uint32_t nch,
-               uint32_t w_pad, const uint32_t *__restrict__ wpre, const uint32_t *__restrict__ mw,
-               const uint32_t *__restrict__ qc, uint16_t *__restrict__ pi, uint32_t *__restrict__ sigma)
+// One CTA per sub-block places its members: the slot x with position p in
+// chunk c takes the next free bit r of the run (c, j) (a shared-memory
+// counter per chunk; the order inside a run is whatever the atomics give,
+// which is fine because pi and sigma are written from the same choice):
+//   pib[32 (j bstride + mw[c][j]) + r] = p mod 2^16   (B-space layout)
+//   sigma: stored bit s-1-x of sub-block j        -> 32 mw[c][j] + r.
+// pib writes scatter inside the sub-block's region only, so the launch keeps
+// few enough CTAs that their regions stay in L2.
+__global__ void __launch_bounds__(1024)
+bk_assign_kernel(const uint32_t *__restrict__ perm, uint32_t s, uint32_t m, uint32_t nch, uint32_t w_pad,
+                 uint32_t bstride, const uint32_t *__restrict__ mw, uint16_t *__restrict__ pib,
+                 uint32_t *__restrict__ sigma)
 {
-    extern __shared__ uint32_t ctr_all[];  // kWarps x m
-    const uint32_t lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
-    uint32_t *ctr = ctr_all + (size_t)w * m;
-    const uint32_t below = (1u << lane) - 1u;
-    const uint32_t gps = w_pad >> 5;  // word groups per stored sub-block
-    for (uint32_t c = blockIdx.x * kWarps + w; c < nch; c += gridDim.x * kWarps) {
-        for (uint32_t j = lane; j < m; j += 32) ctr[j] = 0;
-        __syncwarp();
-        const uint64_t p0 = (uint64_t)c * kChunkBits, p1 = min(n, p0 + kChunkBits);
-        const uint32_t q0 = qc[c];
-        for (uint64_t b = p0; b < p1; b += 32) {
-            const uint64_t p = b + lane;
-            const uint32_t X = p < p1 ? inv[p] : kNoPos;
-            const bool live = X != kNoPos;
-            // dead lanes take sub-block m, which no live lane has
-            const uint32_t j = live ? X / s : m;
-            const uint32_t peers = __match_any_sync(0xffffffffu, j);
-            const uint32_t base = live ? ctr[j] : 0u;
-            __syncwarp();
-            if (live) {
-                const uint32_t r = base + __popc(peers & below);
-                if ((peers & below) == 0) ctr[j] = base + __popc(peers);  // the lowest lane of each sub-block
-                const uint32_t q = q0 + wpre[(size_t)c * (m + 1) + j] + (r >> 5);  // run word
-                const uint32_t bit = r & 31u;
-                pi[((((size_t)(q >> 5) * 16u + (bit >> 1)) * 32u + (q & 31u)) << 1) | (bit & 1u)] =
-                    (uint16_t)(p - p0);
-                const uint32_t cs = s - 1u - (X - j * s);  // stored bit of the slot
-                const uint32_t wd = cs >> 5;
-                sigma[(((size_t)j * gps + (wd >> 5)) * 32u + (cs & 31u)) * 32u + (wd & 31u)] =
-                    (mw[(size_t)c * m + j] << 5) + r;
-            }
-            __syncwarp();
+    extern __shared__ uint32_t sm[];  // nch counters, nch run starts (member bits)
+    uint32_t *ctr = sm, *start = sm + nch;
+    const uint32_t gps = w_pad >> 5;
+    for (uint32_t j = blockIdx.x; j < m; j += gridDim.x) {
+        for (uint32_t c = threadIdx.x; c < nch; c += blockDim.x) {
+            ctr[c] = 0;
+            start[c] = mw[(size_t)c * m + j] << 5;
         }
-        __syncwarp();
+        __syncthreads();
+        const uint32_t *pj = perm + (size_t)j * s;
+        uint16_t *pb = pib + (size_t)j * bstride * 32u;
+        uint32_t *sg = sigma + (size_t)j * gps * 1024u;
+        for (uint32_t x = threadIdx.x; x < s; x += blockDim.x) {
+            const uint32_t p = __ldcs(pj + x);
+            if (p == kNoPos) continue;
+            const uint32_t c = p / kChunkBits;
+            const uint32_t mem = start[c] + atomicAdd(&ctr[c], 1u);
+            pb[mem] = (uint16_t)(p % kChunkBits);
+            const uint32_t cs = s - 1u - x, wd = cs >> 5;
+            sg[((wd >> 5) * 32u + (cs & 31u)) * 32u + (wd & 31u)] = mem;
+        }
+        __syncthreads();
+    }
+}
+
+// pi in the stage-1 layout from the B-space entries: run word q with
+// destination d takes the 32 entries of B word d (padding words: zeros).
+__global__ void __launch_bounds__(256)
+bk_pi_kernel(const uint32_t *__restrict__ pib32, const uint32_t *__restrict__ dst, uint64_t run_words,
+             uint32_t *__restrict__ pi)
+{
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t g = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; g < run_words / 32; g += nwarps) {
+        const uint32_t d = dst[g * 32u + lane];
+        uint4 v[4] = {};
+        if (d != kNoPos) {
+            const uint4 *src = reinterpret_cast<const uint4 *>(pib32 + (size_t)d * 16u);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) v[i] = __ldcs(src + i);
+        }
+        uint32_t *o = pi + g * 512u + lane;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            o[(4 * i + 0) * 32] = v[i].x;
+            o[(4 * i + 1) * 32] = v[i].y;
+            o[(4 * i + 2) * 32] = v[i].z;
+            o[(4 * i + 3) * 32] = v[i].w;
+        }
     }
 }
 
@@ -281,17 +292,17 @@ int gather_buckets_build(const uint32_t *perm, uint64_t perm_len, uint64_t n, ui
                          GatherBuckets *gb, cudaStream_t st, int num_sms)
 {
     gather_buckets_free(gb);
-    if ((uint64_t)m * s >= (1ull << 32) || n >= (1ull << 32) || m > kMaxBuckets || w_pad % 32u || n == 0)
-        return kBucketsNotEligible;
+    (void)perm_len;  // sub-block j is perm[j s .. j s + s) in both layouts
+    if ((uint64_t)m * s >= (1ull << 32) || n >= (1ull << 32) || w_pad % 32u || n == 0) return kBucketsNotEligible;
     const uint32_t nch = (uint32_t)ceil_div(n, kChunkBits);
-    if ((uint64_t)nch * (m + 1) >= (1ull << 32)) return kBucketsNotEligible;
-    uint32_t *inv = nullptr, *cnt = nullptr, *wpre = nullptr, *mw = nullptr, *cwords = nullptr, *total = nullptr;
+    if ((size_t)nch * 8 > kAssignSmemMax || (uint64_t)nch * (m + 1) >= (1ull << 32)) return kBucketsNotEligible;
+    uint32_t *cnt = nullptr, *wpre = nullptr, *mw = nullptr, *cwords = nullptr, *total = nullptr;
+    uint16_t *pib = nullptr;
     int rc = EXTRACT_OK;
     cudaError_t e = cudaSuccess;
     auto fail = [&](int code) { if (rc == EXTRACT_OK) rc = code; };
     do {
-        if ((e = cudaMallocAsync(&inv, n * 4, st)) != cudaSuccess ||
-            (e = cudaMallocAsync(&cnt, (size_t)nch * m * 4, st)) != cudaSuccess ||
+        if ((e = cudaMallocAsync(&cnt, (size_t)nch * m * 4, st)) != cudaSuccess ||
             (e = cudaMallocAsync(&wpre, (size_t)nch * (m + 1) * 4, st)) != cudaSuccess ||
             (e = cudaMallocAsync(&mw, (size_t)nch * m * 4, st)) != cudaSuccess ||
             (e = cudaMallocAsync(&cwords, (size_t)(nch + 1) * 4, st)) != cudaSuccess ||
@@ -300,12 +311,9 @@ int gather_buckets_build(const uint32_t *perm, uint64_t perm_len, uint64_t n, ui
             fail(kBucketsNotEligible);  // no room for the tables
             break;
         }
-        if ((e = cudaMemsetAsync(inv, 0xff, n * 4, st)) != cudaSuccess) { fail(cuda_error(e, "memset")); break; }
-        const uint64_t len = std::min<uint64_t>(perm_len, (uint64_t)m * s);
-        bk_inv_kernel<<<(uint32_t)std::min<uint64_t>(ceil_div(len, 256), (uint64_t)num_sms * 32), 256, 0, st>>>(perm, len, inv);
-        if ((e = cudaFuncSetAttribute(bk_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(m * 4))) !=
+        if ((e = cudaFuncSetAttribute(bk_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(nch * 4))) !=
             cudaSuccess) { fail(cuda_error(e, "smem attribute")); break; }
-        bk_count_kernel<<<std::min<uint32_t>(nch, (uint32_t)num_sms * 4), 512, m * 4, st>>>(inv, n, s, m, nch, cnt);
+        bk_count_kernel<<<std::min<uint32_t>(m, (uint32_t)num_sms * 2), 1024, nch * 4, st>>>(perm, s, m, nch, cnt);
         bk_chunk_scan_kernel<<<std::min<uint32_t>(nch, (uint32_t)num_sms * 2), 1024, 0, st>>>(cnt, m, nch, wpre, cwords);
         bk_block_scan_kernel<<<(uint32_t)ceil_div(m, 128), 128, 0, st>>>(cnt, m, nch, mw, total);
         if ((e = cudaGetLastError()) != cudaSuccess) { fail(cuda_error(e, "bucket scans")); break; }
@@ -329,44 +337,41 @@ int gather_buckets_build(const uint32_t *perm, uint64_t perm_len, uint64_t n, ui
         gb->bstride = bstride;
         gb->run_words = q;
         const uint64_t sig_len = (uint64_t)m * w_pad * 32;
+        const size_t pib_bytes = (size_t)m * bstride * 64;
         if ((e = cudaMalloc(&gb->qc, (size_t)(nch + 1) * 4)) != cudaSuccess ||
             (e = cudaMalloc(&gb->pi, std::max<uint64_t>(q, 1) * 64)) != cudaSuccess ||
             (e = cudaMalloc(&gb->dst, std::max<uint64_t>(q, 1) * 4)) != cudaSuccess ||
             (e = cudaMalloc(&gb->sigma, sig_len * 4)) != cudaSuccess ||
-            (e = cudaMalloc(&gb->B, (size_t)m * bstride * 4)) != cudaSuccess) {
+            (e = cudaMalloc(&gb->B, (size_t)m * bstride * 4)) != cudaSuccess ||
+            (e = cudaMallocAsync(&pib, pib_bytes, st)) != cudaSuccess) {
             cudaGetLastError();
             fail(kBucketsNotEligible);  // no room for the tables
             break;
         }
         if ((e = cudaMemcpyAsync(gb->qc, hq.data(), (size_t)(nch + 1) * 4, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
-            (e = cudaMemsetAsync(gb->pi, 0, std::max<uint64_t>(q, 1) * 64, st)) != cudaSuccess ||
             (e = cudaMemsetAsync(gb->dst, 0xff, std::max<uint64_t>(q, 1) * 4, st)) != cudaSuccess ||
             (e = cudaMemsetAsync(gb->sigma, 0xff, sig_len * 4, st)) != cudaSuccess ||
-            (e = cudaMemsetAsync(gb->B, 0, (size_t)m * bstride * 4, st)) != cudaSuccess) {
+            (e = cudaMemsetAsync(gb->B, 0, (size_t)m * bstride * 4, st)) != cudaSuccess ||
+            (e = cudaMemsetAsync(pib, 0, pib_bytes, st)) != cudaSuccess) {
             fail(cuda_error(e, "bucket tables init"));
             break;
         }
         bk_dst_kernel<<<std::min<uint32_t>(nch, (uint32_t)num_sms * 8), 256, 0, st>>>(cnt, wpre, mw, gb->qc, m, nch,
                                                                                  bstride, gb->dst);
-        if ((e = cudaGetLastError()) != cudaSuccess) { fail(cuda_error(e, "bk_dst_kernel")); break; }
-        const size_t per_warp = (size_t)m * 4;
-        const int warps = (int)std::min<size_t>(8, std::max<size_t>(1, (size_t)(96 * 1024) / per_warp));
-#define EX_BK_FILL(W)                                                                                               \
-    if (warps >= W) {                                                                                               \
-        const size_t smem = per_warp * W;                                                                           \
-        if ((e = cudaFuncSetAttribute(bk_fill_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != \
-            cudaSuccess) { fail(cuda_error(e, "smem attribute")); break; }                                           \
-        bk_fill_kernel<W><<<(uint32_t)std::min<uint64_t>(ceil_div(nch, W), (uint64_t)num_sms * 8), W * 32, smem, st>>>( \
-            inv, n, s, m, nch, w_pad, wpre, mw, gb->qc, reinterpret_cast<uint16_t *>(gb->pi), gb->sigma);        \
-    } else
-        EX_BK_FILL(8) EX_BK_FILL(4) EX_BK_FILL(2) EX_BK_FILL(1) {}
-#undef EX_BK_FILL
-        if (rc != EXTRACT_OK) break;
-        if ((e = cudaGetLastError()) != cudaSuccess) { fail(cuda_error(e, "bk_fill_kernel")); break; }
+        if ((e = cudaFuncSetAttribute(bk_assign_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(nch * 8))) !=
+            cudaSuccess) { fail(cuda_error(e, "smem attribute")); break; }
+        // about 128 MB of sub-block regions in flight, so the scattered pib
+        // writes merge in L2
+        const uint32_t agrid = (uint32_t)std::max<uint64_t>(
+            1, std::min<uint64_t>({(uint64_t)m, (uint64_t)num_sms, (128ull << 20) / std::max<size_t>(1, (size_t)bstride * 64)}));
+        bk_assign_kernel<<<agrid, 1024, nch * 8, st>>>(perm, s, m, nch, w_pad, bstride, mw, pib, gb->sigma);
+        bk_pi_kernel<<<(uint32_t)std::min<uint64_t>(std::max<uint64_t>(1, q / 256), (uint64_t)num_sms * 16), 256, 0, st>>>(
+            reinterpret_cast<const uint32_t *>(pib), gb->dst, q, gb->pi);
+        if ((e = cudaGetLastError()) != cudaSuccess) { fail(cuda_error(e, "bucket tables")); break; }
         if ((e = cudaFuncSetAttribute(bk_stage2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)kStage2SmemMax)) != cudaSuccess) { fail(cuda_error(e, "smem attribute")); break; }
     } while (0);
-    for (void *ptr : {(void *)inv, (void *)cnt, (void *)wpre, (void *)mw, (void *)cwords, (void *)total})
+    for (void *ptr : {(void *)cnt, (void *)wpre, (void *)mw, (void *)cwords, (void *)total, (void *)pib})
         if (ptr) cudaFreeAsync(ptr, st);
     const cudaError_t se = cudaStreamSynchronize(st);
     if (rc == EXTRACT_OK && se != cudaSuccess) rc = cuda_error(se, "bucket gather build");
