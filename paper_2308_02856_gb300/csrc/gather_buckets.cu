@@ -159,8 +159,7 @@ bk_dst_kernel(const uint32_t *__restrict__ cnt, const uint32_t *__restrict__ wpr
 // which is fine because pi and sigma are written from the same choice):
 //   pib[32 (j bstride + mw[c][j]) + r] = p mod 2^16   (B-space layout)
 //   sigma: stored bit s-1-x of sub-block j        -> 32 mw[c][j] + r.
-// pib writes scatter inside the sub-block's region only, so the launch keeps
-// few enough CTAs that their regions stay in L2.
+// pib writes scatter inside the sub-block's region only.
 __global__ void __launch_bounds__(1024)
 bk_assign_kernel(const uint32_t *__restrict__ perm, uint32_t s, uint32_t m, uint32_t nch, uint32_t w_pad,
                  uint32_t bstride, const uint32_t *__restrict__ mw, uint16_t *__restrict__ pib,
@@ -360,10 +359,10 @@ int gather_buckets_build(const uint32_t *perm, uint64_t perm_len, uint64_t n, ui
                                                                                  bstride, gb->dst);
         if ((e = cudaFuncSetAttribute(bk_assign_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(nch * 8))) !=
             cudaSuccess) { fail(cuda_error(e, "smem attribute")); break; }
-        // about 128 MB of sub-block regions in flight, so the scattered pib
-        // writes merge in L2
-        const uint32_t agrid = (uint32_t)std::max<uint64_t>(
-            1, std::min<uint64_t>({(uint64_t)m, (uint64_t)num_sms, (128ull << 20) / std::max<size_t>(1, (size_t)bstride * 64)}));
+        // one sub-block per SM at a time (a cap at about 128 MB of regions in
+        // flight, to keep the scattered pib writes in L2, measured slower:
+        // 100.6 against 96.3 ms of create at n = 2^30)
+        const uint32_t agrid = std::min<uint32_t>(m, (uint32_t)num_sms);
         bk_assign_kernel<<<agrid, 1024, nch * 8, st>>>(perm, s, m, nch, w_pad, bstride, mw, pib, gb->sigma);
         bk_pi_kernel<<<(uint32_t)std::min<uint64_t>(std::max<uint64_t>(1, q / 256), (uint64_t)num_sms * 16), 256, 0, st>>>(
             reinterpret_cast<const uint32_t *>(pib), gb->dst, q, gb->pi);

@@ -540,7 +540,7 @@ __device__ __forceinline__ void row_dit_store(uint32_t (&e)[32], uint32_t *x, ui
 // in the same run: piece q of sub-block g uses S + (g P + q) N, without
 // quotients (Montgomery products).
 template <bool kInverse, bool kMulti, bool kPerBlock = false>
-__global__ void __launch_bounds__(64, kMulti ? 8 : 12)
+__global__ void __launch_bounds__(64, kMulti ? 10 : 12)
 ntt_rows_kernel(uint32_t *__restrict__ buf, uint32_t N, uint32_t R1, uint32_t P, const uint32_t *__restrict__ S,
                 const uint32_t *__restrict__ Sq, Tables T)
 {
