@@ -101,8 +101,9 @@ extern "C" {
    sub-block in shared memory, then each sub-block permuted in shared
    memory), which costs 2 bytes per sampled bit plus 4 bytes per stored
    sub-block bit of extra device memory and makes no random global reads; it
-   needs m*s < 2^32, n <= 25600 * 2^16 and every sub-block's regrouped bits
-   within 220 KiB, and otherwise (or without room) the plain gather is kept.
+   needs n <= 25600 * 2^16 (the per-chunk counters) and every sub-block's
+   regrouped bits within 220 KiB, and otherwise (or without room) the plain
+   gather is kept.
    EXTRACT_GATHER_PLAIN keeps the plain gather (one random input read per
    gathered bit); EXTRACT_GATHER_BUCKETS asks for the tables at any input
    size (EXTRACT_EINVAL if the shape does not suit them).  Both give the

@@ -70,6 +70,12 @@ struct extract_ctx {
     NttLanes lanes;                                   // extra lanes of the NTT hash (own streams, buffers)
     GatherWindows gw;                                 // window-major order for inputs far above L2
     GatherBuckets gb;                                 // bucketed two-stage gather tables
+    // extract_run_host with the bucket tables: copies on their own stream,
+    // overlapped with stage 1 (input pieces) and the hash (output groups)
+    cudaStream_t copy_st = nullptr;
+    cudaEvent_t ev_copy0 = nullptr, ev_out_end = nullptr, ev_copy_done = nullptr;
+    cudaEvent_t ev_piece[8] = {};
+    std::vector<cudaEvent_t> ev_groups;
 };
 
 namespace {
@@ -99,6 +105,13 @@ void free_ctx(extract_ctx *h)
     if (h->aux) cudaStreamDestroy(h->aux);
     gather_windows_free(&h->gw);
     gather_buckets_free(&h->gb);
+    for (cudaEvent_t ev : {h->ev_copy0, h->ev_out_end, h->ev_copy_done})
+        if (ev) cudaEventDestroy(ev);
+    for (cudaEvent_t ev : h->ev_piece)
+        if (ev) cudaEventDestroy(ev);
+    for (cudaEvent_t ev : h->ev_groups)
+        if (ev) cudaEventDestroy(ev);
+    if (h->copy_st) cudaStreamDestroy(h->copy_st);
     for (int l = 0; l < kMaxNttLanes - 1; ++l) {
         cudaFree(h->lanes.work[l]);
         if (h->lanes.ev_join[l]) cudaEventDestroy(h->lanes.ev_join[l]);
@@ -129,6 +142,58 @@ void realign_bits(const uint32_t *src, uint64_t src_words, uint64_t off, uint64_
 int check_ctx(const extract_ctx *h)
 {
     if (!h) return set_error(EXTRACT_EINVAL, "null context");
+    return EXTRACT_OK;
+}
+
+// extract_run_host over the bucket tables.  The input goes up in pieces of
+// whole 2^16-bit chunks on the copy stream and stage 1 takes each piece as
+// soon as it is in; the NTT hash sends each launch group's finished output
+// words down while later groups run (the direct hash's output goes down at
+// the end).  Same results as copy in, extract_run, copy out.
+int run_host_overlapped(extract_ctx *h, cudaStream_t st, const uint32_t *in_host, uint32_t *out_host)
+{
+    constexpr uint32_t kPieces = 8;
+    if (!h->copy_st) {
+        EX_CUDA(cudaStreamCreateWithFlags(&h->copy_st, cudaStreamNonBlocking));
+        EX_CUDA(cudaEventCreateWithFlags(&h->ev_copy0, cudaEventDisableTiming));
+        EX_CUDA(cudaEventCreateWithFlags(&h->ev_out_end, cudaEventDisableTiming));
+        EX_CUDA(cudaEventCreateWithFlags(&h->ev_copy_done, cudaEventDisableTiming));
+        for (cudaEvent_t &ev : h->ev_piece) EX_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        if (h->ntt) {
+            h->ev_groups.assign(ceil_div(h->m, ntt_group(h->ntt)), nullptr);
+            for (cudaEvent_t &ev : h->ev_groups) EX_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        }
+    }
+    const uint64_t words = ceil_div(h->n, 32), out_words = ceil_div((uint64_t)h->m * h->k, 32);
+    constexpr uint64_t kChunkWords = kBucketChunkBits / 32;
+    EX_CUDA(cudaEventRecord(h->ev_copy0, st));  // after the caller's earlier work on st
+    EX_CUDA(cudaStreamWaitEvent(h->copy_st, h->ev_copy0, 0));
+    const uint32_t nch = h->gb.nch, np = std::min<uint32_t>(kPieces, nch);
+    for (uint32_t i = 0; i < np; ++i) {
+        const uint32_t c0 = (uint32_t)((uint64_t)nch * i / np), c1 = (uint32_t)((uint64_t)nch * (i + 1) / np);
+        const uint64_t w0 = std::min<uint64_t>(words, c0 * kChunkWords), w1 = std::min<uint64_t>(words, c1 * kChunkWords);
+        if (w1 > w0)
+            EX_CUDA(cudaMemcpyAsync(h->stage_in + w0, in_host + w0, (w1 - w0) * 4, cudaMemcpyHostToDevice, h->copy_st));
+        EX_CUDA(cudaEventRecord(h->ev_piece[i], h->copy_st));
+        EX_CUDA(cudaStreamWaitEvent(st, h->ev_piece[i], 0));
+        if (int rc = gather_buckets_stage1(h->gb, h->stage_in, h->n, c0, c1, st, h->num_sms)) return rc;
+    }
+    if (int rc = gather_buckets_stage2(h->gb, h->m, h->w_pad, h->arev, st, h->num_sms)) return rc;
+    if (h->ntt) {
+        const NttHostOut ho{out_host, h->copy_st, h->ev_groups.data(), (uint32_t)h->ev_groups.size(), h->ev_out_end};
+        if (int rc = ntt_hash(h->ntt, h->arev, h->w_pad, h->m, h->s, h->k, h->stage_out, st, nullptr, &h->lanes, &ho))
+            return rc;
+    } else {
+        if (int rc = launch_hash(h->plan, h->seed, h->nseeds > 1 ? h->seed_stride : 0u, h->arev, h->w_pad, h->m, h->k,
+                                 h->stage_out, st))
+            return rc;
+        EX_CUDA(cudaEventRecord(h->ev_out_end, st));
+        EX_CUDA(cudaStreamWaitEvent(h->copy_st, h->ev_out_end, 0));
+        EX_CUDA(cudaMemcpyAsync(out_host, h->stage_out, out_words * 4, cudaMemcpyDeviceToHost, h->copy_st));
+    }
+    EX_CUDA(cudaEventRecord(h->ev_copy_done, h->copy_st));
+    EX_CUDA(cudaStreamWaitEvent(st, h->ev_copy_done, 0));
+    EX_CUDA(cudaStreamSynchronize(st));
     return EXTRACT_OK;
 }
 
@@ -262,7 +327,7 @@ int extract_create(extract_ctx **out, uint64_t n, uint32_t m, uint32_t s, uint32
             if (rc == kBucketsNotEligible) {
                 rc = (flags & EXTRACT_GATHER_BUCKETS)
                          ? set_error(EXTRACT_EINVAL, "EXTRACT_GATHER_BUCKETS: the shape does not suit the bucket "
-                                                     "tables (m*s < 2^32, n <= 25600 * 2^16, regions within 220 KiB)")
+                                                     "tables (n <= 25600 * 2^16, regions within 220 KiB)")
                          : EXTRACT_OK;
             } else {
                 have_buckets = rc == EXTRACT_OK;
@@ -325,6 +390,7 @@ int extract_run_host(extract_ctx *h, void *stream, const uint32_t *in_bits_host,
     if (!h->stage_in) EX_CUDA(cudaMalloc(&h->stage_in, in_bytes ? in_bytes : 4));
     if (!h->stage_out) EX_CUDA(cudaMalloc(&h->stage_out, out_bytes));
     cudaStream_t st = (cudaStream_t)stream;
+    if (h->gb.pi) return run_host_overlapped(h, st, in_bits_host, out_bits_host);
     EX_CUDA(cudaMemcpyAsync(h->stage_in, in_bits_host, in_bytes, cudaMemcpyHostToDevice, st));
     if (int rc = extract_run(h, stream, h->stage_in, h->stage_out)) return rc;
     EX_CUDA(cudaMemcpyAsync(out_bits_host, h->stage_out, out_bytes, cudaMemcpyDeviceToHost, st));

@@ -46,7 +46,7 @@
 namespace ex {
 namespace {
 
-constexpr uint32_t kChunkBits = 1u << 16;
+constexpr uint32_t kChunkBits = kBucketChunkBits;
 constexpr uint32_t kChunkWords = kChunkBits / 32;
 constexpr size_t kAssignSmemMax = 200 * 1024;    // two counters per chunk in shared memory
 constexpr size_t kStage2SmemMax = 220 * 1024;    // bytes of B_j a stage-2 CTA holds
@@ -220,13 +220,13 @@ bk_pi_kernel(const uint32_t *__restrict__ pib32, const uint32_t *__restrict__ ds
 // Stage 1: one chunk per CTA iteration; one warp per group of 32 run words.
 __global__ void __launch_bounds__(kStage1Warps * 32)
 bk_stage1_kernel(const uint32_t *__restrict__ in, uint64_t in_words, const uint32_t *__restrict__ pi,
-                 const uint32_t *__restrict__ dst, const uint32_t *__restrict__ qc, uint32_t nch,
+                 const uint32_t *__restrict__ dst, const uint32_t *__restrict__ qc, uint32_t c_begin, uint32_t c_end,
                  uint32_t *__restrict__ B)
 {
     __shared__ __align__(16) uint32_t cw[kChunkWords];
     const uint32_t lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
     const bool aligned = (reinterpret_cast<uintptr_t>(in) & 15u) == 0;
-    for (uint32_t c = blockIdx.x; c < nch; c += gridDim.x) {
+    for (uint32_t c = c_begin + blockIdx.x; c < c_end; c += gridDim.x) {
         const uint64_t w0 = (uint64_t)c * kChunkWords;
         if (aligned && w0 + kChunkWords <= in_words) {
             const uint4 *src = reinterpret_cast<const uint4 *>(in + w0);
@@ -292,7 +292,7 @@ int gather_buckets_build(const uint32_t *perm, uint64_t perm_len, uint64_t n, ui
 {
     gather_buckets_free(gb);
     (void)perm_len;  // sub-block j is perm[j s .. j s + s) in both layouts
-    if ((uint64_t)m * s >= (1ull << 32) || n >= (1ull << 32) || w_pad % 32u || n == 0) return kBucketsNotEligible;
+    if (n > (1ull << 32) || w_pad % 32u || n == 0) return kBucketsNotEligible;
     const uint32_t nch = (uint32_t)ceil_div(n, kChunkBits);
     if ((size_t)nch * 8 > kAssignSmemMax || (uint64_t)nch * (m + 1) >= (1ull << 32)) return kBucketsNotEligible;
     uint32_t *cnt = nullptr, *wpre = nullptr, *mw = nullptr, *cwords = nullptr, *total = nullptr;
@@ -378,16 +378,30 @@ int gather_buckets_build(const uint32_t *perm, uint64_t perm_len, uint64_t n, ui
     return rc;
 }
 
-int gather_buckets_run(const GatherBuckets &gb, const uint32_t *in, uint64_t n, uint32_t m, uint32_t w_pad,
-                       uint32_t *arev, cudaStream_t st, int num_sms)
+int gather_buckets_stage1(const GatherBuckets &gb, const uint32_t *in, uint64_t n, uint32_t c_begin, uint32_t c_end,
+                          cudaStream_t st, int num_sms)
 {
-    bk_stage1_kernel<<<std::min<uint32_t>(gb.nch, (uint32_t)num_sms * 8), kStage1Warps * 32, 0, st>>>(
-        in, ceil_div(n, 32), gb.pi, gb.dst, gb.qc, gb.nch, gb.B);
+    if (c_end <= c_begin) return EXTRACT_OK;
+    bk_stage1_kernel<<<std::min<uint32_t>(c_end - c_begin, (uint32_t)num_sms * 8), kStage1Warps * 32, 0, st>>>(
+        in, ceil_div(n, 32), gb.pi, gb.dst, gb.qc, c_begin, c_end, gb.B);
     EX_LAUNCH("bk_stage1_kernel");
+    return EXTRACT_OK;
+}
+
+int gather_buckets_stage2(const GatherBuckets &gb, uint32_t m, uint32_t w_pad, uint32_t *arev, cudaStream_t st,
+                          int num_sms)
+{
     bk_stage2_kernel<<<std::min<uint32_t>(m, (uint32_t)num_sms), kStage2Warps * 32, (size_t)gb.bstride * 4, st>>>(
         gb.B, gb.bstride, gb.sigma, m, w_pad, arev);
     EX_LAUNCH("bk_stage2_kernel");
     return EXTRACT_OK;
+}
+
+int gather_buckets_run(const GatherBuckets &gb, const uint32_t *in, uint64_t n, uint32_t m, uint32_t w_pad,
+                       uint32_t *arev, cudaStream_t st, int num_sms)
+{
+    if (int rc = gather_buckets_stage1(gb, in, n, 0, gb.nch, st, num_sms)) return rc;
+    return gather_buckets_stage2(gb, m, w_pad, arev, st, num_sms);
 }
 
 void gather_buckets_free(GatherBuckets *gb)

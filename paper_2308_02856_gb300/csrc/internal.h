@@ -87,6 +87,13 @@ int gather_buckets_build(const uint32_t *perm, uint64_t perm_len, uint64_t n, ui
                          GatherBuckets *gb, cudaStream_t st, int num_sms);
 int gather_buckets_run(const GatherBuckets &gb, const uint32_t *in, uint64_t n, uint32_t m, uint32_t w_pad,
                        uint32_t *arev, cudaStream_t st, int num_sms);
+// The two stages alone: stage 1 over input chunks [c_begin, c_end) (of
+// kBucketChunkBits bits each), stage 2 over every sub-block.
+constexpr uint32_t kBucketChunkBits = 1u << 16;
+int gather_buckets_stage1(const GatherBuckets &gb, const uint32_t *in, uint64_t n, uint32_t c_begin, uint32_t c_end,
+                          cudaStream_t st, int num_sms);
+int gather_buckets_stage2(const GatherBuckets &gb, uint32_t m, uint32_t w_pad, uint32_t *arev, cudaStream_t st,
+                          int num_sms);
 void gather_buckets_free(GatherBuckets *gb);
 
 // ---- steps 2-3: the Toeplitz product and concatenation ------------------
@@ -195,8 +202,19 @@ struct NttLanes {
 // of ntt_work_words() words to use instead of the plan's own (null: the
 // plan's).  lanes: optional extra lanes (ordered after prior work on st and
 // joined back into st).
+// Host copy of the output while later groups still run: after launch group
+// i (and group i - 1, which may share its first word) the words that no
+// later group touches go to host on stream st; the rest after the last one.
+struct NttHostOut {
+    uint32_t *host = nullptr;   // ceil(m k / 32) words
+    cudaStream_t st = nullptr;  // copy stream
+    cudaEvent_t *ev = nullptr;  // one event per launch group
+    uint32_t nev = 0;
+    cudaEvent_t ev_end = nullptr;
+};
 int ntt_hash(const NttPlan *p, const uint32_t *arev, uint32_t w_pad, uint32_t m, uint32_t s, uint32_t k,
-             uint32_t *out, cudaStream_t st, uint32_t *work = nullptr, const NttLanes *lanes = nullptr);
+             uint32_t *out, cudaStream_t st, uint32_t *work = nullptr, const NttLanes *lanes = nullptr,
+             const NttHostOut *host_out = nullptr);
 // Gather and hash with the gather of each launch group on `aux` overlapping
 // the transforms of the previous group on `st`; ordered after prior work on
 // st and fully ordered before later work on st.  ev_fork, ev_group: events

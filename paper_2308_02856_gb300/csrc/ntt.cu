@@ -536,6 +536,8 @@ __device__ __forceinline__ void row_dit_store(uint32_t (&e)[32], uint32_t *x, ui
     }
 }
 
+constexpr bool kRowsOneDifCopy = false;
+
 // kPerBlock: the spectra are per sub-block (independent seeds), transformed
 // in the same run: piece q of sub-block g uses S + (g P + q) N, without
 // quotients (Montgomery products).
@@ -552,7 +554,7 @@ ntt_rows_kernel(uint32_t *__restrict__ buf, uint32_t N, uint32_t R1, uint32_t P,
     const size_t so = (size_t)r * kR2 + base;
     const uint32_t *Sb = kPerBlock ? S + (size_t)g * P * N : S;
     uint32_t e[32];
-    row_dif(e, x, sw[w], T, lane, w);
+    if (!(kInverse && kMulti && kRowsOneDifCopy)) row_dif(e, x, sw[w], T, lane, w);
     if (!kInverse) {
 #pragma unroll
         for (int i = 0; i < 32; i += 4)
@@ -567,12 +569,25 @@ ntt_rows_kernel(uint32_t *__restrict__ buf, uint32_t N, uint32_t R1, uint32_t P,
         return;
     }
     uint32_t acc[32];
-    if (kMont) row_mul_mont<false>(e, acc, Sb + so);
-    else row_mul<false>(e, acc, S + so, Sq + so);
-    for (uint32_t q = 1; q < P; ++q) {
-        row_dif(e, x + (size_t)q * N, sw[w], T, lane, w);
-        if (kMont) row_mul_mont<true>(e, acc, Sb + (size_t)q * N + so);
-        else row_mul<true>(e, acc, S + (size_t)q * N + so, Sq + (size_t)q * N + so);
+    if (kRowsOneDifCopy) {
+        // one copy of the piece loop's code (fewer instruction-fetch stalls):
+        // the first piece's products are added to zero
+#pragma unroll
+        for (int i = 0; i < 32; ++i) acc[i] = 0;
+#pragma unroll 1
+        for (uint32_t q = 0; q < P; ++q) {
+            row_dif(e, x + (size_t)q * N, sw[w], T, lane, w);
+            if (kMont) row_mul_mont<true>(e, acc, Sb + (size_t)q * N + so);
+            else row_mul<true>(e, acc, S + (size_t)q * N + so, Sq + (size_t)q * N + so);
+        }
+    } else {
+        if (kMont) row_mul_mont<false>(e, acc, Sb + so);
+        else row_mul<false>(e, acc, S + so, Sq + so);
+        for (uint32_t q = 1; q < P; ++q) {
+            row_dif(e, x + (size_t)q * N, sw[w], T, lane, w);
+            if (kMont) row_mul_mont<true>(e, acc, Sb + (size_t)q * N + so);
+            else row_mul<true>(e, acc, S + (size_t)q * N + so, Sq + (size_t)q * N + so);
+        }
     }
     row_dit_store(acc, x, sw, T, lane, w);
 }
@@ -1337,29 +1352,49 @@ static int ntt_group_run(const NttPlan *p, const uint32_t *arev, uint32_t w_pad,
 
 // Hash every sub-block: out (zeroed here) gets K_j at bit j*k.
 int ntt_hash(const NttPlan *p, const uint32_t *arev, uint32_t w_pad, uint32_t m, uint32_t s, uint32_t k,
-             uint32_t *out, cudaStream_t st, uint32_t *work, const NttLanes *lanes)
+             uint32_t *out, cudaStream_t st, uint32_t *work, const NttLanes *lanes, const NttHostOut *host_out)
 {
     uint32_t *buf = work ? work : p->buf;
-    EX_CUDA(cudaMemsetAsync(out, 0, ceil_div((uint64_t)m * k, 32) * 4, st));
+    const uint64_t out_words = ceil_div((uint64_t)m * k, 32);
+    EX_CUDA(cudaMemsetAsync(out, 0, out_words * 4, st));
     const Pieces pc = sub_block_pieces(p, w_pad, s);
     const uint32_t groups = (uint32_t)ceil_div(m, p->G);
     // lanes past the group count stay idle
     const uint32_t L = 1u + (lanes ? std::min<uint32_t>((uint32_t)lanes->n, groups - 1u) : 0u);
+    // per-group host copies need every word shared by at most two groups
+    const bool per_group = host_out && host_out->nev >= groups && (uint64_t)p->G * k >= 64;
     if (L > 1) {
         EX_CUDA(cudaEventRecord(lanes->ev_fork, st));
         for (uint32_t l = 1; l < L; ++l) EX_CUDA(cudaStreamWaitEvent(lanes->st[l - 1], lanes->ev_fork, 0));
     }
     uint32_t gi = 0;
+    uint64_t copied = 0;  // host words done
     for (uint32_t j0 = 0; j0 < m; j0 += p->G, ++gi) {
         const uint32_t g = std::min(p->G, m - j0);
         const uint32_t l = gi % L;
         cudaStream_t gs = l ? lanes->st[l - 1] : st;
         uint32_t *gb = l ? lanes->work[l - 1] : buf;
         if (int rc = ntt_group_run(p, arev, w_pad, j0, g, k, pc, gb, out, gs)) return rc;
+        if (per_group) {
+            EX_CUDA(cudaEventRecord(host_out->ev[gi], gs));
+            EX_CUDA(cudaStreamWaitEvent(host_out->st, host_out->ev[gi], 0));
+            if (gi) EX_CUDA(cudaStreamWaitEvent(host_out->st, host_out->ev[gi - 1], 0));
+            const uint64_t hi = (uint64_t)(j0 + g) * k / 32;  // words below hold no later group's bits
+            if (hi > copied)
+                EX_CUDA(cudaMemcpyAsync(host_out->host + copied, out + copied, (hi - copied) * 4,
+                                        cudaMemcpyDeviceToHost, host_out->st));
+            copied = std::max(copied, hi);
+        }
     }
     for (uint32_t l = 1; l < L; ++l) {
         EX_CUDA(cudaEventRecord(lanes->ev_join[l - 1], lanes->st[l - 1]));
         EX_CUDA(cudaStreamWaitEvent(st, lanes->ev_join[l - 1], 0));
+    }
+    if (host_out && copied < out_words) {
+        EX_CUDA(cudaEventRecord(host_out->ev_end, st));
+        EX_CUDA(cudaStreamWaitEvent(host_out->st, host_out->ev_end, 0));
+        EX_CUDA(cudaMemcpyAsync(host_out->host + copied, out + copied, (out_words - copied) * 4,
+                                cudaMemcpyDeviceToHost, host_out->st));
     }
     EX_LAUNCH("ntt kernels");
     return EXTRACT_OK;

@@ -154,3 +154,54 @@ def test_rejected_combinations(n, m, s, flags):
     with pytest.raises(X.ExtractError) as e:
         X.Extractor(n, m, s, 1, seed, 3, flags | X.EXTRACT_METHOD_DIRECT)
     assert e.value.code == X.EXTRACT_EINVAL
+
+
+@pytest.mark.parametrize("n,m,s,k,flags", [
+    (300_000, 9, 30_000, 4_000, X.EXTRACT_GATHER_BUCKETS | X.EXTRACT_METHOD_DIRECT),
+    (5 << 20, 5, 1 << 20, 1000, 0),  # default choice at 5 Mbit: the tables
+])
+def test_host_buffers_through_the_buckets_match_the_oracle(n, m, s, k, flags):
+    """extract_run_host overlaps its copies with stage 1 and the hash."""
+    in_w = synth.bernoulli_bits(n, 0.6, 16)
+    seed = synth.uniform_bits(s + k - 1, 6)
+    want = oracle.extract(n, m, s, k, in_w, seed, 2)
+    with X.Extractor(n, m, s, k, seed, 2, flags) as ex:
+        assert "gather=buckets" in ex.describe()
+        for _ in range(2):  # the second call reuses the copy stream and events
+            got = ex.run_host(np.ascontiguousarray(in_w, dtype=np.uint32))
+            assert np.array_equal(got, want)
+
+
+def test_host_buffers_ntt_in_several_launch_groups():
+    """Two launch groups (32 + 8 sub-blocks); k mod 32 = 25, so neighbouring
+    groups share an output word and each group's words go to the host while
+    later groups run.  Sampled rows of every sub-block against the oracle,
+    the first and last rows of each included."""
+    n, m, s, k = 40 << 18, 40, 1 << 18, (1 << 17) - 7
+    in_w = synth.bernoulli_bits(n, 0.6, 16)
+    seed = synth.uniform_bits(s + k - 1, 6)
+    with X.Extractor(n, m, s, k, seed, 2, X.EXTRACT_METHOD_NTT) as ex:
+        plan = ex.describe()
+        assert "gather=buckets" in plan
+        assert int(plan.split(" sub-blocks per launch group")[0].split(",")[-1]) < m
+        got = oracle.bits_of(ex.run_host(np.ascontiguousarray(in_w, dtype=np.uint32)), m * k)
+        dev = oracle.bits_of(ex.run(_dev(in_w)).cpu().numpy().view(np.uint32), m * k)
+    assert np.array_equal(got, dev)
+    keys = oracle.sampling_keys(n, 2)
+    rng = np.random.default_rng(3)
+    for j in range(m):
+        A = oracle.subblock(in_w, oracle.perm_range(keys, j * s, s))
+        rows = np.unique(np.concatenate([np.arange(4), np.arange(k - 4, k), rng.choice(k, 8, replace=False)]))
+        want = np.array([oracle.toeplitz_bit(seed, s, A, int(i)) for i in rows], dtype=np.uint8)
+        assert np.array_equal(got[j * k + rows], want), "sub-block %d" % j
+
+
+def test_iid_host_buffers_through_the_buckets_match_the_oracle():
+    n, m, k = 250_000, 6, 2_000
+    _, _, largest = oracle.iid_order(oracle.sampling_keys(n, 7), m, n, with_order=False)
+    s = largest + 3
+    in_w = synth.bernoulli_bits(n, 0.6, 17)
+    seed = synth.uniform_bits(s + k - 1, 5)
+    with X.Extractor(n, m, s, k, seed, 7, X.EXTRACT_SAMPLING_IID | X.EXTRACT_GATHER_BUCKETS) as ex:
+        got = ex.run_host(np.ascontiguousarray(in_w, dtype=np.uint32))
+    assert np.array_equal(got, oracle.extract(n, m, s, k, in_w, seed, 7, oracle.SAMPLING_IID))
