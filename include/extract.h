@@ -101,15 +101,21 @@ extern "C" {
    sub-block in shared memory, then each sub-block permuted in shared
    memory), which costs 2 bytes per sampled bit plus 4 bytes per stored
    sub-block bit of extra device memory and makes no random global reads; it
-   needs n <= 25600 * 2^16 (the per-chunk counters) and every sub-block's
-   regrouped bits within 220 KiB, and otherwise (or without room) the plain
-   gather is kept.
+   needs n <= 25600 input chunks of 2^16 bits, or of 2^18 bits with 32-bit
+   table entries (4 bytes per sampled bit), and every sub-block's regrouped
+   bits within 220 KiB; otherwise (or without room) the plain gather is
+   kept.
    EXTRACT_GATHER_PLAIN keeps the plain gather (one random input read per
    gathered bit); EXTRACT_GATHER_BUCKETS asks for the tables at any input
    size (EXTRACT_EINVAL if the shape does not suit them).  Both give the
    same sub-blocks.  Not combinable with EXTRACT_IDENTITY_PERM. */
 #define EXTRACT_GATHER_PLAIN      0x20u
 #define EXTRACT_GATHER_BUCKETS    0x40u
+/* Bucket tables over 2^18-bit input chunks (32-bit table entries) even where
+   2^16-bit chunks fit; the library itself takes them when the input has more
+   than 25600 chunks of 2^16 bits or its runs are too short to fit.  Tuning
+   and test hook. */
+#define EXTRACT_GATHER_WIDE_CHUNKS 0x80u
 
 typedef struct extract_ctx extract_ctx;
 

@@ -86,7 +86,7 @@ static_assert(kNttLanes >= 1 && kNttLanes <= (uint32_t)kMaxNttLanes, "NTT lane c
 
 constexpr uint32_t kKnownFlags = EXTRACT_SEED_PER_SUBBLOCK | EXTRACT_IDENTITY_PERM | EXTRACT_METHOD_DIRECT |
                                   EXTRACT_METHOD_NTT | EXTRACT_SAMPLING_IID | EXTRACT_GATHER_PLAIN |
-                                  EXTRACT_GATHER_BUCKETS | (0x3fu << 8) | (0x7u << 16);
+                                  EXTRACT_GATHER_BUCKETS | EXTRACT_GATHER_WIDE_CHUNKS | (0x3fu << 8) | (0x7u << 16);
 
 // Smallest input that gets the bucketed gather by default
 constexpr uint64_t kBucketsMinBits = 1ull << 22;
@@ -146,7 +146,7 @@ int check_ctx(const extract_ctx *h)
 }
 
 // extract_run_host over the bucket tables.  The input goes up in pieces of
-// whole 2^16-bit chunks on the copy stream and stage 1 takes each piece as
+// whole input chunks on the copy stream and stage 1 takes each piece as
 // soon as it is in; the NTT hash sends each launch group's finished output
 // words down while later groups run (the direct hash's output goes down at
 // the end).  Same results as copy in, extract_run, copy out.
@@ -165,7 +165,7 @@ int run_host_overlapped(extract_ctx *h, cudaStream_t st, const uint32_t *in_host
         }
     }
     const uint64_t words = ceil_div(h->n, 32), out_words = ceil_div((uint64_t)h->m * h->k, 32);
-    constexpr uint64_t kChunkWords = kBucketChunkBits / 32;
+    const uint64_t kChunkWords = (1ull << h->gb.clog) / 32;
     EX_CUDA(cudaEventRecord(h->ev_copy0, st));  // after the caller's earlier work on st
     EX_CUDA(cudaStreamWaitEvent(h->copy_st, h->ev_copy0, 0));
     const uint32_t nch = h->gb.nch, np = std::min<uint32_t>(kPieces, nch);
@@ -227,8 +227,9 @@ int extract_create(extract_ctx **out, uint64_t n, uint32_t m, uint32_t s, uint32
     }
     if ((flags & EXTRACT_METHOD_DIRECT) && (flags & EXTRACT_METHOD_NTT))
         return set_error(EXTRACT_EINVAL, "EXTRACT_METHOD_DIRECT and EXTRACT_METHOD_NTT are exclusive");
-    if ((flags & EXTRACT_GATHER_PLAIN) && (flags & EXTRACT_GATHER_BUCKETS))
-        return set_error(EXTRACT_EINVAL, "EXTRACT_GATHER_PLAIN and EXTRACT_GATHER_BUCKETS are exclusive");
+    if ((flags & EXTRACT_GATHER_PLAIN) && (flags & (EXTRACT_GATHER_BUCKETS | EXTRACT_GATHER_WIDE_CHUNKS)))
+        return set_error(EXTRACT_EINVAL, "EXTRACT_GATHER_PLAIN excludes EXTRACT_GATHER_BUCKETS and "
+                                         "EXTRACT_GATHER_WIDE_CHUNKS");
     if (ident && (flags & EXTRACT_GATHER_BUCKETS))
         return set_error(EXTRACT_EINVAL, "EXTRACT_GATHER_BUCKETS needs a sampled order (not EXTRACT_IDENTITY_PERM)");
     const uint32_t split_field = (flags >> 16) & 0x7u;
@@ -323,11 +324,12 @@ int extract_create(extract_ctx **out, uint64_t n, uint32_t m, uint32_t s, uint32
                                   (!(flags & EXTRACT_GATHER_PLAIN) && n >= kBucketsMinBits);
         bool have_buckets = false;
         if (rc == EXTRACT_OK && want_buckets) {
-            rc = gather_buckets_build(h->perm, h->perm_len, n, m, s, h->w_pad, &h->gb, st, h->num_sms);
+            rc = gather_buckets_build(h->perm, h->perm_len, n, m, s, h->w_pad, &h->gb, st, h->num_sms,
+                                      (flags & EXTRACT_GATHER_WIDE_CHUNKS) != 0);
             if (rc == kBucketsNotEligible) {
                 rc = (flags & EXTRACT_GATHER_BUCKETS)
                          ? set_error(EXTRACT_EINVAL, "EXTRACT_GATHER_BUCKETS: the shape does not suit the bucket "
-                                                     "tables (n <= 25600 * 2^16, regions within 220 KiB)")
+                                                     "tables (n <= 25600 * 2^18, regions within 220 KiB)")
                          : EXTRACT_OK;
             } else {
                 have_buckets = rc == EXTRACT_OK;
@@ -482,7 +484,8 @@ int extract_describe(extract_ctx *h, char *buf, uint32_t buflen)
     const HashPlan &p = h->plan;
     char gather[96];
     if (h->gb.pi)
-        snprintf(gather, sizeof gather, "gather=buckets (2^16-bit chunks, %u-word sub-block regions)", h->gb.bstride);
+        snprintf(gather, sizeof gather, "gather=buckets (2^%u-bit chunks, %u-word sub-block regions)", h->gb.clog,
+                 h->gb.bstride);
     else if (h->gw.pos)
         snprintf(gather, sizeof gather, "gather=windows (%u input windows)", h->gw.R);
     else

@@ -71,11 +71,12 @@ void gather_windows_free(GatherWindows *gw);
 // launch_gather.
 struct GatherBuckets {
     uint32_t *qc = nullptr;     // chunks + 1: first run word of each chunk
-    uint32_t *pi = nullptr;     // 16 words per run word: in-chunk positions of its 32 bits
+    uint32_t *pi = nullptr;     // 16 (or 32) words per run word: in-chunk positions of its 32 bits
     uint32_t *dst = nullptr;    // run words: word index into B (kNoPos: padding)
     uint32_t *sigma = nullptr;  // m * w_pad * 32: member bit of every stored bit
     uint32_t *B = nullptr;      // m * bstride words: the runs of each sub-block
     uint32_t nch = 0;           // input chunks
+    uint32_t clog = 16;         // chunk bits log2 (16: 16-bit pi entries, 18: 32-bit)
     uint32_t bstride = 0;       // words per sub-block region of B
     uint64_t run_words = 0;     // run words over all chunks
 };
@@ -84,12 +85,11 @@ struct GatherBuckets {
 // caller keeps the plain gather.
 constexpr int kBucketsNotEligible = 1;
 int gather_buckets_build(const uint32_t *perm, uint64_t perm_len, uint64_t n, uint32_t m, uint32_t s, uint32_t w_pad,
-                         GatherBuckets *gb, cudaStream_t st, int num_sms);
+                         GatherBuckets *gb, cudaStream_t st, int num_sms, bool wide_chunks = false);
 int gather_buckets_run(const GatherBuckets &gb, const uint32_t *in, uint64_t n, uint32_t m, uint32_t w_pad,
                        uint32_t *arev, cudaStream_t st, int num_sms);
 // The two stages alone: stage 1 over input chunks [c_begin, c_end) (of
-// kBucketChunkBits bits each), stage 2 over every sub-block.
-constexpr uint32_t kBucketChunkBits = 1u << 16;
+// 2^gb.clog bits each), stage 2 over every sub-block.
 int gather_buckets_stage1(const GatherBuckets &gb, const uint32_t *in, uint64_t n, uint32_t c_begin, uint32_t c_end,
                           cudaStream_t st, int num_sms);
 int gather_buckets_stage2(const GatherBuckets &gb, uint32_t m, uint32_t w_pad, uint32_t *arev, cudaStream_t st,

@@ -32,6 +32,7 @@ EXTRACT_METHOD_NTT = 0x8
 EXTRACT_SAMPLING_IID = 0x10
 EXTRACT_GATHER_PLAIN = 0x20
 EXTRACT_GATHER_BUCKETS = 0x40
+EXTRACT_GATHER_WIDE_CHUNKS = 0x80
 NO_POS = 0xFFFFFFFF  # padding slot of the i.i.d. law's order
 
 

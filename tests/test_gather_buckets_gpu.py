@@ -41,6 +41,8 @@ def _check_sorted(n, m, s, key, flags=0, offset_words=0, blocks=None):
     seed = synth.uniform_bits(s, 1)
     with X.Extractor(n, m, s, 1, seed, key, flags | X.EXTRACT_GATHER_BUCKETS | X.EXTRACT_METHOD_DIRECT) as ex:
         assert "gather=buckets" in ex.describe()
+        chunk = "2^18-bit chunks" if flags & X.EXTRACT_GATHER_WIDE_CHUNKS else "2^16-bit chunks"
+        assert chunk in ex.describe()
         ex.gather(_dev(in_w, offset_words))
         for j in (range(m) if blocks is None else blocks):
             want = oracle.subblock(in_w, oracle.perm_range(keys, j * s, s))
@@ -61,6 +63,26 @@ def test_sorted_order_subblocks_match_the_oracle(n, m, s, key, flags):
     _check_sorted(n, m, s, key, flags)
 
 
+W = X.EXTRACT_GATHER_WIDE_CHUNKS
+
+
+@pytest.mark.parametrize("n,m,s,key,flags", [
+    (3 * 262144 + 12345, 7, 100_001, 3, W),       # four 2^18-bit chunks, ragged tail, m*s < n
+    (1 << 20, 64, 1 << 14, 2, W),                 # m*s = n
+    (200_000, 9, 20_000, 4, W | X.EXTRACT_KEY_BITS(12)),
+    (262_144, 3, 87_381, 9, W),                   # exactly one chunk
+    (777, 5, 150, 8, W),
+])
+def test_wide_chunks_subblocks_match_the_oracle(n, m, s, key, flags):
+    """2^18-bit input chunks with 32-bit table entries (the form the library
+    takes for inputs of more than 25600 chunks of 2^16 bits)."""
+    _check_sorted(n, m, s, key, flags)
+
+
+def test_wide_chunks_input_not_16_byte_aligned():
+    _check_sorted(3 * 262144 + 100, 6, 100_000, 13, W, offset_words=1)
+
+
 def test_many_small_subblocks():
     """m = 20000 sub-blocks of 50 bits: most runs are empty or one word."""
     _check_sorted(1 << 20, 20000, 50, 12, 0, blocks=[0, 1, 777, 8191, 16383, 19999])
@@ -72,6 +94,7 @@ def test_input_not_16_byte_aligned():
 
 @pytest.mark.parametrize("n,m,key,flags", [
     (100_000, 7, 3, 0), (1 << 18, 64, 2, 0), (200_000, 33, 4, X.EXTRACT_KEY_BITS(14)), (70_000, 1, 5, 0),
+    (600_000, 5, 6, X.EXTRACT_GATHER_WIDE_CHUNKS),
 ])
 def test_iid_law_subblocks_match_the_oracle(n, m, key, flags):
     in_w = synth.bernoulli_bits(n, 0.5, 12)
@@ -147,6 +170,7 @@ def test_too_wide_region_falls_back_or_is_refused():
 
 @pytest.mark.parametrize("n,m,s,flags", [
     (1000, 2, 100, X.EXTRACT_GATHER_BUCKETS | X.EXTRACT_GATHER_PLAIN),
+    (1000, 2, 100, X.EXTRACT_GATHER_WIDE_CHUNKS | X.EXTRACT_GATHER_PLAIN),
     (1000, 2, 100, X.EXTRACT_GATHER_BUCKETS | X.EXTRACT_IDENTITY_PERM),
 ])
 def test_rejected_combinations(n, m, s, flags):
@@ -159,6 +183,7 @@ def test_rejected_combinations(n, m, s, flags):
 @pytest.mark.parametrize("n,m,s,k,flags", [
     (300_000, 9, 30_000, 4_000, X.EXTRACT_GATHER_BUCKETS | X.EXTRACT_METHOD_DIRECT),
     (5 << 20, 5, 1 << 20, 1000, 0),  # default choice at 5 Mbit: the tables
+    (5 << 20, 5, 1 << 20, 1000, X.EXTRACT_GATHER_WIDE_CHUNKS),
 ])
 def test_host_buffers_through_the_buckets_match_the_oracle(n, m, s, k, flags):
     """extract_run_host overlaps its copies with stage 1 and the hash."""
