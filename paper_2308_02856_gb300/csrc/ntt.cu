@@ -369,7 +369,9 @@ __device__ __forceinline__ uint32_t swz(uint32_t t) { return (t & ~31u) | ((t ^ 
 // stages then never mix).
 // kZeroTop: e[j] are bits and the upper half of every column is zero, so the
 // first stage's butterflies (x, 0) -> (x, x w) are one multiply each.
-template <int EPL, int HP0 = EPL / 2, bool kZeroTop = false>
+// kLastLazy: the last stage (twiddle 1) leaves x + y and x - y + 2p
+// unreduced in [0, 4p), for a Montgomery product that takes such inputs.
+template <int EPL, int HP0 = EPL / 2, bool kZeroTop = false, bool kLastLazy = false>
 __device__ __forceinline__ void dif_warp_t(uint32_t (&e)[EPL], uint32_t *sw, const uint2 *__restrict__ tw, int lane)
 {
 #pragma unroll
@@ -397,13 +399,21 @@ __device__ __forceinline__ void dif_warp_t(uint32_t (&e)[EPL], uint32_t *sw, con
 #pragma unroll
             for (int i = 0; i < 32; ++i) {
                 if (i & h) continue;
+                if (kLastLazy && h == 1) {
+                    const uint32_t a = e[32 * q + i], b = e[32 * q + i + 1];
+                    e[32 * q + i] = a + b;
+                    e[32 * q + i + 1] = a - b + k2P;
+                    continue;
+                }
                 const uint2 w = c_low_f[(h - 1) + (i & (h - 1))];
                 bf_dif(e[32 * q + i], e[32 * q + i + h], w.x, w.y);
             }
 }
 
 // DIT: layout B in, layout A out (the exact reverse of dif_warp_t).
-template <int EPL, int HP0 = EPL / 2>
+// kFirstUnit: inputs are in [0, 2p), so the first stage (twiddle 1) is
+// x + y, x - y + 2p with no reduction and no multiply.
+template <int EPL, int HP0 = EPL / 2, bool kFirstUnit = false>
 __device__ __forceinline__ void dit_warp_t(uint32_t (&e)[EPL], uint32_t *sw, const uint2 *__restrict__ tw, int lane)
 {
 #pragma unroll
@@ -413,6 +423,12 @@ __device__ __forceinline__ void dit_warp_t(uint32_t (&e)[EPL], uint32_t *sw, con
 #pragma unroll
             for (int i = 0; i < 32; ++i) {
                 if (i & h) continue;
+                if (kFirstUnit && h == 1) {
+                    const uint32_t a = e[32 * q + i], b = e[32 * q + i + 1];
+                    e[32 * q + i] = a + b;
+                    e[32 * q + i + 1] = a - b + k2P;
+                    continue;
+                }
                 const uint2 w = c_low_i[(h - 1) + (i & (h - 1))];
                 bf_dit(e[32 * q + i], e[32 * q + i + h], w.x, w.y);
             }
@@ -445,6 +461,8 @@ __device__ __forceinline__ void dit_warp_t(uint32_t (&e)[EPL], uint32_t *sw, con
 //                   spectrum q; the products are summed, transformed back,
 //                   and the row is stored in piece 0's place.  kMulti
 //                   false is the P = 1 form.
+// kLazy: outputs in [0, 4p) (for the spectrum product), else [0, 2p)
+template <bool kLazy>
 __device__ __forceinline__ void row_dif(uint32_t (&e)[32], const uint32_t *x, uint32_t *sw, const Tables &T,
                                         int lane, int w)
 {
@@ -459,7 +477,7 @@ __device__ __forceinline__ void row_dif(uint32_t (&e)[32], const uint32_t *x, ui
             e[j] = shoup_lazy(a - b + k2P, tw.x, tw.y);
         }
     }
-    dif_warp_t<32>(e, sw, T.row_stage_f, lane);
+    dif_warp_t<32, 16, false, kLazy>(e, sw, T.row_stage_f, lane);
 }
 
 // e[i] (layout B, from base) times a spectrum row computed in the same run
@@ -515,7 +533,7 @@ __device__ __forceinline__ void row_mul(uint32_t (&e)[32], uint32_t (&acc)[32], 
 __device__ __forceinline__ void row_dit_store(uint32_t (&e)[32], uint32_t *x, uint32_t (*sw)[1024], const Tables &T,
                                               int lane, int w)
 {
-    dit_warp_t<32>(e, sw[w], T.row_stage_i, lane);
+    dit_warp_t<32, 16, true>(e, sw[w], T.row_stage_i, lane);  // the products are in [0, 2p)
     // distance-1024 DIT stage: x' = x + w y, y' = x - w y (w = w_2048^-pos)
 #pragma unroll
     for (int j = 0; j < 32; ++j) {
@@ -552,7 +570,7 @@ ntt_rows_kernel(uint32_t *__restrict__ buf, uint32_t N, uint32_t R1, uint32_t P,
     const size_t so = (size_t)r * kR2 + base;
     const uint32_t *Sb = kPerBlock ? S + (size_t)g * P * N : S;
     uint32_t e[32];
-    if (!(kInverse && kMulti)) row_dif(e, x, sw[w], T, lane, w);
+    if (!(kInverse && kMulti)) row_dif<kInverse>(e, x, sw[w], T, lane, w);
     if (!kInverse) {
 #pragma unroll
         for (int i = 0; i < 32; i += 4)
@@ -574,7 +592,7 @@ ntt_rows_kernel(uint32_t *__restrict__ buf, uint32_t N, uint32_t R1, uint32_t P,
     for (int i = 0; i < 32; ++i) acc[i] = 0;
 #pragma unroll 1
     for (uint32_t q = 0; q < P; ++q) {
-        row_dif(e, x + (size_t)q * N, sw[w], T, lane, w);
+        row_dif<true>(e, x + (size_t)q * N, sw[w], T, lane, w);
         if (kMont) row_mul_mont<true>(e, acc, Sb + (size_t)q * N + so);
         else row_mul<true>(e, acc, S + (size_t)q * N + so, Sq + (size_t)q * N + so);
     }
@@ -602,7 +620,7 @@ ntt_cols_fwd_t_kernel(const uint32_t *__restrict__ bits, Pieces pc, int r1_log, 
     uint32_t e[EPL];
 #pragma unroll
     for (int j = 0; j < EPL; ++j) e[j] = (rb[32u * j + lane] >> c) & 1u;
-    dif_warp_t<EPL>(e, col, T.col_stage_f, lane);
+    dif_warp_t<EPL, EPL / 2, false, true>(e, col, T.col_stage_f, lane);  // the twist takes [0, 4p)
     // layout B: e[32 q + i] is row r = 32 (lane + 32 q) + i, frequency bitrev(r)
     const uint32_t *twr = T.twist_f + (size_t)t2 * R1;
 #pragma unroll
@@ -655,7 +673,7 @@ ntt_cols_inv_t_kernel(const uint32_t *__restrict__ buf, uint64_t sub_stride, int
             e[32 * q + i + 2] = mont_lazy(col[swz(rr + 2)], tw.z);
             e[32 * q + i + 3] = mont_lazy(col[swz(rr + 3)], tw.w);
         }
-    dit_warp_t<EPL>(e, col, T.col_stage_i, lane);
+    dit_warp_t<EPL, EPL / 2, true>(e, col, T.col_stage_i, lane);  // untwisted values are in [0, 2p)
     // layout A: e[j] is coefficient row t1 = 32 j + lane; store its parity
 #pragma unroll
     for (int j = 0; j < EPL; ++j) col[swz(32u * j + lane)] = redp(red2p(e[j])) & 1u;
@@ -776,7 +794,7 @@ ntt_cols_fwd_m_kernel(const uint32_t *__restrict__ bits, Pieces pc, uint32_t N, 
         const uint32_t cc = w * COLS + j / E, t1 = 32u * (j % E) + lane;
         e[j] = (rb[t1 * WPR + (cc >> 5)] >> (cc & 31u)) & 1u;
     }
-    dif_warp_t<32, E / 2, kZeroTop && (E >= 2)>(e, xs + w * 1024, T.col_stage_f, lane);
+    dif_warp_t<32, E / 2, kZeroTop && (E >= 2), true>(e, xs + w * 1024, T.col_stage_f, lane);  // the twist takes [0, 4p)
     // layout B: e[i] is frequency row r = 32 a + i of column cc
     const uint32_t a = lane % E, cc = w * COLS + lane / E;
     const uint32_t *twr = T.twist_f + (size_t)(c0 + cc) * R1 + 32u * a;
@@ -835,7 +853,7 @@ ntt_cols_inv_m_kernel(const uint32_t *__restrict__ buf, uint64_t sub_stride, Tab
         e[i + 3] = mont_lazy(xs[tile_at<E>(32u * a + i + 3, cc)], tw.w);
     }
     __syncthreads();  // the tile is consumed; warps reuse it as scratch
-    dit_warp_t<32, E / 2>(e, xs + w * 1024, T.col_stage_i, lane);
+    dit_warp_t<32, E / 2, true>(e, xs + w * 1024, T.col_stage_i, lane);  // untwisted values are in [0, 2p)
     // layout A: e[j] is coefficient row 32 (j % E) + lane of column w COLS + j / E;
     // only row blocks holding a wanted coefficient [len-1, len+k-1) are packed
     const uint32_t row_lo = (len - 1) / kR2, row_hi = (uint32_t)(((uint64_t)len + k - 2) / kR2);
