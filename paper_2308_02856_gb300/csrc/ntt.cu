@@ -116,6 +116,23 @@ __device__ __forceinline__ void bf_dif(uint32_t &x, uint32_t &y, uint32_t w, uin
     x = red2p(x + y);
     y = shoup_lazy(d, w, wq);
 }
+// DIF butterflies with looser bounds (8p < 2^32): inputs in [0, 4p) give
+// x' in [0, 4p) and y' in [0, 2p); inputs in [0, 2p) give the same bounds
+// with no reduction at all (x' = x + y).
+constexpr uint32_t k4P = 4u * kP;
+__device__ __forceinline__ uint32_t red4p(uint32_t x) { return min(x, x - k4P); }  // [0,8p) -> [0,4p)
+__device__ __forceinline__ void bf_dif_4p(uint32_t &x, uint32_t &y, uint32_t w, uint32_t wq)
+{
+    const uint32_t d = x - y + k4P;
+    x = red4p(x + y);
+    y = shoup_lazy(d, w, wq);
+}
+__device__ __forceinline__ void bf_dif_2p(uint32_t &x, uint32_t &y, uint32_t w, uint32_t wq)
+{
+    const uint32_t d = x - y + k2P;
+    x = x + y;
+    y = shoup_lazy(d, w, wq);
+}
 // DIT butterfly, inputs and outputs in [0, 4p)
 __device__ __forceinline__ void bf_dit(uint32_t &x, uint32_t &y, uint32_t w, uint32_t wq)
 {
@@ -369,9 +386,14 @@ __device__ __forceinline__ uint32_t swz(uint32_t t) { return (t & ~31u) | ((t ^ 
 // stages then never mix).
 // kZeroTop: e[j] are bits and the upper half of every column is zero, so the
 // first stage's butterflies (x, 0) -> (x, x w) are one multiply each.
-// kLastLazy: the last stage (twiddle 1) leaves x + y and x - y + 2p
-// unreduced in [0, 4p), for a Montgomery product that takes such inputs.
-template <int EPL, int HP0 = EPL / 2, bool kZeroTop = false, bool kLastLazy = false>
+// kLazy (inputs in [0, 2p); outputs in [0, 4p), for a Montgomery product
+// that takes them): every stage leaves its sums x + y in [0, 4p) and its
+// differences in [0, 2p), so a pair of two earlier differences needs no
+// reduction; which earlier branch a pair comes from is fixed by its register
+// index, except across the transpose (the lane's parity), where the 4p form
+// is used.  The last stage (twiddle 1) of a difference pair is x + y,
+// x - y + 2p with no multiply.
+template <int EPL, int HP0 = EPL / 2, bool kZeroTop = false, bool kLazy = false>
 __device__ __forceinline__ void dif_warp_t(uint32_t (&e)[EPL], uint32_t *sw, const uint2 *__restrict__ tw, int lane)
 {
 #pragma unroll
@@ -380,8 +402,17 @@ __device__ __forceinline__ void dif_warp_t(uint32_t (&e)[EPL], uint32_t *sw, con
         for (int j = 0; j < EPL; ++j) {
             if (j & hp) continue;
             const uint2 w = __ldg(tw + (32 * hp - 1) + lane + 32 * (j & (hp - 1)));
-            if (kZeroTop && hp == HP0) e[j + hp] = e[j] * w.x;
-            else bf_dif(e[j], e[j + hp], w.x, w.y);
+            if (kZeroTop && hp == HP0) {
+                e[j + hp] = e[j] * w.x;
+            } else if (!kLazy) {
+                bf_dif(e[j], e[j + hp], w.x, w.y);
+            } else {
+                // inputs below 2p: the first stage, the stage after the
+                // zero-top one, or two differences of the previous stage
+                const bool low = hp == HP0 || (kZeroTop && 2 * hp == HP0) || (j & (2 * hp));
+                if (low) bf_dif_2p(e[j], e[j + hp], w.x, w.y);
+                else bf_dif_4p(e[j], e[j + hp], w.x, w.y);
+            }
         }
     }
 #pragma unroll
@@ -399,14 +430,22 @@ __device__ __forceinline__ void dif_warp_t(uint32_t (&e)[EPL], uint32_t *sw, con
 #pragma unroll
             for (int i = 0; i < 32; ++i) {
                 if (i & h) continue;
-                if (kLastLazy && h == 1) {
+                const uint2 w = c_low_f[(h - 1) + (i & (h - 1))];
+                if (!kLazy) {
+                    bf_dif(e[32 * q + i], e[32 * q + i + h], w.x, w.y);
+                    continue;
+                }
+                // h = 16 follows the register stages across the transpose
+                const bool low = h == 16 ? (HP0 == 0 || (kZeroTop && HP0 == 1)) : (i & (2 * h)) != 0;
+                if (h == 1 && low) {
                     const uint32_t a = e[32 * q + i], b = e[32 * q + i + 1];
                     e[32 * q + i] = a + b;
                     e[32 * q + i + 1] = a - b + k2P;
-                    continue;
+                } else if (low) {
+                    bf_dif_2p(e[32 * q + i], e[32 * q + i + h], w.x, w.y);
+                } else {
+                    bf_dif_4p(e[32 * q + i], e[32 * q + i + h], w.x, w.y);
                 }
-                const uint2 w = c_low_f[(h - 1) + (i & (h - 1))];
-                bf_dif(e[32 * q + i], e[32 * q + i + h], w.x, w.y);
             }
 }
 

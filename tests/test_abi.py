@@ -33,6 +33,20 @@ def lib():
     return X.load()
 
 
+def test_binding_constants_match_the_header():
+    """Every plain numeric #define EXTRACT_* in include/*.h has the same value
+    in the Python binding (return codes, create and batch flags)."""
+    seen = 0
+    for h in HEADERS:
+        text = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        for name, val in re.findall(r"^#define\s+(EXTRACT_[A-Z0-9_]+)\s+\(?\s*(-?(?:0x[0-9a-fA-F]+|\d+))u?\s*\)?\s*$",
+                                    text, flags=re.M):
+            assert hasattr(X, name), name
+            assert getattr(X, name) == int(val, 0), name
+            seen += 1
+    assert seen >= 20
+
+
 def test_header_declares_the_boundary():
     d = _declared()
     for name in ("extract_create", "extract_run", "extract_destroy", "extract_last_error"):
