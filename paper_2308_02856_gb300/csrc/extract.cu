@@ -324,7 +324,7 @@ int extract_create(extract_ctx **out, uint64_t n, uint32_t m, uint32_t s, uint32
                                   (!(flags & EXTRACT_GATHER_PLAIN) && n >= kBucketsMinBits);
         bool have_buckets = false;
         if (rc == EXTRACT_OK && want_buckets) {
-            rc = gather_buckets_build(h->perm, h->perm_len, n, m, s, h->w_pad, &h->gb, st, h->num_sms,
+            rc = gather_buckets_build(h->perm, n, m, s, h->w_pad, &h->gb, st, h->num_sms,
                                       (flags & EXTRACT_GATHER_WIDE_CHUNKS) != 0);
             if (rc == kBucketsNotEligible) {
                 rc = (flags & EXTRACT_GATHER_BUCKETS)

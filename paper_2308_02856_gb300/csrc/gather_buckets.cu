@@ -424,10 +424,9 @@ int build_tables(const uint32_t *perm, uint64_t n, uint32_t m, uint32_t s, uint3
 
 }  // namespace
 
-int gather_buckets_build(const uint32_t *perm, uint64_t perm_len, uint64_t n, uint32_t m, uint32_t s, uint32_t w_pad,
-                         GatherBuckets *gb, cudaStream_t st, int num_sms, bool wide_chunks)
+int gather_buckets_build(const uint32_t *perm, uint64_t n, uint32_t m, uint32_t s, uint32_t w_pad, GatherBuckets *gb,
+                         cudaStream_t st, int num_sms, bool wide_chunks)
 {
-    (void)perm_len;  // sub-block j is perm[j s .. j s + s) in both layouts
     gather_buckets_free(gb);
     if (n > (1ull << 32) || w_pad % 32u || n == 0) return kBucketsNotEligible;
     // 2^16-bit chunks (16-bit pi entries) unless they are too many or leave

@@ -84,8 +84,9 @@ struct GatherBuckets {
 // (too many input chunks, a region wider than shared memory, no room); the
 // caller keeps the plain gather.
 constexpr int kBucketsNotEligible = 1;
-int gather_buckets_build(const uint32_t *perm, uint64_t perm_len, uint64_t n, uint32_t m, uint32_t s, uint32_t w_pad,
-                         GatherBuckets *gb, cudaStream_t st, int num_sms, bool wide_chunks = false);
+// Sub-block j's slots are perm[j s .. j s + s) (either sampling law).
+int gather_buckets_build(const uint32_t *perm, uint64_t n, uint32_t m, uint32_t s, uint32_t w_pad, GatherBuckets *gb,
+                         cudaStream_t st, int num_sms, bool wide_chunks = false);
 int gather_buckets_run(const GatherBuckets &gb, const uint32_t *in, uint64_t n, uint32_t m, uint32_t w_pad,
                        uint32_t *arev, cudaStream_t st, int num_sms);
 // The two stages alone: stage 1 over input chunks [c_begin, c_end) (of

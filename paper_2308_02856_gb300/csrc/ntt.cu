@@ -611,6 +611,9 @@ ntt_rows_kernel(uint32_t *__restrict__ buf, uint32_t N, uint32_t R1, uint32_t P,
     uint32_t e[32];
     if (!(kInverse && kMulti)) row_dif<kInverse>(e, x, sw[w], T, lane, w);
     if (!kInverse) {
+        // both warps read both halves of the row in row_dif: no half is
+        // overwritten before the other warp has loaded it
+        __syncthreads();
 #pragma unroll
         for (int i = 0; i < 32; i += 4)
             *reinterpret_cast<uint4 *>(x + base + i) = make_uint4(e[i], e[i + 1], e[i + 2], e[i + 3]);

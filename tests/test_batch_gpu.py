@@ -185,3 +185,31 @@ def test_batch_mixes_ntt_and_direct_jobs():
     for i in (0, 2, 5):
         j = jobs[i]
         _check_rows_against_oracle(j, ins[i], _host(outs[i]), sorted({0, j["m"] - 1}), 16, rng)
+
+
+def test_batch_repeated_runs_stay_exact():
+    """1000 runs of a mixed batch (NTT jobs on concurrent lanes, one with a
+    seed per sub-block, next to the persistent direct launch) against one
+    direct-only run.  Guards the row pass that transforms seed windows in
+    place: without the barrier between its loads and its stores, about one
+    run in a thousand lost one sub-block to the race."""
+    shapes = []
+    for i, (n, s, k, fl) in enumerate([(1 << 20, 1 << 18, 1 << 17, 0), (1 << 14, 1 << 12, 500, 0),
+                                       (3 << 18, 1 << 18, 70_001, 0), (1 << 16, 1 << 13, 4000, 0),
+                                       (1 << 20, 1 << 17, 1 << 15, X.EXTRACT_SEED_PER_SUBBLOCK)]):
+        shapes.append({"n": n, "m": n // s, "s": s, "k": k, "flags": fl, "p": 0.6 + 0.05 * i,
+                       "in_seed": 800 + i, "seed_seed": 900 + i, "key": 1000 + i})
+    jobs, ins = _materialise(shapes)
+    d_in = [_dev(w) for w in ins]
+    with X.Batch(jobs) as b, X.Batch(jobs, X.EXTRACT_BATCH_DIRECT_ONLY) as bd:
+        ref = _outs(jobs, fill=3)
+        bd.run(d_in, ref)
+        outs = _outs(jobs)
+        bad = []
+        for r in range(1000):
+            b.run(d_in, outs)
+            bad += [(r, i) for i in range(len(jobs)) if not torch.equal(outs[i], ref[i])]
+        assert not bad, bad[:10]
+    j = jobs[4]
+    want = oracle.extract(j["n"], j["m"], j["s"], j["k"], ins[4], j["seed"], j["key"], j["flags"])
+    assert np.array_equal(_host(ref[4]), want)
