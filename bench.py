@@ -249,7 +249,8 @@ NTT_TRAFFIC_BYTES = {"qrng_n2^30_m1024_s2^20_k2^19": 129.1e6 * 128,
 
 def ntt_roofline(n, m, s, k, hash_ms, plan, sms=152, workload=None):
     """NTT path: the transform work (P forward pieces, P seed windows when
-    every sub-block has its own seed, one inverse; N/2 log2 N radix-2
+    every sub-block has its own seed and the plan transforms them per run
+    rather than keeping their spectra, one inverse; N/2 log2 N radix-2
     butterflies each, per sub-block) against the integer ALU pipe.  A lazy
     butterfly is 7 integer instructions, 4 of them (adds, subtracts, min) on
     the 64-lane ALU pipe and 3 IMAD on the FMA pipe, so the ALU pipe bounds
@@ -257,7 +258,7 @@ def ntt_roofline(n, m, s, k, hash_ms, plan, sms=152, workload=None):
     import math
     N = int(plan.split("N=")[1].split(" ")[0])
     P = int(plan.split("P=")[1].split(" ")[0]) if "P=" in plan else 1
-    transforms = (2 * P + 1) if "one seed per sub-block" in plan else (P + 1)
+    transforms = (2 * P + 1) if "seed windows transformed per run" in plan else (P + 1)
     bfly = m * transforms * (N // 2) * math.log2(N)
     achieved = bfly / (hash_ms / 1e3) / 1e12
     peak = sms * 64 / 4.0 * 2070e6 / 1e12

@@ -69,9 +69,12 @@ extern "C" {
    forces the number-theoretic-transform middle product modulo the prime
    7*2^26+1.  It splits each sub-block into P = 2^l pieces of h bits (h = s
    for P = 1, else ceil(s/P) rounded up to a multiple of 32) and costs P + 1
-   transforms of the power of two N >= h+k-1 per sub-block (2P + 1 with
-   EXTRACT_SEED_PER_SUBBLOCK, whose seed windows are transformed in every
-   run; then N >= 2^16); it needs s+k-1 > 2^11, s < 7*2^26+1 and
+   transforms of the power of two N >= h+k-1 per sub-block.  With
+   EXTRACT_SEED_PER_SUBBLOCK (then N >= 2^16) the spectra of every
+   sub-block's seed windows are built at create and kept (4 m P N bytes)
+   when they take at most a quarter of the free device memory, else their
+   windows are transformed in every run (2P + 1 transforms).  It needs
+   s+k-1 > 2^11, s < 7*2^26+1 and
    N <= 2^22 for some P <= 16 (EXTRACT_EINVAL otherwise).  Both methods
    give the same bits. */
 #define EXTRACT_METHOD_DIRECT     0x4u

@@ -283,7 +283,16 @@ int extract_create(extract_ctx **out, uint64_t n, uint32_t m, uint32_t s, uint32
     if (use_ntt) {
         cudaStream_t st;
         if ((e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) != cudaSuccess) { free_ctx(h); return cuda_error(e, "stream"); }
-        int rc = ntt_create(&h->ntt, m, s, k, h->seed, st, nullptr, split, per_sub ? h->seed_stride : 0);
+        // independent seeds: keep every sub-block's seed spectrum when it
+        // takes at most a quarter of the free device memory (P + 1 transforms
+        // per run instead of 2P + 1)
+        bool resident = false;
+        if (per_sub) {
+            size_t free_b = 0, total_b = 0;
+            if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess)
+                resident = ntt_resident_spectra_words(m, s, k, split) * 4 <= free_b / 4;
+        }
+        int rc = ntt_create(&h->ntt, m, s, k, h->seed, st, nullptr, split, per_sub ? h->seed_stride : 0, resident);
         cudaStreamDestroy(st);
         if (rc != EXTRACT_OK) { free_ctx(h); return rc; }
         if ((e = cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking)) != cudaSuccess ||
@@ -495,7 +504,9 @@ int extract_describe(extract_ctx *h, char *buf, uint32_t buflen)
                  "ntt: N=%u (%u x 2048) P=%u pieces per sub-block, %u sub-blocks per launch group, "
                  "prime 7*2^26+1, %s; sms=%d; %s",
                  ntt_size(h->ntt), ntt_size(h->ntt) / 2048, ntt_pieces(h->ntt), ntt_group(h->ntt),
-                 h->nseeds > 1 ? "seed windows transformed per run (one seed per sub-block)" : "shared seed spectrum",
+                 h->nseeds > 1 ? (ntt_spectra_resident(h->ntt) ? "seed spectra resident (one seed per sub-block)"
+                                                                : "seed windows transformed per run (one seed per sub-block)")
+                               : "shared seed spectrum",
                  h->num_sms, gather);
         return EXTRACT_OK;
     }

@@ -185,9 +185,17 @@ double ntt_work_butterflies(uint32_t m, uint32_t s, uint32_t k, int split_log2 =
 // Builds the twiddle tables and the seed spectra (synchronous on st).  work:
 // a caller-owned buffer of ntt_work_words() words shared by plans that never
 // run concurrently, or null to allocate one.
-// seed_stride > 0: one seed per sub-block, seed_stride words apart.
+// seed_stride > 0: one seed per sub-block, seed_stride words apart; with
+// resident_spectra the spectra of all m sub-blocks' seed windows are built
+// here and kept (m P N words), else every run transforms them again.
 int ntt_create(NttPlan **out, uint32_t m, uint32_t s, uint32_t k, const uint32_t *seed_dev, cudaStream_t st,
-               uint32_t *work = nullptr, int split_log2 = -1, uint64_t seed_stride = 0);
+               uint32_t *work = nullptr, int split_log2 = -1, uint64_t seed_stride = 0,
+               bool resident_spectra = false);
+// Words of the resident per-sub-block spectra (m P N) of a plan for (m, s, k)
+// with one seed per sub-block.
+uint64_t ntt_resident_spectra_words(uint32_t m, uint32_t s, uint32_t k, int split_log2 = -1);
+// True when the plan keeps every sub-block's seed spectrum.
+bool ntt_spectra_resident(const NttPlan *p);
 // Extra streams and work buffers for ntt_hash: launch group i runs on lane
 // i mod (1 + n) (lane 0 = the caller's stream and buffer), so one group's
 // passes fill the others' last waves.  Events owned by the caller.

@@ -951,8 +951,10 @@ struct NttPlan {
     uint32_t P = 1, h = 0;  // pieces per sub-block and coefficients per piece
     uint32_t *buf = nullptr, *S = nullptr, *Sq = nullptr, *tables = nullptr, *twist = nullptr;
     bool own_buf = true;
-    // independent seeds: every sub-block's windows are transformed per run
+    // independent seeds: every sub-block's windows are transformed per run,
+    // or (resident) once at create into S, m P N words
     bool per_block = false;
+    bool resident = false;
     const uint32_t *seed = nullptr;  // sub-block j's seed at seed + j seed_stride words
     uint64_t seed_stride = 0;
     uint32_t L = 0;                  // bits per seed (s + k - 1)
@@ -1217,8 +1219,10 @@ static int device_setup(cudaStream_t st)
 
 // seed_dev: realigned seed bits (bit t = seed[t]), L = s + k - 1 bits; with
 // seed_stride > 0 one seed per sub-block, seed_stride words apart.
+static Pieces seed_pieces(const NttPlan *p, uint32_t k);
+
 int ntt_create(NttPlan **out, uint32_t m, uint32_t s, uint32_t k, const uint32_t *seed_dev, cudaStream_t st,
-               uint32_t *work, int split_log2, uint64_t seed_stride)
+               uint32_t *work, int split_log2, uint64_t seed_stride, bool resident_spectra)
 {
     *out = nullptr;
     const bool per_block = seed_stride > 0;
@@ -1335,6 +1339,24 @@ int ntt_create(NttPlan **out, uint32_t m, uint32_t s, uint32_t k, const uint32_t
             break;
         }
         if ((rc = device_setup(st)) != EXTRACT_OK) break;
+        if (per_block && resident_spectra) {
+            // every sub-block's seed windows, group by group, through pass A
+            // and the forward row pass into S (sub-block j's piece q at
+            // (j P + q) N), the layout the inverse row pass reads
+            if ((e = cudaMallocAsync(&p->S, (size_t)m * spec * 4, st)) != cudaSuccess) {
+                cudaGetLastError();
+                rc = set_error(EXTRACT_ENOMEM, "ntt: no room for %u resident seed spectra", m);
+                break;
+            }
+            p->resident = true;
+            for (uint32_t j0 = 0; j0 < m && rc == EXTRACT_OK; j0 += p->G) {
+                const uint32_t g = std::min(p->G, m - j0);
+                uint32_t *sj = p->S + (size_t)j0 * spec;
+                if (int lrc = ntt_launch_a(p, p->seed + (size_t)j0 * p->seed_stride, seed_pieces(p, k), false, g, sj, st)) rc = lrc;
+                else ntt_launch_rows(p, sj, g * p->P, 1, nullptr, nullptr, false, st);
+            }
+            if (rc != EXTRACT_OK) break;
+        }
         if (per_block) {
             if ((e = cudaGetLastError()) != cudaSuccess) { rc = cuda_error(e, "ntt tables"); break; }
             if ((e = cudaStreamSynchronize(st)) != cudaSuccess) { rc = cuda_error(e, "ntt tables"); break; }
@@ -1389,6 +1411,8 @@ static int ntt_group_run(const NttPlan *p, const uint32_t *arev, uint32_t w_pad,
     if (int rc = ntt_launch_a(p, arev + (size_t)j0 * w_pad, pc, true, g, gb, gs)) return rc;
     if (!p->per_block) {
         ntt_launch_rows(p, gb, g, p->P, p->S, p->Sq, true, gs);
+    } else if (p->resident) {
+        ntt_launch_rows(p, gb, g, p->P, p->S + (size_t)j0 * p->P * p->N, nullptr, true, gs, true);
     } else {
         // the seed windows' spectra, transformed into the second half
         uint32_t *sb = gb + (size_t)p->G * p->P * p->N;
@@ -1472,6 +1496,12 @@ int ntt_run_overlapped(const NttPlan *p, const uint32_t *in, const uint32_t *per
 }
 
 uint32_t ntt_group(const NttPlan *p) { return p->G; }
+bool ntt_spectra_resident(const NttPlan *p) { return p->resident; }
+uint64_t ntt_resident_spectra_words(uint32_t m, uint32_t s, uint32_t k, int split_log2)
+{
+    const NttShape sh = ntt_shape(s, k, split_log2, true);
+    return (uint64_t)m * sh.P * sh.N;
+}
 uint32_t ntt_size(const NttPlan *p) { return p->N; }
 uint32_t ntt_pieces(const NttPlan *p) { return p->P; }
 
