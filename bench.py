@@ -476,8 +476,8 @@ def run_ours(args):
                                     "(eps %g, p_sift 1/m)" % IID_EPS) if iid else "stable argsort, equal sub-blocks",
                        "seeds": {"input": IN_SEED, "sampling_key": SAMPLING_KEY, "toeplitz": TOEPLITZ_SEED},
                        "order": "resident (built once per sampling key; see create_ms)",
-                       "l2": ("inputs larger than L2: bucket tables (2 B per sampled bit + 4 B per stored "
-                              "sub-block bit) + n/8-byte input read per step" if "gather=buckets" in plan else
+                       "l2": ("inputs larger than L2: bucket tables (about 2.5 B per sampled bit + 2.6 B per "
+                              "stored sub-block bit) + n/8-byte input read per step" if "gather=buckets" in plan else
                               "inputs larger than L2: 4n-byte order + n/8-byte input read per step"),
                        "parallelism": "replicas" if world > 1 else "1 GPU",
                        "plan": plan},
