@@ -280,10 +280,10 @@ __device__ __forceinline__ uint32_t sub_digit(uint64_t label, int b)
 
 // One CTA per bucket (grid-stride over buckets).  Each thread keeps its
 // (up to kSortCap / kSortThreads) entries in registers; shared memory holds
-// only the counting-pass bins and the sorted copy k2 / i2, so 8 CTAs fit on
+// only the counting-pass bins and the binned copy k2 / i2, so 8 CTAs fit on
 // an SM.  A counting pass on the next kSubBits label bits leaves about 4
-// entries per bin, then each thread insertion-sorts one bin by (label,
-// position).
+// entries per bin; each entry's rank inside its bin by (label, position)
+// then places it directly.
 __global__ void __launch_bounds__(kSortThreads)
 perm_local_sort_kernel(uint32_t nb, int b, uint2 key, uint64_t mask, const uint64_t *start,
                        uint32_t *perm, uint32_t *big_list, uint32_t *big_count)
@@ -351,23 +351,20 @@ perm_local_sort_kernel(uint32_t nb, int b, uint2 key, uint64_t mask, const uint6
             }
         }
         __syncthreads();
-        {
-            const uint32_t a = hist[threadIdx.x], z = hist[threadIdx.x + 1];
-            for (uint32_t x = a + 1; x < z; ++x) {
-                const uint64_t kx = k2[x];
-                const uint32_t ix = i2[x];
-                uint32_t y = x;
-                while (y > a && less_pair(kx, ix, k2[y - 1], i2[y - 1])) {
-                    k2[y] = k2[y - 1];
-                    i2[y] = i2[y - 1];
-                    --y;
-                }
-                k2[y] = kx;
-                i2[y] = ix;
+        // every entry's place: its bin's start plus the number of entries of
+        // the bin that sort before it (positions are distinct, so no ties);
+        // all reads of this bucket's perm entries happened before the barriers
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+            const uint32_t e = threadIdx.x + q * kSortThreads;
+            if (e < L) {
+                const uint32_t d = sub_digit(lab[q], b);
+                const uint32_t a = hist[d], z = hist[d + 1];
+                uint32_t rank = 0;
+                for (uint32_t f = a; f < z; ++f) rank += less_pair(k2[f], i2[f], lab[q], idx[q]) ? 1u : 0u;
+                perm[lo + a + rank] = idx[q];
             }
         }
-        __syncthreads();
-        for (uint32_t e = threadIdx.x; e < L; e += blockDim.x) perm[lo + e] = i2[e];
         __syncthreads();
     }
 }
