@@ -239,12 +239,12 @@ def launches_per_step(is_ntt, m, plan, n=0):
 
 
 # DRAM bytes (read + write) of one NTT hash: the ncu capture of one launch
-# group (8 sub-blocks, P = 2, N = 2^20: 129.1 MB over the three passes, cold
+# group (16 sub-blocks, P = 2, N = 2^20: 327.7 MB over the three passes, cold
 # cache; profiles/ntt_kernels_qrng128_n2^27_m128_s2^20_k2^19.md) times the
 # groups of the block.  Set to None whenever the kernels change until they
 # are captured again.
-NTT_TRAFFIC_BYTES = {"qrng_n2^30_m1024_s2^20_k2^19": 129.1e6 * 128,
-                     "qrng128_n2^27_m128_s2^20_k2^19": 129.1e6 * 16}
+NTT_TRAFFIC_BYTES = {"qrng_n2^30_m1024_s2^20_k2^19": 327.7e6 * 64,
+                     "qrng128_n2^27_m128_s2^20_k2^19": 327.7e6 * 8}
 
 
 def ntt_roofline(n, m, s, k, hash_ms, plan, sms=152, workload=None):

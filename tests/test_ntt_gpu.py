@@ -44,7 +44,7 @@ ORACLE_CASES = [
     (4096 * 3, 3, 4096, 1),         # k = 1, N = 4096
     (2049 * 2, 2, 2049, 1),         # s + k - 1 = 2049: the smallest NTT shape
     (6000, 1, 3000, 3000),          # k = s
-    (200_000, 37, 5000, 3001),      # ragged, several launch groups
+    (200_000, 37, 5000, 3001),      # ragged
     (1 << 18, 8, 1 << 15, 1 << 13),  # the small plain sub-block case, N = 2^16
     (70_001, 5, 14_000, 7_000),     # N = 32768, n > m*s
 ]
