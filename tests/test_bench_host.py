@@ -1,5 +1,6 @@
 """Host-side logic of bench.py: the multi-rank aggregation (replicas, weak
-scaling; world_size 2 over gloo on CPU) and the reference arm's JSON line."""
+scaling; world_size 2 over gloo on CPU), the reference arm's JSON line, and
+the launch count and NTT work it derives from the library's plan."""
 import json
 import os
 import subprocess
@@ -54,3 +55,36 @@ def test_reference_arm_prints_one_json_line():
     assert d["value"] > 0 and d["unit"] == "Gbit/s"
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_launch_count_and_ntt_work_follow_the_plan_string():
+    """gpu_launches and the NTT roofline's work are derived from the plan the
+    library describes: the gather form (two bucket stages, window passes or
+    plain passes), the launch groups, and whether seed windows are
+    transformed per run."""
+    import importlib
+    bench = importlib.import_module("bench")
+    ntt = ("ntt: N=1048576 (512 x 2048) P=2 pieces per sub-block, 16 sub-blocks per launch group, prime "
+           "7*2^26+1, %s; sms=152; gather=%s")
+    shared_buckets = ntt % ("shared seed spectrum", "buckets (2^16-bit chunks, 40548-word sub-block regions)")
+    assert bench.launches_per_step(True, 1024, shared_buckets, 1 << 30) == 2 + 3 * 64
+    windows = ntt % ("shared seed spectrum", "windows (8 input windows)")
+    assert bench.launches_per_step(True, 4096, windows, 1 << 32) == 8 + 3 * 256
+    plain_big = ntt % ("shared seed spectrum", "plain")
+    assert bench.launches_per_step(True, 4096, plain_big, 1 << 32) == 4 * 256   # a gather per group
+    plain_small = ntt % ("shared seed spectrum", "plain")
+    assert bench.launches_per_step(True, 64, plain_small, 1 << 24) == 1 + 3 * 4
+    direct = "lop3 tile: rows=1024 ... w_pad=32768 sms=152; gather=plain"
+    assert bench.launches_per_step(False, 128, direct, 1 << 30) == 2 + 1       # two input windows + hash
+    assert bench.launches_per_step(False, 128, direct, 1 << 27) == 1 + 1
+    m, s, k = 1024, 1 << 20, 1 << 19
+    per_run = ntt % ("seed windows transformed per run (one seed per sub-block)", "plain")
+    resident = ntt % ("seed spectra resident (one seed per sub-block)", "plain")
+    w_shared = bench.ntt_roofline(1 << 30, m, s, k, 10.0, shared_buckets)["work_per_launch"]
+    w_per_run = bench.ntt_roofline(1 << 30, m, s, k, 10.0, per_run)["work_per_launch"]
+    w_resident = bench.ntt_roofline(1 << 30, m, s, k, 10.0, resident)["work_per_launch"]
+    assert "m x 3 transforms" in w_shared and "m x 3 transforms" in w_resident
+    assert "m x 5 transforms" in w_per_run
+    bfly = m * 3 * (1 << 19) * 20
+    r = bench.ntt_roofline(1 << 30, m, s, k, 10.0, shared_buckets)
+    assert abs(r["achieved"] - bfly / 1e-2 / 1e12) < 1e-9 and abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-12
