@@ -44,7 +44,6 @@
 #include "internal.h"
 
 #include <algorithm>
-#include <cstdio>
 #include <vector>
 
 namespace ex {
