@@ -136,10 +136,14 @@ typedef struct extract_ctx extract_ctx;
  *   sampling_key   64-bit Philox key of the sampling labels.
  *   flags          EXTRACT_* create flags.
  *
- * Synchronous: it returns once the order is built.  Device memory held:
- * 4n bytes of order (4ms with EXTRACT_SAMPLING_IID, none with
- * EXTRACT_IDENTITY_PERM) plus about n/8 bytes of sub-block buffer and the
- * seed.  Errors: EINVAL, ENOMEM, ECUDA, EABORT (i.i.d. law only).
+ * Synchronous: it returns once the order (and the tables below) are built.
+ * Device memory held: 4n bytes of order (4ms with EXTRACT_SAMPLING_IID, none
+ * with EXTRACT_IDENTITY_PERM) plus about n/8 bytes of sub-block buffer and
+ * the seed; with the bucketed gather about 5 more bytes per sampled bit (see
+ * EXTRACT_GATHER_PLAIN); with the NTT method its tables and one work buffer
+ * of at most 128 MB per lane; with EXTRACT_SEED_PER_SUBBLOCK and the NTT
+ * method possibly the resident seed spectra (see EXTRACT_METHOD_NTT).
+ * Errors: EINVAL, ENOMEM, ECUDA, EABORT (i.i.d. law only).
  */
 int extract_create(extract_ctx **out, uint64_t n, uint32_t m, uint32_t s, uint32_t k,
                    const uint32_t *seed_bits_host, uint64_t sampling_key, uint32_t flags);
@@ -164,10 +168,14 @@ int extract_run(extract_ctx *h, void *stream, const uint32_t *in_bits_dev,
 /*
  * extract_run_host - extract_run on host buffers, end to end: copies the
  * ceil(n/32) input words from in_bits_host to the device, runs steps 1-3 and
- * copies the ceil(m*k/32) output words back to out_bits_host, all on
- * `stream`; returns once the output is in host memory.  The device staging
- * buffers are allocated on the first call and kept until extract_destroy.
- * Page-locked host buffers give full copy bandwidth; pageable ones work.
+ * copies the ceil(m*k/32) output words back to out_bits_host, ordered after
+ * earlier work on `stream`; returns once the output is in host memory.  With
+ * the bucketed gather the copies run on an internal stream of the context and
+ * overlap the work (input pieces feed the gather as they land; the NTT
+ * hash's finished output words go back while later ones are computed).  The
+ * device staging buffers are allocated on the first call and kept until
+ * extract_destroy.  Page-locked host buffers give full copy bandwidth;
+ * pageable ones work.  Calls on one context must not overlap.
  * Errors: EINVAL (null pointers), ENOMEM, ECUDA.
  */
 int extract_run_host(extract_ctx *h, void *stream, const uint32_t *in_bits_host,
