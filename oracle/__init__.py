@@ -4,8 +4,10 @@ TEST INFRASTRUCTURE ONLY: imported by ``tests/``, ``__graft_entry__.smoke()``
 and the CPU-baseline leg of ``bench.py``.  The product path (the CUDA library
 and its binding) never imports this package.
 
-The arithmetic lives in ``oracle.c`` (plain C, one bit at a time); this module
-compiles it with gcc and marshals numpy arrays through ctypes.  Definitions
+The arithmetic lives in ``oracle.c`` (plain C, one bit at a time) and
+``oracle_fast.c`` (the same Toeplitz sum on 64-bit words: AND, XOR and one
+popcount parity per output bit, pinned to the bit loop); this module compiles
+them with gcc and marshals numpy arrays through ctypes.  Definitions
 (Sec. III.B steps 1, 3 and 4 of the paper, Sec. I for K = T . A'):
 
 * sampling label of position i: ``(x0 << 32) | x1`` of Philox4x32-10 with
@@ -29,6 +31,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
+_SRC_FAST = os.path.join(_HERE, "oracle_fast.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
 SEED_PER_SUBBLOCK = 0x1
@@ -47,13 +50,14 @@ def KEY_BITS(b: int) -> int:
 
 
 def build(force: bool = False) -> str:
-    """Compile ``oracle.c`` into ``liboracle.so`` (plain -O2, not tuned)."""
+    """Compile ``oracle.c`` and ``oracle_fast.c`` into ``liboracle.so``
+    (plain -O2, not tuned)."""
     if (not force and os.path.exists(_LIB)
-            and os.path.getmtime(_LIB) >= max(os.path.getmtime(_SRC),
+            and os.path.getmtime(_LIB) >= max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_FAST),
                                               os.path.getmtime(os.path.join(_HERE, "oracle.h")))):
         return _LIB
     tmp = _LIB + ".tmp%d" % os.getpid()
-    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-pthread", "-o", tmp, _SRC, "-lm"]
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-pthread", "-o", tmp, _SRC, _SRC_FAST, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB)
     return _LIB
@@ -98,6 +102,11 @@ def load_library(path: str) -> ctypes.CDLL:
     L.oracle_size_tail_bound.restype = ctypes.c_double
     L.oracle_block_limit.argtypes = [u64, u64, ctypes.c_double, ctypes.c_double]
     L.oracle_block_limit.restype = u64
+    if hasattr(L, "oracle_fast_window"):
+        L.oracle_fast_window.argtypes = [vp, vp, u64, u64, vp, u64, u32, vp, u64, u64, u64, vp, i32]
+        L.oracle_fast_window.restype = i32
+        L.oracle_perm_ranges.argtypes = [u64, vp, u64, vp, vp, vp]
+        L.oracle_perm_ranges.restype = i32
     return L
 
 
@@ -261,3 +270,61 @@ def bits_of(words: np.ndarray, nbits: int) -> np.ndarray:
     """Unpack LSB-first uint32 words into one uint8 per bit (first nbits)."""
     w = np.ascontiguousarray(words, dtype="<u4")
     return np.unpackbits(w.view(np.uint8), bitorder="little")[:nbits]
+
+
+# ---- word-packed restatement (oracle_fast.c) --------------------------------
+
+def fast_window(in_bits, pos, s, k, seed_bits, flags, js, i0, ni, nthreads=None,
+                seed_len_bits=None) -> np.ndarray:
+    """K_j[i] for the sub-blocks ``js`` and rows i in [i0, i0+ni), one byte
+    per bit (shape (len(js), ni)), computed on 64-bit words; ``pos`` holds the
+    sampled positions of those sub-blocks (len(js)*s entries, in js order)."""
+    in_bits = np.ascontiguousarray(in_bits, dtype=np.uint32)
+    pos = np.ascontiguousarray(pos, dtype=np.uint32)
+    seed_bits = np.ascontiguousarray(seed_bits, dtype=np.uint32)
+    js = np.ascontiguousarray(js, dtype=np.uint64)
+    nj = js.shape[0]
+    assert pos.shape[0] == nj * s
+    nbits = int(seed_len_bits) if seed_len_bits is not None else 32 * seed_bits.shape[0]
+    assert nbits <= 32 * seed_bits.shape[0]
+    out = np.empty(max(nj * ni, 1), dtype=np.uint8)
+    rc = lib().oracle_fast_window(_ptr(in_bits), _ptr(pos), s, k, _ptr(seed_bits), nbits, flags,
+                                  _ptr(js) if nj else 0, nj, i0, ni, _ptr(out), _threads(nthreads))
+    if rc:
+        raise ValueError("oracle_fast_window failed (%d)" % rc)
+    return out[:nj * ni].reshape(nj, ni)
+
+
+def perm_ranges(keys: np.ndarray, ranges) -> np.ndarray:
+    """Ranks [lo, lo+cnt) of the stable argsort of ``keys`` for each (lo, cnt)
+    in ``ranges``, concatenated, in one pass over the keys."""
+    keys = np.ascontiguousarray(keys, dtype=np.uint64)
+    lo = np.ascontiguousarray([r[0] for r in ranges], dtype=np.uint64)
+    cnt = np.ascontiguousarray([r[1] for r in ranges], dtype=np.uint64)
+    total = int(cnt.sum()) if len(ranges) else 0
+    out = np.empty(max(total, 1), dtype=np.uint32)
+    rc = lib().oracle_perm_ranges(keys.shape[0], _ptr(keys), len(ranges), _ptr(lo) if len(ranges) else 0,
+                                  _ptr(cnt) if len(ranges) else 0, _ptr(out))
+    if rc:
+        raise RuntimeError("oracle_perm_ranges failed: %d" % rc)
+    return out[:total]
+
+
+def fast_extract(n, m, s, k, in_bits, seed_bits, sampling_key_, flags=0, nthreads=None) -> np.ndarray:
+    """The whole method with the word-packed Toeplitz sum: the oracle's own
+    order (sorted, identity or i.i.d.), every sub-block's rows, output words
+    packed LSB-first with tail bits 0 (the same result as ``extract``)."""
+    if flags & SAMPLING_IID:
+        _, order, largest = iid_order(sampling_keys(n, sampling_key_, flags, nthreads), m, s)
+        if order is None:
+            raise Abort("a sub-block exceeds the limit s = %d" % s)
+        pos = order
+    else:
+        pos = perm(n, sampling_key_, flags, nthreads)[:m * s]
+    nseed = (m if flags & SEED_PER_SUBBLOCK else 1) * (s + k - 1)
+    K = fast_window(in_bits, pos, s, k, seed_bits, flags, np.arange(m), 0, k, nthreads, seed_len_bits=nseed)
+    bits = K.reshape(-1)
+    pad = (-bits.shape[0]) % 32
+    if pad:
+        bits = np.concatenate([bits, np.zeros(pad, dtype=np.uint8)])
+    return np.packbits(bits, bitorder="little").view("<u4").astype(np.uint32)

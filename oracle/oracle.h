@@ -5,8 +5,10 @@
  * statement of what the hashing path computes.  Only the test suite, the
  * package smoke check and the CPU-baseline leg of the benchmark may load it;
  * the CUDA library never links, includes or calls it, and the two share no
- * code.  Every bit of the path is computed one bit at a time, exactly as the
- * definitions below state them.
+ * code.  oracle.c computes every bit of the path one bit at a time, exactly
+ * as the definitions below state them; oracle_fast.c restates steps 5-6 on
+ * 64-bit words (for full-size checks and the timed CPU baseline) and is
+ * pinned to the bit loop.
  *
  * Bit convention (the paper fixes none; this is the reading used throughout):
  *   bit(x, i) = (x[i >> 5] >> (i & 31)) & 1 for every packed string
@@ -121,6 +123,29 @@ int oracle_extract(uint64_t n, uint64_t m, uint64_t s, uint64_t k,
 void oracle_extract_window(const uint32_t *in, const uint32_t *pos, uint64_t s, uint64_t k,
                            const uint32_t *seed, uint32_t flags, uint64_t j0, uint64_t nj,
                            uint64_t i0, uint64_t ni, uint8_t *out, int nthreads);
+
+/* ---- word-packed restatement (oracle_fast.c) ---------------------------
+   Steps 5-6 on 64-bit words: with R_j the sub-block reversed and packed
+   (bit c' = A_j[s-1-c']) and W_i[w] the 64 seed bits from bit i + 64 w,
+   K_j[i] = parity(XOR_w W_i[w] AND R_j[w]).  Pinned to the bit loop above. */
+
+/* K_j[i] for the nj sub-blocks js[0..nj) and rows i in [i0, i0 + ni), given
+   their sampled positions pos[t*s + c] (sub-block js[t]).  seed holds
+   seed_bits bits (s + k - 1, or m (s + k - 1) with ORACLE_SEED_PER_SUBBLOCK,
+   where sub-block j's seed starts at bit j (s + k - 1)).  With
+   ORACLE_SAMPLING_IID, ORACLE_NO_POS entries read as 0.
+   out[t*ni + (i - i0)] is one byte per bit.  Threads split the rows.
+   0 = ok, -1 = bad args, -2 = out of memory. */
+int oracle_fast_window(const uint32_t *in, const uint32_t *pos, uint64_t s, uint64_t k, const uint32_t *seed,
+                       uint64_t seed_bits, uint32_t flags, const uint64_t *js, uint64_t nj, uint64_t i0,
+                       uint64_t ni, uint8_t *out, int nthreads);
+
+/* Ranks [lo[r], lo[r] + cnt[r]) of the stable argsort of keys[0..n) for
+   r < nr, concatenated into out, in one pass over the keys (a 16-bit label
+   histogram, then a sort of the candidates of the needed buckets).
+   0 = ok, -1 = bad args, -2 = out of memory. */
+int oracle_perm_ranges(uint64_t n, const uint64_t *keys, uint64_t nr, const uint64_t *lo, const uint64_t *cnt,
+                       uint32_t *out);
 
 #ifdef __cplusplus
 }
