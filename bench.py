@@ -7,20 +7,35 @@ sampled order, Toeplitz hash of each, concatenation of the outputs.  Building
 the sampled order (extract_create) happens once per sampling key and is
 timed separately (``create_ms``).
 
-Workload: the QRNG-shaped block, n = 2^30 Bernoulli(0.6) input bits, m = 1024
-sub-blocks of s = 2^20 bits, k = 2^19 output bits per sub-block (ratio 0.5),
-shared uniform seed of s + k - 1 bits (input seed 1, sampling key 2, Toeplitz
-seed 3).  The metric is extracted input Gbit/s (input bits hashed per second).
+Default workload: the QKD-shaped block, n = 2^32 Bernoulli(0.9) input bits,
+m = 4096 sub-blocks of s = 2^20 bits, k = 104858 output bits per sub-block
+(ratio 0.1), one shared uniform seed of s + k - 1 bits (input seed 1,
+sampling key 2, Toeplitz seed 3).  The metric is extracted input Gbit/s
+(input bits hashed per second).  Beside it, the same JSON line carries:
 
-Prints ONE JSON line (rank 0).  ``--impl reference`` times the CPU oracle on
-the host cores instead (the reference arm: a bounded sample per step).
-Multi-GPU (torchrun): every rank hashes its own block on its own GPU (replicas,
-weak scaling); no data crosses GPUs.
+* ``plain_per_block``: the plain per-block path on the same block (one
+  launch per sub-block, one thread per output row) and the speed-up over it;
+* ``direct_tiled``: the direct GF(2) kernel on the same block, against the
+  integer-pipe roofline;
+* ``gather``: the gather's time and HBM GB/s;
+* ``batch``: 256 independent blocks of uneven n, s, k in one run, against
+  one launch sequence per block;
+* ``serve``: Poisson job arrivals at 200, 1000 and 5000 jobs/s under an
+  80 GB budget, with p50/p99 latency;
+* ``cpu_baseline``: the word-packed oracle on all host cores, on a bounded
+  sample of the block.
+
+Prints ONE JSON line (rank 0).  ``--impl reference`` times the oracle on the
+host cores instead (the reference arm, a bounded sample per step).
+Multi-GPU (torchrun): every rank hashes its own block on its own GPU
+(replicas, weak scaling); no data crosses GPUs.
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -36,39 +51,44 @@ if ROOT not in sys.path:
 
 WORKLOADS = {
     # name: n, m, s, k, Bernoulli p
+    "qkd_n2^32_m4096_s2^20_k104858": (1 << 32, 4096, 1 << 20, 104858, 0.9),
     "qrng_n2^30_m1024_s2^20_k2^19": (1 << 30, 1024, 1 << 20, 1 << 19, 0.6),
-    # smaller shapes of the same kind, for profiling and quick checks only
+    "small_n2^18_m8_s2^15_k2^13": (1 << 18, 8, 1 << 15, 1 << 13, 0.7),
+    # smaller shapes of the same kinds, for profiling and quick checks only
+    "qkd64_n2^26_m64_s2^20_k104858": (1 << 26, 64, 1 << 20, 104858, 0.9),
     "mid_n2^27_m128_s2^20_k2^16": (1 << 27, 128, 1 << 20, 1 << 16, 0.6),
     "qrng128_n2^27_m128_s2^20_k2^19": (1 << 27, 128, 1 << 20, 1 << 19, 0.6),
     "small_n2^24_m64_s2^18_k2^17": (1 << 24, 64, 1 << 18, 1 << 17, 0.6),
 }
-DEFAULT_WORKLOAD = "qrng_n2^30_m1024_s2^20_k2^19"
+DEFAULT_WORKLOAD = "qkd_n2^32_m4096_s2^20_k104858"
 IN_SEED, SAMPLING_KEY, TOEPLITZ_SEED = 1, 2, 3
 IID_EPS = 1e-8  # abort probability eps_Omega' of the i.i.d. law's limit (the paper's Sec. IV value)
 
-# Integer-pipe roofline of the hashing kernel (bound "alu"): LOP3 results per
-# SM per clock x SMs x maximum SM clock.  The lane count is the one measured
-# by a dependency-free LOP3 probe on GB300 (profiles/lop3_alu_peak.md).
+# Integer-pipe roofline of the direct hashing kernel (bound "alu"): LOP3
+# results per SM per clock x SMs x maximum SM clock; the lane count is the one
+# a dependency-free LOP3 probe measured on GB300.
 LOP3_LANES_PER_SM_CLK = 64
-# DRAM bytes (read + write) of one hashing launch on the QRNG-shaped block:
-# the ncu capture of the mid-size block (m = 128: 18.04 MB,
-# profiles/toeplitz_lop3_kernel_mid_n2^27_m128_s2^20_k2^16.md) scaled by the
-# sub-block count to m = 1024; traffic grows with the sub-block data.  Set to
-# None whenever the kernel changes until it is captured again.
-HASH_TRAFFIC_BYTES = {"qrng_n2^30_m1024_s2^20_k2^19": 18.04e6 * 1024 / 128,
-                      "mid_n2^27_m128_s2^20_k2^16": 18.04e6}
+SM_MAX_MHZ = 2070.0
+FALLBACK_HBM_GBS = 6800.0  # the profiling recipe's fallback copy bandwidth
+
+# DRAM traffic of one NTT hash, from an ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum) scaled to the whole block; each entry carries the
+# SHA-256 of the kernel source it was captured on and is ignored once the
+# source has changed.
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic.json")
+NTT_SOURCE = os.path.join(ROOT, "paper_2308_02856_gb300", "csrc", "ntt.cu")
 
 
-def parse_args():
+def parse_args(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
     ap.add_argument("--mode", choices=["block", "batch", "serve", "compare"], default="block",
-                    help="block: one large block (default); batch: 256 uneven blocks in one persistent "
-                         "launch vs one launch per block; serve: Poisson job arrivals under an HBM budget")
+                    help="block: one large block (default, with the batch and serve results nested); batch / "
+                         "serve: those results alone; compare: the comparison points")
     ap.add_argument("--jobs", type=int, default=0, help="jobs per serving trace (default 120)")
     ap.add_argument("--seeds", choices=["shared", "per-subblock"], default="shared",
                     help="block mode: one Toeplitz seed for all sub-blocks (default), or an independent seed per "
@@ -80,21 +100,35 @@ def parse_args():
                     help="hashing method of the block mode (auto: the library's choice)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=12.0,
-                    help="target CPU time of the oracle sample")
-    return ap.parse_args()
+    ap.add_argument("--no-compare", action="store_true", help="skip the plain per-block and direct-kernel runs")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0,
+                    help="target CPU time of the oracle sample (repeated until reached)")
+    return ap.parse_args(argv)
+
+
+def measured_peaks():
+    """The measured peaks, or the recipe's fallback (labelled)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "basis": "measured (MEASURED_PEAKS.json copy bandwidth)"}
+    except (OSError, ValueError, KeyError):
+        return {"hbm_gbs": FALLBACK_HBM_GBS, "basis": "fallback 6.8 TB/s (no measured peaks file)"}
 
 
 # --------------------------------------------------------------------------
-# clocks during the timed region
+# clocks during a timed region
 # --------------------------------------------------------------------------
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_id: str):
+    def __init__(self, gpu_id: str, period_ms: int = 100):
         self.gpu_id = gpu_id
+        self.period_ms = period_ms
         self.proc = None
         self.path = None
 
@@ -105,9 +139,11 @@ class ClockSampler:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", self.gpu_id, "--query-gpu=" + self.FIELDS,
-                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+                 "--format=csv,noheader,nounits", "-lms", str(self.period_ms)], stdout=self.f,
+                stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+        return self
 
     def stop(self):
         if not self.proc:
@@ -153,48 +189,77 @@ def gpu_id_for(dev) -> str:
 
 
 # --------------------------------------------------------------------------
+# the workload, as both arms print it
+# --------------------------------------------------------------------------
+def workload_config(name, s=None, iid=False, per_sub=False, world=1):
+    n, m, s0, k, p = WORKLOADS[name]
+    s = s0 if s is None else s
+    return {"workload": name + ("_iid" if iid else "") + ("_seed_per_subblock" if per_sub else ""),
+            "n": n, "m": m, "s": s, "k": k, "bernoulli_p": p,
+            "toeplitz_seeds": "one per sub-block" if per_sub else "shared",
+            "sampling": ("i.i.d. labels V_i in [0, m), sub-blocks padded to Eq. 7's limit s (eps %g, p_sift 1/m)"
+                         % IID_EPS) if iid else "stable argsort of 64-bit Philox labels, equal sub-blocks",
+            "seeds": {"input": IN_SEED, "sampling_key": SAMPLING_KEY, "toeplitz": TOEPLITZ_SEED},
+            "order": "resident (built once per sampling key; create_ms reports it)",
+            "l2": "inputs larger than L2: every step reads the n-bit input and the order's gather tables "
+                  "(GBs), far above the 129 MB L2",
+            "parallelism": "replicas (one block per GPU)" if world > 1 else "1 GPU"}
+
+
+def make_inputs(n, m, s, k, p, nseeds=1):
+    from paper_2308_02856_gb300 import synth
+    in_w = synth.bernoulli_bits(n, p, IN_SEED)
+    seed_w = synth.uniform_bits((s + k - 1) * nseeds, TOEPLITZ_SEED)
+    return in_w, seed_w
+
+
+# --------------------------------------------------------------------------
 # CPU oracle sample (cpu_baseline and the reference arm)
 # --------------------------------------------------------------------------
 class OracleSample:
-    """The oracle on a bounded sample of the workload: nj whole sub-blocks'
-    assembly plus ni output rows of each, on nj host threads; scaled to the
-    whole block by the share of Toeplitz rows it computed."""
+    """The word-packed oracle on a bounded sample of the workload: nj whole
+    sub-blocks (assembly from the sampled positions and all k output rows),
+    spread over the block, on all host cores.  The positions come from the
+    oracle's own labels and rank selection, outside the timed part.  Scaled
+    to the whole block by m / nj."""
 
-    def __init__(self, n, m, s, k, in_w, seed_w, target_s, iid=False, per_sub=False):
+    def __init__(self, n, m, s, k, in_w, seed_w, nj=None, iid=False, per_sub=False):
         import oracle
         self.oracle = oracle
         self.n, self.m, self.s, self.k = n, m, s, k
         self.in_w, self.seed_w = in_w, seed_w
         self.cores = os.cpu_count() or 1
-        self.nj = min(self.cores, m)
+        self.js = np.unique(np.linspace(0, m - 1, int(min(m, nj or 2 * self.cores))).astype(np.int64))
+        self.nj = int(self.js.size)
         self.flags = (oracle.SAMPLING_IID if iid else 0) | (oracle.SEED_PER_SUBBLOCK if per_sub else 0)
+        self.seed_len = (s + k - 1) * (m if per_sub else 1)
         keys = oracle.sampling_keys(n, SAMPLING_KEY)
         if iid:  # the oracle's i.i.d. order (padded sub-blocks of s slots)
             _, order, _ = oracle.iid_order(keys, m, s)
-            self.pos = np.ascontiguousarray(order[:self.nj * s])
+            self.pos = np.ascontiguousarray(np.concatenate([order[j * s:(j + 1) * s] for j in self.js]))
         else:
-            self.pos = oracle.perm_range(keys, 0, self.nj * s)
+            self.pos = oracle.perm_ranges(keys, [(int(j) * s, s) for j in self.js])
         del keys
-        # calibrate the rows per sub-block to about target_s of wall time
-        ni = 8
-        t = self._time(ni)
-        self.ni = int(max(8, min(k, ni * target_s / max(t, 1e-3))))
 
-    def _time(self, ni):
+    def time_once(self) -> float:
         t0 = time.perf_counter()
-        self.oracle.extract_window(self.in_w, self.pos, self.s, self.k, self.seed_w, self.flags, 0, self.nj, 0, ni,
-                                   nthreads=self.nj)
+        self.oracle.fast_window(self.in_w, self.pos, self.s, self.k, self.seed_w, self.flags, self.js, 0, self.k,
+                                nthreads=self.cores, seed_len_bits=self.seed_len)
         return time.perf_counter() - t0
 
-    def measure(self):
-        t = self._time(self.ni)
-        frac = (self.nj * self.ni) / float(self.m * self.k)
-        full_s = t / frac
-        return {"value": self.n / full_s / 1e9, "unit": "Gbit/s", "cores": self.nj, "kind": "oracle",
-                "seconds": t,
-                "sample": "oracle bit-loop on %d of %d sub-blocks x %d of %d output rows (%.2e of the "
-                          "Toeplitz work) on %d threads, %.1f s; scaled to the whole block"
-                          % (self.nj, self.m, self.ni, self.k, frac, self.nj, t)}
+    def describe(self, t, reps):
+        return ("word-packed oracle (64-bit AND/XOR, one popcount parity per row) on %d of %d whole sub-blocks, "
+                "all %d rows each (%.2e of the block), on %d threads; %.2f s per sample, mean of %d; scaled "
+                "to the whole block" % (self.nj, self.m, self.k, self.nj / self.m, self.cores, t, reps))
+
+    def measure(self, target_s):
+        ts = [self.time_once()]
+        while sum(ts) < target_s:
+            ts.append(self.time_once())
+        t = statistics.mean(ts)
+        full_s = t * self.m / self.nj
+        return {"value": self.n / full_s / 1e9, "unit": "Gbit/s", "cores": self.cores, "kind": "oracle",
+                "sample": self.describe(t, len(ts))}
 
 
 def max_over_ranks(x: float, dist, device) -> float:
@@ -238,13 +303,22 @@ def launches_per_step(is_ntt, m, plan, n=0):
     return gather + 3 * groups
 
 
-# DRAM bytes (read + write) of one NTT hash: the ncu capture of one launch
-# group (16 sub-blocks, P = 2, N = 2^20: 327.7 MB over the three passes, cold
-# cache; profiles/ntt_kernels_qrng128_n2^27_m128_s2^20_k2^19.md) times the
-# groups of the block.  Set to None whenever the kernels change until they
-# are captured again.
-NTT_TRAFFIC_BYTES = {"qrng_n2^30_m1024_s2^20_k2^19": 327.7e6 * 64,
-                     "qrng128_n2^27_m128_s2^20_k2^19": 327.7e6 * 8}
+def ntt_traffic(workload):
+    """Bytes of DRAM traffic per NTT hash from the committed capture, or
+    (None, why) when there is none for this workload or the kernels changed."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            entries = json.load(f)
+    except (OSError, ValueError):
+        return None, "no capture file"
+    e = entries.get(workload)
+    if not e:
+        return None, "no capture for this workload"
+    with open(NTT_SOURCE, "rb") as f:
+        sha = hashlib.sha256(f.read()).hexdigest()
+    if e.get("source_sha256") != sha:
+        return None, "the NTT kernels changed since the capture"
+    return float(e["bytes_per_hash"]), e.get("basis", "")
 
 
 def ntt_roofline(n, m, s, k, hash_ms, plan, sms=152, workload=None):
@@ -255,29 +329,36 @@ def ntt_roofline(n, m, s, k, hash_ms, plan, sms=152, workload=None):
     butterfly is 7 integer instructions, 4 of them (adds, subtracts, min) on
     the 64-lane ALU pipe and 3 IMAD on the FMA pipe, so the ALU pipe bounds
     it at SMs x 64 / 4 butterflies per clock."""
-    import math
     N = int(plan.split("N=")[1].split(" ")[0])
     P = int(plan.split("P=")[1].split(" ")[0]) if "P=" in plan else 1
     transforms = (2 * P + 1) if "seed windows transformed per run" in plan else (P + 1)
     bfly = m * transforms * (N // 2) * math.log2(N)
     achieved = bfly / (hash_ms / 1e3) / 1e12
-    peak = sms * 64 / 4.0 * 2070e6 / 1e12
+    peak = sms * 64 / 4.0 * SM_MAX_MHZ * 1e6 / 1e12
+    traffic, basis = ntt_traffic(workload) if workload else (None, "no capture for this workload")
     return {"bound": "alu", "achieved": achieved, "unit": "Tbutterfly/s", "peak": peak, "frac": achieved / peak,
-            "traffic": NTT_TRAFFIC_BYTES.get(workload),
+            "traffic": traffic, "traffic_basis": basis,
             "kernel": "the NTT hash: pass A (column DIF), pass B (rows), pass A' (column DIT) per launch group",
             "work_per_launch": "m x %d transforms x N/2 log2 N = %.4g radix-2 butterflies mod p (N=%d, P=%d "
                                "pieces per sub-block%s)" % (transforms, bfly, N, P,
                                                             ", seed windows transformed per run"
                                                             if transforms == 2 * P + 1 else ""),
-            "peak_basis": "%d SMs x 64 ALU lanes / 4 ALU ops per lazy butterfly x 2070 MHz" % sms,
+            "peak_basis": "%d SMs x 64 ALU lanes / 4 ALU ops per lazy butterfly x %.0f MHz" % (sms, SM_MAX_MHZ),
             "note": "does %.0fx less work than the direct m*k*s product" % ((m * k * s / 32.0) / bfly)}
 
 
-def make_inputs(n, m, s, k, p, nseeds=1):
-    from paper_2308_02856_gb300 import synth
-    in_w = synth.bernoulli_bits(n, p, IN_SEED)
-    seed_w = synth.uniform_bits((s + k - 1) * nseeds, TOEPLITZ_SEED)
-    return in_w, seed_w
+def lop3_roofline(m, k, s, hash_ms, sms, clocks=None):
+    """The direct GF(2) kernel (toeplitz_lop3_kernel): m*k*s/32 LOP3 against
+    the integer-ALU roofline."""
+    peak = sms * LOP3_LANES_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e12
+    lop3 = m * k * s / 32.0
+    achieved = lop3 / (hash_ms / 1e3) / 1e12
+    r = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TLOP3/s", "frac": achieved / peak,
+         "kernel": "toeplitz_lop3_kernel", "work_per_launch": "m*k*s/32 = %.4g LOP3 (32 bit-products each)" % lop3,
+         "peak_basis": "%d SMs x %d LOP3/clk/SM x %.0f MHz max SM clock" % (sms, LOP3_LANES_PER_SM_CLK, SM_MAX_MHZ)}
+    if clocks and clocks.get("sm_mhz"):
+        r["frac_at_measured_clock"] = achieved / (sms * LOP3_LANES_PER_SM_CLK * clocks["sm_mhz"] * 1e6 / 1e12)
+    return r
 
 
 # --------------------------------------------------------------------------
@@ -293,29 +374,39 @@ def run_reference(args):
         return 0
     n, m, s, k, p = WORKLOADS[args.workload]
     in_w, seed_w = make_inputs(n, m, s, k, p)
-    per_step = max(1.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
-    smp = OracleSample(n, m, s, k, in_w, seed_w, per_step)
+    smp = OracleSample(n, m, s, k, in_w, seed_w, nj=os.cpu_count() or 1)  # one sub-block per core per step
     for _ in range(args.warmup):
-        smp.measure()
-    res = [smp.measure() for _ in range(args.steps)]
-    secs = [r["seconds"] / ((smp.nj * smp.ni) / float(m * k)) for r in res]
-    ms = statistics.mean(secs) * 1e3
+        smp.time_once()
+    ts = [smp.time_once() for _ in range(args.steps)]
+    t = statistics.mean(ts)
+    ms = t * m / smp.nj * 1e3  # the whole block, scaled from the sample
     value = n / (ms / 1e3) / 1e9
-    cb = dict(res[-1])
-    cb["value"] = value
-    cb.pop("seconds", None)
     line = {
         "impl": "reference",
         "metric": "extracted input Gbit/s", "value": value, "unit": "Gbit/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32 (GF(2) bits)", "data": "synthetic",
-        "config": {"workload": args.workload, "n": n, "m": m, "s": s, "k": k, "bernoulli_p": p,
-                   "order": "resident (built once per sampling key)"},
-        "cpu_baseline": cb,
+        "config": workload_config(args.workload, world=world),
+        "cpu_baseline": {"value": value, "unit": "Gbit/s", "cores": smp.cores, "kind": "oracle",
+                         "sample": smp.describe(t, len(ts)) + "; one sample per step"},
         "e2e": {"value": value, "unit": "Gbit/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "timed_seconds": sum(ts),
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def events_ms(torch, stream, fn, reps):
+    """Mean ms of fn() on `stream`, CUDA events on that stream, synchronised
+    on both sides."""
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
 
 
 def run_ours(args):
@@ -334,6 +425,8 @@ def run_ours(args):
     n, m, s, k, p = WORKLOADS[args.workload]
     props = torch.cuda.get_device_properties(dev)
     sms = props.multi_processor_count
+    gpu = gpu_id_for(dev)
+    peaks = measured_peaks()
 
     X.load()  # fails loudly when the CUDA library is missing
     iid = args.sampling == "iid"
@@ -366,16 +459,15 @@ def run_ours(args):
         step()
     torch.cuda.synchronize()
 
-    # timed region: whole runs (gather + hash, overlapped where the method allows)
+    # timed region: K whole runs (gather + hash), CUDA events on the run's stream
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    clk = ClockSampler(gpu_id_for(dev))
-    clk.start()
+    clk = ClockSampler(gpu).start()
     time.sleep(0.3)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     start.record(stream)
-    for i in range(args.steps):
+    for _ in range(args.steps):
         step()
     end.record(stream)
     torch.cuda.synchronize()
@@ -383,24 +475,23 @@ def run_ours(args):
         dist.barrier()
     clocks = clk.stop()
     ms_total = start.elapsed_time(end)
-
-    # breakdown, outside the timed region: gather alone, then hash alone
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
-            torch.cuda.Event(enable_timing=True)) for _ in range(2)]
-    for a, b, c in evs:
-        a.record(stream)
-        ex.gather(d_in, stream=stream)
-        b.record(stream)
-        ex.hash(d_out, stream=stream)
-        c.record(stream)
-    torch.cuda.synchronize()
-    gather_ms = statistics.mean(a.elapsed_time(b) for a, b, _ in evs)
-    hash_ms = statistics.mean(b.elapsed_time(c) for _, b, c in evs)
     ms_total = max_over_ranks(ms_total, dist, dev)
     ms_step = ms_total / args.steps
     value = aggregate_rate(n, world, ms_step)
 
-    # end to end through the C ABI with host buffers
+    # breakdown, outside the timed region: gather alone, then hash alone
+    gather_ms = events_ms(torch, stream, lambda: ex.gather(d_in, stream=stream), 3)
+    hash_ms = events_ms(torch, stream, lambda: ex.hash(d_out, stream=stream), 3)
+    g_bytes = ex.gather_bytes()
+    g_alg = n // 8 + m * s // 8  # input read once, sampled bits stored once
+    gather = {"ms": gather_ms, "algorithmic_bytes": g_alg, "algorithmic_gbs": g_alg / gather_ms / 1e6,
+              "bytes_by_design": g_bytes, "hbm_gbs": g_bytes / gather_ms / 1e6,
+              "frac_of_copy_peak": g_bytes / gather_ms / 1e6 / peaks["hbm_gbs"], "peak_gbs": peaks["hbm_gbs"],
+              "peak_basis": peaks["basis"],
+              "note": "algorithmic: the n-bit input read once and the m*s sampled bits stored once; by design: "
+                      "also the resident gather tables the library reads every run (extract_gather_bytes)"}
+
+    # end to end through the C ABI with host buffers: K runs, copies inside
     e2e = None
     if not args.no_e2e:
         h_in = torch.from_numpy(in_w.view(np.int32)).pin_memory()
@@ -416,77 +507,66 @@ def run_ours(args):
         e2e = {"value": aggregate_rate(n, world, e2e_s * 1e3), "unit": "Gbit/s", "ms_per_step": e2e_s * 1e3,
                "h2d_bytes_per_step": int(in_w.nbytes), "d2h_bytes_per_step": int(ex.out_words * 4),
                "api": "extract_run_host (pinned host buffers, copies and sync inside the timed region)"}
+        del h_in, h_out
 
-    # the direct GF(2) kernel (toeplitz_lop3_kernel): integer-ALU roofline
-    peak = sms * LOP3_LANES_PER_SM_CLK * 2070e6 / 1e12
-    lop3_per_launch = m * k * s / 32.0
+    # the comparison points on the same block: the plain per-block path and
+    # the direct tiled kernel
+    plain = direct = None
+    if not args.no_compare:
+        clk2 = ClockSampler(gpu).start()
+        pms = events_ms(torch, stream, lambda: ex.run_plain(d_in, d_out, stream=stream), 1)
+        plain = {"ms": pms, "value": aggregate_rate(n, 1, pms), "unit": "Gbit/s", "launches_per_run": m + 2,
+                 "path": "gather, then one launch per sub-block, one thread per output row (extract_run_plain)",
+                 "speedup_of_library_path": pms / ms_step}
+        if is_ntt:
+            flags_d = X.EXTRACT_METHOD_DIRECT | (method_flags & (X.EXTRACT_SAMPLING_IID | X.EXTRACT_SEED_PER_SUBBLOCK))
+            with X.Extractor(n, m, s, k, seed_w, SAMPLING_KEY, flags_d) as exd:
+                exd.gather(d_in, stream=stream)
+                dms = events_ms(torch, stream, lambda: exd.hash(d_out, stream=stream), 2)
+                direct = {"hash_ms": dms, "value": aggregate_rate(n, 1, dms + gather_ms), "unit": "Gbit/s",
+                          "roofline": lop3_roofline(m, k, s, dms, sms, clocks), "plan": exd.describe()}
+        plain["clocks"] = clk2.stop()
+    roofline = (ntt_roofline(n, m, s, k, hash_ms, plan, sms, None if (iid or per_sub) else args.workload)
+                if is_ntt else lop3_roofline(m, k, s, hash_ms, sms, clocks))
+    if not is_ntt:
+        direct = {"hash_ms": hash_ms, "roofline": roofline, "plan": plan}
+    ex.close()
+    del d_in, d_out
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
 
-    def lop3_roofline(hms):
-        achieved = lop3_per_launch / (hms / 1e3) / 1e12
-        r = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TLOP3/s",
-             "frac": achieved / peak, "traffic": HASH_TRAFFIC_BYTES.get(args.workload),
-             "kernel": "toeplitz_lop3_kernel",
-             "work_per_launch": "m*k*s/32 = %.4g LOP3 (32 bit-products each)" % lop3_per_launch,
-             "peak_basis": "%d SMs x %d LOP3/clk/SM x 2070 MHz max SM clock" % (sms, LOP3_LANES_PER_SM_CLK)}
-        if clocks.get("sm_mhz"):
-            r["frac_at_measured_clock"] = achieved / (sms * LOP3_LANES_PER_SM_CLK * clocks["sm_mhz"] * 1e6 / 1e12)
-        return r
-
-    direct = None
-    if is_ntt:
-        roofline = ntt_roofline(n, m, s, k, hash_ms, plan, sms, None if iid else args.workload)
-        # the direct kernel on the same block, for the record (2 timed steps)
-        exd = X.Extractor(n, m, s, k, seed_w, SAMPLING_KEY,
-                          X.EXTRACT_METHOD_DIRECT | (method_flags & (X.EXTRACT_SAMPLING_IID | X.EXTRACT_SEED_PER_SUBBLOCK)))
-        exd.gather(d_in, stream=stream)
-        exd.hash(d_out, stream=stream)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        for _ in range(2):
-            exd.hash(d_out, stream=stream)
-        b.record(stream)
-        torch.cuda.synchronize()
-        dms = a.elapsed_time(b) / 2
-        direct = {"hash_ms": dms, "value": world * n / ((dms + gather_ms) / 1e3) / 1e9, "unit": "Gbit/s",
-                  "roofline": lop3_roofline(dms), "plan": exd.describe()}
-        exd.close()
-    else:
-        roofline = lop3_roofline(hash_ms)
+    batch = serve = None
+    if rank == 0 and world == 1:
+        if not args.no_batch:
+            batch = measure_batch(torch, X, gpu, steps=3, warmup=1, sms=sms)
+        if not args.no_serve:
+            serve = measure_serve(torch, X, gpu, args.jobs or 120)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
-            smp = OracleSample(n, m, s, k, in_w, seed_w, args.cpu_seconds, iid=iid, per_sub=per_sub)
-            cpu = smp.measure()
-            cpu.pop("seconds", None)
+            cpu = OracleSample(n, m, s, k, in_w, seed_w, iid=iid, per_sub=per_sub).measure(args.cpu_seconds)
         except Exception as e:  # the baseline is context; report why it is missing
             cpu = {"value": None, "unit": "Gbit/s", "kind": "oracle", "error": str(e)}
 
-    ex.close()
     if rank == 0:
         line = {
             "metric": "extracted input Gbit/s", "value": value, "unit": "Gbit/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32 (GF(2) bits)", "data": "synthetic",
-            "config": {"workload": args.workload + ("_iid" if iid else "") + ("_seed_per_subblock" if per_sub else ""),
-                       "n": n, "m": m, "s": s, "k": k,
-                       "toeplitz_seeds": "one per sub-block" if per_sub else "shared",
-                       "bernoulli_p": p,
-                       "sampling": ("i.i.d. labels V_i in [0, m), sub-blocks padded to Eq. 7's limit s "
-                                    "(eps %g, p_sift 1/m)" % IID_EPS) if iid else "stable argsort, equal sub-blocks",
-                       "seeds": {"input": IN_SEED, "sampling_key": SAMPLING_KEY, "toeplitz": TOEPLITZ_SEED},
-                       "order": "resident (built once per sampling key; see create_ms)",
-                       "l2": ("inputs larger than L2: bucket tables (about 2.5 B per sampled bit + 2.6 B per "
-                              "stored sub-block bit) + n/8-byte input read per step" if "gather=buckets" in plan else
-                              "inputs larger than L2: 4n-byte order + n/8-byte input read per step"),
-                       "parallelism": "replicas" if world > 1 else "1 GPU",
-                       "plan": plan},
+            "config": workload_config(args.workload, s=s, iid=iid, per_sub=per_sub, world=world),
+            "plan": plan,
             "method": "ntt" if is_ntt else "direct",
             "create_ms": create_ms,
             "gather_ms": gather_ms, "hash_ms": hash_ms,
             "gpu_launches": launches_per_step(is_ntt, m, plan, n) * args.steps,
-            "direct_lop3": direct,
             "roofline": roofline,
+            "gather": gather,
+            "plain_per_block": plain,
+            "speedup_vs_plain_per_block": plain["speedup_of_library_path"] if plain else None,
+            "direct_tiled": direct,
+            "batch": batch,
+            "serve": serve,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "clocks": clocks,
@@ -498,18 +578,17 @@ def run_ours(args):
     return 0
 
 
-def run_batch(args):
+# --------------------------------------------------------------------------
+# batching and serving (the systems forms)
+# --------------------------------------------------------------------------
+def measure_batch(torch, X, gpu, steps=3, warmup=1, sms=152):
     """256 independent blocks: n log-uniform in [2^20, 2^28], s in {2^16,
     2^18, 2^20}, k/s uniform in [0.05, 0.5], p uniform in [0.55, 0.95]
-    (job-shape seed 4): one batch run (the NTT-method jobs on a concurrent
-    stream, the rest in one persistent launch with autotuned tiles replayed
-    from a CUDA graph) against one launch sequence per block, plus the
-    direct-only batch whose persistent kernel gives the LOP3 roofline."""
-    import torch
-    from paper_2308_02856_gb300 import extract as X
+    (job-shape seed 4): one batch run (NTT-method jobs on concurrent lanes,
+    the rest in one persistent launch with autotuned tiles replayed from a
+    CUDA graph) against one launch sequence per block, plus the direct-only
+    batch whose persistent kernel gives the LOP3 roofline."""
     from paper_2308_02856_gb300 import synth
-    torch.cuda.set_device(0)
-    X.load()
     shapes = synth.job_shapes(256, 4, 2 ** 20, 2 ** 28)
     jobs, ins, outs = [], [], []
     for j in shapes:
@@ -525,59 +604,47 @@ def run_batch(args):
     def timed(fn, reps, warm):
         for _ in range(warm):
             fn(ins, outs, stream=st)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(st)
-        for _ in range(reps):
-            fn(ins, outs, stream=st)
-        e1.record(st)
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / reps
-        return {"ms_per_step": ms, "value": total_n / (ms / 1e3) / 1e9,
+        ms = events_ms(torch, st, lambda: fn(ins, outs, stream=st), reps)
+        return {"ms": ms, "value": total_n / (ms / 1e3) / 1e9, "unit": "Gbit/s",
                 "direct_equivalent_tlop3_per_s": lop3 / (ms / 1e3) / 1e12}
 
+    clk = ClockSampler(gpu).start()
     t0 = time.perf_counter()
     b = X.Batch(jobs)
     create_ms = (time.perf_counter() - t0) * 1e3
-    res = {"batched": timed(b.run, args.steps, max(1, args.warmup)),
-           "sequential": timed(b.run_sequential, args.steps, max(1, args.warmup))}
+    batched = timed(b.run, steps, warmup)
+    sequential = timed(b.run_sequential, max(1, steps - 1), warmup)
     desc = b.describe()
     b.close()
     bd = X.Batch(jobs, X.EXTRACT_BATCH_DIRECT_ONLY)
-    res["batched_direct_only"] = timed(bd.run, 1, 1)
+    direct_only = timed(bd.run, 1, 1)
     desc_d = bd.describe()
     bd.close()
-    props = torch.cuda.get_device_properties(0)
-    peak = props.multi_processor_count * LOP3_LANES_PER_SM_CLK * 2070e6 / 1e12
-    ach = res["batched_direct_only"]["direct_equivalent_tlop3_per_s"]
-    line = {"metric": "extracted input Gbit/s (batched)", "value": res["batched"]["value"], "unit": "Gbit/s",
-            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": res["batched"]["ms_per_step"], "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "u32 (GF(2) bits)", "data": "synthetic",
-            "config": {"workload": "batch256_n2^20-2^28_s{2^16,2^18,2^20}", "jobs": len(jobs),
-                       "input_bits": total_n, "direct_lop3_work": lop3, "plan": desc, "plan_direct_only": desc_d},
-            "create_ms": create_ms, "sequential": res["sequential"], "direct_only": res["batched_direct_only"],
-            "speedup_vs_sequential": res["sequential"]["ms_per_step"] / res["batched"]["ms_per_step"],
-            "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TLOP3/s", "frac": ach / peak,
-                         "kernel": "batch_hash_kernel (direct-only batch)"}}
-    print(json.dumps(line), flush=True)
-    return 0
+    clocks = clk.stop()
+    peak = sms * LOP3_LANES_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e12
+    ach = direct_only["direct_equivalent_tlop3_per_s"]
+    del ins, outs
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    return {"workload": "batch256_n2^20-2^28_s{2^16,2^18,2^20}_k/s0.05-0.5", "jobs": len(jobs),
+            "input_bits": total_n, "direct_lop3_work": lop3,
+            "value": batched["value"], "unit": "Gbit/s", "ms": batched["ms"], "create_ms": create_ms,
+            "batched": batched, "sequential": sequential,
+            "speedup_vs_sequential": sequential["ms"] / batched["ms"],
+            "direct_only": dict(direct_only, roofline={"bound": "alu", "achieved": ach, "peak": peak,
+                                                       "unit": "TLOP3/s", "frac": ach / peak,
+                                                       "kernel": "batch_hash_kernel (direct-only batch)"}),
+            "plan": desc, "plan_direct_only": desc_d, "clocks": clocks}
 
 
-def run_serve(args):
-    """Poisson arrivals at 200, 1000 and 5000 jobs/s; n log-uniform in
-    [2^16, 2^30], s in {2^16, 2^18, 2^20} clamped to n, k/s uniform in
-    [0.05, 0.5]; 80 GB budget.  Every rate offers more work than the GPU can
-    hash (mean job ~0.4 TLOP3), so each trace is finite and the line reports
-    offered against sustained load."""
-    import torch
-    from paper_2308_02856_gb300 import extract as X
+def measure_serve(torch, X, gpu, njobs=120, rates=(200.0, 1000.0, 5000.0)):
+    """Poisson arrivals; n log-uniform in [2^16, 2^30], s in {2^16, 2^18,
+    2^20} clamped to n, k/s uniform in [0.05, 0.5]; 80 GB budget.  Every rate
+    offers more work than the GPU can hash, so each trace is finite and the
+    result reports offered against sustained load."""
     from paper_2308_02856_gb300 import synth
-    torch.cuda.set_device(0)
-    X.load()
-    njobs = args.jobs or 120
     out = {}
-    for rate in (200.0, 1000.0, 5000.0):
+    for rate in rates:
         shapes = synth.job_shapes(njobs, 5, 2 ** 16, 2 ** 30)
         jobs, ins, outs = [], [], []
         for j in shapes:
@@ -588,6 +655,7 @@ def run_serve(args):
             outs.append(torch.empty((j["m"] * j["k"] + 31) // 32, dtype=torch.int32, device="cuda"))
         torch.cuda.synchronize()
         arr = synth.poisson_arrivals(njobs, rate, 6)
+        clk = ClockSampler(gpu).start()
         with X.Server(80 * 10 ** 9, max_slots=64, wave_us=2000) as srv:
             t0 = time.perf_counter()
             tickets = []
@@ -599,6 +667,7 @@ def run_serve(args):
             for t in tickets:
                 srv.wait(t)
             st = srv.stats()
+        clocks = clk.stop()
         work = sum(j["m"] * j["k"] * j["s"] / 32.0 for j in jobs)
         out["%d_jobs_per_s" % rate] = {
             "offered_jobs_per_s": rate, "jobs": njobs, "completed": st["completed"],
@@ -606,16 +675,42 @@ def run_serve(args):
             "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"], "max_ms": st["max_ms"],
             "gbit_per_s": st["gbit_per_s"],
             "direct_equivalent_tlop3_per_s": work / st["span_s"] / 1e12 if st["span_s"] else None,
-            "waves": st["waves"], "bytes_peak": st["bytes_peak"]}
+            "waves": st["waves"], "bytes_peak": st["bytes_peak"], "clocks": clocks}
         del ins, outs
+        torch.cuda.synchronize()
         torch.cuda.empty_cache()
-    main_rate = out["1000_jobs_per_s"]
-    line = {"metric": "extracted input Gbit/s (served); p50/p99 job latency", "value": main_rate["gbit_per_s"],
-            "unit": "Gbit/s", "n_gpus": 1, "steps": 1, "warmup": 0, "higher_is_better": True,
+    main = out["1000_jobs_per_s"] if "1000_jobs_per_s" in out else next(iter(out.values()))
+    return {"workload": "serve_poisson_n2^16-2^30_s{2^16,2^18,2^20}_k/s0.05-0.5", "budget_bytes": 80 * 10 ** 9,
+            "max_slots": 64, "wave_us": 2000, "jobs_per_trace": njobs,
+            "value": main["gbit_per_s"], "unit": "Gbit/s", "p50_ms": main["p50_ms"], "p99_ms": main["p99_ms"],
+            "rates": out}
+
+
+def run_batch(args):
+    import torch
+    from paper_2308_02856_gb300 import extract as X
+    torch.cuda.set_device(0)
+    X.load()
+    r = measure_batch(torch, X, gpu_id_for(0), steps=args.steps, warmup=max(1, args.warmup),
+                      sms=torch.cuda.get_device_properties(0).multi_processor_count)
+    line = {"metric": "extracted input Gbit/s (batched)", "value": r["value"], "unit": "Gbit/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32 (GF(2) bits)", "data": "synthetic",
-            "config": {"workload": "serve_poisson_n2^16-2^30", "budget_bytes": 80 * 10 ** 9, "max_slots": 64,
-                       "wave_us": 2000, "jobs_per_trace": njobs},
-            "p50_ms": main_rate["p50_ms"], "p99_ms": main_rate["p99_ms"], "rates": out}
+            "config": {"workload": r["workload"]}, "batch": r}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_serve(args):
+    import torch
+    from paper_2308_02856_gb300 import extract as X
+    torch.cuda.set_device(0)
+    X.load()
+    r = measure_serve(torch, X, gpu_id_for(0), args.jobs or 120)
+    line = {"metric": "extracted input Gbit/s (served); p50/p99 job latency", "value": r["value"],
+            "unit": "Gbit/s", "n_gpus": 1, "steps": 1, "warmup": 0, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32 (GF(2) bits)", "data": "synthetic",
+            "config": {"workload": r["workload"]}, "p50_ms": r["p50_ms"], "p99_ms": r["p99_ms"], "serve": r}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -633,18 +728,6 @@ def run_compare(args):
     torch.cuda.set_device(0)
     X.load()
     st = torch.cuda.Stream()
-
-    def timed(fn, reps):
-        fn()
-        torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(st)
-        for _ in range(reps):
-            fn()
-        b.record(st)
-        torch.cuda.synchronize()
-        return a.elapsed_time(b) / reps
-
     res = {}
     n, m, s, k = 1 << 32, 4096, 1 << 20, 104858
     d_in = synth.bernoulli_bits_device(n, 0.9, IN_SEED)
@@ -652,13 +735,14 @@ def run_compare(args):
     for name, flags, reps in (("library_choice", 0, 3), ("direct_tiled", X.EXTRACT_METHOD_DIRECT, 1)):
         with X.Extractor(n, m, s, k, seed, SAMPLING_KEY, flags) as ex:
             out = ex.new_output()
-            ms = timed(lambda: ex.run(d_in, out, stream=st), reps)
+            ex.run(d_in, out, stream=st)
+            ms = events_ms(torch, st, lambda: ex.run(d_in, out, stream=st), reps)
             res["qkd_n2^32_" + name] = {"ms": ms, "gbit_per_s": n / (ms / 1e3) / 1e9, "plan": ex.describe()}
             if name == "library_choice":  # the two steps alone
-                res["qkd_n2^32_" + name]["gather_ms"] = timed(lambda: ex.gather(d_in, stream=st), 2)
-                res["qkd_n2^32_" + name]["hash_ms"] = timed(lambda: ex.hash(out, stream=st), 2)
+                res["qkd_n2^32_" + name]["gather_ms"] = events_ms(torch, st, lambda: ex.gather(d_in, stream=st), 2)
+                res["qkd_n2^32_" + name]["hash_ms"] = events_ms(torch, st, lambda: ex.hash(out, stream=st), 2)
             if name == "direct_tiled":
-                pms = timed(lambda: ex.run_plain(d_in, out, stream=st), 1)
+                pms = events_ms(torch, st, lambda: ex.run_plain(d_in, out, stream=st), 1)
                 res["qkd_n2^32_plain_per_block"] = {"ms": pms, "gbit_per_s": n / (pms / 1e3) / 1e9,
                                                     "launches": m + 1}
     del d_in
@@ -668,8 +752,9 @@ def run_compare(args):
         seed = synth.uniform_bits(n2 + k2 - 1, TOEPLITZ_SEED)
         with X.Extractor(n2, 1, n2, k2, seed, 0, X.EXTRACT_IDENTITY_PERM) as ex:
             out = ex.new_output()
-            ms = timed(lambda: ex.run(d_in, out, stream=st), 2)
-            pms = timed(lambda: ex.run_plain(d_in, out, stream=st), 1)
+            ex.run(d_in, out, stream=st)
+            ms = events_ms(torch, st, lambda: ex.run(d_in, out, stream=st), 2)
+            pms = events_ms(torch, st, lambda: ex.run_plain(d_in, out, stream=st), 1)
             res["direct_whole_block_n%d_k%d" % (n2, k2)] = {
                 "tiled_ms": ms, "tiled_gbit_per_s": n2 / (ms / 1e3) / 1e9, "plain_ms": pms,
                 "plain_gbit_per_s": n2 / (pms / 1e3) / 1e9, "plan": ex.describe()}

@@ -234,6 +234,16 @@ int extract_read_subblock(extract_ctx *h, uint32_t j, uint32_t *dst_host);
    kernel configuration (tile shape, split, grid) into buf. */
 int extract_describe(extract_ctx *h, char *buf, uint32_t buflen);
 
+/* extract_gather_bytes - the device-memory bytes one extract_gather of this
+   context reads and writes by design: with the bucket tables, the input
+   once, the tables (chunk starts, in-chunk positions, destinations, member
+   fields), the run buffer written and read, and the sub-block buffer; with
+   the window-major order, its entries and slots, the input once and the
+   sub-block buffer; with the plain gather, the order entries (once per
+   input window pass), one 32-byte sector of input per gathered bit and the
+   sub-block buffer.  Host only, no device work. */
+int extract_gather_bytes(extract_ctx *h, uint64_t *bytes);
+
 /*
  * extract_run_static - extract_run for callers that must not allocate device
  * memory.  The paper has no counterpart; this is a library convenience.
@@ -248,27 +258,37 @@ int extract_describe(extract_ctx *h, char *buf, uint32_t buflen);
  *
  * Its scratch (the padded seed plus the gathered sub-blocks) is one fixed
  * array of EXTRACT_STATIC_SCRATCH_WORDS 32-bit words (16 MiB) in the
- * library's static device memory.  Every GPU that loads libextract holds
- * that array until the process exits.
+ * library's static device memory.  A device holds that array from the first
+ * use of the library's device code there (with CUDA's lazy module loading,
+ * the first call of this entry point or of any other on that device) until
+ * the process exits.
  *   n, m, s, k    as for extract_create; one shared seed (no per-sub-block
  *                 seeds).  Shapes whose scratch would exceed the array,
  *                 about m*s > 2^27 bits, are rejected with EXTRACT_EINVAL
  *                 and a message giving the words needed.
- *   perm_dev      device pointer to the sampled order, n uint32 entries (as
- *                 extract_read_perm returns it), or NULL for the identity
- *                 order (direct hashing of consecutive s-bit blocks).
+ *   perm_dev      device pointer to the sampled order as extract_read_perm
+ *                 returns it (its first m*s entries are read), or NULL for
+ *                 the identity order (direct hashing of consecutive s-bit
+ *                 blocks; then m*s <= n).  Every entry must be a position
+ *                 < n or, when n < 2^32, the padding value 0xffffffff,
+ *                 which reads as a 0 bit: an EXTRACT_SAMPLING_IID
+ *                 context's order (m*s slots, which may exceed n) is
+ *                 accepted as it is.
  *   seed_dev      device pointer, ceil((s+k-1)/32) words of seed bits.
  *   in_bits_dev   device pointer, ceil(n/32) input words.
  *   out_bits_dev  device pointer, ceil(m*k/32) words, fully overwritten.
  *   stream        cudaStream_t the work is queued on.
  *
- * The first call on each device looks up the array's device address with
- * cudaGetSymbolAddress while that device is current; make that first call
- * before any stream capture.  All calls share the one array and each call
- * rewrites all of the scratch it reads, so results never depend on earlier
- * calls; but two calls whose work overlaps on the GPU (different streams,
- * or different host threads, without ordering between them) race on the
- * array and give wrong results.  Order them on one stream.
+ * Every call looks up the array's device address with cudaGetSymbolAddress
+ * while the calling device is current (a host-side lookup, nothing is
+ * allocated).  The first call on a device may load the library's device
+ * code there and reserve the array, with the implicit synchronisation that
+ * module loading brings, so make one call at setup, before any stream
+ * capture.  All calls share the one array and each call rewrites all of the
+ * scratch it reads, so results never depend on earlier calls; but two calls
+ * whose work overlaps on the GPU (different streams, or different host
+ * threads, without ordering between them) race on the array and give wrong
+ * results.  Order them on one stream.
  */
 #define EXTRACT_STATIC_SCRATCH_WORDS (4u * 1024u * 1024u)
 int extract_run_static(uint64_t n, uint32_t m, uint32_t s, uint32_t k, const uint32_t *perm_dev,

@@ -47,23 +47,22 @@ static void pack_reversed(const uint32_t *in, const uint32_t *pos, uint64_t s, i
     }
 }
 
-/* The 64 seed bits starting at bit t: bits t .. t+63 of S (little-endian
-   64-bit words, zero past the end of the seed string). */
-static inline uint64_t seed_word_at(const uint64_t *S, uint64_t t)
-{
-    const uint64_t q = t >> 6, b = t & 63u;
-    if (b == 0) return S[q];
-    return (S[q] >> b) | (S[q + 1] << (64u - b));
-}
-
-/* One output bit: parity of XOR_w (W_i[w] AND R[w]), the window starting at
-   bit off + i of the seed string. */
+/* One output bit: parity of XOR_w (W_i[w] AND R[w]), where W_i[w] is the 64
+   seed bits from bit t0 + 64 w, t0 = off + i (S: little-endian 64-bit words,
+   zero past the end of the seed string).  A window word is the two seed
+   words it straddles, funnel-shifted by t0 mod 64, or one word when the
+   window starts on a word boundary. */
 static uint8_t fast_row(const uint64_t *S, uint64_t off, const uint64_t *R, uint64_t nwords, uint64_t i)
 {
+    const uint64_t t0 = off + i, q = t0 >> 6, b = t0 & 63u;
     uint64_t acc = 0;
-    const uint64_t t0 = off + i;
-    for (uint64_t w = 0; w < nwords; ++w)
-        acc ^= seed_word_at(S, t0 + 64u * w) & R[w];
+    if (b == 0) {
+        for (uint64_t w = 0; w < nwords; ++w)
+            acc ^= S[q + w] & R[w];
+    } else {
+        for (uint64_t w = 0; w < nwords; ++w)
+            acc ^= ((S[q + w] >> b) | (S[q + w + 1] << (64u - b))) & R[w];
+    }
     return (uint8_t)(__builtin_popcountll(acc) & 1);
 }
 

@@ -518,6 +518,26 @@ int extract_describe(extract_ctx *h, char *buf, uint32_t buflen)
     return EXTRACT_OK;
 }
 
+int extract_gather_bytes(extract_ctx *h, uint64_t *bytes)
+{
+    if (int rc = check_ctx(h)) return rc;
+    if (!bytes) return set_error(EXTRACT_EINVAL, "bytes is null");
+    const uint64_t sub = (uint64_t)h->m * h->w_pad * 4;
+    if (h->gb.pi) {
+        *bytes = gather_buckets_bytes(h->gb, h->n, h->m, h->w_pad);
+    } else if (h->gw.pos) {
+        *bytes = gather_windows_bytes(h->gw, h->n, h->w_pad);
+    } else {
+        // order entries of the m*s slots, one 32-byte sector of input per
+        // gathered bit (random reads), the sub-block buffer; the order is
+        // read again by every window pass
+        const uint64_t slots = (uint64_t)h->m * h->s;
+        const uint64_t passes = (h->perm && !h->iid && h->n > (1ull << 29) && h->n <= (1ull << 30)) ? 2 : 1;
+        *bytes = (h->perm ? passes * slots * 4 : 0) + slots * 32 + sub;
+    }
+    return EXTRACT_OK;
+}
+
 int extract_destroy(extract_ctx *h)
 {
     if (!h) return EXTRACT_OK;

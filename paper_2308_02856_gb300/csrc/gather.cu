@@ -47,7 +47,7 @@ bool gather_prefers_whole_block(uint64_t input_bits) { return input_bits <= 2 * 
 
 int launch_gather(const uint32_t *in, const uint32_t *perm, uint32_t m, uint32_t s,
                   uint32_t w_pad, uint32_t *arev, cudaStream_t st, int num_sms, uint64_t rank0, bool padded,
-                  uint64_t input_bits)
+                  uint64_t input_bits, bool windows_when_padded)
 {
     if (w_pad % 32u) return set_error(EXTRACT_EINTERNAL, "gather: w_pad %u not a multiple of 32", w_pad);
     const uint64_t groups = (uint64_t)m * (w_pad / 32u);
@@ -63,7 +63,8 @@ int launch_gather(const uint32_t *in, const uint32_t *perm, uint32_t m, uint32_t
     // input, so the random reads stay in L2.  More passes cost more in order
     // re-reads than they save, and the i.i.d. law's increasing positions
     // already read with locality.
-    if (padded || input_bits <= kGatherWindowBits || input_bits > 2 * kGatherWindowBits) {
+    const bool two_windows = input_bits > kGatherWindowBits && input_bits <= 2 * kGatherWindowBits;
+    if (!two_windows || (padded && !windows_when_padded)) {
         if (padded)
             gather_kernel<false, true, false><<<grid, 256, 0, st>>>(in, perm, m, s, w_pad, groups, arev, rank0, 0, 0, false);
         else

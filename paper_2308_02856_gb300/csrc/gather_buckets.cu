@@ -467,6 +467,15 @@ int gather_buckets_run(const GatherBuckets &gb, const uint32_t *in, uint64_t n, 
     return gather_buckets_stage2(gb, m, w_pad, arev, st, num_sms);
 }
 
+uint64_t gather_buckets_bytes(const GatherBuckets &gb, uint64_t n, uint32_t m, uint32_t w_pad)
+{
+    const uint64_t q = gb.run_words, pi_words = gb.clog <= 16 ? 16 : 32;
+    const uint64_t stage1 = ceil_div(n, 32) * 4 + (uint64_t)(gb.nch + 1) * 4 + q * 4 * pi_words + q * 4  // in, qc, pi, dst
+                            + q * 4;                                                                      // run words to B
+    const uint64_t stage2 = q * 4 + (uint64_t)m * w_pad * kSigWords * 4 + (uint64_t)m * w_pad * 4;        // B, sigma, arev
+    return stage1 + stage2;
+}
+
 void gather_buckets_free(GatherBuckets *gb)
 {
     cudaFree(gb->qc);

@@ -159,6 +159,15 @@ int gather_windows_run(const GatherWindows &gw, const uint32_t *in, uint32_t w_p
     return EXTRACT_OK;
 }
 
+uint64_t gather_windows_bytes(const GatherWindows &gw, uint64_t n, uint32_t w_pad)
+{
+    // every pass reads its window's entries (4-byte position, 2-byte slot)
+    // and window starts; the input once; every group's 32 words OR-ed in
+    // shared memory and stored once
+    const uint64_t slots = gw.groups * 1024;
+    return slots * 6 + gw.groups * (gw.R + 1) * 2 * gw.R + ceil_div(n, 32) * 4 + gw.groups * 32 * 4;
+}
+
 void gather_windows_free(GatherWindows *gw)
 {
     cudaFree(gw->pos);

@@ -37,10 +37,13 @@ int build_iid_order(uint64_t n, uint64_t sampling_key, uint64_t mask, uint32_t m
 // then holds sub-blocks starting at that rank).
 // padded: kNoPos entries of perm read as 0 (i.i.d. law).  input_bits: the
 // input's length; sorted-order inputs of one to two half-L2 windows are
-// gathered in one pass per window (0: one pass).
+// gathered in one pass per window (0: one pass).  windows_when_padded: a
+// padded order takes the window passes too (padded orders are otherwise
+// gathered in one pass: the i.i.d. law's increasing positions read with
+// locality).
 int launch_gather(const uint32_t *in, const uint32_t *perm, uint32_t m, uint32_t s,
                   uint32_t w_pad, uint32_t *arev, cudaStream_t st, int num_sms, uint64_t rank0 = 0,
-                  bool padded = false, uint64_t input_bits = 0);
+                  bool padded = false, uint64_t input_bits = 0, bool windows_when_padded = false);
 // True when the gather of an input of this length runs best as one launch
 // (at most two windows); larger inputs are better overlapped with hashing.
 bool gather_prefers_whole_block(uint64_t input_bits);
@@ -63,6 +66,8 @@ int gather_windows_build(const uint32_t *perm, uint32_t m, uint32_t s, uint32_t 
 int gather_windows_run(const GatherWindows &gw, const uint32_t *in, uint32_t w_pad, uint32_t *arev, cudaStream_t st,
                        int num_sms);
 void gather_windows_free(GatherWindows *gw);
+// Device-memory bytes one run of the window-major gather reads and writes by design.
+uint64_t gather_windows_bytes(const GatherWindows &gw, uint64_t n, uint32_t w_pad);
 
 // Bucketed two-stage gather (gather_buckets.cu): per sampling key, tables
 // that regroup every input chunk's bits by sub-block (stage 1) and then
@@ -96,6 +101,10 @@ int gather_buckets_stage1(const GatherBuckets &gb, const uint32_t *in, uint64_t 
 int gather_buckets_stage2(const GatherBuckets &gb, uint32_t m, uint32_t w_pad, uint32_t *arev, cudaStream_t st,
                           int num_sms);
 void gather_buckets_free(GatherBuckets *gb);
+// Device-memory bytes one run of the bucketed gather reads and writes by
+// design: input, chunk starts, pi, destinations, run words (written and
+// read), sigma and the sub-block buffer.
+uint64_t gather_buckets_bytes(const GatherBuckets &gb, uint64_t n, uint32_t m, uint32_t w_pad);
 
 // ---- steps 2-3: the Toeplitz product and concatenation ------------------
 struct HashPlan {

@@ -5,39 +5,30 @@
 // the process lives.
 //
 // Host code must not use the array's name as a device address (on the host
-// it names a host-side shadow); the device address is fetched once per
-// device with cudaGetSymbolAddress, with that device current, and handed to
-// the kernels.
+// it names a host-side shadow); every call fetches the device address with
+// cudaGetSymbolAddress, with the calling device current, and hands it to the
+// kernels.  The lookup is not cached: after a cudaDeviceReset the module is
+// loaded again and the array may sit at a new address.
 #include "common.cuh"
 #include "internal.h"
-
-#include <mutex>
 
 namespace ex {
 namespace {
 
 constexpr uint64_t kScratchWords = EXTRACT_STATIC_SCRATCH_WORDS;
-constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) uint32_t g_static_scratch[kScratchWords];
 
-std::mutex g_setup_mu;
-uint32_t *g_scratch_ptr[kMaxDevices] = {};
-
-// Device address of the scratch array on the current device (set up on the
-// first call for that device).
-int scratch_for_device(int dev, uint32_t **out)
+// Device address of the scratch array on the current device.  The first
+// lookup on a device loads this library's device code there (lazy module
+// loading), which reserves the array.
+int scratch_for_device(uint32_t **out)
 {
-    if (dev < 0 || dev >= kMaxDevices) return set_error(EXTRACT_EINVAL, "device ordinal %d out of range", dev);
-    std::lock_guard<std::mutex> lock(g_setup_mu);
-    if (!g_scratch_ptr[dev]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
-        if (e != cudaSuccess) return cuda_error(e, "cudaGetSymbolAddress(static scratch)");
-        if (!p) return set_error(EXTRACT_EINTERNAL, "static scratch has no device address");
-        g_scratch_ptr[dev] = static_cast<uint32_t *>(p);
-    }
-    *out = g_scratch_ptr[dev];
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess) return cuda_error(e, "cudaGetSymbolAddress(static scratch)");
+    if (!p) return set_error(EXTRACT_EINTERNAL, "static scratch has no device address");
+    *out = static_cast<uint32_t *>(p);
     return EXTRACT_OK;
 }
 
@@ -70,8 +61,13 @@ extern "C" int extract_run_static(uint64_t n, uint32_t m, uint32_t s, uint32_t k
         return set_error(EXTRACT_EINVAL, "extract_run_static: null seed, input or output pointer");
     if (m < 1 || s < 1 || k < 1 || k > s)
         return set_error(EXTRACT_EINVAL, "need m >= 1 and 1 <= k <= s (m=%u s=%u k=%u)", m, s, k);
-    if (n > (1ull << 32) || (uint64_t)m * s > n)
-        return set_error(EXTRACT_EINVAL, "need m*s <= n <= 2^32 (n=%llu m=%u s=%u)", (unsigned long long)n, m, s);
+    if (n > (1ull << 32))
+        return set_error(EXTRACT_EINVAL, "need n <= 2^32 (n=%llu)", (unsigned long long)n);
+    // a padded order (the i.i.d. law's) may hold more slots than positions;
+    // padding slots exist only when n < 2^32, where no position equals them
+    if ((uint64_t)m * s > n && (!perm_dev || n == (1ull << 32)))
+        return set_error(EXTRACT_EINVAL, "need m*s <= n (n=%llu m=%u s=%u)%s", (unsigned long long)n, m, s,
+                         perm_dev ? "" : " for the identity order");
 
     int dev = 0, sms = 0;
     EX_CUDA(cudaGetDevice(&dev));
@@ -88,7 +84,7 @@ extern "C" int extract_run_static(uint64_t n, uint32_t m, uint32_t s, uint32_t k
                          (unsigned long long)need, (unsigned long long)kScratchWords,
                          (unsigned long long)(kScratchWords * 4 >> 20));
     uint32_t *scratch = nullptr;
-    if (int rc = scratch_for_device(dev, &scratch)) return rc;
+    if (int rc = scratch_for_device(&scratch)) return rc;
     uint32_t *seed_stage = scratch;
     uint32_t *arev = scratch + seed_part;
 
@@ -96,6 +92,10 @@ extern "C" int extract_run_static(uint64_t n, uint32_t m, uint32_t s, uint32_t k
     stage_seed_kernel<<<(uint32_t)ceil_div(stride, 256), 256, 0, st>>>(seed_dev, (uint64_t)s + k - 1, stride,
                                                                        seed_stage);
     EX_LAUNCH("stage_seed_kernel");
-    if (int rc = launch_gather(in_bits_dev, perm_dev, m, s, w_pad, arev, st, sms, 0, false, n)) return rc;
+    // Below 2^32 input bits no position equals the padding value, so order
+    // entries that hold it are read as 0: the i.i.d. law's padded orders, and
+    // never a real position of a sorted order.
+    const bool padded = perm_dev && n < (1ull << 32);
+    if (int rc = launch_gather(in_bits_dev, perm_dev, m, s, w_pad, arev, st, sms, 0, padded, n, true)) return rc;
     return launch_hash(plan, seed_stage, 0u, arev, w_pad, m, k, out_bits_dev, st);
 }

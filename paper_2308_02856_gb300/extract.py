@@ -49,7 +49,7 @@ def EXTRACT_NTT_SPLIT(l: int) -> int:
 EXPORTED = [
     "extract_create", "extract_run", "extract_run_host", "extract_gather", "extract_hash", "extract_run_plain",
     "extract_read_perm", "extract_read_subblock", "extract_describe", "extract_destroy",
-    "extract_subblock_sizes", "extract_block_limit",
+    "extract_subblock_sizes", "extract_block_limit", "extract_gather_bytes",
     "extract_last_error", "extract_run_static",
     "extract_batch_create", "extract_batch_run", "extract_batch_run_sequential", "extract_batch_describe",
     "extract_batch_destroy",
@@ -108,6 +108,7 @@ def load() -> ctypes.CDLL:
     L.extract_subblock_sizes.argtypes = [vp, vp]
     L.extract_block_limit.argtypes = [u64, u32, ctypes.c_double, ctypes.c_double, ctypes.POINTER(u64)]
     L.extract_describe.argtypes = [vp, ctypes.c_char_p, u32]
+    L.extract_gather_bytes.argtypes = [vp, ctypes.POINTER(u64)]
     L.extract_destroy.argtypes = [vp]
     L.extract_run_static.argtypes = [u64, u32, u32, u32, vp, vp, vp, vp, vp]
     L.extract_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(extract_job_desc), u32, u32]
@@ -225,6 +226,12 @@ def extract_describe(h) -> str:
     buf = ctypes.create_string_buffer(512)
     _check(load().extract_describe(h, buf, 512))
     return buf.value.decode()
+
+
+def extract_gather_bytes(h) -> int:
+    v = ctypes.c_uint64(0)
+    _check(load().extract_gather_bytes(h, ctypes.byref(v)))
+    return int(v.value)
 
 
 def extract_run_static(n, m, s, k, perm, seed, in_bits, out_bits, stream=None) -> None:
@@ -401,6 +408,10 @@ class Extractor:
 
     def describe(self) -> str:
         return extract_describe(self.h)
+
+    def gather_bytes(self) -> int:
+        """Device-memory bytes one gather of this context reads and writes by design."""
+        return extract_gather_bytes(self.h)
 
     def close(self):
         if self.h:

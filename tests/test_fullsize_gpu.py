@@ -4,9 +4,11 @@
   and checks that the GPU order increases strictly in (label, position)
   order with every entry < n, which makes it a bijection and the unique
   stable argsort.
-* The gather is checked on whole sub-blocks (every bit, as stored for the
-  hash) and the hash on sampled outputs: the oracle selects sub-blocks by
-  rank from its own labels and computes sampled rows one bit at a time.
+* Whole sub-blocks, every bit: the gathered sub-block as stored for the hash,
+  and every output row of its hash, against the word-packed oracle.  The
+  sub-blocks are chosen across many NTT launch groups (the first and last
+  sub-block of each chosen group, and a few in between), from groups run on
+  both of the hash's two lanes.
 """
 import numpy as np
 import pytest
@@ -29,10 +31,22 @@ def _lib():
     X.load()
 
 
-def _full_size_case(n, m, s, k, p, rows_per_block, blocks):
+def _group_blocks(G, groups, extra):
+    """First and last sub-block of each launch group in ``groups`` (groups of
+    G sub-blocks alternate between two lanes), plus ``extra``."""
+    blocks = [G * g + r for g in groups for r in (0, G - 1)] + list(extra)
+    lanes = {g % 2 for g in groups}
+    assert lanes == {0, 1}
+    return sorted(set(blocks))
+
+
+def _full_size_case(n, m, s, k, p, blocks, plan_has):
     in_w = synth.bernoulli_bits(n, p, 1)
     seed = synth.uniform_bits(s + k - 1, 3)
     with X.Extractor(n, m, s, k, seed, 2) as ex:
+        plan = ex.describe()
+        for frag in plan_has:
+            assert frag in plan, plan
         d_in = torch.from_numpy(in_w.view(np.int32)).cuda()
         out = ex.run(d_in)
         got = oracle.bits_of(out.cpu().numpy().view(np.uint32), m * k)
@@ -42,23 +56,33 @@ def _full_size_case(n, m, s, k, p, rows_per_block, blocks):
     keys = oracle.sampling_keys(n, 2)
     assert oracle.check_order(keys, perm) == -1
     del perm
-    rng = np.random.default_rng(1)
-    for j in blocks:
-        pos = oracle.perm_range(keys, j * s, s)
-        A = oracle.subblock(in_w, pos)
+    pos = oracle.perm_ranges(keys, [(j * s, s) for j in blocks])
+    del keys
+    for t, j in enumerate(blocks):
+        A = oracle.subblock(in_w, pos[t * s:(t + 1) * s])
         assert np.array_equal(stored[j], A), "gathered sub-block %d" % j
-        rows = np.unique(np.concatenate([np.arange(16), np.arange(k - 16, k),
-                                         rng.choice(k, rows_per_block, replace=False)]))
-        want = np.array([oracle.toeplitz_bit(seed, s, A, int(i)) for i in rows], dtype=np.uint8)
-        assert np.array_equal(got[j * k + rows], want), "sub-block %d" % j
+    K = oracle.fast_window(in_w, pos, s, k, seed, 0, blocks, 0, k, seed_len_bits=s + k - 1)
+    for t, j in enumerate(blocks):
+        bad = np.flatnonzero(got[j * k:(j + 1) * k] != K[t])
+        assert bad.size == 0, "sub-block %d: %d of %d rows differ, first %s" % (j, bad.size, k, bad[:5])
 
 
 def test_qrng_shaped_block_n2e30():
-    """n = 2^30 Bernoulli(0.6), m = 1024 sub-blocks of s = 2^20, k = 2^19."""
-    _full_size_case(1 << 30, 1024, 1 << 20, 1 << 19, 0.6, 48, [0, 1, 511, 1023])
+    """n = 2^30 Bernoulli(0.6), m = 1024 sub-blocks of s = 2^20, k = 2^19:
+    P = 2 pieces, N = 2^20, 16-sub-block launch groups on two lanes; every
+    row of 32 whole sub-blocks from 14 of the 64 groups."""
+    blocks = _group_blocks(16, (0, 1, 2, 3, 4, 5, 30, 31, 32, 33, 60, 61, 62, 63), (7, 8, 16 * 63 + 7, 16 * 63 + 8))
+    assert len(blocks) == 32
+    _full_size_case(1 << 30, 1024, 1 << 20, 1 << 19, 0.6, blocks,
+                    ("ntt: N=1048576", "P=2 ", "16 sub-blocks per launch group", "gather=buckets (2^16-bit"))
 
 
 def test_qkd_shaped_block_n2e32():
     """n = 2^32 Bernoulli(0.9), m = 4096 sub-blocks of s = 2^20, k = 104858
-    (k mod 32 = 26: every sub-block's output starts at an unaligned bit)."""
-    _full_size_case(1 << 32, 4096, 1 << 20, 104858, 0.9, 32, [0, 1, 2047, 4095])
+    (k mod 32 = 26: every sub-block's output starts at an unaligned bit):
+    P = 8 pieces, N = 2^18, 16-sub-block launch groups on two lanes, bucket
+    tables over 2^18-bit chunks; every row of 16 whole sub-blocks."""
+    blocks = _group_blocks(16, (0, 1, 127, 128, 254, 255), (7, 16 * 255 + 8, 1603, 3228))
+    assert len(blocks) == 16
+    _full_size_case(1 << 32, 4096, 1 << 20, 104858, 0.9, blocks,
+                    ("ntt: N=262144", "P=8 ", "16 sub-blocks per launch group", "gather=buckets (2^18-bit"))

@@ -14,8 +14,8 @@ something other than itself:
 
 Planted mistakes in a copy of oracle_fast.c (a window off by one bit, the
 sub-block not reversed, a dropped last word, a wrong seed offset per
-sub-block, the word-aligned shortcut reading the wrong word, a rank off by
-one) must each be caught.
+sub-block, the word-aligned case reading the wrong word, a funnel shift by
+the wrong amount, a rank off by one) must each be caught.
 """
 import os
 import subprocess
@@ -136,13 +136,13 @@ def test_perm_ranges_matches_stable_argsort():
 # planted mistakes
 # --------------------------------------------------------------------------
 MUTANTS = {
-    "window off by one bit": ("acc ^= seed_word_at(S, t0 + 64u * w) & R[w];",
-                              "acc ^= seed_word_at(S, t0 + 1 + 64u * w) & R[w];"),
+    "window off by one bit": ("const uint64_t t0 = off + i, q", "const uint64_t t0 = off + i + 1, q"),
     "sub-block not reversed": ("const uint64_t cr = s - 1 - c;", "const uint64_t cr = c;"),
-    "last word dropped": ("for (uint64_t w = 0; w < nwords; ++w)\n        acc ^=",
-                          "for (uint64_t w = 0; w + 1 < nwords; ++w)\n        acc ^="),
+    "last word dropped": ("for (uint64_t w = 0; w < nwords; ++w)\n            acc ^= ((S",
+                          "for (uint64_t w = 0; w + 1 < nwords; ++w)\n            acc ^= ((S"),
     "per-sub-block seed offset": ("f->seed_len = s + k - 1;", "f->seed_len = s + k;"),
-    "aligned window reads the next word": ("if (b == 0) return S[q];", "if (b == 0) return S[q + 1];"),
+    "aligned window reads the next word": ("acc ^= S[q + w] & R[w];", "acc ^= S[q + w + 1] & R[w];"),
+    "funnel shift by the wrong amount": ("(S[q + w + 1] << (64u - b))", "(S[q + w + 1] << (63u - b))"),
     "rank off by one": ("out[o++] = c[base[lo_b] + (rank - start[lo_b])].idx;",
                         "out[o++] = c[base[lo_b] + (rank + 1 - start[lo_b])].idx;"),
 }
