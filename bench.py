@@ -96,7 +96,7 @@ def parse_args(argv=None):
     ap.add_argument("--sampling", choices=["sorted", "iid"], default="sorted",
                     help="block mode: sorted order cut into equal sub-blocks (default), or the paper's i.i.d. "
                          "labels with sub-blocks padded to Eq. 7's block size limit")
-    ap.add_argument("--method", choices=["auto", "direct", "ntt"], default="auto",
+    ap.add_argument("--method", choices=["auto", "direct", "ntt", "tensor"], default="auto",
                     help="hashing method of the block mode (auto: the library's choice)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -108,14 +108,20 @@ def parse_args(argv=None):
     return ap.parse_args(argv)
 
 
+FALLBACK_BF16_TFLOPS = 1900.0  # the profiling recipe's fallback dense bf16 rate
+FP8_PER_BF16 = 2.0  # nominal dense FP8 / BF16 tensor rate (4.5 / 2.25 PFLOP/s)
+
+
 def measured_peaks():
     """The measured peaks, or the recipe's fallback (labelled)."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             d = json.load(f)
-        return {"hbm_gbs": float(d["hbm_gbs"]), "basis": "measured (MEASURED_PEAKS.json copy bandwidth)"}
+        return {"hbm_gbs": float(d["hbm_gbs"]), "bf16_tflops": float(d["bf16_tflops"]),
+                "basis": "measured (MEASURED_PEAKS.json)"}
     except (OSError, ValueError, KeyError):
-        return {"hbm_gbs": FALLBACK_HBM_GBS, "basis": "fallback 6.8 TB/s (no measured peaks file)"}
+        return {"hbm_gbs": FALLBACK_HBM_GBS, "bf16_tflops": FALLBACK_BF16_TFLOPS,
+                "basis": "fallback 6.8 TB/s and 1.9 PFLOP/s bf16 (no measured peaks file)"}
 
 
 # --------------------------------------------------------------------------
@@ -347,6 +353,19 @@ def ntt_roofline(n, m, s, k, hash_ms, plan, sms=152, workload=None):
             "note": "does %.0fx less work than the direct m*k*s product" % ((m * k * s / 32.0) / bfly)}
 
 
+def tc_roofline(m, k, s, hash_ms, peaks):
+    """The tensor-core product (tc_hash_kernel, tcgen05.mma kind::f8f6f4 on
+    0/1 e4m3 operands): 2 m k s flops against the dense FP8 rate, taken as
+    the measured bf16 burst rate times the nominal FP8/BF16 ratio."""
+    flops = 2.0 * m * k * s
+    achieved = flops / (hash_ms / 1e3) / 1e12
+    peak = peaks["bf16_tflops"] * FP8_PER_BF16
+    return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "kernel": "tc_hash_kernel", "work_per_launch": "2 m k s = %.4g flops on 0/1 operands" % flops,
+            "peak_basis": "%s bf16 burst %.0f TFLOP/s x %.0f (nominal FP8/BF16 dense ratio)"
+                          % (peaks["basis"], peaks["bf16_tflops"], FP8_PER_BF16)}
+
+
 def lop3_roofline(m, k, s, hash_ms, sms, clocks=None):
     """The direct GF(2) kernel (toeplitz_lop3_kernel): m*k*s/32 LOP3 against
     the integer-ALU roofline."""
@@ -435,7 +454,8 @@ def run_ours(args):
         s = X.extract_block_limit(n, m, IID_EPS, 1.0 / m)
     in_w, seed_w = make_inputs(n, m, s, k, p, m if per_sub else 1)
 
-    method_flags = {"auto": 0, "direct": X.EXTRACT_METHOD_DIRECT, "ntt": X.EXTRACT_METHOD_NTT}[args.method]
+    method_flags = {"auto": 0, "direct": X.EXTRACT_METHOD_DIRECT, "ntt": X.EXTRACT_METHOD_NTT,
+                    "tensor": X.EXTRACT_METHOD_TENSOR}[args.method]
     if iid:
         method_flags |= X.EXTRACT_SAMPLING_IID
     if per_sub:
@@ -446,6 +466,7 @@ def run_ours(args):
     create_ms = (time.perf_counter() - t0) * 1e3
     plan = ex.describe()
     is_ntt = plan.startswith("ntt")
+    is_tc = plan.startswith("tensor")
 
     d_in = torch.from_numpy(in_w.view(np.int32)).to(dev)
     d_out = ex.new_output()
@@ -509,26 +530,38 @@ def run_ours(args):
                "api": "extract_run_host (pinned host buffers, copies and sync inside the timed region)"}
         del h_in, h_out
 
-    # the comparison points on the same block: the plain per-block path and
-    # the direct tiled kernel
-    plain = direct = None
+    # the comparison points on the same block: the plain per-block path, the
+    # direct tiled kernel and the tensor-core product
+    plain = direct = tensor = None
     if not args.no_compare:
         clk2 = ClockSampler(gpu).start()
         pms = events_ms(torch, stream, lambda: ex.run_plain(d_in, d_out, stream=stream), 1)
         plain = {"ms": pms, "value": aggregate_rate(n, 1, pms), "unit": "Gbit/s", "launches_per_run": m + 2,
                  "path": "gather, then one launch per sub-block, one thread per output row (extract_run_plain)",
                  "speedup_of_library_path": pms / ms_step}
-        if is_ntt:
-            flags_d = X.EXTRACT_METHOD_DIRECT | (method_flags & (X.EXTRACT_SAMPLING_IID | X.EXTRACT_SEED_PER_SUBBLOCK))
-            with X.Extractor(n, m, s, k, seed_w, SAMPLING_KEY, flags_d) as exd:
+        keep = method_flags & (X.EXTRACT_SAMPLING_IID | X.EXTRACT_SEED_PER_SUBBLOCK)
+        if is_ntt or is_tc:
+            with X.Extractor(n, m, s, k, seed_w, SAMPLING_KEY, X.EXTRACT_METHOD_DIRECT | keep) as exd:
                 exd.gather(d_in, stream=stream)
                 dms = events_ms(torch, stream, lambda: exd.hash(d_out, stream=stream), 2)
                 direct = {"hash_ms": dms, "value": aggregate_rate(n, 1, dms + gather_ms), "unit": "Gbit/s",
                           "roofline": lop3_roofline(m, k, s, dms, sms, clocks), "plan": exd.describe()}
+        if not is_tc and not per_sub:
+            with X.Extractor(n, m, s, k, seed_w, SAMPLING_KEY, X.EXTRACT_METHOD_TENSOR | keep) as ext:
+                ext.gather(d_in, stream=stream)
+                ext.hash(d_out, stream=stream)
+                tms = events_ms(torch, stream, lambda: ext.hash(d_out, stream=stream), 1)
+                ext.status()
+                tensor = {"hash_ms": tms, "value": aggregate_rate(n, 1, tms + gather_ms), "unit": "Gbit/s",
+                          "roofline": tc_roofline(m, k, s, tms, peaks), "plan": ext.describe()}
         plain["clocks"] = clk2.stop()
-    roofline = (ntt_roofline(n, m, s, k, hash_ms, plan, sms, None if (iid or per_sub) else args.workload)
-                if is_ntt else lop3_roofline(m, k, s, hash_ms, sms, clocks))
-    if not is_ntt:
+    if is_ntt:
+        roofline = ntt_roofline(n, m, s, k, hash_ms, plan, sms, None if (iid or per_sub) else args.workload)
+    elif is_tc:
+        roofline = tc_roofline(m, k, s, hash_ms, peaks)
+        tensor = {"hash_ms": hash_ms, "roofline": roofline, "plan": plan}
+    else:
+        roofline = lop3_roofline(m, k, s, hash_ms, sms, clocks)
         direct = {"hash_ms": hash_ms, "roofline": roofline, "plan": plan}
     ex.close()
     del d_in, d_out
@@ -556,7 +589,7 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "u32 (GF(2) bits)", "data": "synthetic",
             "config": workload_config(args.workload, s=s, iid=iid, per_sub=per_sub, world=world),
             "plan": plan,
-            "method": "ntt" if is_ntt else "direct",
+            "method": "ntt" if is_ntt else "tensor" if is_tc else "direct",
             "create_ms": create_ms,
             "gather_ms": gather_ms, "hash_ms": hash_ms,
             "gpu_launches": launches_per_step(is_ntt, m, plan, n) * args.steps,
@@ -565,6 +598,7 @@ def run_ours(args):
             "plain_per_block": plain,
             "speedup_vs_plain_per_block": plain["speedup_of_library_path"] if plain else None,
             "direct_tiled": direct,
+            "tensor_core": tensor,
             "batch": batch,
             "serve": serve,
             "cpu_baseline": cpu,
@@ -719,8 +753,10 @@ def run_compare(args):
     """The comparison points: on the QKD-shaped block (n = 2^32, m = 4096,
     s = 2^20, k = 104858, p = 0.9) the library's method, the direct tiled
     kernel and the plain per-block path (one launch per sub-block, one thread
-    per output row); and direct whole-block Toeplitz hashing (m = 1, identity
-    order) at n = 2^24, k = 2^23 and at n = 2^18, k = 2^16, tiled and plain.
+    per output row); direct whole-block Toeplitz hashing (m = 1, identity
+    order) at n = 2^24, k = 2^23 and at n = 2^18, k = 2^16, tiled and plain;
+    and the hash time of the three exact methods (tensor cores, NTT, direct
+    LOP3) on shapes from the batch workload's range and on the QKD block.
     Inputs are drawn on the GPU (the parity tests check these shapes)."""
     import torch
     from paper_2308_02856_gb300 import extract as X
@@ -758,6 +794,35 @@ def run_compare(args):
             res["direct_whole_block_n%d_k%d" % (n2, k2)] = {
                 "tiled_ms": ms, "tiled_gbit_per_s": n2 / (ms / 1e3) / 1e9, "plain_ms": pms,
                 "plain_gbit_per_s": n2 / (pms / 1e3) / 1e9, "plan": ex.describe()}
+    # the three exact hashing methods on one block each of shapes from the
+    # batch workload's range (n = 2^28; low, middle and high k/s) and on the
+    # QKD-shaped block: hash time alone, sub-blocks gathered once before
+    methods = {}
+    peaks = measured_peaks()
+    for n3, s3, k3 in ((1 << 28, 1 << 16, 3277), (1 << 28, 1 << 18, 13107), (1 << 28, 1 << 20, 52429),
+                       (1 << 28, 1 << 16, 16384), (1 << 28, 1 << 16, 32768), (1 << 32, 1 << 20, 104858)):
+        m3 = n3 // s3
+        d_in = synth.bernoulli_bits_device(n3, 0.7, IN_SEED)
+        seed = synth.uniform_bits(s3 + k3 - 1, TOEPLITZ_SEED)
+        row = {"n": n3, "m": m3, "s": s3, "k": k3}
+        for name, flags in (("tensor_core", X.EXTRACT_METHOD_TENSOR), ("ntt", X.EXTRACT_METHOD_NTT),
+                            ("direct_lop3", X.EXTRACT_METHOD_DIRECT)):
+            if n3 == 1 << 32 and name == "direct_lop3":
+                continue  # measured above
+            with X.Extractor(n3, m3, s3, k3, seed, SAMPLING_KEY, flags) as ex:
+                out = ex.new_output()
+                ex.run(d_in, out, stream=st)
+                reps = 1 if (n3 == 1 << 32 and name == "tensor_core") else 3
+                hms = events_ms(torch, st, lambda: ex.hash(out, stream=st), reps)
+                ex.status()
+                row[name + "_hash_ms"] = hms
+                if name == "tensor_core":
+                    row["tensor_core_roofline"] = tc_roofline(m3, k3, s3, hms, peaks)
+        row["fastest"] = min((v, k_[:-8]) for k_, v in row.items() if k_.endswith("_hash_ms"))[1]
+        methods["n%d_s%d_k%d" % (n3, s3, k3)] = row
+        del d_in
+        torch.cuda.empty_cache()
+    res["hash_methods"] = methods
     q = res
     line = {"metric": "extracted input Gbit/s (comparison points)", "unit": "Gbit/s", "n_gpus": 1,
             "value": q["qkd_n2^32_library_choice"]["gbit_per_s"], "higher_is_better": True,

@@ -67,9 +67,10 @@ extern "C" {
    the two exact methods for the shape.  EXTRACT_METHOD_DIRECT forces the
    direct GF(2) product (bit-sliced AND/XOR, work m*k*s); EXTRACT_METHOD_NTT
    forces the number-theoretic-transform middle product modulo the prime
-   7*2^26+1.  It splits each sub-block into P = 2^l pieces of h bits (h = s
-   for P = 1, else ceil(s/P) rounded up to a multiple of 32) and costs P + 1
-   transforms of the power of two N >= h+k-1 per sub-block.  With
+   7*2^26+1.  It splits each sub-block into P pieces (1 <= P <= 16) of h
+   bits (h = s for P = 1, else ceil(s/P) rounded up to a multiple of 32) and
+   costs P + 1 transforms of the power of two N >= h+k-1 per sub-block; P
+   is the one with the least predicted work.  With
    EXTRACT_SEED_PER_SUBBLOCK (then N >= 2^16) the spectra of every
    sub-block's seed windows are built at create and kept (4 m P N bytes)
    when they take at most a quarter of the free device memory, else their
@@ -119,6 +120,21 @@ extern "C" {
    than 25600 chunks of 2^16 bits or its runs are too short to fit.  Tuning
    and test hook. */
 #define EXTRACT_GATHER_WIDE_CHUNKS 0x80u
+
+/* The direct GF(2) product on the tensor cores instead (the dense form of
+   Sec. I's K = T . A' with all sub-blocks sharing T): D = T . [A_1 .. A_m]
+   over the integers with 0/1 e4m3 operands on tcgen05.mma (kind::f8f6f4,
+   f32 accumulators in tensor memory), K_j[i] = D[i][j] mod 2.  The sums are
+   read back and reduced to parities every K chunk (4096 by default), so
+   every partial sum stays an exact small integer.  Needs one shared seed
+   (EXTRACT_EINVAL with EXTRACT_SEED_PER_SUBBLOCK); exclusive with the other
+   method flags.  Gives the same bits as the other methods.  A kernel that
+   gives up on a wait (about a second) sets an error word that
+   extract_status reports. */
+#define EXTRACT_METHOD_TENSOR     0x100000u
+/* Tensor-core method: 2^l K blocks of 128 (l = 0 .. 14) summed before each
+   parity read-back instead of 2^5.  Test hook. */
+#define EXTRACT_TC_CHUNK(l)       ((((uint32_t)(l) + 1u) & 0xfu) << 24)
 
 typedef struct extract_ctx extract_ctx;
 
@@ -234,6 +250,11 @@ int extract_read_subblock(extract_ctx *h, uint32_t j, uint32_t *dst_host);
    kernel configuration (tile shape, split, grid) into buf. */
 int extract_describe(extract_ctx *h, char *buf, uint32_t buflen);
 
+/* extract_status - synchronise the device and report whether a kernel of
+   this context gave up on a bounded wait since the last call
+   (EXTRACT_ETIMEDOUT, then cleared) or not (EXTRACT_OK). */
+int extract_status(extract_ctx *h);
+
 /* extract_gather_bytes - the device-memory bytes one extract_gather of this
    context reads and writes by design: with the bucket tables, the input
    once, the tables (chunk starts, in-chunk positions, destinations, member
@@ -312,22 +333,25 @@ typedef struct extract_batch extract_batch;
 #define EXTRACT_BATCH_NO_GRAPH 0x1u  /* launch the kernels directly instead of replaying a CUDA graph */
 #define EXTRACT_BATCH_NO_TUNE  0x2u  /* use the single-block heuristic tile instead of the autotuned one */
 #define EXTRACT_BATCH_DIRECT_ONLY 0x4u  /* hash every job with the direct method (no NTT jobs) */
+#define EXTRACT_BATCH_TENSOR 0x8u       /* test hook: hash every shared-seed job with the tensor-core product */
 
 /*
  * extract_batch_create - set up njobs independent blocks (the method of
  * Sec. III.B applied to each) for hashing in one persistent launch.
  *
  * Builds every job's sampled order (synchronous) and picks each job's
- * method: the NTT method where it is eligible and predicted faster (those
- * jobs run one after another on a stream of the batch, concurrent with the
- * rest), else the direct method, whose tile shape the autotuner chooses
+ * method by least predicted time: the NTT method where it is eligible, the
+ * tensor-core product where the job has one shared seed (those jobs run on
+ * four concurrent lanes of the batch, each with its own stream and work
+ * buffer, longest predicted first to the least-loaded lane, concurrent with
+ * the rest), else the direct method, whose tile shape the autotuner chooses
  * (measured cost per tile variant, cached per device, then the least
  * predicted time including padding).  Direct jobs' word ranges are split so
  * the tiles balance across SMs, the tiles are ordered longest first, and
  * their per-run kernels (zero outputs, gather, persistent hash) are
  * captured into a CUDA graph.  Device memory held: per job as
- * extract_create (plus the NTT tables of NTT jobs and one shared NTT work
- * buffer).
+ * extract_create (plus the NTT tables of NTT jobs and one NTT work buffer
+ * per lane).
  * Errors: EINVAL (empty list, a bad job shape or flags), ENOMEM, ECUDA.
  */
 int extract_batch_create(extract_batch **out, const extract_job_desc *jobs, uint32_t njobs,
@@ -349,6 +373,11 @@ int extract_batch_run(extract_batch *b, void *stream, const uint32_t *const *in_
    baseline the persistent launch is measured against. */
 int extract_batch_run_sequential(extract_batch *b, void *stream, const uint32_t *const *in_bits_dev,
                                  uint32_t *const *out_bits_dev);
+
+/* extract_batch_status - synchronise the device and report whether a
+   tensor-core kernel of the batch gave up on a bounded wait since the last
+   call (EXTRACT_ETIMEDOUT, then cleared) or not (EXTRACT_OK). */
+int extract_batch_status(extract_batch *b);
 
 /* extract_batch_describe - one line: jobs, tiles, graph, chosen variants and
    their measured cost. */

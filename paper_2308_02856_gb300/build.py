@@ -75,14 +75,5 @@ def build(force: bool = False, verbose: bool = False) -> str:
     return LIB
 
 
-def run_alu_probe() -> str:
-    """Build and run csrc/probes/alu_probe.cu (LOP3 and mma.sync issue rates);
-    returns its report."""
-    os.makedirs(OUT_DIR, exist_ok=True)
-    exe = os.path.join(OUT_DIR, "alu_probe")
-    subprocess.run([nvcc(), os.path.join(CSRC, "probes", "alu_probe.cu"), "-o", exe, "-O3"] + ARCH, check=True)
-    return subprocess.run([exe], check=True, capture_output=True, text=True).stdout
-
-
 if __name__ == "__main__":
     build(force="--force" in sys.argv, verbose=True)

@@ -211,14 +211,16 @@ struct BatchJobHost {
     HashPlan plain_plan;  // the single-block heuristic plan (one launch per block)
     uint32_t *perm = nullptr, *arev = nullptr, *seed = nullptr;
     NttPlan *ntt = nullptr;  // set when this job is hashed by the NTT method
+    bool tc = false;         // hashed by the tensor-core product (on a lane, like NTT jobs)
     int table_index = -1;    // row of the device job table (direct-method jobs)
-    int lane = -1;           // NTT lane of an NTT-method job
+    int lane = -1;           // lane of an NTT-method or tensor-core job
 };
 
-// NTT jobs run on a few concurrent lanes (stream + work buffer each), so
-// small transforms fill the GPU together; jobs are assigned longest first
-// to the least loaded lane.
+// NTT and tensor-core jobs run on a few concurrent lanes (stream + NTT work
+// buffer each), so small transforms fill the GPU together; jobs are
+// assigned longest first to the least loaded lane.
 constexpr int kNttLanes = 4;
+constexpr uint32_t kTcBatchChunk = 32;  // K blocks of 128 per parity read-back (4096 K)
 struct NttLane {
     cudaStream_t st = nullptr;
     uint32_t *work = nullptr;
@@ -242,7 +244,8 @@ struct extract_batch {
     uint32_t *d_counter = nullptr;
     uint64_t total_groups = 0, total_out_words = 0;
     double predicted_ms = 0;
-    uint32_t ndirect = 0, nntt = 0;
+    uint32_t ndirect = 0, nntt = 0, ntc = 0;
+    uint32_t *d_err = nullptr;  // error word of the tensor-core kernels
     NttLane lanes[kNttLanes];      // concurrent with the persistent launch
     std::vector<uint32_t> ntt_order;  // NTT jobs, longest predicted first
     cudaEvent_t ev_fork = nullptr;
@@ -270,6 +273,7 @@ void free_batch(extract_batch *b)
         if (L.st) cudaStreamDestroy(L.st);
     }
     if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+    cudaFree(b->d_err);
     cudaFree(b->d_jobs);
     cudaFree(b->d_tiles);
     cudaFree(b->d_counter);
@@ -314,8 +318,10 @@ int extract_batch_create(extract_batch **out, const extract_job_desc *jobs, uint
     if (!out) return set_error(EXTRACT_EINVAL, "out is null");
     *out = nullptr;
     if (!jobs || njobs == 0) return set_error(EXTRACT_EINVAL, "empty job list");
-    if (flags & ~(EXTRACT_BATCH_NO_GRAPH | EXTRACT_BATCH_NO_TUNE | EXTRACT_BATCH_DIRECT_ONLY))
+    if (flags & ~(EXTRACT_BATCH_NO_GRAPH | EXTRACT_BATCH_NO_TUNE | EXTRACT_BATCH_DIRECT_ONLY | EXTRACT_BATCH_TENSOR))
         return set_error(EXTRACT_EINVAL, "unknown batch flags 0x%x", flags);
+    if ((flags & EXTRACT_BATCH_DIRECT_ONLY) && (flags & EXTRACT_BATCH_TENSOR))
+        return set_error(EXTRACT_EINVAL, "EXTRACT_BATCH_DIRECT_ONLY and EXTRACT_BATCH_TENSOR are exclusive");
     const uint32_t known = EXTRACT_SEED_PER_SUBBLOCK | EXTRACT_IDENTITY_PERM | EXTRACT_SAMPLING_IID | (0x3fu << 8);
     for (uint32_t i = 0; i < njobs; ++i) {
         const extract_job_desc &d = jobs[i];
@@ -362,10 +368,21 @@ int extract_batch_create(extract_batch **out, const extract_job_desc *jobs, uint
         const uint64_t tiles = ceil_div(d.k, (uint64_t)kHashWarps * 32 * variant_q(J.variant)) *
                                ceil_div(d.m, (uint64_t)variant_j(J.variant));
         const double direct_ns = (double)tiles * nchunks * tt->ns_per_chunk[J.variant];
-        const bool want_ntt = !(flags & EXTRACT_BATCH_DIRECT_ONLY) && ntt_shape(d.s, d.k, -1, per_sub).N != 0 &&
-                              predict_ntt_s(d.m, d.s, d.k, -1, per_sub) * 1e9 < direct_ns;
-        if (want_ntt) J.table_index = -2;  // marks an NTT job until its plan exists
-        else total_ns += direct_ns;
+        // the least predicted time of the three methods (tensor cores only
+        // with a shared seed; the direct kernel only with DIRECT_ONLY)
+        const bool any = !(flags & EXTRACT_BATCH_DIRECT_ONLY);
+        const double ntt_ns = any && ntt_shape(d.s, d.k, -1, per_sub).N != 0
+                                  ? predict_ntt_s(d.m, d.s, d.k, -1, per_sub) * 1e9 : 1e300;
+        const double tc_ns = any && !per_sub ? predict_tc_s(d.m, d.k, d.s) * 1e9 : 1e300;
+        if ((flags & EXTRACT_BATCH_TENSOR) && !per_sub) {
+            J.table_index = -2;  // marks a lane job until its plan exists
+            J.tc = true;
+        } else if (std::min(ntt_ns, tc_ns) < direct_ns) {
+            J.table_index = -2;
+            J.tc = tc_ns < ntt_ns;
+        } else {
+            total_ns += direct_ns;
+        }
         HashPlan vp;
         vp.q = variant_q(J.variant); vp.j = variant_j(J.variant);
         vp.gx = (uint32_t)ceil_div(d.k, vp.rows());
@@ -379,7 +396,7 @@ int extract_batch_create(extract_batch **out, const extract_job_desc *jobs, uint
     for (uint32_t i = 0; i < njobs; ++i) {
         BatchJobHost &J = b->jobs[i];
         if (J.table_index == -2) {
-            ++b->nntt;
+            ++(J.tc ? b->ntc : b->nntt);
             continue;
         }
         J.table_index = (int)b->ndirect++;
@@ -410,8 +427,12 @@ int extract_batch_create(extract_batch **out, const extract_job_desc *jobs, uint
         for (uint32_t i = 0; i < njobs; ++i)
             if (b->jobs[i].table_index == -2) {
                 const bool ps = (jobs[i].flags & EXTRACT_SEED_PER_SUBBLOCK) != 0;
-                work = std::max(work, ntt_work_words(jobs[i].m, jobs[i].s, jobs[i].k, -1, ps));
-                nj_cost.push_back({predict_ntt_s(jobs[i].m, jobs[i].s, jobs[i].k, -1, ps), i});
+                if (b->jobs[i].tc) {
+                    nj_cost.push_back({predict_tc_s(jobs[i].m, jobs[i].k, jobs[i].s), i});
+                } else {
+                    work = std::max(work, ntt_work_words(jobs[i].m, jobs[i].s, jobs[i].k, -1, ps));
+                    nj_cost.push_back({predict_ntt_s(jobs[i].m, jobs[i].s, jobs[i].k, -1, ps), i});
+                }
             }
         std::stable_sort(nj_cost.begin(), nj_cost.end(), [](const auto &x, const auto &y) { return x.first > y.first; });
         const int nlanes = (int)std::min<size_t>(kNttLanes, nj_cost.size());
@@ -425,7 +446,7 @@ int extract_batch_create(extract_batch **out, const extract_job_desc *jobs, uint
         }
         for (int l = 0; l < nlanes && rc == EXTRACT_OK; ++l) {
             NttLane &L = b->lanes[l];
-            if ((e = cudaMalloc(&L.work, work * 4)) != cudaSuccess) { rc = cuda_error(e, "cudaMalloc(ntt work)"); break; }
+            if (work && (e = cudaMalloc(&L.work, work * 4)) != cudaSuccess) { rc = cuda_error(e, "cudaMalloc(ntt work)"); break; }
             if ((e = cudaStreamCreateWithFlags(&L.st, cudaStreamNonBlocking)) != cudaSuccess ||
                 (e = cudaEventCreateWithFlags(&L.join, cudaEventDisableTiming)) != cudaSuccess) {
                 rc = cuda_error(e, "ntt lane");
@@ -435,6 +456,10 @@ int extract_batch_create(extract_batch **out, const extract_job_desc *jobs, uint
         if (rc != EXTRACT_OK) break;
         if (nlanes && (e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming)) != cudaSuccess) {
             rc = cuda_error(e, "ntt fork event");
+            break;
+        }
+        if (b->ntc && ((e = cudaMalloc(&b->d_err, 4)) != cudaSuccess || (e = cudaMemset(b->d_err, 0, 4)) != cudaSuccess)) {
+            rc = cuda_error(e, "tensor-core error word");
             break;
         }
         for (uint32_t i = 0; i < njobs && rc == EXTRACT_OK; ++i) {
@@ -470,8 +495,8 @@ int extract_batch_create(extract_batch **out, const extract_job_desc *jobs, uint
                 }
             }
             if (J.table_index == -2) {
-                if ((rc = ntt_create(&J.ntt, d.m, d.s, d.k, J.seed, st, b->lanes[J.lane].work, -1,
-                                     J.nseeds > 1 ? J.seed_stride : 0)) != EXTRACT_OK)
+                if (!J.tc && (rc = ntt_create(&J.ntt, d.m, d.s, d.k, J.seed, st, b->lanes[J.lane].work, -1,
+                                              J.nseeds > 1 ? J.seed_stride : 0)) != EXTRACT_OK)
                     break;
                 continue;
             }
@@ -510,12 +535,12 @@ int extract_batch_create(extract_batch **out, const extract_job_desc *jobs, uint
 
     int counts[kNumVariants] = {};
     for (auto &J : b->jobs)
-        if (!J.ntt) counts[J.variant]++;
+        if (J.table_index >= 0) counts[J.variant]++;
     char buf[1024];
     int len = snprintf(buf, sizeof(buf),
-                       "batch: %u jobs (%u NTT on concurrent lanes, %u direct), %u tiles, graph=%s, tuned=%s, "
-                       "direct part predicted %.3f ms; variants",
-                       njobs, b->nntt, b->ndirect, b->ntiles, b->exec ? "yes" : "no",
+                       "batch: %u jobs (%u NTT and %u tensor-core on concurrent lanes, %u direct), %u tiles, graph=%s, "
+                       "tuned=%s, direct part predicted %.3f ms; variants",
+                       njobs, b->nntt, b->ntc, b->ndirect, b->ntiles, b->exec ? "yes" : "no",
                        (flags & EXTRACT_BATCH_NO_TUNE) ? "no" : "yes", b->predicted_ms);
     for (int v = 0; v < kNumVariants && len < (int)sizeof(buf) - 64; ++v)
         if (counts[v])
@@ -541,9 +566,10 @@ int extract_batch_run(extract_batch *b, void *stream, const uint32_t *const *in_
         }
     }
     cudaStream_t st = (cudaStream_t)stream;
-    // NTT jobs: forked onto the batch's own stream, one after another (they
-    // share one work buffer), concurrent with the persistent launch below
-    if (b->nntt) {
+    // NTT and tensor-core jobs: forked onto the batch's lanes (each lane's
+    // jobs one after another on its stream and work buffer), concurrent with
+    // the persistent launch below
+    if (b->nntt + b->ntc) {
         EX_CUDA(cudaEventRecord(b->ev_fork, st));
         for (NttLane &L : b->lanes)
             if (L.st) EX_CUDA(cudaStreamWaitEvent(L.st, b->ev_fork, 0));
@@ -553,7 +579,13 @@ int extract_batch_run(extract_batch *b, void *stream, const uint32_t *const *in_
             if (int rc = launch_gather(in_bits_dev[i], J.perm, J.m, J.s, J.w_pad, J.arev, L.st, b->num_sms, 0,
                                        (J.flags & EXTRACT_SAMPLING_IID) != 0, J.n))
                 return rc;
-            if (int rc = ntt_hash(J.ntt, J.arev, J.w_pad, J.m, J.s, J.k, out_bits_dev[i], L.st, L.work)) return rc;
+            if (J.tc) {
+                if (int rc = launch_hash_tc(J.seed, J.seed_stride, J.arev, J.w_pad, J.m, J.s, J.k, out_bits_dev[i],
+                                            b->d_err, L.st, kTcBatchChunk))
+                    return rc;
+            } else if (int rc = ntt_hash(J.ntt, J.arev, J.w_pad, J.m, J.s, J.k, out_bits_dev[i], L.st, L.work)) {
+                return rc;
+            }
         }
         for (NttLane &L : b->lanes)
             if (L.st) EX_CUDA(cudaEventRecord(L.join, L.st));
@@ -588,12 +620,28 @@ int extract_batch_run_sequential(extract_batch *b, void *stream, const uint32_t 
             return rc;
         if (J.ntt) {
             if (int rc = ntt_hash(J.ntt, J.arev, J.w_pad, J.m, J.s, J.k, out_bits_dev[i], st)) return rc;
+        } else if (J.tc) {
+            if (int rc = launch_hash_tc(J.seed, J.seed_stride, J.arev, J.w_pad, J.m, J.s, J.k, out_bits_dev[i],
+                                        b->d_err, st, kTcBatchChunk))
+                return rc;
         } else if (int rc = launch_hash(J.plain_plan, J.seed, J.nseeds > 1 ? J.seed_stride : 0u, J.arev, J.w_pad,
                                         J.m, J.k, out_bits_dev[i], st)) {
             return rc;
         }
     }
     return EXTRACT_OK;
+}
+
+int extract_batch_status(extract_batch *b)
+{
+    if (!b) return set_error(EXTRACT_EINVAL, "null batch");
+    if (!b->d_err) return EXTRACT_OK;
+    uint32_t v = 0;
+    EX_CUDA(cudaDeviceSynchronize());
+    EX_CUDA(cudaMemcpy(&v, b->d_err, 4, cudaMemcpyDeviceToHost));
+    if (!v) return EXTRACT_OK;
+    EX_CUDA(cudaMemset(b->d_err, 0, 4));
+    return set_error(EXTRACT_ETIMEDOUT, "a tensor-core hash kernel of the batch gave up waiting for its multiplies");
 }
 
 int extract_batch_describe(extract_batch *b, char *buf, uint32_t buflen)

@@ -34,6 +34,17 @@ double predict_direct_s(uint32_t m, uint32_t k, uint32_t s)
     return (double)m * k * ((s + 31) / 32) / 19e12;
 }
 
+// The tensor-core product pays for its padded tile: 128 rows x nt
+// sub-blocks x 128 K per stage.  About 0.7 PMAC/s measured with 256
+// sub-blocks per tile; narrower tiles spend relatively more on building the
+// Toeplitz operand.
+double predict_tc_s(uint32_t m, uint32_t k, uint32_t s)
+{
+    const double nt = tc_tile_n(m);
+    const double macs = (double)round_up(k, 128) * (double)round_up(m, (uint64_t)nt) * (double)round_up(s, 128);
+    return macs / (7e14 * (0.3 + 0.7 * nt / 256.0)) + 5e-6;
+}
+
 double predict_ntt_s(uint32_t m, uint32_t s, uint32_t k, int split_log2, bool per_block_seeds)
 {
     const NttShape sh = ntt_shape(s, k, split_log2, per_block_seeds);
@@ -65,6 +76,8 @@ struct extract_ctx {
     uint32_t *stage_out = nullptr;  // extract_run_host staging, ceil(m*k/32) words
     HashPlan plan;
     NttPlan *ntt = nullptr;  // set when the NTT method hashes this shape
+    bool tc = false;         // the tensor-core direct product hashes this shape
+    uint32_t *dev_err = nullptr;  // device error word of the tensor-core kernel (a wait that gave up)
     cudaStream_t aux = nullptr;                       // gather stream of the overlapped NTT run
     cudaEvent_t ev_fork = nullptr, ev_group = nullptr;
     NttLanes lanes;                                   // extra lanes of the NTT hash (own streams, buffers)
@@ -81,12 +94,20 @@ struct extract_ctx {
 namespace {
 
 // NTT hash lanes (launch groups dealt round robin over streams)
-constexpr uint32_t kNttLanes = 2;
+#ifndef EX_NTT_LANES
+#define EX_NTT_LANES 2
+#endif
+constexpr uint32_t kNttLanes = EX_NTT_LANES;
 static_assert(kNttLanes >= 1 && kNttLanes <= (uint32_t)kMaxNttLanes, "NTT lane count");
 
 constexpr uint32_t kKnownFlags = EXTRACT_SEED_PER_SUBBLOCK | EXTRACT_IDENTITY_PERM | EXTRACT_METHOD_DIRECT |
                                   EXTRACT_METHOD_NTT | EXTRACT_SAMPLING_IID | EXTRACT_GATHER_PLAIN |
-                                  EXTRACT_GATHER_BUCKETS | EXTRACT_GATHER_WIDE_CHUNKS | (0x3fu << 8) | (0x7u << 16);
+                                  EXTRACT_GATHER_BUCKETS | EXTRACT_GATHER_WIDE_CHUNKS | (0x3fu << 8) | (0x7u << 16) |
+                                  EXTRACT_METHOD_TENSOR | (0xfu << 24);
+
+// K blocks of 128 per accumulation chunk of the tensor-core product
+// (EXTRACT_TC_CHUNK(l): 2^l blocks; default 2^5 = 4096 K per chunk)
+constexpr uint32_t kTcChunkLog2Default = 5;
 
 // Smallest input that gets the bucketed gather by default
 constexpr uint64_t kBucketsMinBits = 1ull << 22;
@@ -97,6 +118,7 @@ void free_ctx(extract_ctx *h)
     cudaFree(h->perm);
     cudaFree(h->arev);
     cudaFree(h->seed);
+    cudaFree(h->dev_err);
     cudaFree(h->stage_in);
     cudaFree(h->stage_out);
     ntt_destroy(h->ntt);
@@ -225,8 +247,12 @@ int extract_create(extract_ctx **out, uint64_t n, uint32_t m, uint32_t s, uint32
         return set_error(EXTRACT_EINVAL, "m*s = %llu exceeds n = %llu",
                          (unsigned long long)((uint64_t)m * s), (unsigned long long)n);
     }
-    if ((flags & EXTRACT_METHOD_DIRECT) && (flags & EXTRACT_METHOD_NTT))
-        return set_error(EXTRACT_EINVAL, "EXTRACT_METHOD_DIRECT and EXTRACT_METHOD_NTT are exclusive");
+    if (((flags & EXTRACT_METHOD_DIRECT) != 0) + ((flags & EXTRACT_METHOD_NTT) != 0) +
+            ((flags & EXTRACT_METHOD_TENSOR) != 0) > 1)
+        return set_error(EXTRACT_EINVAL, "EXTRACT_METHOD_DIRECT, EXTRACT_METHOD_NTT and EXTRACT_METHOD_TENSOR are "
+                                         "exclusive");
+    if ((flags & EXTRACT_METHOD_TENSOR) && per_sub)
+        return set_error(EXTRACT_EINVAL, "EXTRACT_METHOD_TENSOR needs one shared seed");
     if ((flags & EXTRACT_GATHER_PLAIN) && (flags & (EXTRACT_GATHER_BUCKETS | EXTRACT_GATHER_WIDE_CHUNKS)))
         return set_error(EXTRACT_EINVAL, "EXTRACT_GATHER_PLAIN excludes EXTRACT_GATHER_BUCKETS and "
                                          "EXTRACT_GATHER_WIDE_CHUNKS");
@@ -240,9 +266,14 @@ int extract_create(extract_ctx **out, uint64_t n, uint32_t m, uint32_t s, uint32
         return set_error(EXTRACT_EINVAL,
                          "the NTT method needs s+k-1 > 2^11, s < 7*2^26+1 and a split with transform length "
                          "<= 2^22 (>= 2^16 with one seed per sub-block) (s=%u k=%u split=%d)", s, k, split);
-    const bool use_ntt = ntt_ok && !(flags & EXTRACT_METHOD_DIRECT) &&
-                         ((flags & EXTRACT_METHOD_NTT) ||
-                          predict_ntt_s(m, s, k, split, per_sub) < predict_direct_s(m, k, s));
+    // automatic choice: the least predicted time among the exact methods
+    // (the tensor-core product only with a shared seed)
+    const uint32_t forced = flags & (EXTRACT_METHOD_DIRECT | EXTRACT_METHOD_NTT | EXTRACT_METHOD_TENSOR);
+    const double t_direct = predict_direct_s(m, k, s);
+    const double t_ntt = ntt_ok ? predict_ntt_s(m, s, k, split, per_sub) : 1e30;
+    const double t_tc = per_sub ? 1e30 : predict_tc_s(m, k, s);
+    const bool use_ntt = forced ? (forced == EXTRACT_METHOD_NTT) : (t_ntt < t_direct && t_ntt <= t_tc);
+    const bool use_tc = forced ? (forced == EXTRACT_METHOD_TENSOR) : (!use_ntt && t_tc < t_direct);
 
     extract_ctx *h = new (std::nothrow) extract_ctx();
     if (!h) return set_error(EXTRACT_ENOMEM, "host allocation failed");
@@ -279,6 +310,13 @@ int extract_create(extract_ctx **out, uint64_t n, uint32_t m, uint32_t s, uint32
     if ((e = cudaMalloc(&h->seed, host.size() * 4)) != cudaSuccess) { free_ctx(h); return cuda_error(e, "cudaMalloc(seed)"); }
     if ((e = cudaMemcpy(h->seed, host.data(), host.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess) {
         free_ctx(h); return cuda_error(e, "copy seed");
+    }
+    if (use_tc) {
+        h->tc = true;
+        if ((e = cudaMalloc(&h->dev_err, 4)) != cudaSuccess || (e = cudaMemset(h->dev_err, 0, 4)) != cudaSuccess) {
+            free_ctx(h);
+            return cuda_error(e, "tensor-core error word");
+        }
     }
     if (use_ntt) {
         cudaStream_t st;
@@ -372,6 +410,11 @@ int extract_hash(extract_ctx *h, void *stream, uint32_t *out_bits_dev)
     if (h->ntt)
         return ntt_hash(h->ntt, h->arev, h->w_pad, h->m, h->s, h->k, out_bits_dev, (cudaStream_t)stream, nullptr,
                         &h->lanes);
+    if (h->tc) {
+        const uint32_t cl = (h->flags >> 24) & 0xfu;
+        return launch_hash_tc(h->seed, h->seed_stride, h->arev, h->w_pad, h->m, h->s, h->k, out_bits_dev, h->dev_err,
+                              (cudaStream_t)stream, 1u << (cl ? cl - 1 : kTcChunkLog2Default));
+    }
     return launch_hash(h->plan, h->seed, h->nseeds > 1 ? h->seed_stride : 0u, h->arev, h->w_pad, h->m,
                        h->k, out_bits_dev, (cudaStream_t)stream);
 }
@@ -510,12 +553,32 @@ int extract_describe(extract_ctx *h, char *buf, uint32_t buflen)
                  h->num_sms, gather);
         return EXTRACT_OK;
     }
+    if (h->tc) {
+        const uint32_t cl = (h->flags >> 24) & 0xfu;
+        snprintf(buf, buflen,
+                 "tensor: tcgen05.mma kind::f8f6f4 e4m3 0/1 operands, f32 accumulator, tiles of 128 rows x %u "
+                 "sub-blocks, K chunk %u; sms=%d; %s",
+                 tc_tile_n(h->m), 128u << (cl ? cl - 1 : kTcChunkLog2Default), h->num_sms, gather);
+        return EXTRACT_OK;
+    }
     snprintf(buf, buflen,
              "lop3 tile: rows=%u (q=%d x %d warps x 32) subblocks=%d words/chunk=%d grid=%ux%ux%u "
              "(row tiles %u, sub-block tiles %u, split-K %u x %u chunks) w_pad=%u sms=%d; %s",
              p.rows(), p.q, p.warps, p.j, p.wc, p.gx * p.gy, 1u, p.splits, p.gx, p.gy, p.splits, p.cps,
              h->w_pad, h->num_sms, gather);
     return EXTRACT_OK;
+}
+
+int extract_status(extract_ctx *h)
+{
+    if (int rc = check_ctx(h)) return rc;
+    if (!h->dev_err) return EXTRACT_OK;
+    uint32_t v = 0;
+    EX_CUDA(cudaDeviceSynchronize());
+    EX_CUDA(cudaMemcpy(&v, h->dev_err, 4, cudaMemcpyDeviceToHost));
+    if (!v) return EXTRACT_OK;
+    EX_CUDA(cudaMemset(h->dev_err, 0, 4));
+    return set_error(EXTRACT_ETIMEDOUT, "a tensor-core hash kernel gave up waiting for its multiplies");
 }
 
 int extract_gather_bytes(extract_ctx *h, uint64_t *bytes)

@@ -137,6 +137,15 @@ int launch_hash(const HashPlan &p, const uint32_t *seed, uint32_t seed_stride,
                 const uint32_t *arev, uint32_t w_pad, uint32_t m, uint32_t k,
                 uint32_t *out, cudaStream_t st);
 
+// The direct product on the tensor cores (tc_hash.cu): one shared seed of
+// seed_words realigned words; out is zeroed on st and receives every K_j;
+// err is set to 1 when a kernel wait gave up.  chunk_blocks: K blocks of 128
+// summed before each parity read-back.
+int launch_hash_tc(const uint32_t *seed, uint64_t seed_words, const uint32_t *arev, uint32_t w_pad, uint32_t m,
+                   uint32_t s, uint32_t k, uint32_t *out, uint32_t *err, cudaStream_t st, uint32_t chunk_blocks);
+// Sub-blocks per tile of the tensor-core product for m sub-blocks.
+uint32_t tc_tile_n(uint32_t m);
+
 // The plain per-block path: one launch per sub-block, one thread per row.
 int launch_hash_plain(const uint32_t *seed, uint32_t seed_stride, const uint32_t *arev,
                       uint32_t w_pad, uint32_t s, uint32_t m, uint32_t k, uint32_t *out,
@@ -208,7 +217,7 @@ bool ntt_spectra_resident(const NttPlan *p);
 // Extra streams and work buffers for ntt_hash: launch group i runs on lane
 // i mod (1 + n) (lane 0 = the caller's stream and buffer), so one group's
 // passes fill the others' last waves.  Events owned by the caller.
-constexpr int kMaxNttLanes = 4;
+constexpr int kMaxNttLanes = 8;
 struct NttLanes {
     int n = 0;  // extra lanes (0 .. kMaxNttLanes - 1)
     cudaStream_t st[kMaxNttLanes - 1] = {};
@@ -251,6 +260,7 @@ uint64_t ntt_plan_bytes(uint32_t s, uint32_t k, int split_log2 = -1, bool per_bl
 // element and stage).
 double predict_direct_s(uint32_t m, uint32_t k, uint32_t s);
 double predict_ntt_s(uint32_t m, uint32_t s, uint32_t k, int split_log2 = -1, bool per_block_seeds = false);
+double predict_tc_s(uint32_t m, uint32_t k, uint32_t s);
 uint32_t ntt_group(const NttPlan *p);
 uint32_t ntt_size(const NttPlan *p);
 uint32_t ntt_pieces(const NttPlan *p);

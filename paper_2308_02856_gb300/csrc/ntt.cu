@@ -60,8 +60,11 @@ constexpr int kRowsB = 2;             // rows per pass-B CTA
 constexpr int kThreads = 256;
 constexpr int kMaxSplitLog2 = 4;      // at most 16 pieces per sub-block
 constexpr uint64_t kMaxWorkWords = 16ull << 20;    // one sub-block's pieces (and windows), <= 64 MB
-constexpr uint64_t kGroupWorkWords = 32ull << 20;  // one launch group's buffer, <= 128 MB (16 sub-blocks
-                                                   // of the QRNG shape: 70.1 against 69.8 Gbit/s with 8)
+#ifndef EX_NTT_GROUP_WORDS
+#define EX_NTT_GROUP_WORDS (32ull << 20)
+#endif
+constexpr uint64_t kGroupWorkWords = EX_NTT_GROUP_WORDS;  // one launch group's buffer, <= 128 MB (16 sub-blocks
+                                                          // of the QRNG shape: 70.1 against 69.8 Gbit/s with 8)
 
 // -p^{-1} mod 2^32 by Newton iteration
 constexpr uint32_t neg_inv32(uint32_t p)
@@ -768,17 +771,30 @@ __device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane)
 // stages pair registers of one column; the swizzled transpose then gives
 // lane l the 32 consecutive elements 32 (l % E) .. 32 (l % E) + 31 of column
 // l / E (layout B), where the distance < 32 stages run: no shuffles.  A CTA
-// of 16 warps covers CW = 16 COLS adjacent columns; its R1 x CW tile sits in
+// of NW warps covers CW = NW COLS adjacent columns; its R1 x CW tile sits in
 // shared memory row-major, the column of row r XOR-ed with COLS (r / 32) so
 // that both the per-lane column writes and the row-wise copies are
 // conflict-free.
-constexpr uint32_t kTileWords = 16384;  // R1 x CW = 32 E x 16 (32 / E)
-size_t smem_multi() { return (size_t)(kTileWords + 1024) * 4; }
+#ifndef EX_COLS_WARPS
+#define EX_COLS_WARPS 8
+#endif
+// Warps per CTA of the multi-column kernels for R1 = 32 E: EX_COLS_WARPS
+// (8 or 16) where E allows it (the row swizzle needs COLS (E - 1) < CW, so
+// at least E warps), else 16.  The R1 x CW tile is 1024 words per warp.
+// Eight warps let four CTAs share an SM instead of two, so one CTA's loads
+// and stores overlap another's butterflies: the 2^32-bit block's hash takes
+// 38.4 instead of 40.3 ms (no change on the 2^30-bit block, E = 16).
+template <int E>
+__host__ __device__ constexpr uint32_t col_warps() { return (EX_COLS_WARPS >= E) ? EX_COLS_WARPS : 16; }
+template <int E>
+constexpr uint32_t tile_words() { return col_warps<E>() * 1024u; }
+template <int E>
+size_t smem_multi() { return (size_t)(tile_words<E>() + 1024) * 4; }
 
 template <int E>
 __device__ __forceinline__ uint32_t tile_at(uint32_t r, uint32_t c)
 {
-    constexpr uint32_t COLS = 32u / E, CW = 16u * COLS;
+    constexpr uint32_t COLS = 32u / E, CW = col_warps<E>() * COLS;
     return r * CW + (c ^ (COLS * (r >> 5)));
 }
 
@@ -820,14 +836,14 @@ __device__ __forceinline__ void stage_row_words(uint32_t *rb, const uint32_t *__
 // Pass A: bits -> DIF along t1 -> twist -> buf, for CW columns per CTA.
 // kZeroTop: pieces of at most N / 2 coefficients (rows t1 >= R1 / 2 zero).
 template <int E, bool kReversed, bool kZeroTop>
-__global__ void __launch_bounds__(512, 2)
+__global__ void __launch_bounds__(col_warps<E>() * 32, 32 / col_warps<E>())
 ntt_cols_fwd_m_kernel(const uint32_t *__restrict__ bits, Pieces pc, uint32_t N, Tables T, uint32_t *__restrict__ buf)
 {
-    constexpr uint32_t COLS = 32u / E, R1 = 32u * E, CW = 16u * COLS, WPR = CW / 32;
+    constexpr uint32_t COLS = 32u / E, R1 = 32u * E, CW = col_warps<E>() * COLS, WPR = CW / 32;
     extern __shared__ uint32_t xs[];  // tile (and warp scratch), then R1 * WPR staged bit words
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const uint32_t g = blockIdx.y, c0 = blockIdx.x * CW;
-    uint32_t *rb = xs + kTileWords;
+    uint32_t *rb = xs + tile_words<E>();
     uint32_t lim;
     const uint32_t *b = piece_src(bits, pc, g, lim);
     stage_row_words<kReversed, WPR>(rb, b, pc.len, lim, R1, c0);
@@ -869,15 +885,15 @@ ntt_cols_fwd_m_kernel(const uint32_t *__restrict__ bits, Pieces pc, uint32_t N, 
 // (through shared memory), and each warp turns one 32 x 32 block of them
 // into row words of 32 adjacent columns with a shuffle transpose.
 template <int E>
-__global__ void __launch_bounds__(512, 2)
+__global__ void __launch_bounds__(col_warps<E>() * 32, 32 / col_warps<E>())
 ntt_cols_inv_m_kernel(const uint32_t *__restrict__ buf, uint64_t sub_stride, Tables T, uint32_t j0, uint32_t len,
                       uint32_t k, uint32_t *__restrict__ out)
 {
-    constexpr uint32_t COLS = 32u / E, R1 = 32u * E, CW = 16u * COLS, WPR = CW / 32;
+    constexpr uint32_t COLS = 32u / E, R1 = 32u * E, CW = col_warps<E>() * COLS, WPR = CW / 32;
     extern __shared__ uint32_t xs[];  // tile (and warp scratch), then CW x (E + 1) column words
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const uint32_t g = blockIdx.y, c0 = blockIdx.x * CW;
-    uint32_t *colw = xs + kTileWords;
+    uint32_t *colw = xs + tile_words<E>();
     const uint32_t *in = buf + (size_t)g * sub_stride;
     for (uint32_t it = threadIdx.x; it < R1 * CW / 2; it += blockDim.x) {
         const uint32_t r = it / (CW / 2), c = 2u * (it % (CW / 2));
@@ -911,7 +927,7 @@ ntt_cols_inv_m_kernel(const uint32_t *__restrict__ buf, uint64_t sub_stride, Tab
     }
     colw[(w * COLS + lane / E) * (E + 1) + lane % E] = mine;  // column, 32-row block
     __syncthreads();
-    // one 32 x 32 bit block per warp (E * CW / 32 = 16 blocks): rows
+    // one 32 x 32 bit block per warp (E * CW / 32 = one per warp): rows
     // 32 b .. 32 b + 31 of columns 32 wi .. 32 wi + 31
     const uint32_t b = w % E, wi = w / E;
     uint32_t x = colw[(32u * wi + lane) * (E + 1) + b];  // lane c: column 32 wi + c
@@ -966,7 +982,7 @@ struct NttPlan {
 namespace {
 
 // dynamic shared memory of the column kernels (+ R1 words of staged row
-// bits); 32 <= R1 < 1024 kernels take smem_multi()
+// bits); 32 <= R1 < 1024 kernels take smem_multi<E>()
 size_t smem_generic(uint32_t R1) { return (size_t)R1 * (kCS + 1) * 4; }         // R1 < 32 kernels
 size_t smem_transposed(uint32_t R1) { return ((size_t)kCW * (R1 + 1) + R1) * 4; }  // R1 >= 1024 kernels
 
@@ -987,13 +1003,15 @@ int ntt_launch_a(const NttPlan *p, const uint32_t *bits, const Pieces &pc, bool 
     const int epl = (int)(R1 / 32);
 #define EX_COLS_FWD_M(E)                                                                                     \
     if (epl == E) {                                                                                          \
-        const dim3 gm(kR2 / (512 / E), g * pc.P);                                                            \
+        constexpr uint32_t nt = col_warps<E>() * 32;                                                        \
+        const dim3 gm(kR2 / (nt / E), g * pc.P);                                                             \
+        const size_t sm = smem_multi<E>();                                                                   \
         if (2ull * pc.len <= p->N) {                                                                         \
-            if (reversed) ntt_cols_fwd_m_kernel<E, true, true><<<gm, 512, smem_multi(), st>>>(bits, pc, p->N, p->T, dst); \
-            else ntt_cols_fwd_m_kernel<E, false, true><<<gm, 512, smem_multi(), st>>>(bits, pc, p->N, p->T, dst); \
+            if (reversed) ntt_cols_fwd_m_kernel<E, true, true><<<gm, nt, sm, st>>>(bits, pc, p->N, p->T, dst); \
+            else ntt_cols_fwd_m_kernel<E, false, true><<<gm, nt, sm, st>>>(bits, pc, p->N, p->T, dst);       \
         } else {                                                                                             \
-            if (reversed) ntt_cols_fwd_m_kernel<E, true, false><<<gm, 512, smem_multi(), st>>>(bits, pc, p->N, p->T, dst); \
-            else ntt_cols_fwd_m_kernel<E, false, false><<<gm, 512, smem_multi(), st>>>(bits, pc, p->N, p->T, dst); \
+            if (reversed) ntt_cols_fwd_m_kernel<E, true, false><<<gm, nt, sm, st>>>(bits, pc, p->N, p->T, dst); \
+            else ntt_cols_fwd_m_kernel<E, false, false><<<gm, nt, sm, st>>>(bits, pc, p->N, p->T, dst);      \
         }                                                                                                    \
         return EXTRACT_OK;                                                                                   \
     }
@@ -1044,8 +1062,9 @@ int ntt_launch_a_inv(const NttPlan *p, const uint32_t *buf, uint32_t g, uint32_t
     const int epl = (int)(R1 / 32);
 #define EX_COLS_INV_M(E)                                                                                 \
     if (epl == E) {                                                                                      \
-        const dim3 gm(kR2 / (512 / E), g);                                                               \
-        ntt_cols_inv_m_kernel<E><<<gm, 512, smem_multi(), st>>>(buf, sub, p->T, j0, p->h, k, out);       \
+        constexpr uint32_t nt = col_warps<E>() * 32;                                                    \
+        const dim3 gm(kR2 / (nt / E), g);                                                                \
+        ntt_cols_inv_m_kernel<E><<<gm, nt, smem_multi<E>(), st>>>(buf, sub, p->T, j0, p->h, k, out);     \
         return EXTRACT_OK;                                                                               \
     }
 #define EX_COLS_INV(E, K, SMEM)                                                          \
@@ -1067,23 +1086,24 @@ int ntt_launch_a_inv(const NttPlan *p, const uint32_t *buf, uint32_t g, uint32_t
 
 }  // namespace
 
-// Split of a sub-block into P = 2^l pieces of h coefficients (h a multiple
-// of 32 when P > 1, so pieces start on word boundaries): each piece is its
-// own middle product with seed window q h .. q h + h + k - 2, and the P
-// products add up in the frequency domain, so one inverse transform serves
-// them all.  Length N = 2^e >= h + k - 1 (2^12 .. 2^22); work (P + 1)
-// transforms of N instead of 2 of the length for s + k - 1.
+// Split of a sub-block into P pieces (1 <= P <= 16) of h coefficients (h a
+// multiple of 32 when P > 1, so pieces start on word boundaries): each piece
+// is its own middle product with seed window q h .. q h + h + k - 2, and the
+// P products add up in the frequency domain, so one inverse transform serves
+// them all.  Length N = 2^e >= h + k - 1 (2^12 .. 2^22); work P + 1
+// transforms of N instead of 2 of the length for s + k - 1.  P need not be a
+// power of two: with k = 0.1 s, seven pieces fit N = 2^18 as eight do (8
+// transforms instead of 9).  split_log2 >= 0 forces P = 2^split_log2.
 NttShape ntt_shape(uint32_t s, uint32_t k, int split_log2, bool per_block_seeds)
 {
     NttShape best{};
     if ((uint64_t)s + k - 1 <= kR2 || s >= kP) return best;
     const uint32_t bufs = per_block_seeds ? 2u : 1u;  // data pieces (+ seed windows)
     double best_cost = 0;
-    for (int l = 0; l <= kMaxSplitLog2; ++l) {
-        if (split_log2 >= 0 && l != split_log2) continue;
-        const uint32_t P = 1u << l;
+    for (uint32_t P = 1; P <= (1u << kMaxSplitLog2); ++P) {
+        if (split_log2 >= 0 && P != (1u << split_log2)) continue;
         const uint64_t h = P == 1 ? s : (((uint64_t)s + P - 1) / P + 31) / 32 * 32;
-        if ((uint64_t)(P - 1) * h >= s) break;  // the last piece would be empty
+        if ((uint64_t)(P - 1) * h >= s) continue;  // the last piece would be empty
         uint64_t N = 2 * kR2;
         while (N < h + k - 1) N <<= 1;
         if (N > (1ull << 22) || bufs * P * N > kMaxWorkWords) continue;
@@ -1186,11 +1206,11 @@ static int device_setup(cudaStream_t st)
     attr((const void *)KF<E, false>, SMEM); \
     attr((const void *)KI<E>, SMEM);
 #define EX_SET_SMEM_M(E)                                                            \
-    attr((const void *)ntt_cols_fwd_m_kernel<E, true, true>, smem_multi());    \
-    attr((const void *)ntt_cols_fwd_m_kernel<E, false, true>, smem_multi());   \
-    attr((const void *)ntt_cols_fwd_m_kernel<E, true, false>, smem_multi());   \
-    attr((const void *)ntt_cols_fwd_m_kernel<E, false, false>, smem_multi());  \
-    attr((const void *)ntt_cols_inv_m_kernel<E>, smem_multi());
+    attr((const void *)ntt_cols_fwd_m_kernel<E, true, true>, smem_multi<E>());    \
+    attr((const void *)ntt_cols_fwd_m_kernel<E, false, true>, smem_multi<E>());   \
+    attr((const void *)ntt_cols_fwd_m_kernel<E, true, false>, smem_multi<E>());   \
+    attr((const void *)ntt_cols_fwd_m_kernel<E, false, false>, smem_multi<E>());  \
+    attr((const void *)ntt_cols_inv_m_kernel<E>, smem_multi<E>());
     EX_SET_SMEM_M(1)
     EX_SET_SMEM_M(2)
     EX_SET_SMEM_M(4)

@@ -44,6 +44,7 @@ enum JobState { kQueued, kAdmitted, kSetupLaunched, kReady, kDone, kFailed };
 
 constexpr int kWaveSlots = 2;
 constexpr int kNttLanes = 2;
+constexpr uint32_t kTcServeChunk = 32;  // K blocks of 128 per parity read-back of the tensor-core product
 constexpr uint32_t kMaxWaveTiles = 1u << 16;
 
 struct SJob {
@@ -64,8 +65,9 @@ struct SJob {
     JobState state = kQueued;
     int rc = EXTRACT_OK;
     cudaEvent_t setup_ev = nullptr;
-    // NTT method: hashed whole on the NTT lane
-    bool use_ntt = false, hashed = false;
+    // NTT method or tensor-core product: hashed whole on a lane
+    bool use_ntt = false, use_tc = false, hashed = false;
+    bool on_lane() const { return use_ntt || use_tc; }
     NttPlan *ntt = nullptr;
     cudaEvent_t done_ev = nullptr;
     Clock::time_point t_submit, t_done;
@@ -142,9 +144,10 @@ struct extract_server {
     uint64_t next_ticket = 1;
     cudaStream_t setup_st = nullptr;
     Wave waves[kWaveSlots];
-    // NTT lanes: one job at a time each (own stream and work buffer),
-    // concurrent with the waves and with each other
+    // lanes: one NTT or tensor-core job at a time each (own stream and NTT
+    // work buffer), concurrent with the waves and with each other
     NttLane lanes[kNttLanes];
+    uint32_t *d_err = nullptr;  // error word of the tensor-core kernels
     std::thread sched_thread, setup_thread;
     // statistics
     uint64_t submitted = 0, admitted = 0, completed = 0, failed = 0, rejected = 0, nwaves = 0;
@@ -282,14 +285,21 @@ bool schedule_step(extract_server *S)
             else if (e != cudaErrorNotReady) { j->rc = cuda_error(e, "setup"); j->state = kFailed; }
         }
         bool finished;
-        if (j->use_ntt) {
+        if (j->on_lane()) {
             finished = false;
             if (j->state == kReady && j->hashed) {
                 const cudaError_t e = cudaEventQuery(j->done_ev);
                 if (e == cudaSuccess) {
                     finished = true;
+                    uint32_t err = 0;  // a tensor-core kernel that gave up on a wait fails its job
+                    if (j->use_tc && cudaMemcpy(&err, S->d_err, 4, cudaMemcpyDeviceToHost) == cudaSuccess && err) {
+                        cudaMemset(S->d_err, 0, 4);
+                        j->rc = set_error(EXTRACT_ETIMEDOUT, "a tensor-core hash kernel gave up waiting");
+                        j->state = kFailed;
+                        finished = false;
+                    }
                 } else if (e != cudaErrorNotReady) {
-                    j->rc = cuda_error(e, "ntt job");
+                    j->rc = cuda_error(e, "lane job");
                     j->state = kFailed;
                 }
             }
@@ -319,17 +329,20 @@ bool schedule_step(extract_server *S)
         }
         ++i;
     }
-    // 4. each free NTT lane takes the ready NTT job with the least predicted time
+    // 4. each free lane takes the ready lane job with the least predicted time
     for (NttLane &L : S->lanes) {
         if (L.cur) continue;
         JobPtr best;
         for (JobPtr &j : S->active)
-            if (j->use_ntt && j->state == kReady && !j->hashed && (!best || j->remaining_ns < best->remaining_ns))
+            if (j->on_lane() && j->state == kReady && !j->hashed && (!best || j->remaining_ns < best->remaining_ns))
                 best = j;
         if (!best) break;
-        int rc = ntt_hash(best->ntt, best->arev, best->w_pad, best->m, best->s, best->k, best->out, L.st, L.work);
+        int rc = best->use_tc
+                     ? launch_hash_tc(best->seed, best->stride, best->arev, best->w_pad, best->m, best->s, best->k,
+                                      best->out, S->d_err, L.st, kTcServeChunk)
+                     : ntt_hash(best->ntt, best->arev, best->w_pad, best->m, best->s, best->k, best->out, L.st, L.work);
         cudaError_t e = rc == EXTRACT_OK ? cudaEventRecord(best->done_ev, L.st) : cudaSuccess;
-        if (rc == EXTRACT_OK && e != cudaSuccess) rc = cuda_error(e, "ntt event");
+        if (rc == EXTRACT_OK && e != cudaSuccess) rc = cuda_error(e, "lane event");
         best->hashed = true;
         if (rc != EXTRACT_OK) {
             best->rc = rc;
@@ -428,6 +441,7 @@ void destroy_server(extract_server *S)
         if (L.st) cudaStreamDestroy(L.st);
         cudaFree(L.work);
     }
+    cudaFree(S->d_err);
     for (auto &kv : S->by_ticket) {
         if (kv.second->setup_ev) cudaEventDestroy(kv.second->setup_ev);
         if (kv.second->done_ev) cudaEventDestroy(kv.second->done_ev);
@@ -465,6 +479,10 @@ int extract_server_create(extract_server **out, uint64_t hbm_budget_bytes, uint3
             if ((e = cudaMalloc(&L.work, ntt_max_work_words() * 4)) != cudaSuccess) { rc = cuda_error(e, "ntt work"); break; }
         }
         if (rc != EXTRACT_OK) break;
+        if ((e = cudaMalloc(&S->d_err, 4)) != cudaSuccess || (e = cudaMemset(S->d_err, 0, 4)) != cudaSuccess) {
+            rc = cuda_error(e, "tensor-core error word");
+            break;
+        }
         for (Wave &w : S->waves) {
             if ((e = cudaStreamCreateWithFlags(&w.st, cudaStreamNonBlocking)) != cudaSuccess) { rc = cuda_error(e, "stream"); break; }
             if ((e = cudaEventCreateWithFlags(&w.ev, cudaEventDisableTiming)) != cudaSuccess) { rc = cuda_error(e, "event"); break; }
@@ -503,9 +521,15 @@ int extract_server_submit(extract_server *S, const extract_job_desc *d, const ui
         const double tiles = (double)ceil_div(d->k, variant_rows((int)j->variant)) *
                              (double)ceil_div(d->m, (uint32_t)variant_j((int)j->variant));
         const double direct_ns = tiles * (j->w_pad / kWordChunk) * S->costs[j->variant];
-        const double ntt_ns = predict_ntt_s(d->m, d->s, d->k, -1, per_sub) * 1e9;
-        j->use_ntt = ntt_shape(d->s, d->k, -1, per_sub).N != 0 && ntt_ns < direct_ns;
+        // the least predicted time of the three methods (the tensor-core
+        // product only with a shared seed)
+        const double ntt_ns = ntt_shape(d->s, d->k, -1, per_sub).N != 0
+                                  ? predict_ntt_s(d->m, d->s, d->k, -1, per_sub) * 1e9 : 1e300;
+        const double tc_ns = per_sub ? 1e300 : predict_tc_s(d->m, d->k, d->s) * 1e9;
+        j->use_ntt = ntt_ns < direct_ns && ntt_ns <= tc_ns;
+        j->use_tc = !j->use_ntt && tc_ns < direct_ns;
         if (j->use_ntt) j->remaining_ns = ntt_ns;
+        if (j->use_tc) j->remaining_ns = tc_ns;
     }
     HashPlan vp;
     vp.q = variant_q(j->variant);
@@ -533,7 +557,7 @@ int extract_server_submit(extract_server *S, const extract_job_desc *d, const ui
     const uint32_t cps = (uint32_t)std::max<double>(1.0, std::min<double>(nchunks,
                                                         S->tile_cap_sm_ns / (ns_chunk * S->sms)));
     const uint32_t gx = (uint32_t)ceil_div(d->k, rows), gy = (uint32_t)ceil_div(d->m, J);
-    for (uint32_t by = 0; by < gy && !j->use_ntt; ++by)
+    for (uint32_t by = 0; by < gy && !j->on_lane(); ++by)
         for (uint32_t bx = 0; bx < gx; ++bx)
             for (uint32_t c = 0; c < nchunks; c += cps) {
                 const uint32_t ce = std::min(nchunks, c + cps);

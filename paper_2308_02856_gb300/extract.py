@@ -33,11 +33,17 @@ EXTRACT_SAMPLING_IID = 0x10
 EXTRACT_GATHER_PLAIN = 0x20
 EXTRACT_GATHER_BUCKETS = 0x40
 EXTRACT_GATHER_WIDE_CHUNKS = 0x80
+EXTRACT_METHOD_TENSOR = 0x100000
 NO_POS = 0xFFFFFFFF  # padding slot of the i.i.d. law's order
 
 
 def EXTRACT_KEY_BITS(b: int) -> int:
     return (int(b) & 0x3F) << 8
+
+
+def EXTRACT_TC_CHUNK(l: int) -> int:
+    """Tensor-core method: 2^l K blocks of 128 per parity read-back (l = 0 .. 14)."""
+    return ((int(l) + 1) & 0xF) << 24
 
 
 def EXTRACT_NTT_SPLIT(l: int) -> int:
@@ -49,9 +55,10 @@ def EXTRACT_NTT_SPLIT(l: int) -> int:
 EXPORTED = [
     "extract_create", "extract_run", "extract_run_host", "extract_gather", "extract_hash", "extract_run_plain",
     "extract_read_perm", "extract_read_subblock", "extract_describe", "extract_destroy",
-    "extract_subblock_sizes", "extract_block_limit", "extract_gather_bytes",
+    "extract_subblock_sizes", "extract_block_limit", "extract_gather_bytes", "extract_status",
     "extract_last_error", "extract_run_static",
     "extract_batch_create", "extract_batch_run", "extract_batch_run_sequential", "extract_batch_describe",
+    "extract_batch_status",
     "extract_batch_destroy",
     "extract_server_create", "extract_server_submit", "extract_server_wait", "extract_server_stats",
     "extract_server_destroy",
@@ -60,6 +67,7 @@ EXPORTED = [
 EXTRACT_BATCH_NO_GRAPH = 0x1
 EXTRACT_BATCH_NO_TUNE = 0x2
 EXTRACT_BATCH_DIRECT_ONLY = 0x4
+EXTRACT_BATCH_TENSOR = 0x8
 
 
 class extract_job_desc(ctypes.Structure):
@@ -109,12 +117,14 @@ def load() -> ctypes.CDLL:
     L.extract_block_limit.argtypes = [u64, u32, ctypes.c_double, ctypes.c_double, ctypes.POINTER(u64)]
     L.extract_describe.argtypes = [vp, ctypes.c_char_p, u32]
     L.extract_gather_bytes.argtypes = [vp, ctypes.POINTER(u64)]
+    L.extract_status.argtypes = [vp]
     L.extract_destroy.argtypes = [vp]
     L.extract_run_static.argtypes = [u64, u32, u32, u32, vp, vp, vp, vp, vp]
     L.extract_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(extract_job_desc), u32, u32]
     L.extract_batch_run.argtypes = [vp, vp, vp, vp]
     L.extract_batch_run_sequential.argtypes = [vp, vp, vp, vp]
     L.extract_batch_describe.argtypes = [vp, ctypes.c_char_p, u32]
+    L.extract_batch_status.argtypes = [vp]
     L.extract_batch_destroy.argtypes = [vp]
     L.extract_server_create.argtypes = [ctypes.POINTER(vp), u64, u32, u32, u32]
     L.extract_server_submit.argtypes = [vp, ctypes.POINTER(extract_job_desc), vp, vp, ctypes.POINTER(u64)]
@@ -228,6 +238,12 @@ def extract_describe(h) -> str:
     return buf.value.decode()
 
 
+def extract_status(h) -> None:
+    """Raises ExtractError(EXTRACT_ETIMEDOUT) when a kernel of the context gave
+    up on a bounded wait since the last call."""
+    _check(load().extract_status(h))
+
+
 def extract_gather_bytes(h) -> int:
     v = ctypes.c_uint64(0)
     _check(load().extract_gather_bytes(h, ctypes.byref(v)))
@@ -284,6 +300,11 @@ class Batch:
         buf = ctypes.create_string_buffer(1024)
         _check(load().extract_batch_describe(self.h, buf, 1024))
         return buf.value.decode()
+
+    def status(self) -> None:
+        """Raises ExtractError(EXTRACT_ETIMEDOUT) when a tensor-core kernel of
+        the batch gave up on a bounded wait since the last call."""
+        _check(load().extract_batch_status(self.h))
 
     def close(self):
         if self.h:
@@ -408,6 +429,9 @@ class Extractor:
 
     def describe(self) -> str:
         return extract_describe(self.h)
+
+    def status(self) -> None:
+        extract_status(self.h)
 
     def gather_bytes(self) -> int:
         """Device-memory bytes one gather of this context reads and writes by design."""

@@ -89,7 +89,7 @@ def test_create_rejects_null_and_unknown_flags(lib):
     h = ctypes.c_void_p()
     assert lib.extract_create(ctypes.byref(h), 64, 1, 64, 8, None, 1, 0) == X.EXTRACT_EINVAL
     seed = np.zeros(8, dtype=np.uint32)
-    assert lib.extract_create(ctypes.byref(h), 64, 1, 64, 8, seed.ctypes.data, 1, 0x100000) == X.EXTRACT_EINVAL
+    assert lib.extract_create(ctypes.byref(h), 64, 1, 64, 8, seed.ctypes.data, 1, 0x200000) == X.EXTRACT_EINVAL
     assert lib.extract_create(None, 64, 1, 64, 8, seed.ctypes.data, 1, 0) == X.EXTRACT_EINVAL
 
 

@@ -75,14 +75,19 @@ def _outs(jobs, fill=-1):
 
 
 @pytest.mark.parametrize("flags", [0, X.EXTRACT_BATCH_NO_GRAPH, X.EXTRACT_BATCH_NO_TUNE,
-                                   X.EXTRACT_BATCH_NO_GRAPH | X.EXTRACT_BATCH_NO_TUNE])
+                                   X.EXTRACT_BATCH_NO_GRAPH | X.EXTRACT_BATCH_NO_TUNE, X.EXTRACT_BATCH_TENSOR])
 def test_batch_matches_oracle(flags):
+    """Every job against the oracle, batched and one launch sequence per
+    block; with EXTRACT_BATCH_TENSOR every shared-seed job goes to the
+    tensor-core product on the lanes."""
     jobs, ins = _small_jobs()
     want = [oracle.extract(j["n"], j["m"], j["s"], j["k"], w, j["seed"], j["key"], j["flags"])
             for j, w in zip(jobs, ins)]
     d_in = [_dev(w) for w in ins]
     with X.Batch(jobs, flags) as b:
         assert "jobs" in b.describe()
+        if flags & X.EXTRACT_BATCH_TENSOR:
+            assert "11 tensor-core" in b.describe(), b.describe()
         outs = _outs(jobs)
         b.run(d_in, outs)
         torch.cuda.synchronize()
@@ -93,6 +98,7 @@ def test_batch_matches_oracle(flags):
         torch.cuda.synchronize()
         for i, (o, w) in enumerate(zip(seq, want)):
             assert np.array_equal(_host(o), w), "sequential job %d" % i
+        b.status()
 
 
 def test_batch_reruns_with_new_buffers():

@@ -31,22 +31,27 @@ def _lib():
     X.load()
 
 
-def _group_blocks(G, groups, extra):
+def _group_blocks(G, m, groups, extra):
     """First and last sub-block of each launch group in ``groups`` (groups of
-    G sub-blocks alternate between two lanes), plus ``extra``."""
-    blocks = [G * g + r for g in groups for r in (0, G - 1)] + list(extra)
-    lanes = {g % 2 for g in groups}
-    assert lanes == {0, 1}
+    G sub-blocks alternate between two lanes; negative indices count from
+    the last group), plus ``extra``."""
+    ng = (m + G - 1) // G
+    groups = sorted({g % ng for g in groups})
+    assert {g % 2 for g in groups} == {0, 1}
+    blocks = [min(m - 1, G * g + r) for g in groups for r in (0, G - 1)] + [j for j in extra if j < m]
     return sorted(set(blocks))
 
 
-def _full_size_case(n, m, s, k, p, blocks, plan_has):
+def _full_size_case(n, m, s, k, p, groups, extra, plan_has, nblocks):
     in_w = synth.bernoulli_bits(n, p, 1)
     seed = synth.uniform_bits(s + k - 1, 3)
     with X.Extractor(n, m, s, k, seed, 2) as ex:
         plan = ex.describe()
         for frag in plan_has:
             assert frag in plan, plan
+        G = int(plan.split(" sub-blocks per launch group")[0].split(",")[-1])
+        blocks = _group_blocks(G, m, groups, extra)
+        assert len(blocks) >= nblocks, blocks
         d_in = torch.from_numpy(in_w.view(np.int32)).cuda()
         out = ex.run(d_in)
         got = oracle.bits_of(out.cpu().numpy().view(np.uint32), m * k)
@@ -69,20 +74,17 @@ def _full_size_case(n, m, s, k, p, blocks, plan_has):
 
 def test_qrng_shaped_block_n2e30():
     """n = 2^30 Bernoulli(0.6), m = 1024 sub-blocks of s = 2^20, k = 2^19:
-    P = 2 pieces, N = 2^20, 16-sub-block launch groups on two lanes; every
-    row of 32 whole sub-blocks from 14 of the 64 groups."""
-    blocks = _group_blocks(16, (0, 1, 2, 3, 4, 5, 30, 31, 32, 33, 60, 61, 62, 63), (7, 8, 16 * 63 + 7, 16 * 63 + 8))
-    assert len(blocks) == 32
-    _full_size_case(1 << 30, 1024, 1 << 20, 1 << 19, 0.6, blocks,
-                    ("ntt: N=1048576", "P=2 ", "16 sub-blocks per launch group", "gather=buckets (2^16-bit"))
+    P = 2 pieces, N = 2^20, launch groups on two lanes; every row of at
+    least 32 whole sub-blocks from 14 launch groups."""
+    _full_size_case(1 << 30, 1024, 1 << 20, 1 << 19, 0.6, (0, 1, 2, 3, 4, 5, 30, 31, 32, 33, -4, -3, -2, -1),
+                    (7, 8, 1016, 1017), ("ntt: N=1048576", "P=2 ", "gather=buckets (2^16-bit"), 32)
 
 
 def test_qkd_shaped_block_n2e32():
     """n = 2^32 Bernoulli(0.9), m = 4096 sub-blocks of s = 2^20, k = 104858
     (k mod 32 = 26: every sub-block's output starts at an unaligned bit):
-    P = 8 pieces, N = 2^18, 16-sub-block launch groups on two lanes, bucket
-    tables over 2^18-bit chunks; every row of 16 whole sub-blocks."""
-    blocks = _group_blocks(16, (0, 1, 127, 128, 254, 255), (7, 16 * 255 + 8, 1603, 3228))
-    assert len(blocks) == 16
-    _full_size_case(1 << 32, 4096, 1 << 20, 104858, 0.9, blocks,
-                    ("ntt: N=262144", "P=8 ", "16 sub-blocks per launch group", "gather=buckets (2^18-bit"))
+    P = 7 pieces, N = 2^18, launch groups on two lanes (the last one
+    partial), bucket tables over 2^18-bit chunks; every row of at least 16
+    whole sub-blocks."""
+    _full_size_case(1 << 32, 4096, 1 << 20, 104858, 0.9, (0, 1, 100, 101, -2, -1), (7, 1603, 2000, 3000, 3228),
+                    ("ntt: N=262144", "P=7 ", "gather=buckets (2^18-bit"), 16)

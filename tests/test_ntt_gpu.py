@@ -61,8 +61,8 @@ def test_ntt_matches_oracle(n, m, s, k):
 
 
 @pytest.mark.parametrize("n,m,s,k,p", [
-    (1 << 22, 4, 1 << 20, 1 << 19, 0.6),     # N = 2^21, the QRNG sub-block shape
-    (1 << 21, 2, 1 << 20, 104858, 0.9),      # N = 2^21, the QKD sub-block shape (k mod 32 = 26)
+    (1 << 22, 4, 1 << 20, 1 << 19, 0.6),     # the QRNG sub-block shape (P = 2, N = 2^20)
+    (1 << 21, 2, 1 << 20, 104858, 0.9),      # the QKD sub-block shape (P = 8, N = 2^18; k mod 32 = 26)
     (3 * ((1 << 21) + 1), 3, (1 << 21) + 1, 1 << 21, 0.5),  # s + k - 1 = 2^22: the largest NTT shape
     (1 << 20, 16, 1 << 16, 1 << 15, 0.55),
     (5_000_000, 9, 333_333, 77_777, 0.8),

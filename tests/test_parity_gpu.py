@@ -97,19 +97,33 @@ CASES = [
 ]
 
 
-def _run_case(n, m, s, k, p, flags, plain=False):
+def _run_case(n, m, s, k, p, flags, plain=False, method=0):
     in_w = synth.bernoulli_bits(n, p, 1)
     seed = synth.uniform_bits(_seed_len(m, s, k, flags), 3)
-    with X.Extractor(n, m, s, k, seed, 2, flags) as ex:
+    with X.Extractor(n, m, s, k, seed, 2, flags | method) as ex:
         out = ex.run_plain(_dev(in_w)) if plain else ex.run(_dev(in_w))
         got = _host(out)
+        if method == X.EXTRACT_METHOD_TENSOR:
+            assert ex.describe().startswith("tensor")
+            ex.status()
+        if method == X.EXTRACT_METHOD_DIRECT:
+            assert ex.describe().startswith("lop3")
     want = oracle.extract(n, m, s, k, in_w, seed, 2, flags)
     return got, want
 
 
+METHODS = {"auto": 0, "direct": X.EXTRACT_METHOD_DIRECT, "tensor": X.EXTRACT_METHOD_TENSOR}
+
+
+@pytest.mark.parametrize("method", sorted(METHODS))
 @pytest.mark.parametrize("n,m,s,k,p,flags", CASES)
-def test_run_matches_oracle(n, m, s, k, p, flags):
-    got, want = _run_case(n, m, s, k, p, flags)
+def test_run_matches_oracle(n, m, s, k, p, flags, method):
+    """Every case under the library's own choice of method and under the
+    direct LOP3 kernel and the tensor-core product forced (the latter needs
+    a shared seed)."""
+    if method == "tensor" and flags & X.EXTRACT_SEED_PER_SUBBLOCK:
+        pytest.skip("the tensor-core product needs a shared seed")
+    got, want = _run_case(n, m, s, k, p, flags, method=METHODS[method])
     assert got.shape == want.shape
     bad = np.nonzero(got != want)[0]
     assert bad.size == 0, "first differing word %s of %d" % (bad[:5], got.size)
