@@ -105,8 +105,8 @@ extern "C" {
    sub-block in shared memory, then each sub-block permuted in shared
    memory), which costs 2 bytes per sampled bit plus 4 bytes per stored
    sub-block bit of extra device memory and makes no random global reads; it
-   needs n <= 25600 input chunks of 2^16 bits, or of 2^18 bits with 32-bit
-   table entries (4 bytes per sampled bit), and every sub-block's regrouped
+   needs n <= 25600 input chunks of 2^16 bits, or of 2^18 bits with 18-bit
+   table entries (2.25 bytes per sampled bit), and every sub-block's regrouped
    bits within 220 KiB; otherwise (or without room) the plain gather is
    kept.
    EXTRACT_GATHER_PLAIN keeps the plain gather (one random input read per
@@ -115,7 +115,7 @@ extern "C" {
    same sub-blocks.  Not combinable with EXTRACT_IDENTITY_PERM. */
 #define EXTRACT_GATHER_PLAIN      0x20u
 #define EXTRACT_GATHER_BUCKETS    0x40u
-/* Bucket tables over 2^18-bit input chunks (32-bit table entries) even where
+/* Bucket tables over 2^18-bit input chunks (18-bit table entries) even where
    2^16-bit chunks fit; the library itself takes them when the input has more
    than 25600 chunks of 2^16 bits or its runs are too short to fit.  Tuning
    and test hook. */
@@ -135,6 +135,12 @@ extern "C" {
 /* Tensor-core method: 2^l K blocks of 128 (l = 0 .. 14) summed before each
    parity read-back instead of 2^5.  Test hook. */
 #define EXTRACT_TC_CHUNK(l)       ((((uint32_t)(l) + 1u) & 0xfu) << 24)
+/* Tensor-core method, test hook of the error path: every CTA of the hash
+   kernel first waits on a barrier that nothing arrives on, so the wait runs
+   out after about a second; the kernel then sets the context's error word
+   and returns without multiplying (extract_status reports
+   EXTRACT_ETIMEDOUT; the output is not valid). */
+#define EXTRACT_TC_TEST_STALL     0x10000000u
 
 typedef struct extract_ctx extract_ctx;
 

@@ -35,14 +35,14 @@ double predict_direct_s(uint32_t m, uint32_t k, uint32_t s)
 }
 
 // The tensor-core product pays for its padded tile: 128 rows x nt
-// sub-blocks x 128 K per stage.  About 0.7 PMAC/s measured with 256
+// sub-blocks x 128 K per stage.  0.66 - 0.86 PMAC/s measured with 256
 // sub-blocks per tile; narrower tiles spend relatively more on building the
 // Toeplitz operand.
 double predict_tc_s(uint32_t m, uint32_t k, uint32_t s)
 {
     const double nt = tc_tile_n(m);
     const double macs = (double)round_up(k, 128) * (double)round_up(m, (uint64_t)nt) * (double)round_up(s, 128);
-    return macs / (7e14 * (0.3 + 0.7 * nt / 256.0)) + 5e-6;
+    return macs / (8e14 * (0.3 + 0.7 * nt / 256.0)) + 5e-6;
 }
 
 double predict_ntt_s(uint32_t m, uint32_t s, uint32_t k, int split_log2, bool per_block_seeds)
@@ -50,7 +50,9 @@ double predict_ntt_s(uint32_t m, uint32_t s, uint32_t k, int split_log2, bool pe
     const NttShape sh = ntt_shape(s, k, split_log2, per_block_seeds);
     const double N = (double)sh.N;
     const double transforms = (per_block_seeds ? 2.0 : 1.0) * sh.P + 1.0;
-    return (double)m * transforms * N * (std::log2(N) + 4.0) * 0.325e-12;
+    // seconds per cost unit, from the measured hash times of shapes between
+    // s = 2^16 and 2^20 (1.9 - 34.7 ms, to within about 20 %)
+    return (double)m * ntt_cost_units((uint32_t)transforms, sh.N) * 0.19e-12;
 }
 
 }  // namespace ex
@@ -103,7 +105,7 @@ static_assert(kNttLanes >= 1 && kNttLanes <= (uint32_t)kMaxNttLanes, "NTT lane c
 constexpr uint32_t kKnownFlags = EXTRACT_SEED_PER_SUBBLOCK | EXTRACT_IDENTITY_PERM | EXTRACT_METHOD_DIRECT |
                                   EXTRACT_METHOD_NTT | EXTRACT_SAMPLING_IID | EXTRACT_GATHER_PLAIN |
                                   EXTRACT_GATHER_BUCKETS | EXTRACT_GATHER_WIDE_CHUNKS | (0x3fu << 8) | (0x7u << 16) |
-                                  EXTRACT_METHOD_TENSOR | (0xfu << 24);
+                                  EXTRACT_METHOD_TENSOR | (0xfu << 24) | EXTRACT_TC_TEST_STALL;
 
 // K blocks of 128 per accumulation chunk of the tensor-core product
 // (EXTRACT_TC_CHUNK(l): 2^l blocks; default 2^5 = 4096 K per chunk)
@@ -413,7 +415,8 @@ int extract_hash(extract_ctx *h, void *stream, uint32_t *out_bits_dev)
     if (h->tc) {
         const uint32_t cl = (h->flags >> 24) & 0xfu;
         return launch_hash_tc(h->seed, h->seed_stride, h->arev, h->w_pad, h->m, h->s, h->k, out_bits_dev, h->dev_err,
-                              (cudaStream_t)stream, 1u << (cl ? cl - 1 : kTcChunkLog2Default));
+                              (cudaStream_t)stream, 1u << (cl ? cl - 1 : kTcChunkLog2Default),
+                              (h->flags & EXTRACT_TC_TEST_STALL) != 0);
     }
     return launch_hash(h->plan, h->seed, h->nseeds > 1 ? h->seed_stride : 0u, h->arev, h->w_pad, h->m,
                        h->k, out_bits_dev, (cudaStream_t)stream);

@@ -14,7 +14,7 @@
 //     fixed when the tables are built); every run word is stored into that
 //     sub-block's region of the run buffer B.  Table: for every run word, the
 //     32 in-chunk positions of its bits (16-bit, pairs in one 32-bit word;
-//     32-bit for 2^18-bit chunks) and the word's place in B.
+//     18-bit fields for 2^18-bit chunks) and the word's place in B.
 //   stage 2, per sub-block j (one CTA, B_j in shared memory): B_j holds the
 //     members of sub-block j, chunk by chunk; stored bit c of the sub-block
 //     is the member sigma_j[c] of B_j.  Table: sigma, one 21-bit index per
@@ -32,7 +32,8 @@
 //
 // Layouts (a group = 32 consecutive words, lane l = word 32 g + l):
 //   pi   [word group g][bit pair b2 < 16][lane]   (bit 2 b2 | bit 2 b2+1 << 16),
-//        or [word group g][bit b < 32][lane] for 2^18-bit chunks
+//        or [word group g][word i < 18][lane] for 2^18-bit chunks (the
+//        lane's 32 positions, 18 bits each, entry b at stream bit 18 b)
 //   dst  [run word]                                word index into B, or kNoPos
 //   qc   [chunk + 1]                               first run word of a chunk
 //                                                  (multiples of 32)
@@ -57,6 +58,8 @@ constexpr uint32_t kSigBits = 21, kSigMask = (1u << kSigBits) - 1u, kSigNone = k
 constexpr uint32_t kSigWords = kSigBits;  // 32 entries x 21 bits / 32
 static_assert((kStage2SmemMax / 4) * 32 <= kSigNone, "member bit indices must stay below the sentinel");
 constexpr int kStage2Warps = 32;
+// pi of 2^18-bit chunks: 18-bit in-chunk positions, a run word's 32 in 18 words
+constexpr uint32_t kPi18Words = 18, kPi18Mask = (1u << 18) - 1u;
 
 __host__ __device__ __forceinline__ uint32_t words_of(uint32_t bits) { return (bits + 31u) >> 5; }
 
@@ -204,7 +207,8 @@ bk_assign_kernel(const uint32_t *__restrict__ perm, uint32_t s, uint32_t m, uint
 
 // pi in the stage-1 layout from the B-space entries: run word q with
 // destination d takes the 32 entries of B word d (kWords 32-bit words: 16
-// for 16-bit entries, 32 for 32-bit ones; padding words: zeros).
+// for 16-bit entries, 32 for 32-bit ones; padding words: zeros).  With
+// 2^18-bit chunks the layout is bk_pi_pack18_kernel's instead.
 template <int kWords>
 __global__ void __launch_bounds__(256)
 bk_pi_kernel(const uint32_t *__restrict__ pib32, const uint32_t *__restrict__ dst, uint64_t run_words,
@@ -233,8 +237,50 @@ bk_pi_kernel(const uint32_t *__restrict__ pib32, const uint32_t *__restrict__ ds
     }
 }
 
+// pi for 2^18-bit chunks: the 32 in-chunk positions of a run word (18 bits
+// each) packed into 18 words, entry b at stream bit 18 b, so stage 1 reads
+// 72 instead of 128 bytes per run word.  Layout [word group g][word i < 18]
+// [lane], like sigma's.
+__global__ void __launch_bounds__(256)
+bk_pi_pack18_kernel(const uint32_t *__restrict__ pib32, const uint32_t *__restrict__ dst, uint64_t run_words,
+                    uint32_t *__restrict__ pi)
+{
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t g = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; g < run_words / 32; g += nwarps) {
+        const uint32_t d = dst[g * 32u + lane];
+        uint32_t e[32];
+#pragma unroll
+        for (int i = 0; i < 32; ++i) e[i] = 0u;
+        if (d != kNoPos) {
+            const uint4 *src = reinterpret_cast<const uint4 *>(pib32 + (size_t)d * 32u);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const uint4 v = __ldcs(src + i);
+                e[4 * i] = v.x & kPi18Mask;
+                e[4 * i + 1] = v.y & kPi18Mask;
+                e[4 * i + 2] = v.z & kPi18Mask;
+                e[4 * i + 3] = v.w & kPi18Mask;
+            }
+        }
+        uint32_t o[kPi18Words];
+#pragma unroll
+        for (int i = 0; i < (int)kPi18Words; ++i) o[i] = 0u;
+#pragma unroll
+        for (int b = 0; b < 32; ++b) {
+            const int bit = 18 * b, wi = bit >> 5, sh = bit & 31;
+            o[wi] |= e[b] << sh;
+            if (sh > 14) o[wi + 1] |= e[b] >> (32 - sh);
+        }
+        uint32_t *out = pi + g * 32u * kPi18Words + lane;
+#pragma unroll
+        for (int i = 0; i < (int)kPi18Words; ++i) out[i * 32] = o[i];
+    }
+}
+
 // Stage 1: one chunk of 2^kLog bits per CTA iteration; one warp per group of
-// 32 run words.  pi entries: 16-bit pairs (kLog = 16) or 32-bit (kLog = 18).
+// 32 run words.  pi entries: 16-bit pairs (kLog = 16) or 18-bit fields
+// (kLog = 18).
 template <int kLog>
 __global__ void __launch_bounds__(kStage1Warps * 32)
 bk_stage1_kernel(const uint32_t *__restrict__ in, uint64_t in_words, const uint32_t *__restrict__ pi,
@@ -242,7 +288,7 @@ bk_stage1_kernel(const uint32_t *__restrict__ in, uint64_t in_words, const uint3
                  uint32_t *__restrict__ B)
 {
     constexpr uint32_t kWords = (1u << kLog) / 32;          // chunk words
-    constexpr int kPiWords = kLog <= 16 ? 16 : 32;           // pi words per run word
+    constexpr int kPiWords = kLog <= 16 ? 16 : (int)kPi18Words;  // pi words per run word
     __shared__ __align__(16) uint32_t cw[kWords];
     const uint32_t lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
     const bool aligned = (reinterpret_cast<uintptr_t>(in) & 15u) == 0;
@@ -274,7 +320,13 @@ bk_stage1_kernel(const uint32_t *__restrict__ in, uint64_t in_words, const uint3
                 }
             } else {
 #pragma unroll
-                for (int b = 0; b < kPiWords; ++b) word |= ((cw[pr[b] >> 5] >> (pr[b] & 31u)) & 1u) << b;
+                for (int b = 0; b < 32; ++b) {
+                    const int bit = 18 * b, wi = bit >> 5, sh = bit & 31;
+                    uint32_t p = pr[wi] >> sh;
+                    if (sh > 14) p |= pr[wi + 1] << (32 - sh);
+                    p &= kPi18Mask;
+                    word |= ((cw[p >> 5] >> (p & 31u)) & 1u) << b;
+                }
             }
             if (to != kNoPos) B[to] = word;
         }
@@ -327,7 +379,8 @@ int build_tables(const uint32_t *perm, uint64_t n, uint32_t m, uint32_t s, uint3
     gather_buckets_free(gb);
     const uint32_t nch = (uint32_t)ceil_div(n, 1ull << clog);
     if ((size_t)nch * 8 > kAssignSmemMax || (uint64_t)nch * (m + 1) >= (1ull << 32)) return kBucketsNotEligible;
-    const uint32_t pi_words = clog <= 16 ? 16 : 32;  // 32-bit words of pi per run word
+    const uint32_t pi_words = clog <= 16 ? 16 : kPi18Words;  // 32-bit words of pi per run word
+    const uint32_t pib_words = clog <= 16 ? 16 : 32;         // the same in the B-space staging copy
     uint32_t *cnt = nullptr, *wpre = nullptr, *mw = nullptr, *cwords = nullptr, *total = nullptr;
     uint32_t *pib = nullptr;
     int rc = EXTRACT_OK;
@@ -370,7 +423,7 @@ int build_tables(const uint32_t *perm, uint64_t n, uint32_t m, uint32_t s, uint3
         gb->bstride = bstride;
         gb->run_words = q;
         const uint64_t sig_len = (uint64_t)m * w_pad * kSigWords;  // 21-bit fields, 32 per 21 words
-        const size_t pib_bytes = (size_t)m * bstride * 4 * pi_words;
+        const size_t pib_bytes = (size_t)m * bstride * 4 * pib_words;
         if ((e = cudaMalloc(&gb->qc, (size_t)(nch + 1) * 4)) != cudaSuccess ||
             (e = cudaMalloc(&gb->pi, std::max<uint64_t>(q, 1) * 4 * pi_words)) != cudaSuccess ||
             (e = cudaMalloc(&gb->dst, std::max<uint64_t>(q, 1) * 4)) != cudaSuccess ||
@@ -407,7 +460,7 @@ int build_tables(const uint32_t *perm, uint64_t n, uint32_t m, uint32_t s, uint3
         } else {
             bk_assign_kernel<uint32_t><<<agrid, 1024, nch * 8, st>>>(perm, s, m, nch, clog, w_pad, bstride, mw, pib,
                                                                     gb->sigma);
-            bk_pi_kernel<32><<<pgrid, 256, 0, st>>>(pib, gb->dst, q, gb->pi);
+            bk_pi_pack18_kernel<<<pgrid, 256, 0, st>>>(pib, gb->dst, q, gb->pi);
         }
         if ((e = cudaGetLastError()) != cudaSuccess) { fail(cuda_error(e, "bucket tables")); break; }
         if ((e = cudaFuncSetAttribute(bk_stage2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -469,7 +522,7 @@ int gather_buckets_run(const GatherBuckets &gb, const uint32_t *in, uint64_t n, 
 
 uint64_t gather_buckets_bytes(const GatherBuckets &gb, uint64_t n, uint32_t m, uint32_t w_pad)
 {
-    const uint64_t q = gb.run_words, pi_words = gb.clog <= 16 ? 16 : 32;
+    const uint64_t q = gb.run_words, pi_words = gb.clog <= 16 ? 16 : kPi18Words;
     const uint64_t stage1 = ceil_div(n, 32) * 4 + (uint64_t)(gb.nch + 1) * 4 + q * 4 * pi_words + q * 4  // in, qc, pi, dst
                             + q * 4;                                                                      // run words to B
     const uint64_t stage2 = q * 4 + (uint64_t)m * w_pad * kSigWords * 4 + (uint64_t)m * w_pad * 4;        // B, sigma, arev

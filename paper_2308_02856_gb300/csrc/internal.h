@@ -141,8 +141,11 @@ int launch_hash(const HashPlan &p, const uint32_t *seed, uint32_t seed_stride,
 // seed_words realigned words; out is zeroed on st and receives every K_j;
 // err is set to 1 when a kernel wait gave up.  chunk_blocks: K blocks of 128
 // summed before each parity read-back.
+// test_stall: every CTA first waits on a barrier nothing arrives on, so the
+// wait runs out, err is set and the kernel returns (the error path's test).
 int launch_hash_tc(const uint32_t *seed, uint64_t seed_words, const uint32_t *arev, uint32_t w_pad, uint32_t m,
-                   uint32_t s, uint32_t k, uint32_t *out, uint32_t *err, cudaStream_t st, uint32_t chunk_blocks);
+                   uint32_t s, uint32_t k, uint32_t *out, uint32_t *err, cudaStream_t st, uint32_t chunk_blocks,
+                   bool test_stall = false);
 // Sub-blocks per tile of the tensor-core product for m sub-blocks.
 uint32_t tc_tile_n(uint32_t m);
 
@@ -261,6 +264,9 @@ uint64_t ntt_plan_bytes(uint32_t s, uint32_t k, int split_log2 = -1, bool per_bl
 double predict_direct_s(uint32_t m, uint32_t k, uint32_t s);
 double predict_ntt_s(uint32_t m, uint32_t s, uint32_t k, int split_log2 = -1, bool per_block_seeds = false);
 double predict_tc_s(uint32_t m, uint32_t k, uint32_t s);
+// Relative cost of the NTT method's transforms (ntt_shape's and
+// predict_ntt_s's unit).
+double ntt_cost_units(uint32_t transforms, uint32_t N);
 uint32_t ntt_group(const NttPlan *p);
 uint32_t ntt_size(const NttPlan *p);
 uint32_t ntt_pieces(const NttPlan *p);

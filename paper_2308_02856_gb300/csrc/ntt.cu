@@ -1086,6 +1086,15 @@ int ntt_launch_a_inv(const NttPlan *p, const uint32_t *buf, uint32_t g, uint32_t
 
 }  // namespace
 
+// Relative cost of `transforms` transforms of length N.  Lengths below 2^16
+// (R1 < 32 columns) run the generic column kernels, with one barrier per
+// stage, measured 3.7x slower per butterfly than the warp-transposed ones.
+double ntt_cost_units(uint32_t transforms, uint32_t N)
+{
+    const double c = (double)transforms * (double)N * (std::log2((double)N) + 4.0);
+    return N < (1u << 16) ? 3.7 * c : c;
+}
+
 // Split of a sub-block into P pieces (1 <= P <= 16) of h coefficients (h a
 // multiple of 32 when P > 1, so pieces start on word boundaries): each piece
 // is its own middle product with seed window q h .. q h + h + k - 2, and the
@@ -1109,7 +1118,7 @@ NttShape ntt_shape(uint32_t s, uint32_t k, int split_log2, bool per_block_seeds)
         if (N > (1ull << 22) || bufs * P * N > kMaxWorkWords) continue;
         if (per_block_seeds && N < (1u << 16)) continue;  // needs the full twist tables (R1 >= 32)
         // transforms per sub-block: P data pieces (+ P seed windows) + 1 inverse
-        const double cost = (double)(bufs * P + 1) * (double)N * (std::log2((double)N) + 4.0);
+        const double cost = ntt_cost_units(bufs * P + 1, (uint32_t)N);
         if (best.N == 0 || cost < best_cost) {
             best = NttShape{(uint32_t)N, P, (uint32_t)h};
             best_cost = cost;

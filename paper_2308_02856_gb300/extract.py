@@ -34,6 +34,7 @@ EXTRACT_GATHER_PLAIN = 0x20
 EXTRACT_GATHER_BUCKETS = 0x40
 EXTRACT_GATHER_WIDE_CHUNKS = 0x80
 EXTRACT_METHOD_TENSOR = 0x100000
+EXTRACT_TC_TEST_STALL = 0x10000000
 NO_POS = 0xFFFFFFFF  # padding slot of the i.i.d. law's order
 
 

@@ -108,3 +108,21 @@ def test_tensor_method_rejects_per_subblock_seeds_and_two_methods():
         with pytest.raises(X.ExtractError) as e:
             X.extract_create(1 << 16, 4, 1 << 14, 100, seed, 1, fl | X.EXTRACT_METHOD_TENSOR)
         assert e.value.code == X.EXTRACT_EINVAL
+
+
+def test_a_wait_that_runs_out_is_reported_and_the_device_stays_usable():
+    """The error path of the bounded waits, without a GPU fault: with the
+    test hook every CTA waits on a barrier nothing arrives on; after about a
+    second the kernel sets the context's error word, frees its tensor memory
+    and returns.  extract_status reports EXTRACT_ETIMEDOUT once, and a run
+    right after it on the same device is bit-exact."""
+    n, m, s, k = 1 << 16, 8, 4096, 1500
+    in_w = synth.bernoulli_bits(n, 0.7, 69)
+    seed = synth.uniform_bits(s + k - 1, 70)
+    with X.Extractor(n, m, s, k, seed, 2, X.EXTRACT_METHOD_TENSOR | X.EXTRACT_TC_TEST_STALL) as ex:
+        ex.run(_dev(in_w))
+        with pytest.raises(X.ExtractError) as e:
+            ex.status()
+        assert e.value.code == X.EXTRACT_ETIMEDOUT
+        ex.status()  # reported once, then cleared
+    assert np.array_equal(_run(n, m, s, k, 0, in_w, seed), oracle.extract(n, m, s, k, in_w, seed, 2))
