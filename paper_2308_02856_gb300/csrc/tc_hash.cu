@@ -167,37 +167,58 @@ struct TcArgs {
     uint32_t chunk;        // K blocks per accumulation chunk
     uint32_t *out;         // zeroed; receives K_j[i] at bit j k + i
     uint32_t *err;         // set to 1 when a wait gave up
+    uint32_t stall;        // test hook: first wait on a barrier nothing arrives on
 };
 
 __device__ __forceinline__ uint32_t seed_word(const TcArgs &a, uint64_t w) { return w < a.seed_words ? __ldg(a.seed + w) : 0u; }
 
-// Build stage `st` for K block kb: Toeplitz rows i0 .. i0+127 (row r, element
-// kk = seed bit i0 + r + 128 kb + kk) and sub-blocks j0 .. j0+nt-1 (row jj,
-// element kk = bit 128 kb + kk of R_{j0+jj}; zero past m).
-__device__ __forceinline__ void build_stage(const TcArgs &a, uint8_t *st, uint32_t i0, uint32_t j0, uint32_t kb)
+// The global words one thread needs to build one stage: three seed words for
+// its Toeplitz row segment and the 128 bits of its sub-block row.  Loaded a
+// stage ahead, so their latency hides behind the current stage's build.
+struct StageWords {
+    uint32_t s0, s1, s2;  // seed words from T0 / 32 (T0 below)
+    uint32_t sh;          // T0 mod 32
+    uint4 bits;           // sub-block row jj = threadIdx.x (0 past m or nt)
+};
+
+// Words for K block kb: Toeplitz row r = t / 2, elements 64 (t % 2) .. +63
+// (seed bits from T0 = i0 + r + 128 kb + 64 (t % 2)); sub-block row t.
+__device__ __forceinline__ StageWords load_stage(const TcArgs &a, uint32_t i0, uint32_t j0, uint32_t kb)
+{
+    const uint32_t t = threadIdx.x;
+    StageWords v;
+    const uint64_t T0 = (uint64_t)i0 + (t >> 1) + (uint64_t)kb * kTcKB + 64u * (t & 1u);
+    const uint64_t w = T0 >> 5;
+    v.sh = (uint32_t)(T0 & 31u);
+    v.s0 = seed_word(a, w);
+    v.s1 = seed_word(a, w + 1);
+    v.s2 = seed_word(a, w + 2);
+    v.bits = make_uint4(0, 0, 0, 0);
+    const uint32_t j = j0 + t;
+    if (t < a.nt && j < a.m) v.bits = __ldg(reinterpret_cast<const uint4 *>(a.arev + (size_t)j * a.w_pad + 4u * kb));
+    return v;
+}
+
+// Build stage `st` from the loaded words: Toeplitz rows i0 .. i0+127 (row r,
+// element kk = seed bit i0 + r + 128 kb + kk) and sub-blocks j0 .. j0+nt-1
+// (row jj, element kk = bit 128 kb + kk of R_{j0+jj}; zero past m).
+__device__ __forceinline__ void build_stage(const TcArgs &a, uint8_t *st, const StageWords &v)
 {
     const uint32_t t = threadIdx.x;
     {   // A: thread t -> row t / 2, elements 64 (t % 2) .. +63
         const uint32_t r = t >> 1, h = t & 1u;
-        const uint64_t T0 = (uint64_t)i0 + r + (uint64_t)kb * kTcKB + 64u * h;
-        const uint64_t w = T0 >> 5;
-        const uint32_t sh = (uint32_t)(T0 & 31u);
-        const uint32_t w0 = seed_word(a, w), w1 = seed_word(a, w + 1), w2 = seed_word(a, w + 2);
-        const uint32_t lo = __funnelshift_r(w0, w1, sh), hi = __funnelshift_r(w1, w2, sh);
+        const uint32_t lo = __funnelshift_r(v.s0, v.s1, v.sh), hi = __funnelshift_r(v.s1, v.s2, v.sh);
         const uint32_t g4[4] = {lo & 0xffffu, lo >> 16, hi & 0xffffu, hi >> 16};
 #pragma unroll
         for (int g = 0; g < 4; ++g)
             *reinterpret_cast<uint4 *>(st + core_off(r, 64u * h + 16u * g)) = expand16(g4[g]);
     }
-    uint8_t *sb = st + kTcStageA;
-    for (uint32_t jj = t; jj < a.nt; jj += kTcThreads) {  // B: one sub-block row per thread
-        const uint32_t j = j0 + jj;
-        uint4 bits = make_uint4(0, 0, 0, 0);
-        if (j < a.m) bits = __ldg(reinterpret_cast<const uint4 *>(a.arev + (size_t)j * a.w_pad + 4u * kb));
-        const uint32_t wv[4] = {bits.x, bits.y, bits.z, bits.w};
+    if (t < a.nt) {  // B: one sub-block row per thread
+        uint8_t *sb = st + kTcStageA;
+        const uint32_t wv[4] = {v.bits.x, v.bits.y, v.bits.z, v.bits.w};
 #pragma unroll
         for (int q = 0; q < 8; ++q)
-            *reinterpret_cast<uint4 *>(sb + core_off(jj, 16u * q)) = expand16((wv[q >> 1] >> (16u * (q & 1))) & 0xffffu);
+            *reinterpret_cast<uint4 *>(sb + core_off(t, 16u * q)) = expand16((wv[q >> 1] >> (16u * (q & 1))) & 0xffffu);
     }
 }
 
@@ -206,8 +227,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_hash_kernel(TcArgs a)
     extern __shared__ __align__(1024) uint8_t sm[];
     const uint32_t stage_bytes = kTcStageA + a.nt * kTcKB;
     uint8_t *stage0 = sm, *stage1 = sm + stage_bytes;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + 2 * stage_bytes);
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 2);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + 2 * stage_bytes);  // 2 stages + 1 never arrived on
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 3);
     volatile uint32_t *abort_flag = tslot + 1;
     const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31u;
     const uint32_t i0 = (blockIdx.x % a.tiles_m) * kTcM, j0 = (blockIdx.x / a.tiles_m) * a.nt;
@@ -215,6 +236,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_hash_kernel(TcArgs a)
     if (tid == 0) {
         mbar_init(smem_u32(&bars[0]), 1);
         mbar_init(smem_u32(&bars[1]), 1);
+        mbar_init(smem_u32(&bars[2]), 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -232,12 +254,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_hash_kernel(TcArgs a)
     const uint32_t lq = warp & 3u, half = a.nt >> 1, c0 = (warp >> 2) * half;
     uint32_t par[kTcMaxN / 2 / 32] = {0, 0, 0, 0};
     int64_t last_commit = -1;
-    for (uint32_t kb = 0; kb < a.nkb; ++kb) {
+    // test hook: a wait that runs out (its barrier's first phase never
+    // completes), exercising the error path without any multiply in flight
+    if (a.stall && !mbar_wait(smem_u32(&bars[2]), 0u)) *abort_flag = 1;
+    __syncthreads();
+    StageWords next = load_stage(a, i0, j0, 0);
+    for (uint32_t kb = 0; kb < a.nkb && !*abort_flag; ++kb) {
         const uint32_t b = kb & 1u;
         uint8_t *st = b ? stage1 : stage0;
+        const StageWords cur = next;
+        if (kb + 1 < a.nkb) next = load_stage(a, i0, j0, kb + 1);  // in flight during this stage
         // the multiplies of K block kb - 2 read this stage: wait for them
         if (kb >= 2 && !mbar_wait(smem_u32(&bars[b]), ((kb - 2) >> 1) & 1u)) *abort_flag = 1;
-        build_stage(a, st, i0, j0, kb);
+        build_stage(a, st, cur);
         fence_async_smem();  // the stage's generic writes, visible to the tensor core
         __syncthreads();
         if (*abort_flag) break;
@@ -307,7 +336,8 @@ uint64_t g_tc_smem_set = 0;  // devices whose kernel attribute is set
 uint32_t tc_tile_n(uint32_t m) { return m >= kTcMaxN ? kTcMaxN : (uint32_t)std::max<uint64_t>(64, round_up(m, 64)); }
 
 int launch_hash_tc(const uint32_t *seed, uint64_t seed_words, const uint32_t *arev, uint32_t w_pad, uint32_t m,
-                   uint32_t s, uint32_t k, uint32_t *out, uint32_t *err, cudaStream_t st, uint32_t chunk_blocks)
+                   uint32_t s, uint32_t k, uint32_t *out, uint32_t *err, cudaStream_t st, uint32_t chunk_blocks,
+                   bool test_stall)
 {
     if (w_pad % 4u) return set_error(EXTRACT_EINTERNAL, "tensor-core hash: w_pad %u not a multiple of 4", w_pad);
     TcArgs a{};
@@ -325,11 +355,12 @@ int launch_hash_tc(const uint32_t *seed, uint64_t seed_words, const uint32_t *ar
     a.chunk = std::max<uint32_t>(1, chunk_blocks);
     a.out = out;
     a.err = err;
+    a.stall = test_stall ? 1u : 0u;
     const uint64_t tiles = (uint64_t)a.tiles_m * ceil_div(m, a.nt);
     if (tiles >= (1ull << 31)) return set_error(EXTRACT_EINVAL, "tensor-core hash: too many tiles");
     // shared memory: two stages and the barriers; at least enough that no
     // more CTAs share an SM than its 512 tensor-memory columns hold
-    const uint32_t need = 2 * (kTcStageA + a.nt * kTcKB) + 64;
+    const uint32_t need = 2 * (kTcStageA + a.nt * kTcKB) + 64;  // stages, 3 barriers, tensor address, flag
     const uint32_t per_sm = 512u / a.ncols;
     const uint32_t smem = std::max<uint32_t>(need, kSmemPerSM / (per_sm + 1) + 1);
     int dev = 0;
