@@ -59,6 +59,7 @@ WORKLOADS = {
     "mid_n2^27_m128_s2^20_k2^16": (1 << 27, 128, 1 << 20, 1 << 16, 0.6),
     "qrng128_n2^27_m128_s2^20_k2^19": (1 << 27, 128, 1 << 20, 1 << 19, 0.6),
     "small_n2^24_m64_s2^18_k2^17": (1 << 24, 64, 1 << 18, 1 << 17, 0.6),
+    "short_n2^28_m4096_s2^16_k3277": (1 << 28, 4096, 1 << 16, 3277, 0.6),
 }
 DEFAULT_WORKLOAD = "qkd_n2^32_m4096_s2^20_k104858"
 IN_SEED, SAMPLING_KEY, TOEPLITZ_SEED = 1, 2, 3
