@@ -635,6 +635,11 @@ int extract_batch_run_sequential(extract_batch *b, void *stream, const uint32_t 
 int extract_batch_status(extract_batch *b)
 {
     if (!b) return set_error(EXTRACT_EINVAL, "null batch");
+    int rc = EXTRACT_OK;
+    for (const BatchJobHost &J : b->jobs)  // every plan's word is read and cleared
+        if (J.ntt)
+            if (int r = ntt_status(J.ntt)) rc = r;
+    if (rc) return rc;
     if (!b->d_err) return EXTRACT_OK;
     uint32_t v = 0;
     EX_CUDA(cudaDeviceSynchronize());

@@ -548,11 +548,12 @@ int extract_describe(extract_ctx *h, char *buf, uint32_t buflen)
     if (h->ntt) {
         snprintf(buf, buflen,
                  "ntt: N=%u (%u x 2048) P=%u pieces per sub-block, %u sub-blocks per launch group, "
-                 "prime 7*2^26+1, %s; sms=%d; %s",
+                 "prime 7*2^26+1, %s, column pass A %s; sms=%d; %s",
                  ntt_size(h->ntt), ntt_size(h->ntt) / 2048, ntt_pieces(h->ntt), ntt_group(h->ntt),
                  h->nseeds > 1 ? (ntt_spectra_resident(h->ntt) ? "seed spectra resident (one seed per sub-block)"
                                                                 : "seed windows transformed per run (one seed per sub-block)")
                                : "shared seed spectrum",
+                 ntt_uses_tensor_cores(h->ntt) ? "on the tensor cores (f16 slices of the DFT matrix)" : "by butterflies",
                  h->num_sms, gather);
         return EXTRACT_OK;
     }
@@ -575,6 +576,8 @@ int extract_describe(extract_ctx *h, char *buf, uint32_t buflen)
 int extract_status(extract_ctx *h)
 {
     if (int rc = check_ctx(h)) return rc;
+    if (h->ntt)
+        if (int rc = ntt_status(h->ntt)) return rc;
     if (!h->dev_err) return EXTRACT_OK;
     uint32_t v = 0;
     EX_CUDA(cudaDeviceSynchronize());

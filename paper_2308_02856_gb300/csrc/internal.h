@@ -269,6 +269,13 @@ double predict_tc_s(uint32_t m, uint32_t k, uint32_t s);
 double ntt_cost_units(uint32_t transforms, uint32_t N);
 uint32_t ntt_group(const NttPlan *p);
 uint32_t ntt_size(const NttPlan *p);
+// pass A runs on the tensor cores (transform lengths 2^16 .. 2^18)
+bool ntt_uses_tensor_cores(const NttPlan *p);
+// the plan's device error word (nonzero: a tensor-core wait gave up)
+uint32_t *ntt_error_word(const NttPlan *p);
+// EXTRACT_ETIMEDOUT (once) when a tensor-core kernel of the plan gave up on
+// a wait since the last call; synchronises the device
+int ntt_status(const NttPlan *p);
 uint32_t ntt_pieces(const NttPlan *p);
 
 }  // namespace ex

@@ -40,6 +40,7 @@
 // to [0, p) only where a parity is taken.
 #include "common.cuh"
 #include "internal.h"
+#include "tcgen05.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -775,6 +776,9 @@ __device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane)
 // shared memory row-major, the column of row r XOR-ed with COLS (r / 32) so
 // that both the per-lane column writes and the row-wise copies are
 // conflict-free.
+#ifndef EX_NTT_TC_COLS
+#define EX_NTT_TC_COLS 1  // pass A on the tensor cores where R1 is 32, 64 or 128
+#endif
 #ifndef EX_COLS_WARPS
 #define EX_COLS_WARPS 8
 #endif
@@ -798,38 +802,63 @@ __device__ __forceinline__ uint32_t tile_at(uint32_t r, uint32_t c)
     return r * CW + (c ^ (COLS * (r >> 5)));
 }
 
+// The word whose bit c is element t0 + c of a piece (t0 % 32 == 0): read
+// from position len - 1 - t (kReversed) or t of b, 0 where t >= len or the
+// position is >= lim.  In two steps, so that the loads can be issued well
+// before the word is needed: row_fetch loads the (at most two) source words,
+// row_finish assembles the word from them.
+template <bool kReversed>
+__device__ __forceinline__ void row_fetch(const uint32_t *__restrict__ b, uint32_t len, uint32_t lim, uint32_t t0,
+                                          uint32_t &a, uint32_t &c)
+{
+    a = c = 0u;
+    if (t0 >= len) return;
+    if (kReversed) {
+        const int32_t hi = (int32_t)(len - 1 - t0), lo = hi - 31;
+        const int32_t top = min(hi, (int32_t)lim - 1);
+        if (top < max(lo, 0)) return;
+        const int32_t w0 = lo >> 5, w1 = top >> 5;  // floor; w1 >= 0
+        if (w0 >= 0) a = __ldg(b + w0);
+        if (w1 != w0) c = __ldg(b + w1);
+    } else if (t0 < min(len, lim)) {
+        a = __ldg(b + (t0 >> 5));
+    }
+}
+template <bool kReversed>
+__device__ __forceinline__ uint32_t row_finish(uint32_t len, uint32_t lim, uint32_t t0, uint32_t a, uint32_t c)
+{
+    if (t0 >= len) return 0u;
+    if (kReversed) {
+        const int32_t hi = (int32_t)(len - 1 - t0), lo = hi - 31;
+        const int32_t top = min(hi, (int32_t)lim - 1);
+        if (top < max(lo, 0)) return 0u;
+        const int32_t w0 = lo >> 5;
+        const uint64_t v = ((uint64_t)c << 32) | a;
+        const int32_t nb = top - lo + 1;  // 1 .. 32 positions kept
+        const uint32_t f32 = (uint32_t)(v >> (lo - 32 * w0)) & (nb >= 32 ? ~0u : (1u << nb) - 1u);
+        return __brev(f32);  // position lo + i -> column 31 - i
+    }
+    const uint32_t end = min(len, lim);
+    if (t0 >= end) return 0u;
+    return end - t0 < 32u ? a & ((1u << (end - t0)) - 1u) : a;
+}
+template <bool kReversed>
+__device__ __forceinline__ uint32_t row_word(const uint32_t *__restrict__ b, uint32_t len, uint32_t lim, uint32_t t0)
+{
+    uint32_t a, c;
+    row_fetch<kReversed>(b, len, lim, t0, a, c);
+    return row_finish<kReversed>(len, lim, t0, a, c);
+}
+
 // Staged bits for CW >= 32 columns: rb[t1 * CW/32 + w] bit c is element
-// t = t1 R2 + c0 + 32 w + c, read as in stage_row_bits (c0 % 32 == 0).
+// t = t1 R2 + c0 + 32 w + c (c0 % 32 == 0).
 template <bool kReversed, uint32_t WPR>
 __device__ __forceinline__ void stage_row_words(uint32_t *rb, const uint32_t *__restrict__ b, uint32_t len,
                                                 uint32_t lim, uint32_t R1, uint32_t c0)
 {
     for (uint32_t it = threadIdx.x; it < R1 * WPR; it += blockDim.x) {
         const uint32_t t1 = it / WPR, wi = it % WPR;
-        const uint32_t t0 = t1 * kR2 + c0 + 32u * wi;
-        uint32_t f = 0;
-        if (t0 < len) {
-            if (kReversed) {
-                const int32_t hi = (int32_t)(len - 1 - t0), lo = hi - 31;
-                const int32_t top = min(hi, (int32_t)lim - 1);
-                if (top >= max(lo, 0)) {
-                    const int32_t w0 = lo >> 5, w1 = top >> 5;  // floor; w1 >= 0
-                    const uint32_t a = w0 >= 0 ? __ldg(b + w0) : 0u;
-                    const uint32_t c = w1 != w0 ? __ldg(b + w1) : 0u;
-                    const uint64_t v = ((uint64_t)c << 32) | a;
-                    const int32_t nb = top - lo + 1;  // 1 .. 32 positions kept
-                    const uint32_t f32 = (uint32_t)(v >> (lo - 32 * w0)) & (nb >= 32 ? ~0u : (1u << nb) - 1u);
-                    f = __brev(f32);  // position lo + i -> column 31 - i
-                }
-            } else {
-                const uint32_t end = min(len, lim);
-                if (t0 < end) {
-                    f = __ldg(b + (t0 >> 5));
-                    if (end - t0 < 32u) f &= (1u << (end - t0)) - 1u;
-                }
-            }
-        }
-        rb[it] = f;
+        rb[it] = row_word<kReversed>(b, len, lim, t1 * kR2 + c0 + 32u * wi);
     }
 }
 
@@ -946,6 +975,257 @@ ntt_cols_inv_m_kernel(const uint32_t *__restrict__ buf, uint64_t sub_stride, Tab
     if (sh && (x >> (32u - sh))) atomicXor(out + (P >> 5) + 1, x >> (32u - sh));
 }
 
+// ---- pass A on the tensor cores (R1 in {32, 64, 128}) -------------------
+// Pass A's inputs are bits, so its column DFTs are one exact integer GEMM per
+// piece:
+//   buf[r][t2] = w_N^(K t2) * sum_{t1} F[r][t1] x[t1 R2 + t2]  (mod p),
+//   F[r][t1] = w_R1^(K t1),  K = bitrev(r),
+// the values the butterfly kernels above write (in [0, 2p)).  F is cut into
+// three 11-bit slices, F = F_0 + 2^11 F_1 + 2^22 F_2, each exact in f16; the
+// bits are 0/1 in f16; every slice's sum has at most R1 terms below 2^11, so
+// its f32 accumulator holds it exactly (below 2^18).  tcgen05.mma kind::f16
+// with M = 128 columns t2 (one tensor-memory lane each), N = the three
+// slices' rows of one half of the rows r (3 R1 / 2; each half has its own
+// accumulators), K = the rows t1 that can hold data, rounded up to 16 (a
+// piece of len coefficients has data in rows t1 < len / R2 only).  Each
+// half's accumulators start at 2^23 (one multiply of two constant tiles,
+// 256 x 32768), so a sum S < 2^18 reads back as the f32 bits 2^23 + S: the
+// integer S sits in the low bits with no conversion.  F's slices stay in
+// shared memory; the epilogue joins the three sums mod p, applies the twist
+// and stores rows of buf with the lanes on consecutive columns.
+//
+// Persistent CTAs, one per SM, 21 warps in three roles:
+//   warp 0      tensor-memory allocation; lane 0 issues the multiplies
+//   warps 1-4   bits -> f16 operand (two shared-memory stages): warp 1 + w
+//               expands columns 32 w .. 32 w + 31 of the 128-column tile
+//   warps 5-20  epilogue: warp 5 + e takes a quarter of the rows (half
+//               e / 8, its first or second R1 / 4 rows by (e / 4) % 2) in the
+//               columns of its lane quarter (warp % 4)
+// Each CTA keeps one 128-column block cb = blockIdx.x % 16 and walks the
+// pieces blockIdx.x / 16, + g, + 2 g, ... (16 g CTAs), so an epilogue thread
+// holds the twists of its column and rows in registers, loaded once.
+// Every wait gives up after about a second (error word set, tensor memory
+// freed after the last multiplies, return).
+struct TcColsArgs {
+    const uint32_t *bits;
+    Pieces pc;
+    uint32_t N;
+    uint32_t npieces;     // pieces (virtual blocks) of the launch
+    uint32_t g;           // CTAs per column block
+    uint32_t k16;         // K steps of 16 rows t1
+    const uint4 *fimg;    // F's slices in the shared-memory layout (6 R1^2 bytes)
+    const uint32_t *twt;  // twist w_N^(bitrev(r) t2) at r R2 + t2, Montgomery form
+    uint32_t *buf;
+    uint32_t *err;
+};
+
+constexpr uint32_t kTcColsThreads = 21 * 32;
+constexpr uint32_t kTcColsTile = 128;                    // columns t2 per tile
+constexpr uint32_t kTcColBlocks = kR2 / kTcColsTile;     // 16 column blocks per row
+constexpr uint32_t kHalfOne = 0x3C00u;                   // 1.0 in f16
+constexpr uint16_t kHalf256 = 0x5C00u, kHalf32768 = 0x7800u;  // 2^8, 2^15 in f16: product 2^23
+constexpr uint32_t kF32Int = 0x4B000000u;                // bits of 2^23: v + 2^23 holds integer v < 2^23
+constexpr uint32_t kJoin = kF32Int * (1u + (1u << 11));  // the two offsets of u0 + 2^11 u1 (mod 2^32)
+constexpr uint32_t kQ22 = (uint32_t)((1ull << 54) / kP); // Shoup quotient of 2^22
+
+__host__ __device__ constexpr uint32_t tc_cols_ncols(uint32_t R1)
+{
+    return 3 * R1 <= 128 ? 128u : 3 * R1 <= 256 ? 256u : 512u;
+}
+// shared memory: F's slices, two stages, the two 16-column constant tiles
+// (128 and 3 R1 / 2 rows), 8 barriers, tensor address, flag; at least half
+// an SM's, so that one CTA holds an SM's tensor memory
+__host__ __device__ constexpr uint32_t tc_cols_smem_need(uint32_t R1)
+{
+    return 6 * R1 * R1 + 512 * R1 + 4096 + 48 * R1 + 72;
+}
+__host__ __device__ constexpr uint32_t tc_cols_smem(uint32_t R1)
+{
+    return tc_cols_smem_need(R1) > kSmemPerSM / 2 + 1 ? tc_cols_smem_need(R1) : kSmemPerSM / 2 + 1;
+}
+
+// two bits -> two f16 (1.0 where set): element 2 i in the low half
+__device__ __forceinline__ uint32_t two_halves(uint32_t y) { return (((y & 3u) * 0x8001u) & 0x10001u) * kHalfOne; }
+
+template <uint32_t R1, bool kReversed>
+__global__ void __launch_bounds__(kTcColsThreads, 1) ntt_cols_fwd_tc_kernel(TcColsArgs a)
+{
+    constexpr uint32_t NH = R1 / 2, kF = 6 * R1 * R1, kStage = 256 * R1, SBO = 16 * R1;
+    constexpr uint32_t kCols = tc_cols_ncols(R1), kBiasA = 4096, kBiasB = 48 * R1;
+    extern __shared__ __align__(128) uint8_t sm[];
+    uint8_t *fs = sm, *as = sm + kF, *ba = sm + kF + 2 * kStage, *bb = ba + kBiasA;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(bb + kBiasB);  // a_full[2] a_empty[2] d_full[2] d_empty[2]
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 8);
+    volatile uint32_t *abort_flag = tslot + 1;
+    const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31u;
+    const uint32_t cb = blockIdx.x % kTcColBlocks, v0 = blockIdx.x / kTcColBlocks;
+    if (tid == 0) {
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(smem_u32(&bars[i]), 128);      // the four operand warps
+            mbar_init(smem_u32(&bars[2 + i]), 1);    // tcgen05.commit
+            mbar_init(smem_u32(&bars[4 + i]), 1);    // tcgen05.commit
+            mbar_init(smem_u32(&bars[6 + i]), 256);  // the eight epilogue warps of the half
+        }
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    for (uint32_t i = tid; i < kF / 16; i += blockDim.x) reinterpret_cast<uint4 *>(fs)[i] = __ldg(a.fimg + i);
+    // constant tiles (K = 16, K-major, core matrices of 8 rows x 16 bytes):
+    // column 0 is 256 (rows of A) and 32768 (rows of B), the rest 0
+    for (uint32_t i = tid; i < (kBiasA + kBiasB) / 16; i += blockDim.x) reinterpret_cast<uint4 *>(ba)[i] = make_uint4(0, 0, 0, 0);
+    __syncthreads();
+    if (tid < 128) *reinterpret_cast<uint16_t *>(ba + (tid >> 3) * 256 + (tid & 7) * 16) = kHalf256;
+    if (tid < 3 * NH) *reinterpret_cast<uint16_t *>(bb + (tid >> 3) * 256 + (tid & 7) * 16) = kHalf32768;
+    fence_async_smem();
+    if (warp == 0) {
+        tmem_alloc(smem_u32(tslot), kCols);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // descriptors advance by 256 bytes (16 in the address field) per
+            // K step; the address field does not overflow (shared memory < 256 KB)
+            const uint32_t idesc = tc_idesc_mn(128, 3 * NH);
+            const uint64_t ad0 = smem_desc(smem_u32(as), 128, SBO), fd0 = smem_desc(smem_u32(fs), 128, SBO);
+            const uint64_t bad = smem_desc(smem_u32(ba), 128, 256), bbd = smem_desc(smem_u32(bb), 128, 256);
+            int64_t last = -1;  // last tile whose multiplies were committed
+            uint32_t i = 0;
+            for (uint32_t v = v0; v < a.npieces; v += a.g, ++i) {
+                const uint32_t s = i & 1u;
+                if (!mbar_wait(smem_u32(&bars[s]), (i >> 1) & 1u)) { *abort_flag = 1; break; }
+                bool ok = true;
+                for (uint32_t h = 0; h < 2 && ok; ++h) {
+                    if (i >= 1 && !mbar_wait(smem_u32(&bars[6 + h]), (i - 1) & 1u)) { ok = false; break; }
+                    tc_fence_after();
+                    // the three slices of half h are rows 3 h NH .. 3 h NH + 3 NH - 1 of
+                    // the F image: one multiply with N = 3 NH gives all three sums
+                    uint64_t ad = ad0 + ((s * kStage) >> 4), bd = fd0 + ((3 * h * NH / 8 * SBO) >> 4);
+                    tc_mma_f16(tmem + 3 * h * NH, bad, bbd, idesc, 0u);  // 2^23 everywhere
+                    for (uint32_t ks = 0; ks < a.k16; ++ks) {
+                        tc_mma_f16(tmem + 3 * h * NH, ad, bd, idesc, 1u);
+                        ad += 16;
+                        bd += 16;
+                    }
+                    tc_commit(smem_u32(&bars[4 + h]));
+                }
+                tc_commit(smem_u32(&bars[2 + s]));
+                last = i;
+                if (!ok) { *abort_flag = 1; break; }
+            }
+            // the stage barrier of the last commit arrives once every multiply is done
+            if (last >= 0) mbar_wait(smem_u32(&bars[2 + (last & 1)]), (uint32_t)(last >> 1) & 1u);
+        }
+        __syncwarp();
+    } else if (warp <= 4) {
+        constexpr uint32_t RB = R1 / 32;  // 32-row blocks
+        const uint32_t wc = warp - 1, m = 32 * wc + lane;  // this lane's tile column (row m of A)
+        const uint32_t c0 = cb * kTcColsTile + 32 * wc, nrb = (16 * a.k16 + 31) / 32;
+        // source words of the pieces two tiles ahead are in flight while a
+        // stage is built (lane: row 32 u + lane of this warp's 32 columns)
+        uint32_t wa0[RB], wb0[RB], wa1[RB], wb1[RB];
+        auto fetch = [&](uint32_t v, uint32_t (&wa)[RB], uint32_t (&wb)[RB]) {
+            if (v >= a.npieces) return;
+            uint32_t lim;
+            const uint32_t *src = piece_src(a.bits, a.pc, v, lim);
+#pragma unroll
+            for (uint32_t u = 0; u < RB; ++u)
+                if (u < nrb) row_fetch<kReversed>(src, a.pc.len, lim, (32 * u + lane) * kR2 + c0, wa[u], wb[u]);
+        };
+        // build stage i & 1 from piece v; false when a wait gave up
+        auto build = [&](uint32_t v, uint32_t i, const uint32_t (&wa)[RB], const uint32_t (&wb)[RB]) -> bool {
+            const uint32_t s = i & 1u;
+            if (i >= 2 && !__all_sync(~0u, mbar_wait(smem_u32(&bars[2 + s]), ((i >> 1) - 1) & 1u))) return false;
+            uint32_t lim;
+            piece_src(a.bits, a.pc, v, lim);
+            uint8_t *st = as + s * kStage + (m >> 3) * SBO + (m & 7u) * 16;
+#pragma unroll
+            for (uint32_t u = 0; u < RB; ++u) {
+                if (u >= nrb) break;
+                const uint32_t t0 = (32 * u + lane) * kR2 + c0;
+                // lane = row 32 u + lane -> lane = column c0 + lane, bit i = row 32 u + i
+                const uint32_t x = transpose32(row_finish<kReversed>(a.pc.len, lim, t0, wa[u], wb[u]), lane);
+#pragma unroll
+                for (uint32_t q = 0; q < 4; ++q) {
+                    const uint32_t y = x >> (8 * q);
+                    *reinterpret_cast<uint4 *>(st + (4 * u + q) * 128) =
+                        make_uint4(two_halves(y), two_halves(y >> 2), two_halves(y >> 4), two_halves(y >> 6));
+                }
+            }
+            fence_async_smem();  // the stage's generic writes, visible to the tensor core
+            mbar_arrive(smem_u32(&bars[s]));
+            return true;
+        };
+        fetch(v0, wa0, wb0);
+        fetch(v0 + a.g, wa1, wb1);
+        uint32_t i = 0;
+        for (uint32_t v = v0; v < a.npieces;) {
+            if (!build(v, i, wa0, wb0)) { *abort_flag = 1; break; }
+            fetch(v + 2 * a.g, wa0, wb0);
+            v += a.g;
+            ++i;
+            if (v >= a.npieces) break;
+            if (!build(v, i, wa1, wb1)) { *abort_flag = 1; break; }
+            fetch(v + 2 * a.g, wa1, wb1);
+            v += a.g;
+            ++i;
+        }
+    } else {
+        constexpr uint32_t NQ = NH / 2;  // rows per epilogue warp
+        const uint32_t e = warp - 5, h = e >> 3, q = warp & 3u, r0 = h * NH + ((e >> 2) & 1u) * NQ;
+        const uint32_t tl = tmem + ((32u * q) << 16) + 3 * h * NH + (r0 - h * NH);
+        const uint32_t t2 = cb * kTcColsTile + 32 * q + lane;
+        uint32_t tw[NQ];  // twists of rows r0 .. r0 + NQ - 1 in this lane's column
+#pragma unroll
+        for (uint32_t j = 0; j < NQ; ++j) tw[j] = __ldg(a.twt + (size_t)(r0 + j) * kR2 + t2);
+        uint32_t i = 0;
+        for (uint32_t v = v0; v < a.npieces; v += a.g, ++i) {
+            if (!__all_sync(~0u, mbar_wait(smem_u32(&bars[4 + h]), i & 1u))) {
+                *abort_flag = 1;
+                break;
+            }
+            tc_fence_after();
+            uint32_t *o = a.buf + (size_t)v * a.N + (size_t)r0 * kR2 + t2;
+#pragma unroll
+            for (uint32_t rc = 0; rc < NQ; rc += 8) {
+                uint32_t s0[8], s1[8], s2[8];  // f32 bits of 2^23 + S: S in the low bits
+                tmem_ld8(tl + rc, s0);
+                tmem_ld8(tl + NH + rc, s1);
+                tmem_ld8(tl + 2 * NH + rc, s2);
+                tmem_wait_ld();
+#pragma unroll
+                for (uint32_t j = 0; j < 8; ++j) {
+                    // F_0 x + 2^11 F_1 x + (2^22 F_2 x mod p) < 2^18 + 2^29 + 2p < 4p
+                    const uint32_t val = s0[j] + (s1[j] << 11) + shoup_lazy(s2[j] - kF32Int, 1u << 22, kQ22) - kJoin;
+                    o[(size_t)(rc + j) * kR2] = mont_lazy(val, tw[rc + j]);
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(smem_u32(&bars[6 + h]));
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (*abort_flag && tid == 0) atomicOr(a.err, 1u);
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, kCols);
+    }
+}
+
+// Transposed twist table for the tensor-core pass A: twt[r R2 + t2] =
+// w_N^(bitrev(r) t2), Montgomery form.
+__global__ void ntt_twist_t_kernel(uint32_t *twt, uint32_t R1, int r1_log, Tables T)
+{
+    const uint32_t total = R1 * kR2;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x)
+        twt[i] = twist_mont(T.tw_lo_f, T.tw_hi_f, bitrev(i / kR2, r1_log) * (i % kR2));
+}
+
 // ---- host side -----------------------------------------------------------
 uint32_t powmod(uint64_t b, uint64_t e)
 {
@@ -960,6 +1240,20 @@ uint32_t powmod(uint64_t b, uint64_t e)
 }
 uint32_t shoup_q(uint32_t w) { return (uint32_t)(((uint64_t)w << 32) / kP); }
 uint32_t to_mont(uint32_t w) { return (uint32_t)(((uint64_t)w << 32) % kP); }
+uint32_t host_bitrev(uint32_t x, int bits)
+{
+    uint32_t r = 0;
+    for (int i = 0; i < bits; ++i) r |= ((x >> i) & 1u) << (bits - 1 - i);
+    return r;
+}
+// f16 bits of an integer 0 <= v < 2048 (exact: at most 11 significant bits)
+uint16_t half_of_int(uint32_t v)
+{
+    if (!v) return 0;
+    int e = 0;
+    while ((v >> (e + 1)) != 0) ++e;
+    return (uint16_t)(((uint32_t)(e + 15) << 10) | ((v << (10 - e)) & 0x3ffu));
+}
 
 }  // namespace
 
@@ -977,6 +1271,12 @@ struct NttPlan {
     uint64_t seed_stride = 0;
     uint32_t L = 0;                  // bits per seed (s + k - 1)
     Tables T{};
+    // tensor-core pass A (R1 in {32, 64, 128}): transposed twist (N words),
+    // then F's slices in the shared-memory layout (6 R1^2 bytes)
+    bool tc_cols = false;
+    uint32_t *tc_mem = nullptr;
+    uint32_t sms = 0;
+    uint32_t *err = nullptr;  // device word: a tensor-core wait gave up
 };
 
 namespace {
@@ -986,10 +1286,43 @@ namespace {
 size_t smem_generic(uint32_t R1) { return (size_t)R1 * (kCS + 1) * 4; }         // R1 < 32 kernels
 size_t smem_transposed(uint32_t R1) { return ((size_t)kCW * (R1 + 1) + R1) * 4; }  // R1 >= 1024 kernels
 
+// The tensor-core pass A for the g * pc.P pieces of g source rows.
+int ntt_launch_a_tc(const NttPlan *p, const uint32_t *bits, const Pieces &pc, bool reversed, uint32_t g,
+                    uint32_t *dst, cudaStream_t st)
+{
+    const uint32_t R1 = p->R1;
+    const uint64_t pieces = (uint64_t)g * pc.P;
+    if (pieces >= (1ull << 31)) return set_error(EXTRACT_EINTERNAL, "ntt: %llu pieces", (unsigned long long)pieces);
+    TcColsArgs a{};
+    a.bits = bits;
+    a.pc = pc;
+    a.N = p->N;
+    a.npieces = (uint32_t)pieces;
+    a.g = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(p->sms / kTcColBlocks, pieces));
+    a.k16 = (uint32_t)std::min<uint64_t>(R1 / 16, std::max<uint64_t>(1, ceil_div(pc.len, 16ull * kR2)));
+    a.twt = p->tc_mem;
+    a.fimg = reinterpret_cast<const uint4 *>(p->tc_mem + p->N);
+    a.buf = dst;
+    a.err = p->err;
+    const uint32_t grid = a.g * kTcColBlocks;
+#define EX_TC_COLS(R)                                                                                       \
+    if (R1 == R) {                                                                                          \
+        if (reversed) ntt_cols_fwd_tc_kernel<R, true><<<grid, kTcColsThreads, tc_cols_smem(R), st>>>(a);    \
+        else ntt_cols_fwd_tc_kernel<R, false><<<grid, kTcColsThreads, tc_cols_smem(R), st>>>(a);            \
+        return EXTRACT_OK;                                                                                  \
+    }
+    EX_TC_COLS(32)
+    EX_TC_COLS(64)
+    EX_TC_COLS(128)
+#undef EX_TC_COLS
+    return set_error(EXTRACT_EINTERNAL, "ntt: no tensor-core column kernel for R1=%u", R1);
+}
+
 // pass A for the g * pc.P pieces of g source rows into dst (N words each)
 int ntt_launch_a(const NttPlan *p, const uint32_t *bits, const Pieces &pc, bool reversed, uint32_t g, uint32_t *dst,
                  cudaStream_t st)
 {
+    if (p->tc_cols) return ntt_launch_a_tc(p, bits, pc, reversed, g, dst, st);
     const dim3 grid(kR2 / kCW, g * pc.P);
     const uint32_t R1 = p->R1;
     if (R1 < 32) {
@@ -1137,6 +1470,7 @@ void ntt_destroy_async(NttPlan *p, cudaStream_t st)
     if (p->Sq) cudaFreeAsync(p->Sq, st);
     if (p->tables) cudaFreeAsync(p->tables, st);
     if (p->twist) cudaFreeAsync(p->twist, st);
+    if (p->tc_mem) cudaFreeAsync(p->tc_mem, st);
     delete p;
 }
 
@@ -1148,6 +1482,7 @@ void ntt_destroy(NttPlan *p)
     cudaFree(p->Sq);
     cudaFree(p->tables);
     cudaFree(p->twist);
+    cudaFree(p->tc_mem);
     delete p;
 }
 
@@ -1229,6 +1564,13 @@ static int device_setup(cudaStream_t st)
     EX_SET_SMEM(64, ntt_cols_fwd_t_kernel, ntt_cols_inv_t_kernel, smem_transposed(2048))
 #undef EX_SET_SMEM
 #undef EX_SET_SMEM_M
+#define EX_SET_SMEM_TC(R)                                                         \
+    attr((const void *)ntt_cols_fwd_tc_kernel<R, true>, tc_cols_smem(R));  \
+    attr((const void *)ntt_cols_fwd_tc_kernel<R, false>, tc_cols_smem(R));
+    EX_SET_SMEM_TC(32)
+    EX_SET_SMEM_TC(64)
+    EX_SET_SMEM_TC(128)
+#undef EX_SET_SMEM_TC
     if (e != cudaSuccess) return cuda_error(e, "ntt smem attribute");
     uint2 lf[31], li[31];
     for (uint32_t hh = 1; hh <= 16; hh <<= 1) {
@@ -1326,6 +1668,8 @@ int ntt_create(NttPlan **out, uint32_t m, uint32_t s, uint32_t k, const uint32_t
         const uint32_t w2 = powmod(w, kR2);
         for (uint32_t x = 0; x < std::max<uint32_t>(1, R1); ++x) h.push_back(to_mont(powmod(w2, x)));
     }
+    const size_t o_err = h.size();
+    h.push_back(0);
     int rc = EXTRACT_OK;
     do {
         cudaError_t e;
@@ -1333,6 +1677,7 @@ int ntt_create(NttPlan **out, uint32_t m, uint32_t s, uint32_t k, const uint32_t
         if ((e = cudaMemcpyAsync(p->tables, h.data(), h.size() * 4, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
             (e = cudaStreamSynchronize(st)) != cudaSuccess) { rc = cuda_error(e, "ntt tables copy"); break; }
         const uint32_t *t = p->tables;
+        p->err = p->tables + o_err;
         p->T.col_f = t + o_col_f; p->T.col_fq = t + o_col_f + ch;
         p->T.col_i = t + o_col_i; p->T.col_iq = t + o_col_i + ch;
         p->T.row_f = t + o_row_f; p->T.row_fq = t + o_row_f + kR2 / 2;
@@ -1368,6 +1713,43 @@ int ntt_create(NttPlan **out, uint32_t m, uint32_t s, uint32_t k, const uint32_t
         } else if (per_block) {
             rc = set_error(EXTRACT_EINVAL, "independent seeds need N >= 2^16");
             break;
+        }
+        if (EX_NTT_TC_COLS && (R1 == 32 || R1 == 64 || R1 == 128)) {
+            // F's three 11-bit slices as f16 in the layout of the kernel's
+            // shared memory: row r of slice l is image row n = (3 h + l) R1/2
+            // + r - h R1/2 for the half h = r / (R1/2) it falls in (the three
+            // slices of a half are consecutive rows, one multiply's N), at
+            // byte (n / 8) 16 R1 + (kk / 8) 128 + (n % 8) 16 + (kk % 8) 2 for
+            // column kk = t1
+            const size_t fwords = (size_t)3 * R1 * R1 / 2;
+            std::vector<uint16_t> img((size_t)3 * R1 * R1);
+            const uint32_t wr = powmod(kGen, (kP - 1) / R1);
+            const uint32_t NH = R1 / 2;
+            for (uint32_t r = 0; r < R1; ++r) {
+                const uint64_t K = host_bitrev(r, p->r1_log);
+                const uint32_t h = r / NH;
+                for (uint32_t kk = 0; kk < R1; ++kk) {
+                    const uint32_t f = powmod(wr, K * kk % R1);
+                    for (uint32_t l = 0; l < 3; ++l) {
+                        const uint32_t n = (3 * h + l) * NH + (r - h * NH);
+                        const size_t byte = (size_t)(n >> 3) * 16 * R1 + (kk >> 3) * 128 + (n & 7) * 16 + (kk & 7) * 2;
+                        img[byte / 2] = half_of_int((f >> (11 * l)) & 2047u);
+                    }
+                }
+            }
+            int dev = 0, sms = 0;
+            if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
+                (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
+                (e = cudaMallocAsync(&p->tc_mem, ((size_t)p->N + fwords) * 4, st)) != cudaSuccess ||
+                (e = cudaMemcpyAsync(p->tc_mem + p->N, img.data(), fwords * 4, cudaMemcpyHostToDevice, st)) !=
+                    cudaSuccess) {
+                rc = cuda_error(e, "ntt tensor-core tables");
+                break;
+            }
+            ntt_twist_t_kernel<<<(uint32_t)std::min<uint64_t>(ceil_div(p->N, 256), 8192), 256, 0, st>>>(
+                p->tc_mem, R1, p->r1_log, p->T);
+            p->sms = (uint32_t)sms;
+            p->tc_cols = true;
         }
         if ((rc = device_setup(st)) != EXTRACT_OK) break;
         if (per_block && resident_spectra) {
@@ -1534,6 +1916,19 @@ uint64_t ntt_resident_spectra_words(uint32_t m, uint32_t s, uint32_t k, int spli
     return (uint64_t)m * sh.P * sh.N;
 }
 uint32_t ntt_size(const NttPlan *p) { return p->N; }
+bool ntt_uses_tensor_cores(const NttPlan *p) { return p->tc_cols; }
+uint32_t *ntt_error_word(const NttPlan *p) { return p ? p->err : nullptr; }
+
+int ntt_status(const NttPlan *p)
+{
+    if (!p || !p->err) return EXTRACT_OK;
+    uint32_t v = 0;
+    EX_CUDA(cudaDeviceSynchronize());
+    EX_CUDA(cudaMemcpy(&v, p->err, 4, cudaMemcpyDeviceToHost));
+    if (!v) return EXTRACT_OK;
+    EX_CUDA(cudaMemset(p->err, 0, 4));
+    return set_error(EXTRACT_ETIMEDOUT, "a tensor-core NTT pass gave up waiting for its multiplies");
+}
 uint32_t ntt_pieces(const NttPlan *p) { return p->P; }
 
 }  // namespace ex

@@ -292,8 +292,9 @@ bool schedule_step(extract_server *S)
                 if (e == cudaSuccess) {
                     finished = true;
                     uint32_t err = 0;  // a tensor-core kernel that gave up on a wait fails its job
-                    if (j->use_tc && cudaMemcpy(&err, S->d_err, 4, cudaMemcpyDeviceToHost) == cudaSuccess && err) {
-                        cudaMemset(S->d_err, 0, 4);
+                    uint32_t *ew = j->use_tc ? S->d_err : j->ntt ? ntt_error_word(j->ntt) : nullptr;
+                    if (ew && cudaMemcpy(&err, ew, 4, cudaMemcpyDeviceToHost) == cudaSuccess && err) {
+                        cudaMemset(ew, 0, 4);
                         j->rc = set_error(EXTRACT_ETIMEDOUT, "a tensor-core hash kernel gave up waiting");
                         j->state = kFailed;
                         finished = false;

@@ -31,6 +31,7 @@
 // tensor memory and returns.
 #include "common.cuh"
 #include "internal.h"
+#include "tcgen05.cuh"
 
 #include <algorithm>
 #include <mutex>
@@ -44,98 +45,10 @@ constexpr uint32_t kTcThreads = 256;
 constexpr uint32_t kTcMaxN = 256;              // sub-blocks per tile
 constexpr uint32_t kTcStageA = kTcM * kTcKB;   // 16 KB of Toeplitz rows per stage
 constexpr uint32_t kE4M3One = 0x38u;           // 1.0 in e4m3
-constexpr long long kWaitCycles = 2000000000;  // about a second at the SM clock
-constexpr uint32_t kSmemPerSM = 233472;        // shared memory of one SM (228 KB)
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// Waits for the phase of the given parity to complete; false after about a
-// second without it.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
-{
-    const long long t0 = clock64();
-    while (!mbar_try_wait(bar, parity))
-        if (clock64() - t0 > kWaitCycles) return false;
-    return true;
-}
-
-__device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols)
-{
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem), "r"(ncols)
-                 : "memory");
-}
-__device__ __forceinline__ void tmem_relinquish()
-{
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
-{
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
-}
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
-// D (tensor memory) (+)= A . B^T for one K = 32 step
-__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t accum)
-{
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
-        : "memory");
-}
-// arrive on the mbarrier once every earlier tcgen05.mma of this thread is done
-__device__ __forceinline__ void tc_commit(uint32_t bar)
-{
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-                 : "memory");
-}
-
-// 32 consecutive 32-bit columns of this thread's tensor-memory lane
-#define EX_R(i) "=r"(v[i])
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32])
-{
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-        : EX_R(0), EX_R(1), EX_R(2), EX_R(3), EX_R(4), EX_R(5), EX_R(6), EX_R(7), EX_R(8), EX_R(9), EX_R(10),
-          EX_R(11), EX_R(12), EX_R(13), EX_R(14), EX_R(15), EX_R(16), EX_R(17), EX_R(18), EX_R(19), EX_R(20),
-          EX_R(21), EX_R(22), EX_R(23), EX_R(24), EX_R(25), EX_R(26), EX_R(27), EX_R(28), EX_R(29), EX_R(30),
-          EX_R(31)
-        : "r"(taddr));
-}
-#undef EX_R
-__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-
-// Shared-memory matrix descriptor: K-major, no swizzle; LBO = byte distance
-// between core matrices along K, SBO = between groups of 8 rows; version 1.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
-{
-    return (uint64_t)((addr >> 4) & 0x3fffu) | ((uint64_t)((lbo >> 4) & 0x3fffu) << 16) |
-           ((uint64_t)((sbo >> 4) & 0x3fffu) << 32) | (1ull << 46);
-}
 
 // Instruction descriptor of kind::f8f6f4: f32 accumulator, A and B e4m3,
 // both K-major, N = nt, M = 128.
-__host__ __device__ constexpr uint32_t tc_idesc(uint32_t nt)
-{
-    return (1u << 4) | ((nt >> 3) << 17) | ((kTcM >> 4) << 24);
-}
+__host__ __device__ constexpr uint32_t tc_idesc(uint32_t nt) { return tc_idesc_mn(kTcM, nt); }
 
 // 16 bits -> 16 e4m3 bytes (byte t = 1.0 when bit t is set, else 0)
 __device__ __forceinline__ uint4 expand16(uint32_t b)
