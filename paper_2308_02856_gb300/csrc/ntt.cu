@@ -17,7 +17,9 @@
 //
 // Four-step layout, N = R1 x R2 with R2 = 2048 (element t = t1 R2 + t2):
 //   pass A  (columns t2 of one piece per CTA): load the bits, R1-point DIF
-//           NTT along t1, multiply by w_N^(k1 t2);
+//           NTT along t1, multiply by w_N^(k1 t2); for R1 = 32, 64, 128 the
+//           column DFTs of the bits run on the tensor cores instead, as an
+//           exact integer GEMM (ntt_cols_fwd_tc_kernel);
 //   pass B  (two warps per row): 2048-point DIF NTT of each piece's row,
 //           multiply by that piece's seed spectrum (laid out the same way,
 //           1/N folded in), sum over pieces, 2048-point inverse DIT NTT;
@@ -602,12 +604,36 @@ __device__ __forceinline__ void row_dit_store(uint32_t (&e)[32], uint32_t *x, ui
 // kPerBlock: the spectra are per sub-block (independent seeds), transformed
 // in the same run: piece q of sub-block g uses S + (g P + q) N, without
 // quotients (Montgomery products).
+// The distance-1024 DIF stage of a row held in shared memory (xs): warp 0
+// keeps the sums, warp 1 the twisted differences (layout A, [0, 2p)).
+__device__ __forceinline__ void row_first_stage(uint32_t (&e)[32], const uint32_t *xs, const Tables &T, int lane,
+                                                int w)
+{
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+        const uint32_t pos = 32u * j + lane;
+        const uint32_t a = xs[pos], b = xs[pos + 1024];
+        if (w == 0) {
+            e[j] = red2p(a + b);
+        } else {
+            const uint2 tw = __ldg(T.row_stage_f + 1023 + pos);
+            e[j] = shoup_lazy(a - b + k2P, tw.x, tw.y);
+        }
+    }
+}
+
+// kMulti (the P-piece inverse form): each piece's row comes into shared
+// memory by one bulk copy, issued while the previous piece is transformed;
+// a copy that does not land within about a second sets *err and the row is
+// left unwritten.
 template <bool kInverse, bool kMulti, bool kPerBlock = false>
 __global__ void __launch_bounds__(64, kMulti ? 10 : 12)
 ntt_rows_kernel(uint32_t *__restrict__ buf, uint32_t N, uint32_t R1, uint32_t P, const uint32_t *__restrict__ S,
-                const uint32_t *__restrict__ Sq, Tables T)
+                const uint32_t *__restrict__ Sq, Tables T, uint32_t *err)
 {
     __shared__ __align__(16) uint32_t sw[2][1024];
+    __shared__ __align__(16) uint32_t xs[kInverse && kMulti ? kR2 : 4];
+    __shared__ uint64_t xbar;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const uint32_t row = blockIdx.x, g = row / R1, r = row % R1;
     uint32_t *x = buf + (size_t)g * P * N + (size_t)r * kR2;
@@ -638,11 +664,31 @@ ntt_rows_kernel(uint32_t *__restrict__ buf, uint32_t N, uint32_t R1, uint32_t P,
     uint32_t acc[32];
 #pragma unroll
     for (int i = 0; i < 32; ++i) acc[i] = 0;
+    const uint32_t xb = smem_u32(xs), mb = smem_u32(&xbar);
+    if (threadIdx.x == 0) {
+        mbar_init(mb, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        bulk_load(xb, x, kR2 * 4, mb);
+    }
+    __syncthreads();
+    uint32_t q = 0;
 #pragma unroll 1
-    for (uint32_t q = 0; q < P; ++q) {
-        row_dif<true>(e, x + (size_t)q * N, sw[w], T, lane, w);
+    for (; q < P; ++q) {
+        if (!__syncthreads_and(mbar_wait(mb, q & 1u))) break;  // the same view in both warps
+        row_first_stage(e, xs, T, lane, w);
+        __syncthreads();  // both warps have read the row: the next piece's copy may land
+        if (threadIdx.x == 0 && q + 1 < P) bulk_load(xb, x + (size_t)(q + 1) * N, kR2 * 4, mb);
+        dif_warp_t<32, 16, false, true>(e, sw[w], T.row_stage_f, lane);
         if (kMont) row_mul_mont<true>(e, acc, Sb + (size_t)q * N + so);
         else row_mul<true>(e, acc, S + (size_t)q * N + so, Sq + (size_t)q * N + so);
+    }
+    if (q < P) {
+        // no copy may still be landing in shared memory when the CTA exits
+        if (threadIdx.x == 0) {
+            atomicOr(err, 1u);
+            mbar_wait(mb, q & 1u);
+        }
+        return;
     }
     row_dit_store(acc, x, sw, T, lane, w);
 }
@@ -1373,11 +1419,12 @@ void ntt_launch_rows(const NttPlan *p, uint32_t *dst, uint32_t g, uint32_t P, co
                      bool inverse, cudaStream_t st, bool per_block = false)
 {
     const uint32_t rows = p->R1 * g;
-    if (!inverse) ntt_rows_kernel<false, false><<<rows, 64, 0, st>>>(dst, p->N, p->R1, 1, S, Sq, p->T);
-    else if (per_block && P == 1) ntt_rows_kernel<true, false, true><<<rows, 64, 0, st>>>(dst, p->N, p->R1, 1, S, Sq, p->T);
-    else if (per_block) ntt_rows_kernel<true, true, true><<<rows, 64, 0, st>>>(dst, p->N, p->R1, P, S, Sq, p->T);
-    else if (P == 1) ntt_rows_kernel<true, false><<<rows, 64, 0, st>>>(dst, p->N, p->R1, 1, S, Sq, p->T);
-    else ntt_rows_kernel<true, true><<<rows, 64, 0, st>>>(dst, p->N, p->R1, P, S, Sq, p->T);
+    uint32_t *e = p->err;
+    if (!inverse) ntt_rows_kernel<false, false><<<rows, 64, 0, st>>>(dst, p->N, p->R1, 1, S, Sq, p->T, e);
+    else if (per_block && P == 1) ntt_rows_kernel<true, false, true><<<rows, 64, 0, st>>>(dst, p->N, p->R1, 1, S, Sq, p->T, e);
+    else if (per_block) ntt_rows_kernel<true, true, true><<<rows, 64, 0, st>>>(dst, p->N, p->R1, P, S, Sq, p->T, e);
+    else if (P == 1) ntt_rows_kernel<true, false><<<rows, 64, 0, st>>>(dst, p->N, p->R1, 1, S, Sq, p->T, e);
+    else ntt_rows_kernel<true, true><<<rows, 64, 0, st>>>(dst, p->N, p->R1, P, S, Sq, p->T, e);
 }
 
 // pass A' for g sub-blocks of buf (P N words apart), output bits of

@@ -1,7 +1,7 @@
-// Fifth-generation tensor-core primitives (sm_103a inline PTX) shared by the
-// tensor-core hash (tc_hash.cu) and the tensor-core column pass of the NTT
-// (ntt.cu): mbarriers with bounded waits, tensor-memory allocation and
-// loads, shared-memory matrix descriptors and tcgen05.mma.
+// Fifth-generation tensor-core and asynchronous-copy primitives (sm_103a
+// inline PTX) shared by the tensor-core hash (tc_hash.cu) and the NTT
+// (ntt.cu): mbarriers with bounded waits, bulk copies, tensor-memory
+// allocation and loads, shared-memory matrix descriptors and tcgen05.mma.
 #pragma once
 
 #include <cstdint>
@@ -78,6 +78,20 @@ __device__ __forceinline__ void tc_mma_f16(uint32_t d_tmem, uint64_t adesc, uint
         "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
         : "memory");
 }
+// One bulk copy of `bytes` bytes (a multiple of 16; both addresses 16-byte
+// aligned) from global to shared memory; the mbarrier's phase completes when
+// they have landed (this thread's arrival carries the expected byte count).
+__device__ __forceinline__ void bulk_load(uint32_t dst_smem, const void *src, uint32_t bytes, uint32_t bar)
+{
+    asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(bar),
+                 "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     dst_smem),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
 // arrive on the mbarrier once every earlier tcgen05.mma of this thread is done
 __device__ __forceinline__ void tc_commit(uint32_t bar)
 {
