@@ -676,6 +676,12 @@ ntt_rows_kernel(uint32_t *__restrict__ buf, uint32_t N, uint32_t R1, uint32_t P,
     for (; q < P; ++q) {
         if (!__syncthreads_and(mbar_wait(mb, q & 1u))) break;  // the same view in both warps
         row_first_stage(e, xs, T, lane, w);
+        // the next piece's copy overwrites the row through the async proxy: every
+        // load of it must have returned first (a barrier alone does not wait for
+        // loads in flight), and the reads are ordered before the copy's writes
+#pragma unroll
+        for (int j = 0; j < 32; ++j) asm volatile("" ::"r"(e[j]));
+        fence_async_smem();
         __syncthreads();  // both warps have read the row: the next piece's copy may land
         if (threadIdx.x == 0 && q + 1 < P) bulk_load(xb, x + (size_t)(q + 1) * N, kR2 * 4, mb);
         dif_warp_t<32, 16, false, true>(e, sw[w], T.row_stage_f, lane);

@@ -88,3 +88,27 @@ def test_qkd_shaped_block_n2e32():
     whole sub-blocks."""
     _full_size_case(1 << 32, 4096, 1 << 20, 104858, 0.9, (0, 1, 100, 101, -2, -1), (7, 1603, 2000, 3000, 3228),
                     ("ntt: N=262144", "P=7 ", "gather=buckets (2^18-bit"), 16)
+
+
+@pytest.mark.parametrize("n,m,s,k", [
+    (1 << 32, 4096, 1 << 20, 104858),   # P = 7, N = 2^18: tensor-core pass A, bulk-copied rows in pass B
+    (1 << 30, 1024, 1 << 20, 1 << 19),  # P = 2, N = 2^20
+])
+def test_repeated_runs_are_bit_identical(n, m, s, k):
+    """Races show up as outputs that change from run to run on the same input
+    (a rare one slips past sampled parity checks): twelve hashes of one
+    gathered block and three whole runs must all give the same words."""
+    import hashlib
+    in_w = synth.bernoulli_bits_device(n, 0.8, 5)
+    seed = synth.uniform_bits(s + k - 1, 6)
+    with X.Extractor(n, m, s, k, seed, 2) as ex:
+        out = ex.new_output()
+        digests = set()
+        for _ in range(3):
+            ex.run(in_w, out)
+            digests.add(hashlib.sha256(out.cpu().numpy().tobytes()).hexdigest())
+        for _ in range(12):
+            ex.hash(out)
+            digests.add(hashlib.sha256(out.cpu().numpy().tobytes()).hexdigest())
+        ex.status()
+    assert len(digests) == 1, "%d different outputs from 15 runs on one input" % len(digests)
