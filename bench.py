@@ -351,7 +351,11 @@ def ntt_roofline(n, m, s, k, hash_ms, plan, sms=152, workload=None):
                                                             ", seed windows transformed per run"
                                                             if transforms == 2 * P + 1 else ""),
             "peak_basis": "%d SMs x 64 ALU lanes / 4 ALU ops per lazy butterfly x %.0f MHz" % (sms, SM_MAX_MHZ),
-            "note": "does %.0fx less work than the direct m*k*s product" % ((m * k * s / 32.0) / bfly)}
+            "note": "does %.0fx less work than the direct m*k*s product%s" % (
+                (m * k * s / 32.0) / bfly,
+                "; the column transforms of pass A (%d of the %d butterfly levels of each forward transform) run "
+                "on the tensor cores as an exact GEMM, so the figure counts transform work, not ALU instructions"
+                % (int(math.log2(N)) - 11, int(math.log2(N))) if "on the tensor cores" in plan else "")}
 
 
 def tc_roofline(m, k, s, hash_ms, peaks):

@@ -52,6 +52,11 @@ CASES = [
     (2 * 250_000, 2, 250_000, 12_000, 0),       # N = 2^18, 8 K steps (all)
     (1 << 21, 2, 1 << 20, 104_858, 3),          # the QKD sub-block shape in 8 pieces: N = 2^18
     (1 << 21, 2, 1 << 20, 104_858, None),       # ... in the library's 7 pieces of 149824 bits
+    # more pieces than 9 per 128-column block: CTAs take several pieces, so the
+    # accumulator buffers are reused (each row group's phase parities)
+    (1 << 20, 32, 1 << 15, 1 << 13, None),      # N = 2^16, 32 pieces
+    (20 * 70_001, 20, 70_001, 9_999, 0),        # N = 2^17, 20 pieces
+    (48 * 150_001, 48, 150_001, 10_000, 0),     # N = 2^18, 48 pieces
 ]
 
 
