@@ -203,6 +203,25 @@ int extract_run(extract_ctx *h, void *stream, const uint32_t *in_bits_dev,
 int extract_run_host(extract_ctx *h, void *stream, const uint32_t *in_bits_host,
                      uint32_t *out_bits_host);
 
+/*
+ * extract_run_host_many - extract_run_host on `count` blocks in a row (a
+ * stream of blocks, as QKD and QRNG post-processing deliver them): block b's
+ * input comes from in_bits_host[b] (ceil(n/32) words) and its output goes to
+ * out_bits_host[b] (ceil(m*k/32) words); the two host arrays of pointers are
+ * read before the call returns.  The copies run on two internal streams of
+ * the context and overlap the work of the neighbouring blocks: block b+1's
+ * input goes up while block b is hashed, block b's output comes down while
+ * block b+1 is gathered and hashed.  Each block is gathered and hashed in
+ * order on `stream`, with the same results as extract_run_host one block at
+ * a time.  Returns once every output is in host memory.  Two device staging
+ * buffers each way are allocated on the first call and kept until
+ * extract_destroy.  Page-locked host buffers give full copy bandwidth and
+ * the overlap; calls on one context must not overlap.
+ * Errors: EINVAL (null pointers), ENOMEM, ECUDA.
+ */
+int extract_run_host_many(extract_ctx *h, void *stream, const uint32_t *const *in_bits_host,
+                          uint32_t *const *out_bits_host, uint32_t count);
+
 /* extract_gather - step 1's gather alone: fills the context's sub-block
    buffer from in_bits_dev (same contract as extract_run). */
 int extract_gather(extract_ctx *h, void *stream, const uint32_t *in_bits_dev);

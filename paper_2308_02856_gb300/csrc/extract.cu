@@ -91,6 +91,11 @@ struct extract_ctx {
     cudaEvent_t ev_copy0 = nullptr, ev_out_end = nullptr, ev_copy_done = nullptr;
     cudaEvent_t ev_piece[8] = {};
     std::vector<cudaEvent_t> ev_groups;
+    // extract_run_host_many: two staging buffers each way, copies in and out
+    // on their own streams; stage_in / stage_out serve as buffer 0
+    uint32_t *stage_in1 = nullptr, *stage_out1 = nullptr;
+    cudaStream_t copy_in_st = nullptr, copy_out_st = nullptr;
+    cudaEvent_t ev_many0 = nullptr, ev_in[2] = {}, ev_gathered[2] = {}, ev_hashed[2] = {}, ev_out[2] = {};
 };
 
 namespace {
@@ -123,6 +128,13 @@ void free_ctx(extract_ctx *h)
     cudaFree(h->dev_err);
     cudaFree(h->stage_in);
     cudaFree(h->stage_out);
+    cudaFree(h->stage_in1);
+    cudaFree(h->stage_out1);
+    for (cudaStream_t s : {h->copy_in_st, h->copy_out_st})
+        if (s) cudaStreamDestroy(s);
+    for (cudaEvent_t ev : {h->ev_many0, h->ev_in[0], h->ev_in[1], h->ev_gathered[0], h->ev_gathered[1],
+                           h->ev_hashed[0], h->ev_hashed[1], h->ev_out[0], h->ev_out[1]})
+        if (ev) cudaEventDestroy(ev);
     ntt_destroy(h->ntt);
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
     if (h->ev_group) cudaEventDestroy(h->ev_group);
@@ -451,6 +463,56 @@ int extract_run_host(extract_ctx *h, void *stream, const uint32_t *in_bits_host,
     EX_CUDA(cudaMemcpyAsync(h->stage_in, in_bits_host, in_bytes, cudaMemcpyHostToDevice, st));
     if (int rc = extract_run(h, stream, h->stage_in, h->stage_out)) return rc;
     EX_CUDA(cudaMemcpyAsync(out_bits_host, h->stage_out, out_bytes, cudaMemcpyDeviceToHost, st));
+    EX_CUDA(cudaStreamSynchronize(st));
+    return EXTRACT_OK;
+}
+
+int extract_run_host_many(extract_ctx *h, void *stream, const uint32_t *const *in_bits_host,
+                          uint32_t *const *out_bits_host, uint32_t count)
+{
+    if (int rc = check_ctx(h)) return rc;
+    if (!count) return EXTRACT_OK;
+    if (!in_bits_host || !out_bits_host) return set_error(EXTRACT_EINVAL, "null pointer array");
+    for (uint32_t b = 0; b < count; ++b)
+        if (!in_bits_host[b] || !out_bits_host[b]) return set_error(EXTRACT_EINVAL, "null host buffer %u", b);
+    const size_t in_bytes = ceil_div(h->n, 32) * 4, out_bytes = ceil_div((uint64_t)h->m * h->k, 32) * 4;
+    for (uint32_t **buf : {&h->stage_in, &h->stage_in1})
+        if (!*buf) EX_CUDA(cudaMalloc(buf, in_bytes ? in_bytes : 4));
+    for (uint32_t **buf : {&h->stage_out, &h->stage_out1})
+        if (!*buf) EX_CUDA(cudaMalloc(buf, out_bytes));
+    if (!h->copy_in_st) {
+        EX_CUDA(cudaStreamCreateWithFlags(&h->copy_in_st, cudaStreamNonBlocking));
+        EX_CUDA(cudaStreamCreateWithFlags(&h->copy_out_st, cudaStreamNonBlocking));
+        EX_CUDA(cudaEventCreateWithFlags(&h->ev_many0, cudaEventDisableTiming));
+        for (int i = 0; i < 2; ++i)
+            for (cudaEvent_t *ev : {&h->ev_in[i], &h->ev_gathered[i], &h->ev_hashed[i], &h->ev_out[i]})
+                EX_CUDA(cudaEventCreateWithFlags(ev, cudaEventDisableTiming));
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    uint32_t *const sin[2] = {h->stage_in, h->stage_in1};
+    uint32_t *const sout[2] = {h->stage_out, h->stage_out1};
+    EX_CUDA(cudaEventRecord(h->ev_many0, st));  // after the caller's earlier work on st
+    EX_CUDA(cudaStreamWaitEvent(h->copy_in_st, h->ev_many0, 0));
+    EX_CUDA(cudaStreamWaitEvent(h->copy_out_st, h->ev_many0, 0));
+    for (uint32_t b = 0; b < count; ++b) {
+        const int i = (int)(b & 1u);
+        // block b's input into staging buffer i once block b - 2's gather has read it
+        if (b >= 2) EX_CUDA(cudaStreamWaitEvent(h->copy_in_st, h->ev_gathered[i], 0));
+        EX_CUDA(cudaMemcpyAsync(sin[i], in_bits_host[b], in_bytes, cudaMemcpyHostToDevice, h->copy_in_st));
+        EX_CUDA(cudaEventRecord(h->ev_in[i], h->copy_in_st));
+        EX_CUDA(cudaStreamWaitEvent(st, h->ev_in[i], 0));
+        if (int rc = extract_gather(h, st, sin[i])) return rc;
+        EX_CUDA(cudaEventRecord(h->ev_gathered[i], st));
+        // its output into staging buffer i once block b - 2's output is in host memory
+        if (b >= 2) EX_CUDA(cudaStreamWaitEvent(st, h->ev_out[i], 0));
+        if (int rc = extract_hash(h, st, sout[i])) return rc;
+        EX_CUDA(cudaEventRecord(h->ev_hashed[i], st));
+        EX_CUDA(cudaStreamWaitEvent(h->copy_out_st, h->ev_hashed[i], 0));
+        EX_CUDA(cudaMemcpyAsync(out_bits_host[b], sout[i], out_bytes, cudaMemcpyDeviceToHost, h->copy_out_st));
+        EX_CUDA(cudaEventRecord(h->ev_out[i], h->copy_out_st));
+    }
+    EX_CUDA(cudaStreamWaitEvent(st, h->ev_out[(count - 1) & 1u], 0));
+    if (count >= 2) EX_CUDA(cudaStreamWaitEvent(st, h->ev_out[count & 1u], 0));
     EX_CUDA(cudaStreamSynchronize(st));
     return EXTRACT_OK;
 }

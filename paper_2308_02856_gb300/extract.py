@@ -54,7 +54,8 @@ def EXTRACT_NTT_SPLIT(l: int) -> int:
 
 # Every symbol include/extract.h declares (checked by the CPU test suite).
 EXPORTED = [
-    "extract_create", "extract_run", "extract_run_host", "extract_gather", "extract_hash", "extract_run_plain",
+    "extract_create", "extract_run", "extract_run_host", "extract_run_host_many", "extract_gather", "extract_hash",
+    "extract_run_plain",
     "extract_read_perm", "extract_read_subblock", "extract_describe", "extract_destroy",
     "extract_subblock_sizes", "extract_block_limit", "extract_gather_bytes", "extract_status",
     "extract_last_error", "extract_run_static",
@@ -109,6 +110,7 @@ def load() -> ctypes.CDLL:
     L.extract_create.argtypes = [ctypes.POINTER(vp), u64, u32, u32, u32, vp, u64, u32]
     L.extract_run.argtypes = [vp, vp, vp, vp]
     L.extract_run_host.argtypes = [vp, vp, vp, vp]
+    L.extract_run_host_many.argtypes = [vp, vp, vp, vp, u32]
     L.extract_gather.argtypes = [vp, vp, vp]
     L.extract_hash.argtypes = [vp, vp, vp]
     L.extract_run_plain.argtypes = [vp, vp, vp, vp]
@@ -194,6 +196,15 @@ def _host_ptr(x, writable=False) -> int:
 
 def extract_run_host(h, stream, in_bits_host, out_bits_host) -> None:
     _check(load().extract_run_host(h, _stream(stream), _host_ptr(in_bits_host), _host_ptr(out_bits_host)))
+
+
+def extract_run_host_many(h, stream, ins_host, outs_host) -> None:
+    if len(ins_host) != len(outs_host):
+        raise ValueError("one output per input")
+    n = len(ins_host)
+    pin = (ctypes.c_void_p * max(1, n))(*[_host_ptr(x) for x in ins_host])
+    pout = (ctypes.c_void_p * max(1, n))(*[_host_ptr(x) for x in outs_host])
+    _check(load().extract_run_host_many(h, _stream(stream), pin, pout, n))
 
 
 def extract_gather(h, stream, in_bits) -> None:
@@ -402,6 +413,12 @@ class Extractor:
             out_bits_host = np.empty(self.out_words, dtype=np.uint32)
         extract_run_host(self.h, stream, in_bits_host, out_bits_host)
         return out_bits_host
+
+    def run_host_many(self, ins_host, outs_host=None, stream=None):
+        if outs_host is None:
+            outs_host = [np.empty(self.out_words, dtype=np.uint32) for _ in ins_host]
+        extract_run_host_many(self.h, stream, ins_host, outs_host)
+        return outs_host
 
     def run_plain(self, in_bits, out_bits=None, stream=None):
         if out_bits is None:

@@ -230,3 +230,30 @@ def test_iid_host_buffers_through_the_buckets_match_the_oracle():
     with X.Extractor(n, m, s, k, seed, 7, X.EXTRACT_SAMPLING_IID | X.EXTRACT_GATHER_BUCKETS) as ex:
         got = ex.run_host(np.ascontiguousarray(in_w, dtype=np.uint32))
     assert np.array_equal(got, oracle.extract(n, m, s, k, in_w, seed, 7, oracle.SAMPLING_IID))
+
+
+@pytest.mark.parametrize("n,m,s,k,flags,count", [
+    (300_000, 9, 30_000, 4_000, X.EXTRACT_GATHER_BUCKETS | X.EXTRACT_METHOD_DIRECT, 5),
+    (5 << 20, 5, 1 << 20, 1000, 0, 4),                    # NTT, bucket tables
+    (1 << 18, 8, 1 << 15, 1 << 13, X.EXTRACT_GATHER_PLAIN, 3),
+    (1 << 18, 8, 1 << 15, 1 << 13, X.EXTRACT_METHOD_TENSOR, 1),
+])
+def test_host_many_blocks_match_the_oracle(n, m, s, k, flags, count):
+    """extract_run_host_many on a stream of different blocks (pinned host
+    buffers; the copies of neighbouring blocks overlap the work, the staging
+    buffers alternate): every block's output equals the oracle's, and a
+    second call on the same context (reusing streams, events and staging)
+    gives the same."""
+    seed = synth.uniform_bits(s + k - 1, 6)
+    ins = [synth.bernoulli_bits(n, 0.5 + 0.05 * b, 40 + b) for b in range(count)]
+    wants = [oracle.fast_extract(n, m, s, k, w, seed, 2) for w in ins]
+    pins = [torch.from_numpy(np.ascontiguousarray(w, dtype=np.uint32).view(np.int32)).pin_memory() for w in ins]
+    with X.Extractor(n, m, s, k, seed, 2, flags) as ex:
+        for _ in range(2):
+            outs = [torch.empty(ex.out_words, dtype=torch.int32).pin_memory() for _ in range(count)]
+            ex.run_host_many(pins, outs)
+            for b in range(count):
+                assert np.array_equal(outs[b].numpy().view(np.uint32), wants[b]), "block %d" % b
+        with pytest.raises(X.ExtractError) as e:
+            X.extract_run_host_many(ex.h, None, [pins[0]], [0])  # a null output buffer
+        assert e.value.code == X.EXTRACT_EINVAL
