@@ -63,11 +63,15 @@ constexpr int kRowsB = 2;             // rows per pass-B CTA
 constexpr int kThreads = 256;
 constexpr int kMaxSplitLog2 = 4;      // at most 16 pieces per sub-block
 constexpr uint64_t kMaxWorkWords = 16ull << 20;    // one sub-block's pieces (and windows), <= 64 MB
+// One launch group's work buffer: up to 1 GB (140 sub-blocks of the QKD shape,
+// 128 of the QRNG shape).  Large groups amortise each launch's set-up and
+// fill the GPU in every pass; the QKD-shaped block's hash takes 26.9 ms with
+// 1 GB groups against 30.9 ms with 128 MB (18 sub-blocks), 28.3 with 192 MB
+// and 27.0 with 512 MB (two lanes; a third lane gains nothing at 1 GB).
 #ifndef EX_NTT_GROUP_WORDS
-#define EX_NTT_GROUP_WORDS (32ull << 20)
+#define EX_NTT_GROUP_WORDS (256ull << 20)
 #endif
-constexpr uint64_t kGroupWorkWords = EX_NTT_GROUP_WORDS;  // one launch group's buffer, <= 128 MB (16 sub-blocks
-                                                          // of the QRNG shape: 70.1 against 69.8 Gbit/s with 8)
+constexpr uint64_t kGroupWorkWords = EX_NTT_GROUP_WORDS;
 
 // -p^{-1} mod 2^32 by Newton iteration
 constexpr uint32_t neg_inv32(uint32_t p)
@@ -1552,7 +1556,9 @@ uint64_t ntt_plan_bytes(uint32_t s, uint32_t k, int split_log2, bool per_block_s
 static uint32_t group_size(uint32_t m, const NttShape &sh, bool per_block_seeds)
 {
     const uint64_t per_sub = (per_block_seeds ? 2ull : 1ull) * sh.P * sh.N;
-    return (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(m, kGroupWorkWords / per_sub));
+    // pass A launches one CTA row per piece (grid y = sub-blocks x P < 2^16)
+    const uint64_t cap = 32768u / sh.P;
+    return (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(std::min<uint64_t>(m, cap), kGroupWorkWords / per_sub));
 }
 
 uint64_t ntt_max_work_words() { return kGroupWorkWords; }

@@ -32,13 +32,14 @@ def _lib():
 
 
 def _group_blocks(G, m, groups, extra):
-    """First and last sub-block of each launch group in ``groups`` (groups of
-    G sub-blocks alternate between two lanes; negative indices count from
-    the last group), plus ``extra``."""
+    """The first, last and two inner sub-blocks of each launch group in
+    ``groups`` (groups of G sub-blocks alternate between two lanes; negative
+    indices count from the last group), plus ``extra``."""
     ng = (m + G - 1) // G
     groups = sorted({g % ng for g in groups})
     assert {g % 2 for g in groups} == {0, 1}
-    blocks = [min(m - 1, G * g + r) for g in groups for r in (0, G - 1)] + [j for j in extra if j < m]
+    offsets = sorted({0, G // 3, (2 * G) // 3, G - 1})
+    blocks = [min(m - 1, G * g + r) for g in groups for r in offsets] + [j for j in extra if j < m]
     return sorted(set(blocks))
 
 
@@ -75,7 +76,7 @@ def _full_size_case(n, m, s, k, p, groups, extra, plan_has, nblocks):
 def test_qrng_shaped_block_n2e30():
     """n = 2^30 Bernoulli(0.6), m = 1024 sub-blocks of s = 2^20, k = 2^19:
     P = 2 pieces, N = 2^20, launch groups on two lanes; every row of at
-    least 32 whole sub-blocks from 14 launch groups."""
+    least 32 whole sub-blocks from every launch group."""
     _full_size_case(1 << 30, 1024, 1 << 20, 1 << 19, 0.6, (0, 1, 2, 3, 4, 5, 30, 31, 32, 33, -4, -3, -2, -1),
                     (7, 8, 1016, 1017), ("ntt: N=1048576", "P=2 ", "gather=buckets (2^16-bit"), 32)
 

@@ -198,11 +198,12 @@ def test_host_buffers_through_the_buckets_match_the_oracle(n, m, s, k, flags):
 
 
 def test_host_buffers_ntt_in_several_launch_groups():
-    """Two launch groups (64 + 16 sub-blocks); k mod 32 = 25, so neighbouring
-    groups share an output word and each group's words go to the host while
-    later groups run.  Sampled rows of every sub-block against the oracle,
-    the first and last rows of each included."""
-    n, m, s, k = 80 << 18, 80, 1 << 18, (1 << 17) - 7
+    """Two launch groups (128 + 16 sub-blocks of the QRNG sub-block shape);
+    k mod 32 = 25, so neighbouring groups share an output word and each
+    group's words go to the host while later groups run.  Sampled rows of
+    every sub-block against the oracle, the first and last rows of each
+    included."""
+    n, m, s, k = 144 << 20, 144, 1 << 20, (1 << 19) - 7
     in_w = synth.bernoulli_bits(n, 0.6, 16)
     seed = synth.uniform_bits(s + k - 1, 6)
     with X.Extractor(n, m, s, k, seed, 2, X.EXTRACT_METHOD_NTT) as ex:
