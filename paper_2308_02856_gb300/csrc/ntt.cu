@@ -405,7 +405,10 @@ __device__ __forceinline__ uint32_t swz(uint32_t t) { return (t & ~31u) | ((t ^ 
 // index, except across the transpose (the lane's parity), where the 4p form
 // is used.  The last stage (twiddle 1) of a difference pair is x + y,
 // x - y + 2p with no multiply.
-template <int EPL, int HP0 = EPL / 2, bool kZeroTop = false, bool kLazy = false>
+// kPad: the transpose scratch is padded (row stride 33 words) instead of
+// XOR-swizzled: every access is a lane-dependent base plus a constant offset,
+// so no index arithmetic per element; 33 EPL words of scratch.
+template <int EPL, int HP0 = EPL / 2, bool kZeroTop = false, bool kLazy = false, bool kPad = false>
 __device__ __forceinline__ void dif_warp_t(uint32_t (&e)[EPL], uint32_t *sw, const uint2 *__restrict__ tw, int lane)
 {
 #pragma unroll
@@ -428,12 +431,13 @@ __device__ __forceinline__ void dif_warp_t(uint32_t (&e)[EPL], uint32_t *sw, con
         }
     }
 #pragma unroll
-    for (int j = 0; j < EPL; ++j) sw[swz(32u * j + lane)] = e[j];
+    for (int j = 0; j < EPL; ++j) sw[kPad ? 33u * j + lane : swz(32u * j + lane)] = e[j];
     __syncwarp();
 #pragma unroll
     for (int q = 0; q < EPL / 32; ++q)
 #pragma unroll
-        for (int i = 0; i < 32; ++i) e[32 * q + i] = sw[swz(32u * (lane + 32 * q) + i)];
+        for (int i = 0; i < 32; ++i)
+            e[32 * q + i] = sw[kPad ? 33u * (lane + 32 * q) + i : swz(32u * (lane + 32 * q) + i)];
     __syncwarp();
 #pragma unroll
     for (int h = 16; h >= 1; h >>= 1)
@@ -464,7 +468,7 @@ __device__ __forceinline__ void dif_warp_t(uint32_t (&e)[EPL], uint32_t *sw, con
 // DIT: layout B in, layout A out (the exact reverse of dif_warp_t).
 // kFirstUnit: inputs are in [0, 2p), so the first stage (twiddle 1) is
 // x + y, x - y + 2p with no reduction and no multiply.
-template <int EPL, int HP0 = EPL / 2, bool kFirstUnit = false>
+template <int EPL, int HP0 = EPL / 2, bool kFirstUnit = false, bool kPad = false>
 __device__ __forceinline__ void dit_warp_t(uint32_t (&e)[EPL], uint32_t *sw, const uint2 *__restrict__ tw, int lane)
 {
 #pragma unroll
@@ -486,10 +490,11 @@ __device__ __forceinline__ void dit_warp_t(uint32_t (&e)[EPL], uint32_t *sw, con
 #pragma unroll
     for (int q = 0; q < EPL / 32; ++q)
 #pragma unroll
-        for (int i = 0; i < 32; ++i) sw[swz(32u * (lane + 32 * q) + i)] = e[32 * q + i];
+        for (int i = 0; i < 32; ++i)
+            sw[kPad ? 33u * (lane + 32 * q) + i : swz(32u * (lane + 32 * q) + i)] = e[32 * q + i];
     __syncwarp();
 #pragma unroll
-    for (int j = 0; j < EPL; ++j) e[j] = sw[swz(32u * j + lane)];
+    for (int j = 0; j < EPL; ++j) e[j] = sw[kPad ? 33u * j + lane : swz(32u * j + lane)];
     __syncwarp();
 #pragma unroll
     for (int hp = 1; hp <= HP0; hp <<= 1) {
@@ -501,6 +506,13 @@ __device__ __forceinline__ void dit_warp_t(uint32_t (&e)[EPL], uint32_t *sw, con
         }
     }
 }
+
+// Pass B's per-warp transpose scratch: padded rows (EX_ROW_PAD), else XOR swizzle
+#ifndef EX_ROW_PAD
+#define EX_ROW_PAD 1
+#endif
+constexpr bool kRowPad = EX_ROW_PAD != 0;
+constexpr uint32_t kRowSw = kRowPad ? 33u * 32u : 1024u;
 
 // Pass B: one CTA of two warps per 2048-word row; warp w owns half
 // [1024 w, 1024 w + 1024).  The distance-1024 DIF stage is done while
@@ -528,7 +540,7 @@ __device__ __forceinline__ void row_dif(uint32_t (&e)[32], const uint32_t *x, ui
             e[j] = shoup_lazy(a - b + k2P, tw.x, tw.y);
         }
     }
-    dif_warp_t<32, 16, false, kLazy>(e, sw, T.row_stage_f, lane);
+    dif_warp_t<32, 16, false, kLazy, kRowPad>(e, sw, T.row_stage_f, lane);
 }
 
 // e[i] (layout B, from base) times a spectrum row computed in the same run
@@ -581,10 +593,10 @@ __device__ __forceinline__ void row_mul(uint32_t (&e)[32], uint32_t (&acc)[32], 
 }
 
 // inverse DIT of acc (layout B) and the distance-1024 stage, stored to x
-__device__ __forceinline__ void row_dit_store(uint32_t (&e)[32], uint32_t *x, uint32_t (*sw)[1024], const Tables &T,
+__device__ __forceinline__ void row_dit_store(uint32_t (&e)[32], uint32_t *x, uint32_t (*sw)[kRowSw], const Tables &T,
                                               int lane, int w)
 {
-    dit_warp_t<32, 16, true>(e, sw[w], T.row_stage_i, lane);  // the products are in [0, 2p)
+    dit_warp_t<32, 16, true, kRowPad>(e, sw[w], T.row_stage_i, lane);  // the products are in [0, 2p)
     // distance-1024 DIT stage: x' = x + w y, y' = x - w y (w = w_2048^-pos)
 #pragma unroll
     for (int j = 0; j < 32; ++j) {
@@ -635,7 +647,7 @@ __global__ void __launch_bounds__(64, kMulti ? 10 : 12)
 ntt_rows_kernel(uint32_t *__restrict__ buf, uint32_t N, uint32_t R1, uint32_t P, const uint32_t *__restrict__ S,
                 const uint32_t *__restrict__ Sq, Tables T, uint32_t *err)
 {
-    __shared__ __align__(16) uint32_t sw[2][1024];
+    __shared__ __align__(16) uint32_t sw[2][kRowSw];
     __shared__ __align__(16) uint32_t xs[kInverse && kMulti ? kR2 : 4];
     __shared__ uint64_t xbar;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -688,7 +700,7 @@ ntt_rows_kernel(uint32_t *__restrict__ buf, uint32_t N, uint32_t R1, uint32_t P,
         fence_async_smem();
         __syncthreads();  // both warps have read the row: the next piece's copy may land
         if (threadIdx.x == 0 && q + 1 < P) bulk_load(xb, x + (size_t)(q + 1) * N, kR2 * 4, mb);
-        dif_warp_t<32, 16, false, true>(e, sw[w], T.row_stage_f, lane);
+        dif_warp_t<32, 16, false, true, kRowPad>(e, sw[w], T.row_stage_f, lane);
         if (kMont) row_mul_mont<true>(e, acc, Sb + (size_t)q * N + so);
         else row_mul<true>(e, acc, S + (size_t)q * N + so, Sq + (size_t)q * N + so);
     }
