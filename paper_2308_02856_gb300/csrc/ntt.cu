@@ -856,10 +856,18 @@ __device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane)
 // Eight warps let four CTAs share an SM instead of two, so one CTA's loads
 // and stores overlap another's butterflies: the 2^32-bit block's hash takes
 // 38.4 instead of 40.3 ms (no change on the 2^30-bit block, E = 16).
+// Per-warp transpose scratch of the multi-column kernels: padded rows
+// (EX_COL_PAD; 33 x 32 words), else XOR swizzle (1024 words).  The R1 x CW
+// tile (1024 words per warp) shares the region.
+#ifndef EX_COL_PAD
+#define EX_COL_PAD 1
+#endif
+constexpr bool kColPad = EX_COL_PAD != 0;
+constexpr uint32_t kColSw = kColPad ? 33u * 32u : 1024u;
 template <int E>
 __host__ __device__ constexpr uint32_t col_warps() { return (EX_COLS_WARPS >= E) ? EX_COLS_WARPS : 16; }
 template <int E>
-constexpr uint32_t tile_words() { return col_warps<E>() * 1024u; }
+constexpr uint32_t tile_words() { return col_warps<E>() * kColSw; }
 template <int E>
 size_t smem_multi() { return (size_t)(tile_words<E>() + 1024) * 4; }
 
@@ -951,7 +959,7 @@ ntt_cols_fwd_m_kernel(const uint32_t *__restrict__ bits, Pieces pc, uint32_t N, 
         const uint32_t cc = w * COLS + j / E, t1 = 32u * (j % E) + lane;
         e[j] = (rb[t1 * WPR + (cc >> 5)] >> (cc & 31u)) & 1u;
     }
-    dif_warp_t<32, E / 2, kZeroTop && (E >= 2), true>(e, xs + w * 1024, T.col_stage_f, lane);  // the twist takes [0, 4p)
+    dif_warp_t<32, E / 2, kZeroTop && (E >= 2), true, kColPad>(e, xs + w * kColSw, T.col_stage_f, lane);  // the twist takes [0, 4p)
     // layout B: e[i] is frequency row r = 32 a + i of column cc
     const uint32_t a = lane % E, cc = w * COLS + lane / E;
     const uint32_t *twr = T.twist_f + (size_t)(c0 + cc) * R1 + 32u * a;
@@ -1010,7 +1018,7 @@ ntt_cols_inv_m_kernel(const uint32_t *__restrict__ buf, uint64_t sub_stride, Tab
         e[i + 3] = mont_lazy(xs[tile_at<E>(32u * a + i + 3, cc)], tw.w);
     }
     __syncthreads();  // the tile is consumed; warps reuse it as scratch
-    dit_warp_t<32, E / 2, true>(e, xs + w * 1024, T.col_stage_i, lane);  // untwisted values are in [0, 2p)
+    dit_warp_t<32, E / 2, true, kColPad>(e, xs + w * kColSw, T.col_stage_i, lane);  // untwisted values are in [0, 2p)
     // layout A: e[j] is coefficient row 32 (j % E) + lane of column w COLS + j / E;
     // only row blocks holding a wanted coefficient [len-1, len+k-1) are packed
     const uint32_t row_lo = (len - 1) / kR2, row_hi = (uint32_t)(((uint64_t)len + k - 2) / kR2);
