@@ -30,8 +30,9 @@
 //
 // Warp transforms: a warp holds 32 EPL values, lane l / register j at
 // position 32 j + l (for R1 < 1024, 32 / E whole columns of 32 E); stages
-// with pair distance >= 32 run inside registers, then a swizzled
-// shared-memory transpose (word 32 j + (l ^ j)) gives each lane whole rows
+// with pair distance >= 32 run inside registers, then a shared-memory
+// transpose (padded rows: word 33 j + l; the transposed-warp kernels for
+// R1 >= 1024 use the XOR swizzle 32 j + (l ^ j)) gives each lane whole rows
 // of 32 and the distance < 32 stages run in registers too, with their
 // twiddles as constant-bank operands.
 //
