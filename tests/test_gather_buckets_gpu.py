@@ -258,3 +258,27 @@ def test_host_many_blocks_match_the_oracle(n, m, s, k, flags, count):
         with pytest.raises(X.ExtractError) as e:
             X.extract_run_host_many(ex.h, None, [pins[0]], [0])  # a null output buffer
         assert e.value.code == X.EXTRACT_EINVAL
+
+
+def test_host_many_blocks_iid_law_and_independent_seeds():
+    """extract_run_host_many with the paper's i.i.d. law (padded sub-blocks)
+    and with one seed per sub-block: three blocks each, every output equal
+    to the oracle's."""
+    n, m, k = 250_000, 6, 2_000
+    _, _, largest = oracle.iid_order(oracle.sampling_keys(n, 7), m, n, with_order=False)
+    s = largest + 3
+    seed = synth.uniform_bits(s + k - 1, 5)
+    ins = [synth.bernoulli_bits(n, 0.6 + 0.1 * b, 60 + b) for b in range(3)]
+    pins = [torch.from_numpy(np.ascontiguousarray(w, dtype=np.uint32).view(np.int32)).pin_memory() for w in ins]
+    with X.Extractor(n, m, s, k, seed, 7, X.EXTRACT_SAMPLING_IID) as ex:
+        outs = ex.run_host_many(pins)
+    for b in range(3):
+        assert np.array_equal(outs[b], oracle.extract(n, m, s, k, ins[b], seed, 7, oracle.SAMPLING_IID)), b
+    n, m, s, k = 1 << 20, 8, 1 << 17, 1 << 15
+    seed = synth.uniform_bits((s + k - 1) * m, 42)
+    ins = [synth.bernoulli_bits(n, 0.55 + 0.1 * b, 70 + b) for b in range(3)]
+    pins = [torch.from_numpy(np.ascontiguousarray(w, dtype=np.uint32).view(np.int32)).pin_memory() for w in ins]
+    with X.Extractor(n, m, s, k, seed, 2, X.EXTRACT_SEED_PER_SUBBLOCK | X.EXTRACT_METHOD_NTT) as ex:
+        outs = ex.run_host_many(pins)
+    for b in range(3):
+        assert np.array_equal(outs[b], oracle.fast_extract(n, m, s, k, ins[b], seed, 2, oracle.SEED_PER_SUBBLOCK)), b
